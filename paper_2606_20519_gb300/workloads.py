@@ -1,0 +1,212 @@
+"""Seeded synthetic inputs for the PSD-cone projection, shared by the tests,
+the benchmark and the smoke check.
+
+This module only *makes inputs*: random orthogonal factors, spectra and the
+svec storage layout the projection reads (the vec_R map of App. D.1 of the
+paper, real symmetric case: lower triangle column by column, off-diagonal
+entries times sqrt(2)).  It holds none of the projection's arithmetic; the
+expected projection of a constructed matrix Q diag(lam) Q^T is formed by the
+tests themselves.
+
+All randomness comes from ``numpy.random.Generator(PCG64(seed))``.  The
+workloads mirror the process-matrix step (n = d^4) and the instrument step
+(n = d^2) of the paper's see-saw (Sec. III, App. B.4, App. A.3).  The paper
+solves SDPs from GYNI games whose iterates are not available here, so every
+matrix is synthetic: a spectrum of the stated shape under a Haar-random
+orthogonal basis, or a symmetrised Gaussian matrix.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SQRT2 = np.sqrt(2.0)
+SEED_BASE = 20519
+
+
+def rng_for(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def svec_len(n: int) -> int:
+    return n * (n + 1) // 2
+
+
+def to_svec(X: np.ndarray) -> np.ndarray:
+    """Storage layout of a symmetric matrix: lower triangle, column-major,
+    off-diagonals scaled by sqrt(2).  For a symmetric matrix this equals the
+    upper triangle read row by row."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    r, c = np.triu_indices(n)
+    s = X[r, c].copy()
+    s[r != c] *= SQRT2
+    return s
+
+
+def haar_orthogonal(rng: np.random.Generator, n: int) -> np.ndarray:
+    """Haar-distributed orthogonal matrix: QR of a Gaussian matrix with the
+    signs of R's diagonal moved into Q (Mezzadri 2007)."""
+    G = rng.standard_normal((n, n))
+    Q, R = np.linalg.qr(G)
+    return Q * np.sign(np.diag(R))[None, :]
+
+
+def from_spectrum(rng: np.random.Generator, lam: np.ndarray):
+    """X = Q diag(lam) Q^T with Haar Q.  Returns (X, Q, lam)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    Q = haar_orthogonal(rng, lam.size)
+    X = (Q * lam[None, :]) @ Q.T
+    X = 0.5 * (X + X.T)
+    return X, Q, lam
+
+
+def sym_gaussian(rng: np.random.Generator, n: int) -> np.ndarray:
+    """Sym(G) = (G + G^T) / 2 with G iid N(0, 1)."""
+    G = rng.standard_normal((n, n))
+    return 0.5 * (G + G.T)
+
+
+# ---------------------------------------------------------------- spectra
+
+def spectrum_plain(rng, n: int) -> np.ndarray:
+    """Single-projection spectrum: about half U[0.1, 2], half U[-2, -0.1],
+    one exact zero when n is odd (n = 81: 40 / 40 / 1)."""
+    npos = (n - 1) // 2 if n % 2 else n // 2
+    nneg = n - npos - (1 if n % 2 else 0)
+    parts = [rng.uniform(0.1, 2.0, npos), rng.uniform(-2.0, -0.1, nneg)]
+    if n % 2:
+        parts.append(np.zeros(1))
+    return np.concatenate(parts)
+
+
+def spectrum_admm(rng, n: int) -> np.ndarray:
+    """ADMM-like start spectrum: 48 % N(0, std 1e-6) clustered at zero, 32 %
+    U[0.01, 1], the rest U[-1, -0.01] (n = 625: 300 / 200 / 125)."""
+    n0 = int(round(n * 300 / 625))
+    npos = int(round(n * 200 / 625))
+    nneg = n - n0 - npos
+    return np.concatenate([rng.normal(0.0, 1e-6, n0), rng.uniform(0.01, 1.0, npos),
+                           rng.uniform(-1.0, -0.01, nneg)])
+
+
+def spectrum_precision(rng, n: int) -> np.ndarray:
+    """Precision stress spectrum: half U[-1, 1], a quarter N(0, std 1e-8),
+    a quarter of magnitude 10^U[-4, 2] with a random sign."""
+    h = n // 2
+    q = (n - h) // 2
+    r = n - h - q
+    mags = 10.0 ** rng.uniform(-4.0, 2.0, r)
+    signs = np.where(rng.uniform(size=r) < 0.5, -1.0, 1.0)
+    return np.concatenate([rng.uniform(-1.0, 1.0, h), rng.normal(0.0, 1e-8, q), signs * mags])
+
+
+def spectrum_vjp(rng, n: int, cluster: float = 1e-9) -> np.ndarray:
+    """Derivative stress spectrum: U[-1, 1] with 10 % of the eigenvalues at
+    +cluster and -cluster, half each (n = 1296: 65 + 65)."""
+    nc = int(round(0.1 * n))
+    nc -= nc % 2
+    base = rng.uniform(-1.0, 1.0, n - nc)
+    return np.concatenate([base, np.full(nc // 2, cluster), np.full(nc // 2, -cluster)])
+
+
+# ---------------------------------------------------------------- workloads
+
+@dataclass
+class Batch:
+    """Packed svec cones: x[offsets[i]:offsets[i+1]] is cone i of side sides[i]."""
+    x: np.ndarray
+    offsets: np.ndarray
+    sides: np.ndarray
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def count(self) -> int:
+        return int(self.sides.size)
+
+
+def pack(svecs, sides) -> Batch:
+    sides = np.asarray(sides, dtype=np.int32)
+    lens = np.array([svec_len(int(n)) for n in sides], dtype=np.int64)
+    offsets = np.zeros(sides.size + 1, dtype=np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    x = np.concatenate(svecs) if len(svecs) else np.zeros(0)
+    return Batch(x=x, offsets=offsets, sides=sides)
+
+
+def single_projection(seed: int = SEED_BASE + 1, n: int = 81):
+    """One n x n matrix Q diag(lam) Q^T with the plain spectrum
+    (n = 81 = d^4 at d = 3).  Returns (svec, Q, lam)."""
+    rng = rng_for(seed)
+    lam = spectrum_plain(rng, n)
+    X, Q, lam = from_spectrum(rng, lam)
+    return to_svec(X), Q, lam
+
+
+def admm_sequence(seed: int = SEED_BASE + 2, n: int = 625, steps: int = 200, step_scale: float = 1e-3):
+    """ADMM-like sequence X_{k+1} = X_k + 1e-3 Sym(G_k) starting from
+    Q diag(lam0) Q^T with the clustered spectrum (n = 625 = d^4 at d = 5).
+    Returns (list of svecs, Q, lam0)."""
+    rng = rng_for(seed)
+    lam = spectrum_admm(rng, n)
+    X, Q, lam = from_spectrum(rng, lam)
+    out = [to_svec(X)]
+    for _ in range(steps - 1):
+        X = X + step_scale * sym_gaussian(rng, n)
+        out.append(to_svec(X))
+    return out, Q, lam
+
+
+def precision_batch(seed: int = SEED_BASE + 3, n: int = 4096, batch: int = 4) -> Batch:
+    """``batch`` matrices with the precision stress spectrum
+    (n = 4096 = d^4 at d = 8).  extra['Q'], extra['lam'] hold the factors."""
+    rng = rng_for(seed)
+    svecs, Qs, lams = [], [], []
+    for _ in range(batch):
+        lam = spectrum_precision(rng, n)
+        X, Q, lam = from_spectrum(rng, lam)
+        svecs.append(to_svec(X))
+        Qs.append(Q)
+        lams.append(lam)
+    b = pack(svecs, [n] * batch)
+    b.extra.update(Q=Qs, lam=lams)
+    return b
+
+
+INSTRUMENT_SIDES = (4, 9, 16, 25, 36, 49, 64)
+
+
+def uneven_batch(seed: int = SEED_BASE + 4, restarts: int = 64, small_sides=INSTRUMENT_SIDES,
+                 copies: int = 2, big_sides=(625, 1296)) -> Batch:
+    """Many uneven cones: each see-saw restart contributes ``copies`` blocks
+    of every instrument side d^2 plus one process block whose side alternates
+    through ``big_sides``.  Entries are Sym(G) + u I with u ~ U[-0.5, 0.5] per
+    block.  Default: 64 x (14 + 1) = 960 cones."""
+    rng = rng_for(seed)
+    svecs, sides = [], []
+    for r in range(restarts):
+        blocks = [s for s in small_sides for _ in range(copies)]
+        if big_sides:
+            blocks.append(big_sides[r % len(big_sides)])
+        for n in blocks:
+            X = sym_gaussian(rng, n) + rng.uniform(-0.5, 0.5) * np.eye(n)
+            svecs.append(to_svec(X))
+            sides.append(n)
+    return pack(svecs, sides)
+
+
+def vjp_batch(seed: int = SEED_BASE + 5, n: int = 1296, batch: int = 8, cluster: float = 1e-9) -> Batch:
+    """``batch`` matrices with the derivative stress spectrum (n = 1296 = d^4
+    at d = 6) plus Gaussian cotangents in extra['g'] (same layout as x)."""
+    rng = rng_for(seed)
+    svecs, Qs, lams = [], [], []
+    for _ in range(batch):
+        lam = spectrum_vjp(rng, n, cluster)
+        X, Q, lam = from_spectrum(rng, lam)
+        svecs.append(to_svec(X))
+        Qs.append(Q)
+        lams.append(lam)
+    b = pack(svecs, [n] * batch)
+    b.extra.update(Q=Qs, lam=lams, g=rng.standard_normal(b.x.size))
+    return b
