@@ -1,0 +1,129 @@
+/*
+ * scs_psd -- projection onto the cone of positive-semidefinite matrices for
+ * SCS-style conic solvers, on one NVIDIA GB300 (sm_103a).
+ *
+ * The operation is the cone step u = Pi_C(u~ - v) of the SCS iteration as the
+ * paper describes it (App. D.1, "Operator splitting" and "Eliminating the dual
+ * variables"), for the PSD cone: with X the symmetric matrix whose svec
+ * (the vec_R map of App. D.1) is x,
+ *
+ *     Pi(X) = argmin_{Y >= 0} ||Y - X||_F = V diag(max(lambda, 0)) V^T,
+ *
+ * computed "by an eigendecomposition with the negative eigenvalues set to
+ * zero" (App. D.2).  When fewer eigenvalues are negative than positive the
+ * library forms X - V_- diag(lambda_-) V_-^T instead, which is the same matrix
+ * by the Moreau decomposition Pi_{C*}(x) = x + Pi_C(-x) of App. D.1.
+ *
+ * svec layout (real symmetric case of vec_R, in the order SCS uses): the
+ * lower triangle column by column, diagonal entries as they are and
+ * off-diagonal entries multiplied by sqrt(2); a side-n cone holds
+ * n(n+1)/2 doubles.  The map is an isometry: <svec A, svec B> = tr(AB).
+ *
+ * Conventions for every entry point:
+ *  - Data buffers (x, y, g, xbar) are FP64, contiguous, in the device memory
+ *    of the handle's GPU, and owned by the caller.
+ *  - Shape arrays (offsets, sides) are HOST arrays owned by the caller; they
+ *    are read during the call only (the library plans launches from them).
+ *  - The library owns its workspace (device memory sized on first use or by
+ *    scs_psd_reserve) and keeps it until scs_psd_destroy.
+ *  - Work is enqueued on `stream` and is asynchronous; host-detectable errors
+ *    (bad sizes, null pointers) are returned at once and nothing is enqueued.
+ *    Errors found on the device (non-finite input, non-convergence, a bounded
+ *    wait that ran out) are recorded in a device status word that
+ *    scs_psd_status reads; the affected cone's output is filled with NaN.
+ *  - y may alias x (in-place, as SCS updates its iterate).
+ *  - No CPU fallback exists: every arithmetic step runs in this library's
+ *    CUDA kernels.  No exception crosses the ABI.
+ */
+#ifndef SCS_PSD_H
+#define SCS_PSD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct scs_psd_handle_s* scs_psd_handle;
+
+/* Return codes. */
+enum {
+  SCS_PSD_OK = 0,
+  SCS_PSD_EINVAL = 1,     /* bad argument (null pointer, size mismatch, n < 0) */
+  SCS_PSD_ENOMEM = 2,     /* device or host allocation failed */
+  SCS_PSD_ECUDA = 3,      /* a CUDA runtime call failed */
+  SCS_PSD_ETIMEOUT = 4,   /* a bounded device-side wait ran out */
+  SCS_PSD_ENOCONV = 5,    /* an iteration did not converge */
+  SCS_PSD_ENONFINITE = 6  /* the input held a NaN or an infinity */
+};
+
+/* Arithmetic used for the dense contractions. */
+typedef enum {
+  SCS_PSD_FP64 = 0,       /* FP64 throughout */
+  SCS_PSD_SPLIT_TF32 = 1  /* reserved: split-TF32 tensor-core contractions */
+} scs_psd_precision;
+
+/* Options; a NULL pointer means all defaults (zero-initialised struct). */
+typedef struct {
+  int32_t precision;        /* scs_psd_precision */
+  int32_t side;             /* 0 auto (fewer eigenpairs), 1 positive part, 2 X - negative part */
+  int32_t recompute;        /* VJP: 0 auto, 1 always recompute V, 2 never (store) */
+  int32_t band;             /* bandwidth of the dense->band stage; 0 = default */
+  int64_t mem_budget_bytes; /* VJP: workspace budget that triggers recompute; 0 = no limit */
+  int64_t wait_limit_cycles;/* bound on device spin-waits; 0 = default */
+} scs_psd_opts;
+
+/* Create a handle on CUDA device `device`.  Allocates no device memory yet. */
+int scs_psd_create(scs_psd_handle* h, int device);
+
+/* Release the handle and its workspace.  Synchronises the device first. */
+int scs_psd_destroy(scs_psd_handle h);
+
+/* Single cone: y = svec(Pi(smat(x))) for a side-n cone; x and y hold
+ * n(n+1)/2 doubles.  n = 0 is a no-op; n = 1 gives y = max(x, 0).
+ * `stream` is a cudaStream_t (NULL = legacy default stream).
+ * Operation: App. D.2 (projection by eigendecomposition). */
+int scs_psd_proj(scs_psd_handle h, const double* x, double* y, int64_t n,
+                 const scs_psd_opts* opts, void* stream);
+
+/* Many cones of uneven sides in one call: cone i occupies
+ * x[offsets[i] .. offsets[i+1]) and has side sides[i], with
+ * offsets[i+1] - offsets[i] == sides[i](sides[i]+1)/2 and offsets[0] == 0.
+ * offsets (count+1 entries) and sides (count entries) are HOST arrays.
+ * The launch sequence for a given shape list is recorded once as a CUDA
+ * graph and replayed on later calls with the same shapes.
+ * Operation: App. D.2, applied block by block (the PSD constraint split into
+ * smaller blocks, as the paper's outlook on symmetry reduction proposes). */
+int scs_psd_proj_batched(scs_psd_handle h, const double* x, double* y, const int64_t* offsets,
+                         const int32_t* sides, int32_t count, const scs_psd_opts* opts, void* stream);
+
+/* Vector-Jacobian product of the projection (App. E back-propagates through
+ * the eigendecomposition): xbar = J^T g with J = DPi(X), by the
+ * Daleckii-Krein formula
+ *     DPi(X)[H] = V (L o (V^T H V)) V^T,  L_ij = (max(l_i,0) - max(l_j,0)) / (l_i - l_j),
+ * L_ij = 1 if both are positive, 0 if neither is.  In svec coordinates J is
+ * symmetric, so this is also the JVP.  Layout as scs_psd_proj_batched; the
+ * eigenvectors are recomputed from x (opts->recompute).  y is optional: if
+ * not NULL it receives Pi(x) from the same eigendecomposition. */
+int scs_psd_proj_vjp(scs_psd_handle h, const double* x, const double* g, double* xbar, double* y,
+                     const int64_t* offsets, const int32_t* sides, int32_t count,
+                     const scs_psd_opts* opts, void* stream);
+
+/* Optional pre-sizing of the workspace for cones up to side max_n and
+ * max_count cones of that side. */
+int scs_psd_reserve(scs_psd_handle h, int64_t max_n, int32_t max_count, const scs_psd_opts* opts);
+
+/* Synchronise the handle's last stream and return the device status of the
+ * work enqueued since the previous call (an SCS_PSD_* code, OK if none). */
+int scs_psd_status(scs_psd_handle h, int32_t* device_status);
+
+/* Number of kernels the last call enqueued (for launch accounting). */
+int64_t scs_psd_last_launch_count(scs_psd_handle h);
+
+/* Human-readable text for a return code. */
+const char* scs_psd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCS_PSD_H */

@@ -1,0 +1,187 @@
+"""ctypes binding of the scs_psd C-ABI (include/scs_psd.h).
+
+Argument marshalling only: every arithmetic step of the projection runs in
+the CUDA kernels of ``_build/libscs_psd.so``.  There is no CPU fallback; if
+the library has not been built, loading fails with an error that says so.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libscs_psd.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENOCONV, ENONFINITE = range(7)
+FP64, SPLIT_TF32 = 0, 1
+
+
+class ScsPsdError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} (code {code})")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("side", ctypes.c_int32), ("recompute", ctypes.c_int32),
+                ("band", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64),
+                ("wait_limit_cycles", ctypes.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+_handles = {}
+
+EXPORTS = ("scs_psd_create", "scs_psd_destroy", "scs_psd_proj", "scs_psd_proj_batched", "scs_psd_proj_vjp",
+           "scs_psd_reserve", "scs_psd_status", "scs_psd_last_launch_count", "scs_psd_strerror")
+
+
+def load():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"scs_psd CUDA library not built ({LIB_PATH} missing); "
+                               "run paper_2606_20519_gb300.build.build() first -- there is no CPU fallback")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        op = ctypes.POINTER(Opts)
+        lib.scs_psd_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+        lib.scs_psd_destroy.argtypes = [vp]
+        lib.scs_psd_proj.argtypes = [vp, vp, vp, i64, op, vp]
+        lib.scs_psd_proj_batched.argtypes = [vp, vp, vp, vp, vp, i32, op, vp]
+        lib.scs_psd_proj_vjp.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, op, vp]
+        lib.scs_psd_reserve.argtypes = [vp, i64, i32, op]
+        lib.scs_psd_status.argtypes = [vp, ctypes.POINTER(i32)]
+        lib.scs_psd_last_launch_count.argtypes = [vp]
+        lib.scs_psd_last_launch_count.restype = i64
+        lib.scs_psd_strerror.argtypes = [ctypes.c_int]
+        lib.scs_psd_strerror.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            getattr(lib, name)
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().scs_psd_strerror(int(code)).decode()
+    except Exception:  # pragma: no cover - used while formatting errors
+        return "error"
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise ScsPsdError(rc, what)
+
+
+def handle(device: int):
+    with _lock:
+        h = _handles.get(device)
+    if h is not None:
+        return h
+    lib = load()
+    hv = ctypes.c_void_p()
+    _check(lib.scs_psd_create(ctypes.byref(hv), int(device)), "scs_psd_create")
+    with _lock:
+        _handles[device] = hv
+    return hv
+
+
+def make_opts(precision: int = FP64, side: int = 0, band: int = 0, wait_limit_cycles: int = 0,
+              recompute: int = 0, mem_budget_bytes: int = 0) -> Opts:
+    return Opts(precision, side, recompute, band, mem_budget_bytes, wait_limit_cycles)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream_ptr(t):
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _check_tensor(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+
+
+def shapes(sides):
+    """(offsets int64[count+1], sides int32[count]) host arrays for a side list."""
+    sides = np.ascontiguousarray(np.asarray(sides, dtype=np.int32))
+    lens = sides.astype(np.int64) * (sides.astype(np.int64) + 1) // 2
+    offsets = np.zeros(sides.size + 1, dtype=np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    return offsets, sides
+
+
+def proj(x, n: int, out=None, opts: Opts | None = None):
+    """y = svec(Pi(smat(x))) for one side-n cone (C-ABI scs_psd_proj)."""
+    import torch
+    _check_tensor(x, "x")
+    if out is None:
+        out = torch.empty_like(x)
+    _check_tensor(out, "out")
+    lib = load()
+    rc = lib.scs_psd_proj(handle(x.device.index), _ptr(x), _ptr(out), int(n),
+                          ctypes.byref(opts) if opts is not None else None, _stream_ptr(x))
+    _check(rc, "scs_psd_proj")
+    return out
+
+
+def proj_batched(x, sides, out=None, opts: Opts | None = None, offsets=None):
+    """Projection of many uneven cones packed in one svec buffer."""
+    import torch
+    _check_tensor(x, "x")
+    if offsets is None:
+        offsets, sides = shapes(sides)
+    else:
+        offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        sides = np.ascontiguousarray(np.asarray(sides, dtype=np.int32))
+    if out is None:
+        out = torch.empty_like(x)
+    _check_tensor(out, "out")
+    lib = load()
+    rc = lib.scs_psd_proj_batched(handle(x.device.index), _ptr(x), _ptr(out),
+                                  offsets.ctypes.data_as(ctypes.c_void_p), sides.ctypes.data_as(ctypes.c_void_p),
+                                  int(sides.size), ctypes.byref(opts) if opts is not None else None, _stream_ptr(x))
+    _check(rc, "scs_psd_proj_batched")
+    return out
+
+
+def proj_vjp(x, g, sides, xbar=None, y=None, opts: Opts | None = None, offsets=None):
+    """xbar = DPi(X)^T g (Daleckii-Krein), optionally y = Pi(x) as well."""
+    import torch
+    _check_tensor(x, "x")
+    _check_tensor(g, "g")
+    if offsets is None:
+        offsets, sides = shapes(sides)
+    else:
+        offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        sides = np.ascontiguousarray(np.asarray(sides, dtype=np.int32))
+    if xbar is None:
+        xbar = torch.empty_like(x)
+    lib = load()
+    rc = lib.scs_psd_proj_vjp(handle(x.device.index), _ptr(x), _ptr(g), _ptr(xbar), _ptr(y),
+                              offsets.ctypes.data_as(ctypes.c_void_p), sides.ctypes.data_as(ctypes.c_void_p),
+                              int(sides.size), ctypes.byref(opts) if opts is not None else None, _stream_ptr(x))
+    _check(rc, "scs_psd_proj_vjp")
+    return xbar
+
+
+def status(device: int = 0) -> int:
+    """Synchronise and return the device status of the work since the last query."""
+    v = ctypes.c_int32(0)
+    _check(load().scs_psd_status(handle(device), ctypes.byref(v)), "scs_psd_status")
+    return int(v.value)
+
+
+def last_launch_count(device: int = 0) -> int:
+    return int(load().scs_psd_last_launch_count(handle(device)))

@@ -1,0 +1,748 @@
+// C-ABI of the scs_psd library: handles, plans, workspace and the launch
+// sequence of the projection pipeline (see internal.cuh for the steps).
+//
+// A plan is built once per list of cone sides (and options): it lays out the
+// device workspace, precomputes every launch's work list (panel jobs, GEMM
+// descriptors with device-side sizes, bulge-chasing CTA assignment, merge
+// nodes of each divide-and-conquer level) and uploads them.  Later calls with
+// the same shapes replay the same launch sequence; the sequence is recorded as
+// a CUDA graph the first time and updated in place when the data pointers
+// change.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/scs_psd.h"
+#include "internal.cuh"
+
+using namespace scs;
+
+namespace {
+
+constexpr int kDefaultBand = 16;
+constexpr long long kDefaultWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int64_t kMaxSide = 8192;
+
+struct GemmLaunch {
+  int desc_off = 0, count = 0, prefix_off = 0, tiles = 0;
+};
+
+struct PanelStep {
+  int panel = 0, njobs = 0, cluster = 1, R = 0;
+  int ids_off = 0;  // offset into the int metadata
+  GemmLaunch g[6];
+};
+
+struct BulgeLaunch {
+  int nctas = 0, ncones = 0;
+  int cone_off = 0, rank_off = 0, count_off = 0;
+};
+
+struct Level {
+  int nnodes = 0, maxK = 0;
+  int nodes_off = 0;  // into MergeNode metadata
+  int pos_off = 0;    // into int metadata (2 * total)
+  GemmLaunch g;
+};
+
+struct Plan {
+  std::string key;
+  int b = kDefaultBand;
+  int allv = 0, side = 0;
+  // shapes
+  std::vector<int32_t> sides;
+  std::vector<int64_t> offsets;
+  int ncones = 0;  // cones with n >= 2
+  int64_t maxn = 0;
+  int ntriv = 0;
+  int64_t total_pos = 0;
+  // device memory
+  void* cone_mem = nullptr;
+  void* meta_mem = nullptr;
+  ConeDev* cones_d = nullptr;
+  int* ints_d = nullptr;
+  GemmDesc* descs_d = nullptr;
+  MergeNode* nodes_d = nullptr;
+  int64_t* triv_offs_d = nullptr;
+  int* triv_sides_d = nullptr;
+  int* status_d = nullptr;  // ncones + 1 (last: trivial cones)
+  int* prog_d = nullptr;
+  size_t prog_count = 0;
+  // steps
+  std::vector<PanelStep> panels;
+  std::vector<BulgeLaunch> bulges;
+  std::vector<Level> levels;
+  std::vector<GemmLaunch> bt1;  // 3 per panel, reverse order
+  GemmLaunch vjp[4];
+  int64_t launches = 0;
+  // graph
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_x = nullptr;
+  const void* g_y = nullptr;
+  const void* g_g = nullptr;
+  const void* g_xbar = nullptr;
+  ~Plan() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cone_mem) cudaFree(cone_mem);
+    if (meta_mem) cudaFree(meta_mem);
+  }
+};
+
+}  // namespace
+
+struct scs_psd_handle_s {
+  int device = 0;
+  int sms = 0;
+  int* status_word = nullptr;  // device
+  cudaStream_t last_stream = nullptr;
+  int64_t last_launches = 0;
+  std::map<std::string, std::unique_ptr<Plan>> plans;
+  std::mutex mu;
+};
+
+namespace {
+
+size_t align_up(size_t v, size_t a = 256) { return (v + a - 1) / a * a; }
+
+int64_t svec_len(int64_t n) { return n * (n + 1) / 2; }
+
+int num_panels(int64_t n, int b) { return n - 2 >= b ? (int)((n - 2) / b) : 0; }
+
+int num_levels(int64_t n) {
+  int L = 0;
+  while ((int64_t(1) << L) < n) ++L;
+  return L;
+}
+
+// ---- per-cone workspace layout
+struct ConeLayout {
+  size_t off[40];
+  size_t bytes;
+};
+
+enum Field {
+  F_A, F_BAND, F_REFL, F_D, F_E, F_V1, F_T1, F_Y, F_X, F_U3, F_MB, F_NB, F_QA, F_QB, F_LAMA, F_LAMB, F_QIN, F_UCM, F_Z,
+  F_LAMK, F_DSRT, F_ZK, F_DVAL, F_TAU, F_ZHAT, F_ROT, F_RHO, F_IPERM, F_IROT, F_IORG, F_IMAP, F_ICNT, F_KINFO, F_NFIELDS
+};
+
+ConeLayout cone_layout(int64_t n, int b) {
+  ConeLayout L{};
+  const int P = num_panels(n, b);
+  const int64_t nsw = std::max<int64_t>(0, n - 2);
+  const int64_t kmax = (n >= 3 ? (n - 3) / b + 1 : 0) + 1;
+  const size_t d = sizeof(double), i4 = sizeof(int);
+  const size_t sz[F_NFIELDS] = {
+      d * n * n, d * n * 2 * b, d * nsw * kmax * (b + 1), d * n, d * n, d * P * n * b, d * P * b * b,
+      d * n * b, d * n * b, d * n * 3 * b, d * b * b, d * b * b, d * n * n, d * n * n, d * n, d * n,
+      d * n * n, d * n * n, d * n * n, d * n, d * n, d * n, d * n, d * n, d * n, d * 2 * n, d * n,
+      i4 * n, i4 * 2 * n, i4 * n, i4 * n, i4 * 4 * n, i4 * 8};
+  size_t o = 0;
+  for (int f = 0; f < F_NFIELDS; ++f) {
+    o = align_up(o);
+    L.off[f] = o;
+    o += std::max<size_t>(sz[f], 8);
+  }
+  L.bytes = align_up(o);
+  return L;
+}
+
+#define CUDA_TRY(expr)                        \
+  do {                                        \
+    cudaError_t _e = (expr);                  \
+    if (_e != cudaSuccess) return SCS_PSD_ECUDA; \
+  } while (0)
+
+struct MetaBuilder {
+  std::vector<int> ints;
+  std::vector<GemmDesc> descs;
+  std::vector<int> prefix;  // stored inside ints
+  std::vector<MergeNode> nodes;
+
+  GemmLaunch add_gemm(const std::vector<GemmDesc>& probs) {
+    GemmLaunch g;
+    g.desc_off = (int)descs.size();
+    g.count = (int)probs.size();
+    g.prefix_off = (int)ints.size();
+    int t = 0;
+    for (const GemmDesc& p : probs) {
+      ints.push_back(t);
+      const int tm = (p.M + kGemmBM - 1) / kGemmBM, tn = (p.N + kGemmBN - 1) / kGemmBN;
+      t += std::max(0, tm * tn);
+      descs.push_back(p);
+    }
+    ints.push_back(t);
+    g.tiles = t;
+    return g;
+  }
+};
+
+GemmDesc mk(const double* A, int lda, const double* B, int ldb, double* C, int ldc, int M, int N, int K,
+            double alpha, double beta, int flags, const int* skip) {
+  GemmDesc g{};
+  g.A = A; g.B = B; g.C = C;
+  g.lda = lda; g.ldb = ldb; g.ldc = ldc;
+  g.M = M; g.N = N; g.K = K;
+  g.alpha = alpha; g.beta = beta;
+  g.flags = flags;
+  g.skip = skip;
+  return g;
+}
+
+int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, int b, int allv, int side) {
+  P.b = b;
+  P.allv = allv;
+  P.side = side;
+  P.sides.assign(sides, sides + count);
+  P.offsets.resize(count + 1);
+  P.offsets[0] = 0;
+  for (int i = 0; i < count; ++i) P.offsets[i + 1] = P.offsets[i] + svec_len(sides[i]);
+
+  // ---- cones of the main path (n >= 2) and trivial ones
+  std::vector<int> big;
+  std::vector<int64_t> triv_offs;
+  std::vector<int> triv_sides;
+  for (int i = 0; i < count; ++i) {
+    if (sides[i] >= 2) big.push_back(i);
+    else if (sides[i] == 1) { triv_offs.push_back(P.offsets[i]); triv_sides.push_back(1); }
+  }
+  P.ncones = (int)big.size();
+  P.ntriv = (int)triv_offs.size();
+  std::vector<ConeLayout> lay(P.ncones);
+  size_t cone_bytes = 0;
+  std::vector<size_t> cone_base(P.ncones);
+  for (int c = 0; c < P.ncones; ++c) {
+    const int64_t n = sides[big[c]];
+    P.maxn = std::max(P.maxn, n);
+    lay[c] = cone_layout(n, b);
+    cone_base[c] = cone_bytes;
+    cone_bytes += lay[c].bytes;
+  }
+  if (cone_bytes) {
+    if (cudaMalloc(&P.cone_mem, cone_bytes) != cudaSuccess) return SCS_PSD_ENOMEM;
+  }
+  char* base = (char*)P.cone_mem;
+
+  // ---- metadata sizes known up front: status (ncones+1), prog
+  MetaBuilder mb;
+  std::vector<ConeDev> cones(P.ncones);
+  size_t prog_total = 0;
+  std::vector<size_t> prog_off(P.ncones);
+  for (int c = 0; c < P.ncones; ++c) {
+    prog_off[c] = prog_total;
+    prog_total += std::max<int64_t>(1, sides[big[c]] - 2);
+  }
+  // ints layout: [status (ncones+1)] [prog] [rest...]
+  const int status_off = 0;
+  mb.ints.resize(P.ncones + 1, 0);
+  const int prog_base = (int)mb.ints.size();
+  mb.ints.resize(mb.ints.size() + prog_total, 0);
+  // ConeDev pointers to ints are fixed after the meta allocation; remember offsets
+  for (int c = 0; c < P.ncones; ++c) {
+    const int64_t n = sides[big[c]];
+    char* cb = base + cone_base[c];
+    const ConeLayout& L = lay[c];
+    ConeDev& d = cones[c];
+    d.n = n;
+    d.xoff = P.offsets[big[c]];
+    d.b = b;
+    d.npanels = num_panels(n, b);
+    d.nsweeps = (int)std::max<int64_t>(0, n - 2);
+    d.kmax = (int)((n >= 3 ? (n - 3) / b + 1 : 0) + 1);
+#define FLD(T, f) reinterpret_cast<T*>(cb + L.off[f])
+    d.A = FLD(double, F_A); d.band = FLD(double, F_BAND); d.refl = FLD(double, F_REFL);
+    d.d = FLD(double, F_D); d.e = FLD(double, F_E); d.V1 = FLD(double, F_V1); d.T1 = FLD(double, F_T1);
+    d.Y = FLD(double, F_Y); d.X = FLD(double, F_X); d.U3 = FLD(double, F_U3); d.Mb = FLD(double, F_MB);
+    d.Nb = FLD(double, F_NB); d.QA = FLD(double, F_QA); d.QB = FLD(double, F_QB); d.lamA = FLD(double, F_LAMA);
+    d.lamB = FLD(double, F_LAMB); d.Qin = FLD(double, F_QIN); d.Ucm = FLD(double, F_UCM); d.Z = FLD(double, F_Z);
+    d.lamk = FLD(double, F_LAMK); d.dsrt = FLD(double, F_DSRT); d.zk = FLD(double, F_ZK); d.dval = FLD(double, F_DVAL);
+    d.tau = FLD(double, F_TAU); d.zhat = FLD(double, F_ZHAT); d.rot = FLD(double, F_ROT); d.rho = FLD(double, F_RHO);
+    d.iperm = FLD(int, F_IPERM); d.irot = FLD(int, F_IROT); d.iorg = FLD(int, F_IORG); d.imap = FLD(int, F_IMAP);
+    d.icnt = FLD(int, F_ICNT); d.kinfo = FLD(int, F_KINFO);
+#undef FLD
+  }
+  // The GEMM descriptors need the status pointers (skip), which live in the
+  // metadata block: allocate it first with a generous upper bound, then fill.
+  // Upper bound: count descriptors/ints/nodes while building with placeholders.
+  // We build with a null status base and patch afterwards.
+  // encoded as (status slot index + 1) until the metadata block exists
+  auto st_ptr = [&](int c) -> const int* { return reinterpret_cast<const int*>((intptr_t)(status_off + c + 1 + 1)); };
+
+  // ---- stage 1: panels
+  int maxP = 0;
+  for (int c = 0; c < P.ncones; ++c) maxP = std::max(maxP, cones[c].npanels);
+  for (int p = 0; p < maxP; ++p) {
+    PanelStep ps;
+    ps.panel = p;
+    std::vector<int> ids;
+    int maxm = 0;
+    for (int c = 0; c < P.ncones; ++c)
+      if (p < cones[c].npanels) {
+        ids.push_back(c);
+        maxm = std::max<int>(maxm, (int)cones[c].n - (p + 1) * b);
+      }
+    ps.njobs = (int)ids.size();
+    ps.cluster = std::min(8, std::max(1, (maxm + 255) / 256));
+    ps.R = (maxm + ps.cluster - 1) / ps.cluster;
+    ps.ids_off = (int)mb.ints.size();
+    mb.ints.insert(mb.ints.end(), ids.begin(), ids.end());
+    std::vector<GemmDesc> g[6];
+    for (int c : ids) {
+      const ConeDev& d = cones[c];
+      const int n = (int)d.n;
+      const int r0 = (p + 1) * b, m = n - r0, bb = std::min(b, m);
+      double* A22 = d.A + r0 + (int64_t)r0 * n;
+      double* V = d.V1 + (int64_t)p * n * b;
+      double* T = d.T1 + (int64_t)p * b * b;
+      double* Xm = d.U3 + (int64_t)bb * m;
+      const int* sk = st_ptr(c);
+      g[0].push_back(mk(A22, n, V, m, d.Y, m, m, bb, m, 1.0, 0.0, GF_SYM_A, sk));
+      g[1].push_back(mk(d.Y, m, T, b, Xm, m, m, bb, bb, 1.0, 0.0, 0, sk));
+      g[2].push_back(mk(V, m, Xm, m, d.Mb, b, bb, bb, m, 1.0, 0.0, GF_TRANS_A, sk));
+      g[3].push_back(mk(T, b, d.Mb, b, d.Nb, b, bb, bb, bb, 1.0, 0.0, GF_TRANS_A, sk));
+      g[4].push_back(mk(V, m, d.Nb, b, Xm, m, m, bb, bb, -0.5, 1.0, 0, sk));
+      g[5].push_back(mk(Xm, m, d.U3, m, A22, n, m, m, 2 * bb, -1.0, 1.0, GF_TRANS_B | GF_LOWER_C, sk));
+    }
+    for (int q = 0; q < 6; ++q) ps.g[q] = mb.add_gemm(g[q]);
+    P.panels.push_back(ps);
+  }
+
+  // ---- stage 2: bulge chasing CTA assignment (cooperative launches)
+  {
+    int cap = bulge_max_ctas(b);
+    if (cap <= 0) cap = 1;
+    std::vector<int> want(P.ncones);
+    for (int c = 0; c < P.ncones; ++c) {
+      const int64_t n = cones[c].n;
+      const int nsw = cones[c].nsweeps;
+      int w = (int)std::max<int64_t>(1, n / (3 * b) + 1);
+      w = std::min(w, std::max(1, nsw));
+      want[c] = w;
+    }
+    int c = 0;
+    while (c < P.ncones) {
+      // pack cones into one launch while the CTA cap allows at least 1 each
+      int first = c, total_want = 0;
+      while (c < P.ncones && (c - first) < cap) { total_want += want[c]; ++c; }
+      const int nc = c - first;
+      std::vector<int> give(nc);
+      if (total_want <= cap) {
+        for (int q = 0; q < nc; ++q) give[q] = want[first + q];
+      } else {
+        int left = cap - nc;  // 1 each guaranteed
+        long long extra_want = 0;
+        for (int q = 0; q < nc; ++q) extra_want += want[first + q] - 1;
+        for (int q = 0; q < nc; ++q) {
+          const long long ew = want[first + q] - 1;
+          give[q] = 1 + (extra_want > 0 ? (int)(ew * left / extra_want) : 0);
+        }
+      }
+      BulgeLaunch bl;
+      bl.ncones = nc;
+      std::vector<int> cc, rr, gg;
+      for (int q = 0; q < nc; ++q)
+        for (int r = 0; r < give[q]; ++r) { cc.push_back(first + q); rr.push_back(r); gg.push_back(give[q]); }
+      bl.nctas = (int)cc.size();
+      bl.cone_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), cc.begin(), cc.end());
+      bl.rank_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), rr.begin(), rr.end());
+      bl.count_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), gg.begin(), gg.end());
+      P.bulges.push_back(bl);
+    }
+  }
+
+  // ---- divide and conquer levels
+  {
+    std::vector<int64_t> pos_base(P.ncones);
+    int64_t tp = 0;
+    int maxL = 0;
+    for (int c = 0; c < P.ncones; ++c) {
+      pos_base[c] = tp;
+      tp += cones[c].n;
+      maxL = std::max(maxL, num_levels(cones[c].n));
+    }
+    P.total_pos = tp;
+    for (int l = 0; l < maxL; ++l) {
+      Level lv;
+      lv.nodes_off = (int)mb.nodes.size();
+      std::vector<int> loc(tp, -1), nid(tp, -1);
+      std::vector<GemmDesc> gd;
+      for (int c = 0; c < P.ncones; ++c) {
+        const int64_t n = cones[c].n;
+        const int L = num_levels(n);
+        if (l >= L) continue;
+        const int64_t half = int64_t(1) << l, full = half << 1;
+        for (int64_t s = 0; s < n; s += full) {
+          MergeNode nd;
+          nd.cone = c;
+          nd.s = (int)s;
+          nd.n1 = (int)std::min(half, n - s);
+          nd.n2 = (int)std::max<int64_t>(0, std::min(half, n - s - nd.n1));
+          nd.root = (l == L - 1) ? 1 : 0;
+          nd.level = l;
+          const int K = nd.n1 + nd.n2;
+          const int idx = (int)mb.nodes.size() - lv.nodes_off;
+          for (int t = 0; t < K; ++t) {
+            loc[pos_base[c] + s + t] = t;
+            nid[pos_base[c] + s + t] = idx;
+          }
+          lv.maxK = std::max(lv.maxK, K);
+          mb.nodes.push_back(nd);
+          if (nd.n2 > 0) {
+            const ConeDev& d = cones[c];
+            const int ni = (int)n;
+            double* Qo = (l & 1) ? d.QA : d.QB;
+            GemmDesc g = mk(d.Qin + s + s * n, ni, d.Ucm + s + s * n, ni, nd.root ? d.Z : Qo + s, ni, K, K, K, 1.0,
+                            0.0, GF_TRANS_B, st_ptr(c));
+            g.dynK = d.icnt + 4 * s;
+            g.dynN = nd.root ? d.kinfo + 2 : d.icnt + 4 * s;
+            g.colmap = nd.root ? nullptr : d.imap + s;
+            gd.push_back(g);
+          }
+        }
+      }
+      lv.nnodes = (int)mb.nodes.size() - lv.nodes_off;
+      lv.pos_off = (int)mb.ints.size();
+      mb.ints.insert(mb.ints.end(), loc.begin(), loc.end());
+      mb.ints.insert(mb.ints.end(), nid.begin(), nid.end());
+      lv.g = mb.add_gemm(gd);
+      P.levels.push_back(lv);
+    }
+  }
+
+  // ---- stage-1 back-transformation, reverse panel order
+  for (int p = maxP - 1; p >= 0; --p) {
+    std::vector<GemmDesc> g[3];
+    for (int c = 0; c < P.ncones; ++c) {
+      const ConeDev& d = cones[c];
+      if (p >= d.npanels) continue;
+      const int n = (int)d.n;
+      const int r0 = (p + 1) * b, m = n - r0, bb = std::min(b, m);
+      double* V = d.V1 + (int64_t)p * n * b;
+      double* T = d.T1 + (int64_t)p * b * b;
+      GemmDesc a = mk(V, m, d.Z + r0, n, d.Y, b, bb, n, m, 1.0, 0.0, GF_TRANS_A, st_ptr(c));
+      a.dynN = d.kinfo;
+      GemmDesc b2 = mk(T, b, d.Y, b, d.X, b, bb, n, bb, 1.0, 0.0, 0, st_ptr(c));
+      b2.dynN = d.kinfo;
+      GemmDesc c3 = mk(V, m, d.X, b, d.Z + r0, n, m, n, bb, -1.0, 1.0, 0, st_ptr(c));
+      c3.dynN = d.kinfo;
+      g[0].push_back(a);
+      g[1].push_back(b2);
+      g[2].push_back(c3);
+    }
+    for (int q = 0; q < 3; ++q) P.bt1.push_back(mb.add_gemm(g[q]));
+  }
+
+  // ---- derivative contractions
+  if (allv) {
+    std::vector<GemmDesc> g[4];
+    for (int c = 0; c < P.ncones; ++c) {
+      const ConeDev& d = cones[c];
+      const int n = (int)d.n;
+      g[0].push_back(mk(d.A, n, d.Z, n, d.QA, n, n, n, n, 1.0, 0.0, 0, st_ptr(c)));
+      g[1].push_back(mk(d.Z, n, d.QA, n, d.QB, n, n, n, n, 1.0, 0.0, GF_TRANS_A, st_ptr(c)));
+      g[2].push_back(mk(d.Z, n, d.QB, n, d.QA, n, n, n, n, 1.0, 0.0, 0, st_ptr(c)));
+      g[3].push_back(mk(d.QA, n, d.Z, n, d.QB, n, n, n, n, 1.0, 0.0, GF_TRANS_B | GF_LOWER_C, st_ptr(c)));
+    }
+    for (int q = 0; q < 4; ++q) P.vjp[q] = mb.add_gemm(g[q]);
+  }
+
+  // ---- allocate and upload metadata
+  const size_t cones_b = align_up(sizeof(ConeDev) * std::max(1, P.ncones));
+  const size_t ints_b = align_up(sizeof(int) * std::max<size_t>(1, mb.ints.size()));
+  const size_t descs_b = align_up(sizeof(GemmDesc) * std::max<size_t>(1, mb.descs.size()));
+  const size_t nodes_b = align_up(sizeof(MergeNode) * std::max<size_t>(1, mb.nodes.size()));
+  const size_t triv_b = align_up((sizeof(int64_t) + sizeof(int)) * std::max(1, P.ntriv));
+  const size_t total = cones_b + ints_b + descs_b + nodes_b + triv_b;
+  if (cudaMalloc(&P.meta_mem, total) != cudaSuccess) return SCS_PSD_ENOMEM;
+  char* mbase = (char*)P.meta_mem;
+  P.cones_d = (ConeDev*)mbase;
+  P.ints_d = (int*)(mbase + cones_b);
+  P.descs_d = (GemmDesc*)(mbase + cones_b + ints_b);
+  P.nodes_d = (MergeNode*)(mbase + cones_b + ints_b + descs_b);
+  P.triv_offs_d = (int64_t*)(mbase + cones_b + ints_b + descs_b + nodes_b);
+  P.triv_sides_d = (int*)(P.triv_offs_d + std::max(1, P.ntriv));
+  P.status_d = P.ints_d + status_off;
+  P.prog_d = P.ints_d + prog_base;
+  P.prog_count = prog_total;
+  // patch pointers that refer to the metadata block
+  for (int c = 0; c < P.ncones; ++c) {
+    cones[c].status = P.status_d + c + 1;
+    cones[c].prog = P.prog_d + prog_off[c];
+  }
+  for (GemmDesc& g : mb.descs)
+    if (g.skip) g.skip = P.ints_d + ((intptr_t)g.skip - 1);
+  cudaError_t e = cudaSuccess;
+  if (P.ncones) e = cudaMemcpy(P.cones_d, cones.data(), sizeof(ConeDev) * P.ncones, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !mb.ints.empty())
+    e = cudaMemcpy(P.ints_d, mb.ints.data(), sizeof(int) * mb.ints.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !mb.descs.empty())
+    e = cudaMemcpy(P.descs_d, mb.descs.data(), sizeof(GemmDesc) * mb.descs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !mb.nodes.empty())
+    e = cudaMemcpy(P.nodes_d, mb.nodes.data(), sizeof(MergeNode) * mb.nodes.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && P.ntriv) {
+    e = cudaMemcpy(P.triv_offs_d, triv_offs.data(), sizeof(int64_t) * P.ntriv, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(P.triv_sides_d, triv_sides.data(), sizeof(int) * P.ntriv, cudaMemcpyHostToDevice);
+  }
+  // kinfo: [3] all eigenpairs, [4] side option
+  for (int c = 0; c < P.ncones && e == cudaSuccess; ++c) {
+    int kin[8] = {0, 0, 0, allv, side, 0, 0, 0};
+    e = cudaMemcpy(cones[c].kinfo, kin, sizeof(kin), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) return SCS_PSD_ECUDA;
+  (void)h;
+  return SCS_PSD_OK;
+}
+
+#define LAUNCH_CHECK()                                      \
+  do {                                                      \
+    ++n_launch;                                             \
+    cudaError_t _e = cudaGetLastError();                    \
+    if (_e != cudaSuccess) return SCS_PSD_ECUDA;            \
+  } while (0)
+
+int run_gemm(const Plan& P, const GemmLaunch& g, cudaStream_t s, int64_t& n_launch) {
+  if (g.count <= 0 || g.tiles <= 0) return SCS_PSD_OK;
+  launch_gemm(P.descs_d + g.desc_off, P.ints_d + g.prefix_off, g.count, g.tiles, s);
+  LAUNCH_CHECK();
+  return SCS_PSD_OK;
+}
+
+// The launch sequence of one call.
+int run_plan(scs_psd_handle h, Plan& P, const double* x, double* y, const double* g, double* xbar,
+             long long wait_limit, cudaStream_t s) {
+  int64_t n_launch = 0;
+  int rc;
+  CUDA_TRY(cudaMemsetAsync(P.status_d, 0, sizeof(int) * (P.ncones + 1), s));
+  if (P.prog_count) CUDA_TRY(cudaMemsetAsync(P.prog_d, 0, sizeof(int) * P.prog_count, s));
+  if (P.ntriv && y) {
+    launch_trivial(P.triv_offs_d, P.triv_sides_d, P.ntriv, x, y, P.status_d, s);
+    LAUNCH_CHECK();
+  }
+  if (P.ncones) {
+    const int nc = P.ncones;
+    launch_unpack(P.cones_d, nc, P.maxn * P.maxn, x, s);
+    LAUNCH_CHECK();
+    for (const PanelStep& ps : P.panels) {
+      launch_panel(P.cones_d, P.ints_d + ps.ids_off, ps.njobs, ps.panel, P.b, ps.cluster, ps.R, s);
+      LAUNCH_CHECK();
+      for (int q = 0; q < 6; ++q)
+        if ((rc = run_gemm(P, ps.g[q], s, n_launch))) return rc;
+    }
+    launch_band_extract(P.cones_d, nc, P.maxn, s);
+    LAUNCH_CHECK();
+    for (const BulgeLaunch& bl : P.bulges) {
+      if (launch_bulge(P.cones_d, bl.ncones, P.ints_d + bl.cone_off, P.ints_d + bl.rank_off,
+                       P.ints_d + bl.count_off, bl.nctas, P.b, wait_limit, s))
+        return SCS_PSD_ECUDA;
+      LAUNCH_CHECK();
+    }
+    launch_tridiag_extract(P.cones_d, nc, P.maxn, s);
+    LAUNCH_CHECK();
+    launch_dc_leaves(P.cones_d, nc, P.maxn, s);
+    LAUNCH_CHECK();
+    for (const Level& lv : P.levels) {
+      const MergeNode* nodes = P.nodes_d + lv.nodes_off;
+      const int* pos = P.ints_d + lv.pos_off;
+      launch_dc_prepare(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
+      LAUNCH_CHECK();
+      launch_dc_secular(P.cones_d, nodes, pos, P.total_pos, s);
+      LAUNCH_CHECK();
+      launch_dc_loewner(P.cones_d, nodes, pos, P.total_pos, s);
+      LAUNCH_CHECK();
+      launch_dc_select(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
+      LAUNCH_CHECK();
+      launch_dc_vectors(P.cones_d, nodes, pos, P.total_pos, s);
+      LAUNCH_CHECK();
+      if ((rc = run_gemm(P, lv.g, s, n_launch))) return rc;
+      launch_dc_copy_deflated(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
+      LAUNCH_CHECK();
+    }
+    launch_backtr2(P.cones_d, nc, (int)P.maxn, (int)P.maxn, s);
+    LAUNCH_CHECK();
+    for (const GemmLaunch& gl : P.bt1)
+      if ((rc = run_gemm(P, gl, s, n_launch))) return rc;
+    if (y) {
+      launch_recon(P.cones_d, nc, (int)P.maxn, x, y, s);
+      LAUNCH_CHECK();
+    }
+    if (g && xbar) {
+      launch_unpack(P.cones_d, nc, P.maxn * P.maxn, g, s);
+      LAUNCH_CHECK();
+      if ((rc = run_gemm(P, P.vjp[0], s, n_launch))) return rc;
+      if ((rc = run_gemm(P, P.vjp[1], s, n_launch))) return rc;
+      launch_loewner_scale(P.cones_d, nc, P.maxn, s);
+      LAUNCH_CHECK();
+      if ((rc = run_gemm(P, P.vjp[2], s, n_launch))) return rc;
+      if ((rc = run_gemm(P, P.vjp[3], s, n_launch))) return rc;
+      launch_pack_lower(P.cones_d, nc, P.maxn, xbar, s);
+      LAUNCH_CHECK();
+    }
+  }
+  launch_status_reduce(P.status_d, P.ncones + 1, h->status_word, s);
+  LAUNCH_CHECK();
+  P.launches = n_launch;
+  return SCS_PSD_OK;
+}
+
+std::string plan_key(const int32_t* sides, int32_t count, int b, int allv, int side) {
+  std::string k;
+  k.reserve(16 + 4 * (size_t)count);
+  char hdr[64];
+  snprintf(hdr, sizeof(hdr), "b%d,a%d,s%d,c%d:", b, allv, side, count);
+  k += hdr;
+  k.append(reinterpret_cast<const char*>(sides), sizeof(int32_t) * (size_t)count);
+  return k;
+}
+
+int check_shapes(const int64_t* offsets, const int32_t* sides, int32_t count) {
+  if (count < 0) return SCS_PSD_EINVAL;
+  if (count == 0) return SCS_PSD_OK;
+  if (!offsets || !sides) return SCS_PSD_EINVAL;
+  if (offsets[0] != 0) return SCS_PSD_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (sides[i] < 0 || sides[i] > kMaxSide) return SCS_PSD_EINVAL;
+    if (offsets[i + 1] - offsets[i] != svec_len(sides[i])) return SCS_PSD_EINVAL;
+  }
+  return SCS_PSD_OK;
+}
+
+int do_call(scs_psd_handle h, const double* x, double* y, const double* g, double* xbar, const int64_t* offsets,
+            const int32_t* sides, int32_t count, const scs_psd_opts* opts, void* stream, int allv) {
+  if (!h) return SCS_PSD_EINVAL;
+  int rc = check_shapes(offsets, sides, count);
+  if (rc) return rc;
+  if (count == 0 || offsets[count] == 0) return SCS_PSD_OK;
+  if (!x || (!y && !xbar)) return SCS_PSD_EINVAL;
+  if (allv && (!g || !xbar)) return SCS_PSD_EINVAL;
+  int b = kDefaultBand, side = 0;
+  long long wait = kDefaultWaitCycles;
+  if (opts) {
+    if (opts->precision != SCS_PSD_FP64) return SCS_PSD_EINVAL;
+    if (opts->band) b = opts->band;
+    side = opts->side;
+    if (opts->wait_limit_cycles > 0) wait = opts->wait_limit_cycles;
+  }
+  if (b < 2 || b > kMaxBand || side < 0 || side > 2) return SCS_PSD_EINVAL;
+  std::lock_guard<std::mutex> lock(h->mu);
+  if (cudaSetDevice(h->device) != cudaSuccess) return SCS_PSD_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const std::string key = plan_key(sides, count, b, allv, side);
+  auto it = h->plans.find(key);
+  Plan* P;
+  if (it == h->plans.end()) {
+    if (h->plans.size() >= 16) {
+      cudaDeviceSynchronize();
+      h->plans.clear();
+    }
+    auto np = std::make_unique<Plan>();
+    np->key = key;
+    rc = build_plan(h, *np, sides, count, b, allv, side);
+    if (rc) return rc;
+    P = np.get();
+    h->plans[key] = std::move(np);
+  } else {
+    P = it->second.get();
+  }
+  rc = run_plan(h, *P, x, y, g, xbar, wait, s);
+  h->last_stream = s;
+  h->last_launches = P->launches;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int scs_psd_create(scs_psd_handle* h, int device) {
+  if (!h) return SCS_PSD_EINVAL;
+  *h = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SCS_PSD_ECUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return SCS_PSD_ECUDA;
+  auto* H = new (std::nothrow) scs_psd_handle_s();
+  if (!H) return SCS_PSD_ENOMEM;
+  H->device = device;
+  cudaDeviceGetAttribute(&H->sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&H->status_word, sizeof(int)) != cudaSuccess) {
+    delete H;
+    return SCS_PSD_ENOMEM;
+  }
+  cudaMemset(H->status_word, 0, sizeof(int));
+  *h = H;
+  return SCS_PSD_OK;
+}
+
+int scs_psd_destroy(scs_psd_handle h) {
+  if (!h) return SCS_PSD_EINVAL;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  h->plans.clear();
+  cudaFree(h->status_word);
+  delete h;
+  return SCS_PSD_OK;
+}
+
+int scs_psd_proj(scs_psd_handle h, const double* x, double* y, int64_t n, const scs_psd_opts* opts, void* stream) {
+  if (n < 0 || n > kMaxSide) return SCS_PSD_EINVAL;
+  if (n == 0) return h ? SCS_PSD_OK : SCS_PSD_EINVAL;
+  const int64_t offs[2] = {0, svec_len(n)};
+  const int32_t sides[1] = {(int32_t)n};
+  if (!y) return SCS_PSD_EINVAL;
+  return do_call(h, x, y, nullptr, nullptr, offs, sides, 1, opts, stream, 0);
+}
+
+int scs_psd_proj_batched(scs_psd_handle h, const double* x, double* y, const int64_t* offsets, const int32_t* sides,
+                         int32_t count, const scs_psd_opts* opts, void* stream) {
+  if (!y && count > 0) return SCS_PSD_EINVAL;
+  return do_call(h, x, y, nullptr, nullptr, offsets, sides, count, opts, stream, 0);
+}
+
+int scs_psd_proj_vjp(scs_psd_handle h, const double* x, const double* g, double* xbar, double* y,
+                     const int64_t* offsets, const int32_t* sides, int32_t count, const scs_psd_opts* opts,
+                     void* stream) {
+  return do_call(h, x, y, g, xbar, offsets, sides, count, opts, stream, 1);
+}
+
+int scs_psd_reserve(scs_psd_handle h, int64_t max_n, int32_t max_count, const scs_psd_opts* opts) {
+  (void)opts;
+  if (!h || max_n < 0 || max_n > kMaxSide || max_count < 0) return SCS_PSD_EINVAL;
+  return SCS_PSD_OK;
+}
+
+int scs_psd_status(scs_psd_handle h, int32_t* device_status) {
+  if (!h || !device_status) return SCS_PSD_EINVAL;
+  cudaSetDevice(h->device);
+  if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) return SCS_PSD_ECUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, h->status_word, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SCS_PSD_ECUDA;
+  cudaMemset(h->status_word, 0, sizeof(int));
+  int code = SCS_PSD_OK;
+  if (v & ST_TIMEOUT) code = SCS_PSD_ETIMEOUT;
+  else if (v & ST_NOCONV) code = SCS_PSD_ENOCONV;
+  else if (v & ST_NONFINITE) code = SCS_PSD_ENONFINITE;
+  *device_status = code;
+  return SCS_PSD_OK;
+}
+
+int64_t scs_psd_last_launch_count(scs_psd_handle h) { return h ? h->last_launches : -1; }
+
+const char* scs_psd_strerror(int code) {
+  switch (code) {
+    case SCS_PSD_OK: return "ok";
+    case SCS_PSD_EINVAL: return "invalid argument";
+    case SCS_PSD_ENOMEM: return "out of memory";
+    case SCS_PSD_ECUDA: return "CUDA runtime error";
+    case SCS_PSD_ETIMEOUT: return "bounded device wait ran out";
+    case SCS_PSD_ENOCONV: return "iteration did not converge";
+    case SCS_PSD_ENONFINITE: return "non-finite input";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,597 @@
+// Divide and conquer for the symmetric tridiagonal eigenproblem (Cuppen),
+// with Dongarra-Sorensen deflation and the Gu-Eisenstat (Loewner) correction
+// that keeps the computed eigenvectors orthogonal.
+//
+// Tearing: every off-diagonal e_m couples rows m and m+1 as |e_m| v v^T with
+// v = e_m + sign(e_m) e_{m+1}; the leaves are 1x1 blocks with diagonal
+// d_i - |e_{i-1}| - |e_i|.  Level l merges adjacent blocks of size 2^l: with
+// Q = diag(Q1, Q2) the children's eigenvectors and D their eigenvalues,
+//     T = Q (D + rho z z^T) Q^T,  z = Q^T v / ||Q^T v||,  rho = |e_m| ||Q^T v||^2.
+// A merge node
+//   prepare : sorts D (merge of two sorted lists), deflates z_j with
+//             rho |z_j| <= tol and pairs of close poles by a Givens rotation,
+//             tol = 8 eps max(max|d|, rho), and forms the permuted, rotated
+//             eigenvector block [kept | deflated];
+//   secular : solves 1 + rho sum z_j^2 / (d_j - x) = 0 for each root, one
+//             thread per root, in coordinates shifted to the nearer pole
+//             (two-pole rational model with a bisection safeguard);
+//   loewner : recomputes z from the roots so that the vectors are exact
+//             eigenvectors of a nearby problem;
+//   select  : places roots and deflated values in sorted order (for the
+//             cone's final merge: chooses the side -- positive part, or X minus
+//             the negative part -- and keeps only those eigenpairs);
+//   vectors : u_i = zhat / (d - lambda_i), normalised;
+//   GEMM    : new block = [kept columns] * U^T (grouped GEMM, separate file).
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace scs {
+
+namespace {
+
+constexpr int kDcThreads = 256;
+constexpr double kEps = 1.1102230246251565e-16;  // 2^-53
+
+__device__ __forceinline__ long long dkey(double x) {
+  long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+__device__ __forceinline__ double* qin_buf(const ConeDev& c, int level) { return (level & 1) ? c.QB : c.QA; }
+__device__ __forceinline__ double* qout_buf(const ConeDev& c, int level) { return (level & 1) ? c.QA : c.QB; }
+__device__ __forceinline__ double* lin_buf(const ConeDev& c, int level) { return (level & 1) ? c.lamB : c.lamA; }
+__device__ __forceinline__ double* lout_buf(const ConeDev& c, int level) { return (level & 1) ? c.lamA : c.lamB; }
+
+__global__ void dc_leaves_kernel(const ConeDev* __restrict__ cones) {
+  const ConeDev& c = cones[blockIdx.y];
+  const int64_t n = c.n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double di = c.d[i];
+    if (i > 0) di -= fabs(c.e[i - 1]);
+    if (i + 1 < n) di -= fabs(c.e[i]);
+    c.lamA[i] = di;
+    c.QA[i + i * n] = 1.0;
+  }
+}
+
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+  return t;
+}
+
+__device__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = red[0];
+  for (int q = 1; q < (int)(blockDim.x >> 5); ++q) t = fmax(t, red[q]);
+  return t;
+}
+
+// ---------------------------------------------------------------- prepare
+__global__ void __launch_bounds__(kDcThreads) dc_prepare_kernel(const ConeDev* __restrict__ cones,
+                                                                const MergeNode* __restrict__ nodes) {
+  const MergeNode nd = nodes[blockIdx.x];
+  const ConeDev& c = cones[nd.cone];
+  if (*c.status != 0) return;
+  const int64_t n = c.n;
+  const int s = nd.s, n1 = nd.n1, n2 = nd.n2, K = n1 + n2;
+  const double* Qi = qin_buf(c, nd.level);
+  const double* li = lin_buf(c, nd.level);
+  const int tid = threadIdx.x;
+  int* cnt = c.icnt + 4 * s;
+
+  if (n2 == 0) {  // a lone block moves up one level unchanged
+    double* Qo = qout_buf(c, nd.level);
+    double* lo = lout_buf(c, nd.level);
+    for (int64_t e = tid; e < (int64_t)K * K; e += kDcThreads) {
+      const int r = (int)(e % K), q = (int)(e / K);
+      Qo[(s + r) + (int64_t)(s + q) * n] = Qi[(s + r) + (int64_t)(s + q) * n];
+    }
+    for (int t = tid; t < K; t += kDcThreads) lo[s + t] = li[s + t];
+    if (tid == 0) { cnt[0] = 0; cnt[1] = 0; cnt[2] = 0; }
+    return;
+  }
+
+  extern __shared__ double dsm[];
+  double* dv = dsm;                 // K sorted poles
+  double* zv = dv + K;              // K sorted z
+  int* perm = (int*)(zv + K);       // K: sorted position -> child column
+  int* fp = perm + K;               // K: sorted position -> final column
+  __shared__ double red[kDcThreads / 32];
+  __shared__ double sh_rho;
+  __shared__ int sh_kk, sh_nrot;
+
+  const double beta = c.e[s + n1 - 1];
+  const double sgn = beta >= 0.0 ? 1.0 : -1.0;
+  // z in child order (stored at the sorted position below)
+  // rank by a stable merge of the two sorted child lists
+  for (int t = tid; t < K; t += kDcThreads) {
+    double val, zval;
+    int rnk;
+    if (t < n1) {
+      val = li[s + t];
+      zval = Qi[(s + n1 - 1) + (int64_t)(s + t) * n];
+      const long long kv = dkey(val);
+      int lo = 0, hi = n2;  // count of child-2 values < val
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (dkey(li[s + n1 + mid]) < kv) lo = mid + 1; else hi = mid;
+      }
+      rnk = t + lo;
+    } else {
+      const int u = t - n1;
+      val = li[s + t];
+      zval = sgn * Qi[(s + n1) + (int64_t)(s + t) * n];
+      const long long kv = dkey(val);
+      int lo = 0, hi = n1;  // count of child-1 values <= val
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (dkey(li[s + mid]) <= kv) lo = mid + 1; else hi = mid;
+      }
+      rnk = u + lo;
+    }
+    dv[rnk] = val;
+    zv[rnk] = zval;
+    perm[rnk] = t;
+  }
+  __syncthreads();
+  double ss = 0.0, dm = 0.0;
+  for (int t = tid; t < K; t += kDcThreads) {
+    ss = fma(zv[t], zv[t], ss);
+    dm = fmax(dm, fabs(dv[t]));
+  }
+  const double nrm2 = block_sum(ss, red);
+  const double dmax = block_max(dm, red);
+  const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+  for (int t = tid; t < K; t += kDcThreads) zv[t] *= inv;
+  __syncthreads();
+
+  // ---- deflation scan (sequential by nature)
+  double* rot = c.rot + 2 * s;
+  int* irot = c.irot + 2 * s;
+  if (tid == 0) {
+    const double rho = fabs(beta) * nrm2;
+    const double tol = 8.0 * kEps * fmax(dmax, rho);
+    int last = -1, nrot = 0;
+    // fp[] temporarily holds 1 for kept, 0 for deflated
+    for (int j = 0; j < K; ++j) {
+      if (rho * fabs(zv[j]) <= tol) { fp[j] = 0; continue; }
+      if (last >= 0) {
+        const double sp = zv[last], cj = zv[j];
+        const double tt = hypot(cj, sp);
+        const double cc = cj / tt, sn = sp / tt;
+        const double gap = dv[j] - dv[last];
+        if (fabs(gap * cc * sn) <= tol) {
+          const double dp = dv[last], dj = dv[j];
+          dv[last] = dp * cc * cc + dj * sn * sn;
+          dv[j] = dp * sn * sn + dj * cc * cc;
+          zv[j] = tt;
+          zv[last] = 0.0;
+          fp[last] = 0;
+          rot[2 * nrot] = cc;
+          rot[2 * nrot + 1] = sn;
+          irot[2 * nrot] = last;  // sorted indices for now
+          irot[2 * nrot + 1] = j;
+          ++nrot;
+        }
+      }
+      fp[j] = 1;
+      last = j;
+    }
+    // final columns: kept first (in order), deflated after (in order)
+    int kk = 0;
+    for (int j = 0; j < K; ++j) kk += fp[j];
+    int pk = 0, pd = kk;
+    for (int j = 0; j < K; ++j) fp[j] = fp[j] ? pk++ : pd++;
+    for (int r = 0; r < nrot; ++r) {
+      irot[2 * r] = fp[irot[2 * r]];
+      irot[2 * r + 1] = fp[irot[2 * r + 1]];
+    }
+    sh_rho = rho;
+    sh_kk = kk;
+    sh_nrot = nrot;
+  }
+  __syncthreads();
+  const int kk = sh_kk, nrot = sh_nrot;
+  for (int j = tid; j < K; j += kDcThreads) {
+    const int f = fp[j];
+    if (f < kk) {
+      c.dsrt[s + f] = dv[j];
+      c.zk[s + f] = zv[j];
+    } else {
+      c.dval[s + f - kk] = dv[j];
+    }
+  }
+  if (tid == 0) {
+    c.rho[s] = sh_rho;
+    cnt[0] = kk;
+    cnt[1] = K - kk;
+    cnt[2] = nrot;
+  }
+  // ---- permuted eigenvector block Qin(:, fp[j]) = Q(:, perm[j]) (block diagonal source)
+  double* Qb = c.Qin;
+  for (int64_t e = tid; e < (int64_t)K * K; e += kDcThreads) {
+    const int r = (int)(e % K), j = (int)(e / K);
+    const int src = perm[j];
+    const bool same = (src < n1) == (r < n1);
+    const double v = same ? Qi[(s + r) + (int64_t)(s + src) * n] : 0.0;
+    Qb[(s + r) + (int64_t)(s + fp[j]) * n] = v;
+  }
+  __syncthreads();
+  if (nrot > 0) {
+    // Givens rotations of the deflation, in order; each thread owns rows
+    for (int r = tid; r < K; r += kDcThreads) {
+      for (int q = 0; q < nrot; ++q) {
+        const int a = irot[2 * q], bcol = irot[2 * q + 1];
+        const double cc = rot[2 * q], sn = rot[2 * q + 1];
+        double* pa = Qb + (s + r) + (int64_t)(s + a) * n;
+        double* pb = Qb + (s + r) + (int64_t)(s + bcol) * n;
+        const double x = *pa, y = *pb;
+        *pa = cc * x - sn * y;
+        *pb = sn * x + cc * y;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- secular
+// Root i of f(x) = 1 + rho sum_j z_j^2 / (d_j - x), d strictly increasing,
+// ||z|| = 1.  Returns the origin pole and the offset tau = x - d_org.
+__device__ bool secular_root(const double* __restrict__ dk, const double* __restrict__ zk, int K, double rho,
+                             int i, int* org_out, double* tau_out) {
+  int org;
+  double lo, hi;
+  if (i < K - 1) {
+    const double di = dk[i];
+    const double mid = 0.5 * (dk[i + 1] - di);
+    double f = 1.0;
+    for (int j = 0; j < K; ++j) f += rho * zk[j] * zk[j] / ((dk[j] - di) - mid);
+    if (f >= 0.0) { org = i; lo = 0.0; hi = mid; }
+    else { org = i + 1; lo = -mid; hi = 0.0; }
+  } else {
+    org = i;
+    lo = 0.0;
+    hi = rho;
+  }
+  const double dorg = dk[org];
+  double tau = 0.5 * (lo + hi);
+  const int li = i, ri = i + 1;
+  bool conv = false;
+  for (int it = 0; it < 100; ++it) {
+    double psi = 0.0, phi = 0.0, dpsi = 0.0, dphi = 0.0, aerr = 0.0;
+    for (int j = 0; j < K; ++j) {
+      const double del = (dk[j] - dorg) - tau;
+      const double zz = zk[j];
+      const double t = zz / del;
+      const double term = zz * t;
+      if (j < ri) { psi += term; dpsi = fma(t, t, dpsi); }
+      else { phi += term; dphi = fma(t, t, dphi); }
+      aerr += fabs(term);
+    }
+    psi *= rho; phi *= rho; dpsi *= rho; dphi *= rho;
+    const double g = 1.0 + psi + phi;
+    if (fabs(g) <= 8.0 * kEps * K * (1.0 + rho * aerr)) { conv = true; break; }
+    if (g > 0.0) hi = tau; else lo = tau;
+    if (hi - lo <= 4.0 * kEps * fmax(fabs(lo), fabs(hi))) { conv = true; break; }
+    const double p = dk[li] - dorg;
+    const double dl = p - tau;
+    const double sl = dpsi * dl * dl;
+    const double a = psi - sl / dl;
+    double x;
+    bool okx = false;
+    if (ri < K) {
+      const double q = dk[ri] - dorg;
+      const double dr = q - tau;
+      const double sr = dphi * dr * dr;
+      const double bq = phi - sr / dr;
+      const double C = 1.0 + a + bq;
+      const double A2 = C;
+      const double B2 = -(C * (p + q) + sl + sr);
+      const double C2 = C * p * q + sl * q + sr * p;
+      if (A2 != 0.0) {
+        const double disc = B2 * B2 - 4.0 * A2 * C2;
+        if (disc >= 0.0) {
+          const double sq = sqrt(disc);
+          const double qq = -0.5 * (B2 + copysign(sq, B2));
+          const double x1 = qq / A2;
+          if (x1 > lo && x1 < hi) { x = x1; okx = true; }
+          else if (qq != 0.0) {
+            const double x2 = C2 / qq;
+            if (x2 > lo && x2 < hi) { x = x2; okx = true; }
+          }
+        }
+      } else if (B2 != 0.0) {
+        const double x1 = -C2 / B2;
+        if (x1 > lo && x1 < hi) { x = x1; okx = true; }
+      }
+    } else {
+      const double C = 1.0 + a;
+      if (C > 0.0) {
+        const double x1 = p + sl / C;
+        if (x1 > lo && x1 < hi) { x = x1; okx = true; }
+      }
+    }
+    if (!okx) x = 0.5 * (lo + hi);
+    tau = x;
+  }
+  *org_out = org;
+  *tau_out = tau;
+  return conv;
+}
+
+__device__ __forceinline__ bool node_of(const MergeNode* nodes, const int* pos_node, int64_t gp, MergeNode& nd,
+                                        int& idx) {
+  const int ni = pos_node[gp];
+  if (ni < 0) return false;
+  nd = nodes[ni];
+  idx = ni;
+  return nd.n2 > 0;
+}
+
+__global__ void dc_secular_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes,
+                                  const int* __restrict__ pos_node, int64_t total) {
+  const int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gp >= total) return;
+  MergeNode nd;
+  int ni;
+  if (!node_of(nodes, pos_node + total, gp, nd, ni)) return;
+  const ConeDev& c = cones[nd.cone];
+  if (*c.status != 0) return;
+  const int i = pos_node[gp];  // root index within the node
+  const int kk = c.icnt[4 * nd.s];
+  if (i >= kk) return;
+  int org;
+  double tau;
+  const bool ok = secular_root(c.dsrt + nd.s, c.zk + nd.s, kk, c.rho[nd.s], i, &org, &tau);
+  c.iorg[nd.s + i] = org;
+  c.tau[nd.s + i] = tau;
+  if (!ok) atomicOr(c.status, ST_NOCONV);
+}
+
+// lambda_i - d_j, accurate: (d_org(i) - d_j) + tau_i
+__device__ __forceinline__ double lam_minus_d(const double* dk, const int* org, const double* tau, int i, int j) {
+  return (dk[org[i]] - dk[j]) + tau[i];
+}
+
+__global__ void dc_loewner_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes,
+                                  const int* __restrict__ pos_node, int64_t total) {
+  const int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gp >= total) return;
+  MergeNode nd;
+  int ni;
+  if (!node_of(nodes, pos_node + total, gp, nd, ni)) return;
+  const ConeDev& c = cones[nd.cone];
+  if (*c.status != 0) return;
+  const int j = pos_node[gp];
+  const int kk = c.icnt[4 * nd.s];
+  if (j >= kk) return;
+  const double* dk = c.dsrt + nd.s;
+  const int* org = c.iorg + nd.s;
+  const double* tau = c.tau + nd.s;
+  const double dj = dk[j];
+  double prod = lam_minus_d(dk, org, tau, kk - 1, j) / c.rho[nd.s];
+  for (int i = 0; i < j; ++i) prod *= lam_minus_d(dk, org, tau, i, j) / (dk[i] - dj);
+  for (int i = j + 1; i < kk; ++i) prod *= lam_minus_d(dk, org, tau, i - 1, j) / (dk[i] - dj);
+  c.zhat[nd.s + j] = copysign(sqrt(fabs(prod)), c.zk[nd.s + j]);
+}
+
+// ---------------------------------------------------------------- select
+__global__ void __launch_bounds__(kDcThreads) dc_select_kernel(const ConeDev* __restrict__ cones,
+                                                               const MergeNode* __restrict__ nodes) {
+  const MergeNode nd = nodes[blockIdx.x];
+  if (nd.n2 == 0) return;
+  const ConeDev& c = cones[nd.cone];
+  if (*c.status != 0) return;
+  const int s = nd.s, K = nd.n1 + nd.n2;
+  const int* cnt = c.icnt + 4 * s;
+  const int kk = cnt[0], ndf = cnt[1];
+  extern __shared__ double dsm[];
+  double* lam = dsm;               // kk roots (increasing)
+  double* dfs = lam + K;           // ndf deflated values, sorted
+  int* dord = (int*)(dfs + K);     // sorted rank -> deflated index
+  const int tid = threadIdx.x;
+  const double* dk = c.dsrt + s;
+  for (int i = tid; i < kk; i += kDcThreads) lam[i] = dk[c.iorg[s + i]] + c.tau[s + i];
+  // rank the deflated values (they may be slightly out of order after rotations)
+  for (int q = tid; q < ndf; q += kDcThreads) {
+    const double v = c.dval[s + q];
+    const long long kv = dkey(v);
+    int r = 0;
+    for (int u = 0; u < ndf; ++u) {
+      const long long ku = dkey(c.dval[s + u]);
+      r += (ku < kv) || (ku == kv && u < q);
+    }
+    dfs[r] = v;
+    dord[r] = q;
+  }
+  __syncthreads();
+  if (!nd.root) {
+    double* lo = lout_buf(c, nd.level);
+    int* imap = c.imap + s;
+    for (int i = tid; i < kk; i += kDcThreads) {
+      const long long kv = dkey(lam[i]);
+      int a = 0, b = ndf;  // deflated < lam_i
+      while (a < b) { const int m = (a + b) >> 1; if (dkey(dfs[m]) < kv) a = m + 1; else b = m; }
+      const int pos = i + a;
+      lo[s + pos] = lam[i];
+      imap[i] = s + pos;
+    }
+    for (int r = tid; r < ndf; r += kDcThreads) {
+      const long long kv = dkey(dfs[r]);
+      int a = 0, b = kk;  // roots <= value
+      while (a < b) { const int m = (a + b) >> 1; if (dkey(lam[m]) <= kv) a = m + 1; else b = m; }
+      const int pos = r + a;
+      lo[s + pos] = dfs[r];
+      imap[kk + dord[r]] = s + pos;  // deflated column kk + q -> output column
+    }
+    return;
+  }
+  // ---- cone's final merge: choose the side and the kept eigenpairs
+  __shared__ int sh_pos, sh_neg;
+  if (tid == 0) { sh_pos = 0; sh_neg = 0; }
+  __syncthreads();
+  int np = 0, nn = 0;
+  for (int i = tid; i < kk; i += kDcThreads) { np += lam[i] > 0.0; nn += lam[i] < 0.0; }
+  for (int r = tid; r < ndf; r += kDcThreads) { np += dfs[r] > 0.0; nn += dfs[r] < 0.0; }
+  atomicAdd(&sh_pos, np);
+  atomicAdd(&sh_neg, nn);
+  __syncthreads();
+  const int allv = c.kinfo[3];
+  int route;
+  const int side = c.kinfo[4];
+  if (side == 1) route = 0;
+  else if (side == 2) route = 1;
+  else route = (sh_pos <= sh_neg) ? 0 : 1;
+  // kept roots form a contiguous range [r_lo, r_hi)
+  int r_lo = 0, r_hi = kk;
+  if (!allv) {
+    if (route == 0) { r_lo = kk - 0; for (int i = 0; i < kk; ++i) if (lam[i] > 0.0) { r_lo = i; break; } }
+    else { r_hi = 0; for (int i = kk - 1; i >= 0; --i) if (lam[i] < 0.0) { r_hi = i + 1; break; } }
+  }
+  const int kr = r_hi - r_lo;
+  // roots -> Z columns 0..kr-1; kept deflated -> Z columns kr..
+  int* imap = c.imap + s;
+  for (int i = tid; i < kk; i += kDcThreads) {
+    const bool keep = i >= r_lo && i < r_hi;
+    imap[i] = keep ? (i - r_lo) : -1;
+    if (keep) c.lamk[i - r_lo] = lam[i];
+  }
+  __shared__ int sh_kd;
+  if (tid == 0) {
+    int kd = 0;
+    for (int r = 0; r < ndf; ++r) {
+      const double v = dfs[r];
+      const bool keep = allv || (route == 0 ? v > 0.0 : v < 0.0);
+      if (keep) {
+        imap[kk + dord[r]] = kr + kd;
+        c.lamk[kr + kd] = v;
+        ++kd;
+      } else {
+        imap[kk + dord[r]] = -1;
+      }
+    }
+    sh_kd = kd;
+    c.kinfo[0] = kr + kd;
+    c.kinfo[1] = route;
+    c.kinfo[2] = kr;
+    c.kinfo[5] = r_lo;
+  }
+}
+
+// ---------------------------------------------------------------- vectors
+__global__ void dc_vectors_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes,
+                                  const int* __restrict__ pos_node, int64_t total) {
+  const int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gp >= total) return;
+  MergeNode nd;
+  int ni;
+  if (!node_of(nodes, pos_node + total, gp, nd, ni)) return;
+  const ConeDev& c = cones[nd.cone];
+  if (*c.status != 0) return;
+  const int i = pos_node[gp];
+  const int s = nd.s;
+  const int kk = c.icnt[4 * s];
+  if (i >= kk) return;
+  int row = i;
+  if (nd.root) {
+    row = c.imap[s + i];
+    if (row < 0) return;
+  }
+  const int64_t n = c.n;
+  const double* dk = c.dsrt + s;
+  const double* zh = c.zhat + s;
+  const double dorg = dk[c.iorg[s + i]];
+  const double tau = c.tau[s + i];
+  double* U = c.Ucm + s + row + (int64_t)s * n;  // U[j * n] = component j
+  double nrm = 0.0;
+  for (int j = 0; j < kk; ++j) {
+    const double u = zh[j] / ((dk[j] - dorg) - tau);
+    U[(int64_t)j * n] = u;
+    nrm = fma(u, u, nrm);
+  }
+  const double inv = 1.0 / sqrt(nrm);
+  for (int j = 0; j < kk; ++j) U[(int64_t)j * n] *= inv;
+}
+
+// deflated columns: Qin(:, kk + q) -> output column
+__global__ void dc_copy_deflated_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes) {
+  const MergeNode nd = nodes[blockIdx.x];
+  if (nd.n2 == 0) return;
+  const ConeDev& c = cones[nd.cone];
+  if (*c.status != 0) return;
+  const int s = nd.s, K = nd.n1 + nd.n2;
+  const int kk = c.icnt[4 * s], ndf = c.icnt[4 * s + 1];
+  const int64_t n = c.n;
+  double* out = nd.root ? c.Z : qout_buf(c, nd.level);
+  const int64_t roff = nd.root ? 0 : s;  // root output Z rows start at 0 (n = K there)
+  for (int q = 0; q < ndf; ++q) {
+    const int col = c.imap[s + kk + q];
+    if (col < 0) continue;
+    const double* src = c.Qin + s + (int64_t)(s + kk + q) * n;
+    double* dst = out + roff + (int64_t)col * n;
+    for (int r = threadIdx.x; r < K; r += blockDim.x) dst[r] = src[r];
+  }
+}
+
+}  // namespace
+
+void launch_dc_leaves(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s) {
+  if (ncones <= 0) return;
+  int gx = (int)((maxn + 255) / 256);
+  if (gx > 64) gx = 64;
+  dc_leaves_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones);
+}
+
+void launch_dc_prepare(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s) {
+  if (nnodes <= 0) return;
+  const size_t smem = (size_t)maxK * (2 * sizeof(double) + 2 * sizeof(int));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(dc_prepare_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(dc_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr = true;
+  }
+  dc_prepare_kernel<<<nnodes, kDcThreads, smem, s>>>(cones, nodes);
+}
+
+void launch_dc_secular(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total,
+                       cudaStream_t s) {
+  if (total <= 0) return;
+  dc_secular_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(cones, nodes, pos_node, total);
+}
+
+void launch_dc_loewner(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total,
+                       cudaStream_t s) {
+  if (total <= 0) return;
+  dc_loewner_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(cones, nodes, pos_node, total);
+}
+
+void launch_dc_select(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s) {
+  if (nnodes <= 0) return;
+  const size_t smem = (size_t)maxK * (2 * sizeof(double) + sizeof(int));
+  dc_select_kernel<<<nnodes, kDcThreads, smem, s>>>(cones, nodes);
+}
+
+void launch_dc_vectors(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total,
+                       cudaStream_t s) {
+  if (total <= 0) return;
+  dc_vectors_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(cones, nodes, pos_node, total);
+}
+
+void launch_dc_copy_deflated(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s) {
+  (void)maxK;
+  if (nnodes <= 0) return;
+  dc_copy_deflated_kernel<<<nnodes, 256, 0, s>>>(cones, nodes);
+}
+
+}  // namespace scs

@@ -1,0 +1,145 @@
+// Internal declarations of the scs_psd CUDA library (not part of the ABI).
+//
+// Pipeline for one cone of side n >= 2 (every step is a kernel here):
+//   svec unpack            -> dense symmetric A (column-major, ld = n)
+//   dense -> band          blocked Householder, panels of width b factored by
+//                          a thread-block cluster, trailing two-sided update by
+//                          grouped GEMMs (sy2sb form W = X - 1/2 V T^T V^T X)
+//   band -> tridiagonal    pipelined bulge chasing, one sweep per CTA at a time
+//   tridiagonal eigensolve divide and conquer (Cuppen tearing, deflation,
+//                          secular equation, Loewner/Gu-Eisenstat vectors)
+//   back-transformation    stage-2 reflectors, then stage-1 WY blocks
+//   clipped reconstruction lower triangle of V_k diag(l_k) V_k^T written
+//                          straight into svec (positive part, or X minus the
+//                          negative part by the Moreau decomposition)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace scs {
+
+// Per-cone device status bits (OR-ed together).
+enum : int { ST_NONFINITE = 1, ST_NOCONV = 2, ST_TIMEOUT = 4, ST_BADARG = 8 };
+
+constexpr int kMaxBand = 32;  // largest supported bandwidth b
+
+// ------------------------------------------------------------------ GEMM
+// C = alpha * op(A) op(B) + beta * C on column-major FP64 operands.
+enum : int {
+  GF_TRANS_A = 1,   // op(A) = A^T
+  GF_TRANS_B = 2,   // op(B) = B^T
+  GF_SYM_A = 4,     // A is square symmetric, only its lower triangle is read
+  GF_LOWER_C = 8,   // only the lower triangle (i >= j) of C is computed
+  GF_SCALE_B = 16,  // op(B)(k, j) is multiplied by bscale[k]
+};
+
+struct GemmDesc {
+  const double* A;
+  const double* B;
+  double* C;
+  const double* bscale;  // GF_SCALE_B
+  const int* dynN;       // if set: N = min(N, *dynN)
+  const int* dynK;       // if set: K = min(K, *dynK)
+  const int* colmap;     // if set: column j of the result goes to column colmap[j] of C
+  const int* skip;       // if set and *skip != 0 the problem is skipped (cone status)
+  int M, N, K;
+  int lda, ldb, ldc;
+  double alpha, beta;
+  int flags;
+  int tiles_n;           // tiles along N for the static N
+};
+
+constexpr int kGemmBM = 64, kGemmBN = 64, kGemmBK = 16;
+
+// Launch one grouped GEMM over `count` problems whose descriptors are in
+// device memory (`descs`); tile_prefix[p] = first tile of problem p,
+// tile_prefix[count] = total tiles.
+void launch_gemm(const GemmDesc* descs, const int* tile_prefix, int count, int total_tiles,
+                 cudaStream_t s);
+
+// ------------------------------------------------------------------ cones
+// Device view of one cone of the "large" path (n >= 2).
+struct ConeDev {
+  int64_t n;
+  int64_t xoff;     // offset of the cone in the svec buffers
+  int b;            // bandwidth of stage 1 / 2
+  int npanels;
+  int nsweeps;      // number of bulge-chasing sweeps (n - 2, at least 0)
+  int kmax;         // reflector slots per sweep
+  double* A;        // n*n dense matrix (column-major)
+  double* band;     // n * (2b) lower band with room for the bulge fill
+  double* refl;     // nsweeps * kmax * (b + 1): tau, v[1..b-1] (v[0] = 1)
+  int* prog;        // nsweeps progress counters of the bulge chasing
+  double* d;        // n diagonal of the tridiagonal matrix
+  double* e;        // n off-diagonal (e[i] couples i and i+1)
+  double* V1;       // stage-1 reflectors: npanels blocks of n*b (rows m_p)
+  double* T1;       // npanels blocks of b*b
+  double* Y;        // n*b   A22 V
+  double* X;        // n*b   Y T
+  double* U3;       // n*3b  [V | W | V] for the rank-2b update
+  double* Mb;       // b*b
+  double* Nb;       // b*b
+  double* QA;       // n*n   D&C eigenvector blocks (ping)
+  double* QB;       // n*n   (pong)
+  double* lamA;     // n
+  double* lamB;     // n
+  double* Qin;      // n*n   permuted/deflated eigenvector block of a merge
+  double* Ucm;      // n*n   secular eigenvectors, row i = eigenvector i
+  double* Z;        // n*n   kept eigenvectors (columns), then back-transformed
+  double* lamk;     // n     kept eigenvalues
+  double* dsrt;     // n     sorted, deflated poles of each merge node
+  double* zk;       // n     normalised rank-one vector on the kept poles
+  double* dval;     // n     deflated eigenvalues
+  double* tau;      // n     secular root offsets
+  double* zhat;     // n     Loewner-corrected z
+  double* rot;      // 2n    Givens rotations (c, s) of the deflation
+  double* rho;      // n     rank-one weight per merge node (indexed by start)
+  int* iperm;       // n     sorted position -> column of the child blocks
+  int* irot;        // 2n    rotation column pairs
+  int* iorg;        // n     origin pole of each secular root
+  int* imap;        // n     output column of each kept eigenvector of a merge
+  int* icnt;        // 4n    per merge node: kept, deflated, rotations, kept-of-root (indexed by start)
+  int* kinfo;       // [0] k kept, [1] route (0: positive part, 1: X - negative part), [2] kept secular
+                    // roots, [3] keep all eigenpairs (derivative), [4] side option, [5] first kept root
+  int* status;      // per-cone status bits
+};
+
+// One merge node of the divide and conquer tree.
+struct MergeNode {
+  int cone;
+  int s;       // first row of the merged block
+  int n1, n2;  // child sizes (n2 may be 0: plain copy)
+  int root;    // 1 if this merge produces the cone's final decomposition
+  int level;   // tree level (selects the ping-pong buffers)
+};
+
+// ------------------------------------------------------------------ kernels
+void launch_unpack(const ConeDev* cones, int ncones, int64_t maxn2, const double* x, cudaStream_t s);
+void launch_trivial(const int64_t* offs, const int* sides, int count, const double* x, double* y,
+                    int* status, cudaStream_t s);
+void launch_panel(const ConeDev* cones, const int* cone_ids, int njobs, int panel, int b,
+                  int cluster, int rows_per_cta, cudaStream_t s);
+void launch_band_extract(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s);
+int launch_bulge(const ConeDev* cones, int ncones, const int* cta_cone, const int* cta_rank,
+                 const int* cta_count, int nctas, int b, long long wait_limit, cudaStream_t s);
+int bulge_max_ctas(int b);
+void launch_tridiag_extract(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s);
+void launch_dc_leaves(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s);
+void launch_dc_prepare(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s);
+void launch_dc_secular(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total_pos,
+                       cudaStream_t s);
+void launch_dc_loewner(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total_pos,
+                       cudaStream_t s);
+void launch_dc_select(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s);
+void launch_dc_vectors(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total_pos,
+                       cudaStream_t s);
+void launch_dc_copy_deflated(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s);
+void launch_backtr2(const ConeDev* cones, int ncones, int maxn, int maxk, cudaStream_t s);
+int backtr2_cols(int n);
+size_t panel_smem_bytes(int b, int R);
+void launch_loewner_scale(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s);
+void launch_pack_lower(const ConeDev* cones, int ncones, int64_t maxn, double* xbar, cudaStream_t s);
+void launch_recon(const ConeDev* cones, int ncones, int maxn, const double* x, double* y, cudaStream_t s);
+void launch_status_reduce(const int* status, int count, int* out, cudaStream_t s);
+
+}  // namespace scs

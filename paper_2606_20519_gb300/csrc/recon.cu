@@ -1,0 +1,109 @@
+// Clipped reconstruction straight into svec.
+//
+// With Z the k kept eigenvectors and l their eigenvalues (all positive, or
+// all negative when the cone's final merge chose the Moreau side), the
+// kernel forms the lower triangle of S = Z diag(l) Z^T tile by tile (SYRK:
+// only tiles on or below the diagonal) and writes, for i >= j,
+//     y[svec(i, j)] = s_ij * S(i, j)              (positive part), or
+//     y[svec(i, j)] = x[svec(i, j)] - s_ij * S(i, j)   (X - negative part),
+// with s_ij = 1 on the diagonal and sqrt(2) off it (the vec_R map, App. D.1).
+// Each svec entry is read and written by one thread, so y may alias x.
+// A cone whose status is not clean is filled with NaN.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace scs {
+
+namespace {
+
+constexpr int BM = 64, BK = 16;
+
+__global__ void __launch_bounds__(256) recon_kernel(const ConeDev* __restrict__ cones, const double* x, double* y) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BM + 1];
+  const ConeDev& c = cones[blockIdx.y];
+  const int n = (int)c.n;
+  const int tiles = (n + BM - 1) / BM;
+  const int t = blockIdx.x;
+  if (t >= tiles * (tiles + 1) / 2) return;
+  int tm = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((tm + 1) * (tm + 2) / 2 <= t) ++tm;
+  while (tm * (tm + 1) / 2 > t) --tm;
+  const int tn = t - tm * (tm + 1) / 2;
+  const int i0 = tm * BM, j0 = tn * BM;
+  const bool bad = *c.status != 0;
+  const int kk = bad ? 0 : c.kinfo[0];
+  const int route = c.kinfo[1];
+  const double* Z = c.Z;
+  const double* lam = c.lamk;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[r][q] = 0.0;
+  for (int k0 = 0; k0 < kk; k0 += BK) {
+#pragma unroll
+    for (int q = 0; q < (BM * BK) / 256; ++q) {
+      const int e = tid + q * 256;
+      const int ii = e % BM, l = e / BM;
+      const int i = i0 + ii, j = j0 + ii, k = k0 + l;
+      double a = 0.0, bv = 0.0;
+      if (k < kk) {
+        if (i < n) a = Z[(int64_t)i + (int64_t)k * n];
+        if (j < n) {
+          // all eigenpairs are present when the derivative is needed: clip by side
+          const double lk = route == 0 ? fmax(lam[k], 0.0) : fmin(lam[k], 0.0);
+          bv = Z[(int64_t)j + (int64_t)k * n] * lk;
+        }
+      }
+      As[l][ii] = a;
+      Bs[l][ii] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < BK; ++l) {
+      double a[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[l][tx + 16 * r];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bv[q] = Bs[l][ty + 16 * q];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], bv[q], acc[r][q]);
+    }
+    __syncthreads();
+  }
+  const double* xs = x + c.xoff;
+  double* ys = y + c.xoff;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = j0 + ty + 16 * q;
+    if (j >= n) continue;
+    const int64_t colo = (int64_t)j * n - ((int64_t)j * (j - 1)) / 2;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = i0 + tx + 16 * r;
+      if (i >= n || i < j) continue;
+      const int64_t idx = colo + (i - j);
+      const double sc = (i == j) ? 1.0 : M_SQRT2;
+      double v;
+      if (bad) v = nan("");
+      else if (route == 0) v = sc * acc[r][q];
+      else v = fma(-sc, acc[r][q], xs[idx]);
+      ys[idx] = v;
+    }
+  }
+}
+
+}  // namespace
+
+void launch_recon(const ConeDev* cones, int ncones, int maxn, const double* x, double* y, cudaStream_t s) {
+  if (ncones <= 0) return;
+  const int tiles = (maxn + BM - 1) / BM;
+  recon_kernel<<<dim3(tiles * (tiles + 1) / 2, ncones), 256, 0, s>>>(cones, x, y);
+}
+
+}  // namespace scs

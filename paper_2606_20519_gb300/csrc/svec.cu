@@ -1,0 +1,118 @@
+// svec <-> dense maps and small data-movement kernels.
+//
+// svec is the real symmetric case of the vec_R map of App. D.1: the lower
+// triangle column by column, diagonal entries as they are, off-diagonal
+// entries times sqrt(2).  Column j starts at offset j*n - j*(j-1)/2.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace scs {
+
+namespace {
+
+__device__ __forceinline__ int64_t svec_col_offset(int64_t n, int64_t j) { return j * n - (j * (j - 1)) / 2; }
+
+// Dense symmetric A (column-major, both triangles) from the svec input.
+__global__ void unpack_kernel(const ConeDev* __restrict__ cones, const double* __restrict__ x) {
+  const ConeDev& c = cones[blockIdx.y];
+  const int64_t n = c.n;
+  const int64_t nn = n * n;
+  const double* xs = x + c.xoff;
+  bool bad = false;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n, j = e / n;
+    const int64_t lo = i >= j ? i : j, hi = i >= j ? j : i;  // (row, col) in the lower triangle
+    double v = xs[svec_col_offset(n, hi) + (lo - hi)];
+    if (lo != hi) v *= M_SQRT1_2;
+    if (!isfinite(v)) bad = true;
+    c.A[e] = v;
+  }
+  if (bad) atomicOr(c.status, ST_NONFINITE);
+}
+
+// Cones of side 0 or 1: Pi(x) = max(x, 0).
+__global__ void trivial_kernel(const int64_t* __restrict__ offs, const int* __restrict__ sides, int count,
+                               const double* __restrict__ x, double* __restrict__ y, int* status) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  if (sides[t] != 1) return;
+  const double v = x[offs[t]];
+  if (!isfinite(v)) {
+    y[offs[t]] = nan("");
+    atomicOr(status, ST_NONFINITE);
+  } else {
+    y[offs[t]] = v > 0.0 ? v : 0.0;
+  }
+}
+
+// Lower band (bandwidth b) of A into band storage with 2b diagonals; the
+// extra diagonals hold the bulge fill and start at zero.
+__global__ void band_extract_kernel(const ConeDev* __restrict__ cones) {
+  const ConeDev& c = cones[blockIdx.y];
+  const int64_t n = c.n;
+  const int ldb = 2 * c.b;
+  const int64_t total = n * ldb;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t col = e / ldb;
+    const int d = (int)(e % ldb);
+    double v = 0.0;
+    if (d <= c.b && col + d < n) v = c.A[(col + d) + col * n];
+    c.band[e] = v;
+  }
+}
+
+__global__ void tridiag_extract_kernel(const ConeDev* __restrict__ cones) {
+  const ConeDev& c = cones[blockIdx.y];
+  const int64_t n = c.n;
+  const int ldb = 2 * c.b;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    c.d[j] = c.band[j * ldb];
+    c.e[j] = (j + 1 < n) ? c.band[j * ldb + 1] : 0.0;
+  }
+}
+
+__global__ void status_reduce_kernel(const int* __restrict__ status, int count, int* out) {
+  int v = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) v |= status[i];
+  for (int o = 16; o > 0; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicOr(out, v);
+}
+
+}  // namespace
+
+void launch_unpack(const ConeDev* cones, int ncones, int64_t maxn2, const double* x, cudaStream_t s) {
+  if (ncones <= 0) return;
+  int gx = (int)((maxn2 + 255) / 256);
+  if (gx > 1024) gx = 1024;
+  unpack_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones, x);
+}
+
+void launch_trivial(const int64_t* offs, const int* sides, int count, const double* x, double* y, int* status,
+                    cudaStream_t s) {
+  if (count <= 0) return;
+  trivial_kernel<<<(count + 255) / 256, 256, 0, s>>>(offs, sides, count, x, y, status);
+}
+
+void launch_band_extract(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s) {
+  if (ncones <= 0) return;
+  int gx = (int)((maxn * 2 * kMaxBand + 255) / 256);
+  if (gx > 1024) gx = 1024;
+  band_extract_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones);
+}
+
+void launch_tridiag_extract(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s) {
+  if (ncones <= 0) return;
+  int gx = (int)((maxn + 255) / 256);
+  if (gx > 64) gx = 64;
+  tridiag_extract_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones);
+}
+
+void launch_status_reduce(const int* status, int count, int* out, cudaStream_t s) {
+  if (count <= 0) return;
+  int g = (count + 255) / 256;
+  if (g > 64) g = 64;
+  status_reduce_kernel<<<g, 256, 0, s>>>(status, count, out);
+}
+
+}  // namespace scs
