@@ -31,6 +31,8 @@ constexpr int64_t kMaxSide = 8192;
 
 struct GemmLaunch {
   int desc_off = 0, count = 0, prefix_off = 0, tiles = 0;
+  int variant = GEMM_SQUARE, needs_reduce = 0;
+  int64_t max_mn = 0;
 };
 
 struct PanelStep {
@@ -128,7 +130,8 @@ struct ConeLayout {
 
 enum Field {
   F_A, F_BAND, F_REFL, F_D, F_E, F_V1, F_T1, F_Y, F_X, F_U3, F_MB, F_NB, F_QA, F_QB, F_LAMA, F_LAMB, F_QIN, F_UCM, F_Z,
-  F_LAMK, F_DSRT, F_ZK, F_DVAL, F_TAU, F_ZHAT, F_ROT, F_RHO, F_IPERM, F_IROT, F_IORG, F_IMAP, F_ICNT, F_KINFO, F_NFIELDS
+  F_LAMK, F_DSRT, F_ZK, F_DVAL, F_TAU, F_ZHAT, F_ROT, F_RHO, F_UNRM, F_IPERM, F_IFP, F_IROT, F_IORG, F_IMAP, F_ICNT,
+  F_KINFO, F_NFIELDS
 };
 
 ConeLayout cone_layout(int64_t n, int b) {
@@ -140,8 +143,8 @@ ConeLayout cone_layout(int64_t n, int b) {
   const size_t sz[F_NFIELDS] = {
       d * n * n, d * n * 2 * b, d * nsw * kmax * (b + 1), d * n, d * n, d * P * n * b, d * P * b * b,
       d * n * b, d * n * b, d * n * 3 * b, d * b * b, d * b * b, d * n * n, d * n * n, d * n, d * n,
-      d * n * n, d * n * n, d * n * n, d * n, d * n, d * n, d * n, d * n, d * n, d * 2 * n, d * n,
-      i4 * n, i4 * 2 * n, i4 * n, i4 * n, i4 * 4 * n, i4 * 8};
+      d * n * n, d * n * n, d * n * n, d * n, d * n, d * n, d * n, d * n, d * n, d * 2 * n, d * n, d * n,
+      i4 * n, i4 * n, i4 * 2 * n, i4 * n, i4 * n, i4 * 4 * n, i4 * 8};
   size_t o = 0;
   for (int f = 0; f < F_NFIELDS; ++f) {
     o = align_up(o);
@@ -161,22 +164,46 @@ ConeLayout cone_layout(int64_t n, int b) {
 struct MetaBuilder {
   std::vector<int> ints;
   std::vector<GemmDesc> descs;
-  std::vector<int> prefix;  // stored inside ints
+  std::vector<int64_t> part_off;  // per descriptor: offset in the split-K scratch (doubles)
   std::vector<MergeNode> nodes;
+  int sms = 148;
+  int64_t scratch_doubles = 0;
 
-  GemmLaunch add_gemm(const std::vector<GemmDesc>& probs) {
+  // Picks the tile shape for the launch and a split-K factor per problem so
+  // that the launch has about two CTAs per SM.
+  GemmLaunch add_gemm(std::vector<GemmDesc> probs) {
     GemmLaunch g;
     g.desc_off = (int)descs.size();
     g.count = (int)probs.size();
     g.prefix_off = (int)ints.size();
-    int t = 0;
+    int maxM = 0, maxN = 0;
+    for (const GemmDesc& p : probs) { maxM = std::max(maxM, p.M); maxN = std::max(maxN, p.N); }
+    g.variant = (maxN <= 16 && maxM > 16) ? GEMM_TALL : (maxM <= 16 && maxN > 16) ? GEMM_SHORT : GEMM_SQUARE;
+    int bm, bn;
+    gemm_tile_shape(g.variant, &bm, &bn);
+    int64_t base = 0;
     for (const GemmDesc& p : probs) {
+      int64_t tiles = (int64_t)((p.M + bm - 1) / bm) * ((p.N + bn - 1) / bn);
+      if (p.flags & GF_LOWER_C) tiles = (tiles + (p.M + bm - 1) / bm) / 2 + 1;
+      base += tiles;
+    }
+    int S = 1;
+    if (base > 0 && base < 2 * sms) S = (int)std::min<int64_t>(64, (2 * sms + base - 1) / base);
+    int t = 0;
+    int64_t off = 0;
+    for (GemmDesc& p : probs) {
+      const int Sp = std::max(1, std::min(S, p.K / 64));
+      p.splitk = Sp;
       ints.push_back(t);
-      const int tm = (p.M + kGemmBM - 1) / kGemmBM, tn = (p.N + kGemmBN - 1) / kGemmBN;
-      t += std::max(0, tm * tn);
+      const int tm = (p.M + bm - 1) / bm, tn = (p.N + bn - 1) / bn;
+      t += std::max(0, tm * tn) * Sp;
+      part_off.push_back(Sp > 1 ? off : -1);
+      if (Sp > 1) { off += (int64_t)Sp * p.M * p.N; g.needs_reduce = 1; }
+      g.max_mn = std::max<int64_t>(g.max_mn, (int64_t)p.M * p.N);
       descs.push_back(p);
     }
     ints.push_back(t);
+    scratch_doubles = std::max(scratch_doubles, off);
     g.tiles = t;
     return g;
   }
@@ -191,6 +218,7 @@ GemmDesc mk(const double* A, int lda, const double* B, int ldb, double* C, int l
   g.alpha = alpha; g.beta = beta;
   g.flags = flags;
   g.skip = skip;
+  g.splitk = 1;
   return g;
 }
 
@@ -230,6 +258,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
 
   // ---- metadata sizes known up front: status (ncones+1), prog
   MetaBuilder mb;
+  mb.sms = h->sms > 0 ? h->sms : 148;
   std::vector<ConeDev> cones(P.ncones);
   size_t prog_total = 0;
   std::vector<size_t> prog_off(P.ncones);
@@ -262,6 +291,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
     d.lamB = FLD(double, F_LAMB); d.Qin = FLD(double, F_QIN); d.Ucm = FLD(double, F_UCM); d.Z = FLD(double, F_Z);
     d.lamk = FLD(double, F_LAMK); d.dsrt = FLD(double, F_DSRT); d.zk = FLD(double, F_ZK); d.dval = FLD(double, F_DVAL);
     d.tau = FLD(double, F_TAU); d.zhat = FLD(double, F_ZHAT); d.rot = FLD(double, F_ROT); d.rho = FLD(double, F_RHO);
+    d.unrm = FLD(double, F_UNRM); d.ifp = FLD(int, F_IFP);
     d.iperm = FLD(int, F_IPERM); d.irot = FLD(int, F_IROT); d.iorg = FLD(int, F_IORG); d.imap = FLD(int, F_IMAP);
     d.icnt = FLD(int, F_ICNT); d.kinfo = FLD(int, F_KINFO);
 #undef FLD
@@ -457,7 +487,8 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   const size_t descs_b = align_up(sizeof(GemmDesc) * std::max<size_t>(1, mb.descs.size()));
   const size_t nodes_b = align_up(sizeof(MergeNode) * std::max<size_t>(1, mb.nodes.size()));
   const size_t triv_b = align_up((sizeof(int64_t) + sizeof(int)) * std::max(1, P.ntriv));
-  const size_t total = cones_b + ints_b + descs_b + nodes_b + triv_b;
+  const size_t scratch_b = align_up(sizeof(double) * std::max<int64_t>(1, mb.scratch_doubles));
+  const size_t total = cones_b + ints_b + descs_b + nodes_b + triv_b + scratch_b;
   if (cudaMalloc(&P.meta_mem, total) != cudaSuccess) return SCS_PSD_ENOMEM;
   char* mbase = (char*)P.meta_mem;
   P.cones_d = (ConeDev*)mbase;
@@ -466,6 +497,9 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   P.nodes_d = (MergeNode*)(mbase + cones_b + ints_b + descs_b);
   P.triv_offs_d = (int64_t*)(mbase + cones_b + ints_b + descs_b + nodes_b);
   P.triv_sides_d = (int*)(P.triv_offs_d + std::max(1, P.ntriv));
+  double* scratch = (double*)(mbase + cones_b + ints_b + descs_b + nodes_b + triv_b);
+  for (size_t q = 0; q < mb.descs.size(); ++q)
+    mb.descs[q].partial = mb.part_off[q] >= 0 ? scratch + mb.part_off[q] : nullptr;
   P.status_d = P.ints_d + status_off;
   P.prog_d = P.ints_d + prog_base;
   P.prog_count = prog_total;
@@ -508,7 +542,9 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
 
 int run_gemm(const Plan& P, const GemmLaunch& g, cudaStream_t s, int64_t& n_launch) {
   if (g.count <= 0 || g.tiles <= 0) return SCS_PSD_OK;
-  launch_gemm(P.descs_d + g.desc_off, P.ints_d + g.prefix_off, g.count, g.tiles, s);
+  launch_gemm(P.descs_d + g.desc_off, P.ints_d + g.prefix_off, g.count, g.tiles, g.variant, g.needs_reduce,
+              g.max_mn, s);
+  if (g.needs_reduce) ++n_launch;
   LAUNCH_CHECK();
   return SCS_PSD_OK;
 }
@@ -551,13 +587,19 @@ int run_plan(scs_psd_handle h, Plan& P, const double* x, double* y, const double
       const int* pos = P.ints_d + lv.pos_off;
       launch_dc_prepare(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
       LAUNCH_CHECK();
+      launch_dc_build_qin(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
+      LAUNCH_CHECK();
+      launch_dc_apply_rot(P.cones_d, nodes, pos, P.total_pos, s);
+      LAUNCH_CHECK();
       launch_dc_secular(P.cones_d, nodes, pos, P.total_pos, s);
       LAUNCH_CHECK();
       launch_dc_loewner(P.cones_d, nodes, pos, P.total_pos, s);
       LAUNCH_CHECK();
       launch_dc_select(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
       LAUNCH_CHECK();
-      launch_dc_vectors(P.cones_d, nodes, pos, P.total_pos, s);
+      launch_dc_vecnorm(P.cones_d, nodes, pos, P.total_pos, s);
+      LAUNCH_CHECK();
+      launch_dc_vectors(P.cones_d, nodes, pos, P.total_pos, lv.maxK, s);
       LAUNCH_CHECK();
       if ((rc = run_gemm(P, lv.g, s, n_launch))) return rc;
       launch_dc_copy_deflated(P.cones_d, nodes, lv.nnodes, lv.maxK, s);

@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kDcThreads) dc_prepare_kernel(const ConeDev* _
     sh_nrot = nrot;
   }
   __syncthreads();
-  const int kk = sh_kk, nrot = sh_nrot;
+  const int kk = sh_kk;
   for (int j = tid; j < K; j += kDcThreads) {
     const int f = fp[j];
     if (f < kk) {
@@ -211,51 +211,97 @@ __global__ void __launch_bounds__(kDcThreads) dc_prepare_kernel(const ConeDev* _
     } else {
       c.dval[s + f - kk] = dv[j];
     }
+    c.iperm[s + j] = perm[j];
+    c.ifp[s + j] = f;
   }
   if (tid == 0) {
     c.rho[s] = sh_rho;
     cnt[0] = kk;
     cnt[1] = K - kk;
-    cnt[2] = nrot;
+    cnt[2] = sh_nrot;
   }
-  // ---- permuted eigenvector block Qin(:, fp[j]) = Q(:, perm[j]) (block diagonal source)
+}
+
+// Permuted eigenvector block Qin(:, fp[j]) = Q(:, perm[j]) of each merge node;
+// the source is block diagonal (child 1 rows x child 1 columns, child 2 rows x
+// child 2 columns).  blockIdx.x = node, blockIdx.y = chunk of 32 columns.
+__global__ void dc_build_qin_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes) {
+  const MergeNode nd = nodes[blockIdx.x];
+  if (nd.n2 == 0) return;
+  const ConeDev& c = cones[nd.cone];
+  if (*c.status != 0) return;
+  const int64_t n = c.n;
+  const int s = nd.s, n1 = nd.n1, K = nd.n1 + nd.n2;
+  const int j0 = blockIdx.y * 32;
+  if (j0 >= K) return;
+  const double* Qi = qin_buf(c, nd.level);
   double* Qb = c.Qin;
-  for (int64_t e = tid; e < (int64_t)K * K; e += kDcThreads) {
-    const int r = (int)(e % K), j = (int)(e / K);
-    const int src = perm[j];
-    const bool same = (src < n1) == (r < n1);
-    const double v = same ? Qi[(s + r) + (int64_t)(s + src) * n] : 0.0;
-    Qb[(s + r) + (int64_t)(s + fp[j]) * n] = v;
-  }
-  __syncthreads();
-  if (nrot > 0) {
-    // Givens rotations of the deflation, in order; each thread owns rows
-    for (int r = tid; r < K; r += kDcThreads) {
-      for (int q = 0; q < nrot; ++q) {
-        const int a = irot[2 * q], bcol = irot[2 * q + 1];
-        const double cc = rot[2 * q], sn = rot[2 * q + 1];
-        double* pa = Qb + (s + r) + (int64_t)(s + a) * n;
-        double* pb = Qb + (s + r) + (int64_t)(s + bcol) * n;
-        const double x = *pa, y = *pb;
-        *pa = cc * x - sn * y;
-        *pb = sn * x + cc * y;
-      }
+  const int jend = min(K, j0 + 32);
+  for (int j = j0; j < jend; ++j) {
+    const int src = c.iperm[s + j];
+    const int dst = c.ifp[s + j];
+    const bool first = src < n1;
+    for (int r = threadIdx.x; r < K; r += blockDim.x) {
+      const bool same = first == (r < n1);
+      Qb[(s + r) + (int64_t)(s + dst) * n] = same ? Qi[(s + r) + (int64_t)(s + src) * n] : 0.0;
     }
   }
 }
 
+// Givens rotations of the deflation, in order; one thread per row.
+__global__ void dc_apply_rot_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes,
+                                    const int* __restrict__ pos_node, int64_t total) {
+  const int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gp >= total) return;
+  const int ni = pos_node[total + gp];
+  if (ni < 0) return;
+  const MergeNode nd = nodes[ni];
+  if (nd.n2 == 0) return;
+  const ConeDev& c = cones[nd.cone];
+  if (*c.status != 0) return;
+  const int s = nd.s;
+  const int nrot = c.icnt[4 * s + 2];
+  if (nrot == 0) return;
+  const int r = pos_node[gp];
+  const int64_t n = c.n;
+  const double* rot = c.rot + 2 * s;
+  const int* irot = c.irot + 2 * s;
+  double* row = c.Qin + (s + r) + (int64_t)s * n;
+  for (int q = 0; q < nrot; ++q) {
+    const int a = irot[2 * q], bcol = irot[2 * q + 1];
+    const double cc = rot[2 * q], sn = rot[2 * q + 1];
+    double* pa = row + (int64_t)a * n;
+    double* pb = row + (int64_t)bcol * n;
+    const double x = *pa, y = *pb;
+    *pa = cc * x - sn * y;
+    *pb = sn * x + cc * y;
+  }
+}
+
 // ---------------------------------------------------------------- secular
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_prod_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v *= __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Root i of f(x) = 1 + rho sum_j z_j^2 / (d_j - x), d strictly increasing,
-// ||z|| = 1.  Returns the origin pole and the offset tau = x - d_org.
-__device__ bool secular_root(const double* __restrict__ dk, const double* __restrict__ zk, int K, double rho,
-                             int i, int* org_out, double* tau_out) {
+// ||z|| = 1, solved by one warp (the sums are split over the lanes; every
+// lane ends with the same values).  Returns the origin pole and the offset
+// tau = x - d_org; false if the iteration cap was reached.
+__device__ bool secular_root_warp(const double* __restrict__ dk, const double* __restrict__ zk, int K, double rho,
+                                  int i, int lane, int* org_out, double* tau_out) {
   int org;
   double lo, hi;
   if (i < K - 1) {
     const double di = dk[i];
     const double mid = 0.5 * (dk[i + 1] - di);
-    double f = 1.0;
-    for (int j = 0; j < K; ++j) f += rho * zk[j] * zk[j] / ((dk[j] - di) - mid);
+    double f = 0.0;
+    for (int j = lane; j < K; j += 32) f += zk[j] * zk[j] / ((dk[j] - di) - mid);
+    f = 1.0 + rho * warp_sum_d(f);
     if (f >= 0.0) { org = i; lo = 0.0; hi = mid; }
     else { org = i + 1; lo = -mid; hi = 0.0; }
   } else {
@@ -269,7 +315,7 @@ __device__ bool secular_root(const double* __restrict__ dk, const double* __rest
   bool conv = false;
   for (int it = 0; it < 100; ++it) {
     double psi = 0.0, phi = 0.0, dpsi = 0.0, dphi = 0.0, aerr = 0.0;
-    for (int j = 0; j < K; ++j) {
+    for (int j = lane; j < K; j += 32) {
       const double del = (dk[j] - dorg) - tau;
       const double zz = zk[j];
       const double t = zz / del;
@@ -278,7 +324,11 @@ __device__ bool secular_root(const double* __restrict__ dk, const double* __rest
       else { phi += term; dphi = fma(t, t, dphi); }
       aerr += fabs(term);
     }
-    psi *= rho; phi *= rho; dpsi *= rho; dphi *= rho;
+    psi = rho * warp_sum_d(psi);
+    phi = rho * warp_sum_d(phi);
+    dpsi = rho * warp_sum_d(dpsi);
+    dphi = rho * warp_sum_d(dphi);
+    aerr = warp_sum_d(aerr);
     const double g = 1.0 + psi + phi;
     if (fabs(g) <= 8.0 * kEps * K * (1.0 + rho * aerr)) { conv = true; break; }
     if (g > 0.0) hi = tau; else lo = tau;
@@ -287,7 +337,7 @@ __device__ bool secular_root(const double* __restrict__ dk, const double* __rest
     const double dl = p - tau;
     const double sl = dpsi * dl * dl;
     const double a = psi - sl / dl;
-    double x;
+    double x = 0.0;
     bool okx = false;
     if (ri < K) {
       const double q = dk[ri] - dorg;
@@ -329,33 +379,46 @@ __device__ bool secular_root(const double* __restrict__ dk, const double* __rest
   return conv;
 }
 
-__device__ __forceinline__ bool node_of(const MergeNode* nodes, const int* pos_node, int64_t gp, MergeNode& nd,
-                                        int& idx) {
-  const int ni = pos_node[gp];
-  if (ni < 0) return false;
-  nd = nodes[ni];
-  idx = ni;
-  return nd.n2 > 0;
+// Warp-per-position kernels: warp w handles position w of the level's
+// position map (a root index or a pole index within its node).
+struct WarpPos {
+  MergeNode nd;
+  int idx;
+  bool ok;
+};
+
+__device__ __forceinline__ WarpPos warp_pos(const MergeNode* nodes, const int* pos_node, int64_t total) {
+  WarpPos w;
+  w.ok = false;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= total) return w;
+  const int ni = pos_node[total + gw];
+  if (ni < 0) return w;
+  w.nd = nodes[ni];
+  if (w.nd.n2 == 0) return w;
+  w.idx = pos_node[gw];
+  w.ok = true;
+  return w;
 }
 
 __global__ void dc_secular_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes,
                                   const int* __restrict__ pos_node, int64_t total) {
-  const int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gp >= total) return;
-  MergeNode nd;
-  int ni;
-  if (!node_of(nodes, pos_node + total, gp, nd, ni)) return;
-  const ConeDev& c = cones[nd.cone];
+  const WarpPos w = warp_pos(nodes, pos_node, total);
+  if (!w.ok) return;
+  const ConeDev& c = cones[w.nd.cone];
   if (*c.status != 0) return;
-  const int i = pos_node[gp];  // root index within the node
-  const int kk = c.icnt[4 * nd.s];
+  const int s = w.nd.s, i = w.idx;
+  const int kk = c.icnt[4 * s];
   if (i >= kk) return;
+  const int lane = threadIdx.x & 31;
   int org;
   double tau;
-  const bool ok = secular_root(c.dsrt + nd.s, c.zk + nd.s, kk, c.rho[nd.s], i, &org, &tau);
-  c.iorg[nd.s + i] = org;
-  c.tau[nd.s + i] = tau;
-  if (!ok) atomicOr(c.status, ST_NOCONV);
+  const bool ok = secular_root_warp(c.dsrt + s, c.zk + s, kk, c.rho[s], i, lane, &org, &tau);
+  if (lane == 0) {
+    c.iorg[s + i] = org;
+    c.tau[s + i] = tau;
+    if (!ok) atomicOr(c.status, ST_NOCONV);
+  }
 }
 
 // lambda_i - d_j, accurate: (d_org(i) - d_j) + tau_i
@@ -363,26 +426,29 @@ __device__ __forceinline__ double lam_minus_d(const double* dk, const int* org, 
   return (dk[org[i]] - dk[j]) + tau[i];
 }
 
+// Loewner (Gu-Eisenstat) z: zhat_j^2 = prod_i (lambda_i - d_j) / (rho prod_{i != j} (d_i - d_j)),
+// evaluated as a product of ratios that are all in (0, 1].
 __global__ void dc_loewner_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes,
                                   const int* __restrict__ pos_node, int64_t total) {
-  const int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gp >= total) return;
-  MergeNode nd;
-  int ni;
-  if (!node_of(nodes, pos_node + total, gp, nd, ni)) return;
-  const ConeDev& c = cones[nd.cone];
+  const WarpPos w = warp_pos(nodes, pos_node, total);
+  if (!w.ok) return;
+  const ConeDev& c = cones[w.nd.cone];
   if (*c.status != 0) return;
-  const int j = pos_node[gp];
-  const int kk = c.icnt[4 * nd.s];
+  const int s = w.nd.s, j = w.idx;
+  const int kk = c.icnt[4 * s];
   if (j >= kk) return;
-  const double* dk = c.dsrt + nd.s;
-  const int* org = c.iorg + nd.s;
-  const double* tau = c.tau + nd.s;
+  const int lane = threadIdx.x & 31;
+  const double* dk = c.dsrt + s;
+  const int* org = c.iorg + s;
+  const double* tau = c.tau + s;
   const double dj = dk[j];
-  double prod = lam_minus_d(dk, org, tau, kk - 1, j) / c.rho[nd.s];
-  for (int i = 0; i < j; ++i) prod *= lam_minus_d(dk, org, tau, i, j) / (dk[i] - dj);
-  for (int i = j + 1; i < kk; ++i) prod *= lam_minus_d(dk, org, tau, i - 1, j) / (dk[i] - dj);
-  c.zhat[nd.s + j] = copysign(sqrt(fabs(prod)), c.zk[nd.s + j]);
+  double prod = 1.0;
+  for (int i = lane; i < kk; i += 32) {
+    if (i < j) prod *= lam_minus_d(dk, org, tau, i, j) / (dk[i] - dj);
+    else if (i > j) prod *= lam_minus_d(dk, org, tau, i - 1, j) / (dk[i] - dj);
+  }
+  prod = warp_prod_d(prod) * (lam_minus_d(dk, org, tau, kk - 1, j) / c.rho[s]);
+  if (lane == 0) c.zhat[s + j] = copysign(sqrt(fabs(prod)), c.zk[s + j]);
 }
 
 // ---------------------------------------------------------------- select
@@ -466,7 +532,6 @@ __global__ void __launch_bounds__(kDcThreads) dc_select_kernel(const ConeDev* __
     imap[i] = keep ? (i - r_lo) : -1;
     if (keep) c.lamk[i - r_lo] = lam[i];
   }
-  __shared__ int sh_kd;
   if (tid == 0) {
     int kd = 0;
     for (int r = 0; r < ndf; ++r) {
@@ -480,7 +545,6 @@ __global__ void __launch_bounds__(kDcThreads) dc_select_kernel(const ConeDev* __
         imap[kk + dord[r]] = -1;
       }
     }
-    sh_kd = kd;
     c.kinfo[0] = kr + kd;
     c.kinfo[1] = route;
     c.kinfo[2] = kr;
@@ -489,19 +553,49 @@ __global__ void __launch_bounds__(kDcThreads) dc_select_kernel(const ConeDev* __
 }
 
 // ---------------------------------------------------------------- vectors
+__global__ void dc_vecnorm_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes,
+                                  const int* __restrict__ pos_node, int64_t total) {
+  const WarpPos w = warp_pos(nodes, pos_node, total);
+  if (!w.ok) return;
+  const ConeDev& c = cones[w.nd.cone];
+  if (*c.status != 0) return;
+  const int s = w.nd.s, i = w.idx;
+  const int kk = c.icnt[4 * s];
+  if (i >= kk) return;
+  if (w.nd.root && c.imap[s + i] < 0) return;
+  const int lane = threadIdx.x & 31;
+  const double* dk = c.dsrt + s;
+  const double* zh = c.zhat + s;
+  const double dorg = dk[c.iorg[s + i]];
+  const double tau = c.tau[s + i];
+  double nrm = 0.0;
+  for (int j = lane; j < kk; j += 32) {
+    const double u = zh[j] / ((dk[j] - dorg) - tau);
+    nrm = fma(u, u, nrm);
+  }
+  nrm = warp_sum_d(nrm);
+  if (lane == 0) c.unrm[s + i] = 1.0 / sqrt(nrm);
+}
+
+// U(row, j) = zhat_j / (d_j - lambda_i) / ||.||; thread = root (consecutive
+// threads write consecutive rows), blockIdx.y = chunk of components j.
+constexpr int kVecChunk = 64;
 __global__ void dc_vectors_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes,
                                   const int* __restrict__ pos_node, int64_t total) {
   const int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gp >= total) return;
-  MergeNode nd;
-  int ni;
-  if (!node_of(nodes, pos_node + total, gp, nd, ni)) return;
+  const int ni = pos_node[total + gp];
+  if (ni < 0) return;
+  const MergeNode nd = nodes[ni];
+  if (nd.n2 == 0) return;
   const ConeDev& c = cones[nd.cone];
   if (*c.status != 0) return;
   const int i = pos_node[gp];
   const int s = nd.s;
   const int kk = c.icnt[4 * s];
   if (i >= kk) return;
+  const int j0 = blockIdx.y * kVecChunk;
+  if (j0 >= kk) return;
   int row = i;
   if (nd.root) {
     row = c.imap[s + i];
@@ -512,18 +606,14 @@ __global__ void dc_vectors_kernel(const ConeDev* __restrict__ cones, const Merge
   const double* zh = c.zhat + s;
   const double dorg = dk[c.iorg[s + i]];
   const double tau = c.tau[s + i];
+  const double inv = c.unrm[s + i];
   double* U = c.Ucm + s + row + (int64_t)s * n;  // U[j * n] = component j
-  double nrm = 0.0;
-  for (int j = 0; j < kk; ++j) {
-    const double u = zh[j] / ((dk[j] - dorg) - tau);
-    U[(int64_t)j * n] = u;
-    nrm = fma(u, u, nrm);
-  }
-  const double inv = 1.0 / sqrt(nrm);
-  for (int j = 0; j < kk; ++j) U[(int64_t)j * n] *= inv;
+  const int jend = min(kk, j0 + kVecChunk);
+  for (int j = j0; j < jend; ++j) U[(int64_t)j * n] = inv * (zh[j] / ((dk[j] - dorg) - tau));
 }
 
-// deflated columns: Qin(:, kk + q) -> output column
+// deflated columns: Qin(:, kk + q) -> output column; blockIdx.x = node,
+// blockIdx.y = chunk of 8 deflated columns.
 __global__ void dc_copy_deflated_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes) {
   const MergeNode nd = nodes[blockIdx.x];
   if (nd.n2 == 0) return;
@@ -531,10 +621,13 @@ __global__ void dc_copy_deflated_kernel(const ConeDev* __restrict__ cones, const
   if (*c.status != 0) return;
   const int s = nd.s, K = nd.n1 + nd.n2;
   const int kk = c.icnt[4 * s], ndf = c.icnt[4 * s + 1];
+  const int q0 = blockIdx.y * 8;
+  if (q0 >= ndf) return;
   const int64_t n = c.n;
   double* out = nd.root ? c.Z : qout_buf(c, nd.level);
-  const int64_t roff = nd.root ? 0 : s;  // root output Z rows start at 0 (n = K there)
-  for (int q = 0; q < ndf; ++q) {
+  const int64_t roff = nd.root ? 0 : s;
+  const int qend = min(ndf, q0 + 8);
+  for (int q = q0; q < qend; ++q) {
     const int col = c.imap[s + kk + q];
     if (col < 0) continue;
     const double* src = c.Qin + s + (int64_t)(s + kk + q) * n;
@@ -567,13 +660,30 @@ void launch_dc_prepare(const ConeDev* cones, const MergeNode* nodes, int nnodes,
 void launch_dc_secular(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total,
                        cudaStream_t s) {
   if (total <= 0) return;
-  dc_secular_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(cones, nodes, pos_node, total);
+  dc_secular_kernel<<<(unsigned)((total * 32 + 127) / 128), 128, 0, s>>>(cones, nodes, pos_node, total);
 }
 
 void launch_dc_loewner(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total,
                        cudaStream_t s) {
   if (total <= 0) return;
-  dc_loewner_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(cones, nodes, pos_node, total);
+  dc_loewner_kernel<<<(unsigned)((total * 32 + 127) / 128), 128, 0, s>>>(cones, nodes, pos_node, total);
+}
+
+void launch_dc_vecnorm(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total,
+                       cudaStream_t s) {
+  if (total <= 0) return;
+  dc_vecnorm_kernel<<<(unsigned)((total * 32 + 127) / 128), 128, 0, s>>>(cones, nodes, pos_node, total);
+}
+
+void launch_dc_build_qin(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s) {
+  if (nnodes <= 0) return;
+  dc_build_qin_kernel<<<dim3(nnodes, (maxK + 31) / 32), 256, 0, s>>>(cones, nodes);
+}
+
+void launch_dc_apply_rot(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total,
+                         cudaStream_t s) {
+  if (total <= 0) return;
+  dc_apply_rot_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(cones, nodes, pos_node, total);
 }
 
 void launch_dc_select(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s) {
@@ -582,16 +692,16 @@ void launch_dc_select(const ConeDev* cones, const MergeNode* nodes, int nnodes, 
   dc_select_kernel<<<nnodes, kDcThreads, smem, s>>>(cones, nodes);
 }
 
-void launch_dc_vectors(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total,
+void launch_dc_vectors(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total, int maxK,
                        cudaStream_t s) {
   if (total <= 0) return;
-  dc_vectors_kernel<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(cones, nodes, pos_node, total);
+  dc_vectors_kernel<<<dim3((unsigned)((total + 127) / 128), (maxK + kVecChunk - 1) / kVecChunk), 128, 0, s>>>(
+      cones, nodes, pos_node, total);
 }
 
 void launch_dc_copy_deflated(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s) {
-  (void)maxK;
   if (nnodes <= 0) return;
-  dc_copy_deflated_kernel<<<nnodes, 256, 0, s>>>(cones, nodes);
+  dc_copy_deflated_kernel<<<dim3(nnodes, (maxK + 7) / 8), 256, 0, s>>>(cones, nodes);
 }
 
 }  // namespace scs

@@ -1,14 +1,21 @@
 // Grouped FP64 GEMM used by every dense contraction of the FP64 path:
 // the two-sided trailing update of the dense->band stage, the stage-1
-// back-transformation, and the eigenvector updates of the divide and conquer.
+// back-transformation, the eigenvector updates of the divide and conquer and
+// the derivative contractions.
 //
 // FP64 on GB300 runs at about 2 DFMA per clock per SM, so the kernel is bound
-// by the FP64 pipe, not by memory: a 64x64 tile, 256 threads each owning a
-// 4x4 block of independent accumulators, operands staged through shared
-// memory.  Problems of different sizes share one launch (a tile prefix sum
-// maps blockIdx.x to a problem), and sizes that are only known on the device
-// (number of kept eigenvectors, non-deflated poles) are read from device
-// memory so that the launch sequence is static and can be captured in a graph.
+// by the FP64 pipe, not by memory: the goal is to keep every SM's FP64 pipe
+// busy with no wasted lanes.  256 threads form a 16 x 16 grid, each owning a
+// (BM/16) x (BN/16) block of independent accumulators; operands are staged
+// through shared memory.  Three tile shapes cover the shapes of this
+// pipeline: 64x64 (square-ish), 128x16 (tall, N = band width) and 16x128
+// (short, M = band width).  Long reductions with few output tiles are split
+// along K (split-K): each slice writes its partial product to scratch and a
+// second kernel sums the slices in a fixed order, so results are
+// bit-for-bit repeatable.  Problems of different sizes share one launch (a
+// tile prefix sum maps blockIdx.x to a problem), and sizes that are only
+// known on the device (kept eigenvectors, non-deflated poles) are read from
+// device memory so that the launch sequence is static.
 #include "internal.cuh"
 
 namespace scs {
@@ -24,10 +31,12 @@ __device__ __forceinline__ int find_problem(const int* prefix, int count, int ti
   return lo;
 }
 
-constexpr int BM = kGemmBM, BN = kGemmBN, BK = kGemmBK;
+constexpr int BK = kGemmBK;
 
+template <int BM, int BN>
 __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restrict__ descs,
                                                        const int* __restrict__ prefix, int count) {
+  constexpr int TM = BM / 16, TN = BN / 16;
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
 
@@ -39,21 +48,28 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restric
   if (g.dynN) N = min(N, *g.dynN);
   if (g.dynK) K = min(K, *g.dynK);
   const int M = g.M;
+  const int S = g.splitk;
   const int tiles_m = (M + BM - 1) / BM;
-  const int local = tile - prefix[p];
+  int local = tile - prefix[p];
+  const int kb = local % S;
+  local /= S;
   const int tm = local % tiles_m, tn = local / tiles_m;
   const int i0 = tm * BM, j0 = tn * BN;
-  if (j0 >= N || i0 >= M) return;
   const int flags = g.flags;
-  if ((flags & GF_LOWER_C) && tn > tm) return;
+  const bool lowc = flags & GF_LOWER_C;
+  if (j0 >= N || i0 >= M) return;
+  if (lowc && j0 > i0 + BM - 1) return;
+  const int kchunk = ((g.K + S - 1) / S + BK - 1) / BK * BK;
+  const int kbeg = kb * kchunk;
+  const int kend = min(K, kbeg + kchunk);
 
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
+  double acc[TM][TN];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < TM; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+    for (int c = 0; c < TN; ++c) acc[r][c] = 0.0;
 
   const double* __restrict__ A = g.A;
   const double* __restrict__ B = g.B;
@@ -61,63 +77,79 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restric
   const bool ta = flags & GF_TRANS_A, tb = flags & GF_TRANS_B, sa = flags & GF_SYM_A;
   const bool scl = flags & GF_SCALE_B;
 
-  for (int k0 = 0; k0 < K; k0 += BK) {
-    // ---- A tile: op(A)(i0 + ii, k0 + kk)
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
-    for (int q = 0; q < (BM * BK) / 256; ++q) {
+    for (int q = 0; q < (BM * BK + 255) / 256; ++q) {
       const int e = tid + q * 256;
-      int ii, kk;
-      if (ta) { kk = e % BK; ii = e / BK; } else { ii = e % BM; kk = e / BM; }
-      const int i = i0 + ii, k = k0 + kk;
-      double v = 0.0;
-      if (i < M && k < K) {
-        if (sa) v = (i >= k) ? A[(int64_t)i + (int64_t)k * lda] : A[(int64_t)k + (int64_t)i * lda];
-        else if (ta) v = A[(int64_t)k + (int64_t)i * lda];
-        else v = A[(int64_t)i + (int64_t)k * lda];
+      if ((BM * BK) % 256 == 0 || e < BM * BK) {
+        int ii, kk;
+        if (ta) { kk = e % BK; ii = e / BK; } else { ii = e % BM; kk = e / BM; }
+        const int i = i0 + ii, k = k0 + kk;
+        double v = 0.0;
+        if (i < M && k < kend) {
+          if (sa) v = (i >= k) ? A[(int64_t)i + (int64_t)k * lda] : A[(int64_t)k + (int64_t)i * lda];
+          else if (ta) v = A[(int64_t)k + (int64_t)i * lda];
+          else v = A[(int64_t)i + (int64_t)k * lda];
+        }
+        As[kk][ii] = v;
       }
-      As[kk][ii] = v;
     }
-    // ---- B tile: op(B)(k0 + kk, j0 + jj)
 #pragma unroll
-    for (int q = 0; q < (BN * BK) / 256; ++q) {
+    for (int q = 0; q < (BN * BK + 255) / 256; ++q) {
       const int e = tid + q * 256;
-      int jj, kk;
-      if (tb) { jj = e % BN; kk = e / BN; } else { kk = e % BK; jj = e / BK; }
-      const int j = j0 + jj, k = k0 + kk;
-      double v = 0.0;
-      if (j < N && k < K) {
-        v = tb ? B[(int64_t)j + (int64_t)k * ldb] : B[(int64_t)k + (int64_t)j * ldb];
-        if (scl) v *= g.bscale[k];
+      if ((BN * BK) % 256 == 0 || e < BN * BK) {
+        int jj, kk;
+        if (tb) { jj = e % BN; kk = e / BN; } else { kk = e % BK; jj = e / BK; }
+        const int j = j0 + jj, k = k0 + kk;
+        double v = 0.0;
+        if (j < N && k < kend) {
+          v = tb ? B[(int64_t)j + (int64_t)k * ldb] : B[(int64_t)k + (int64_t)j * ldb];
+          if (scl) v *= g.bscale[k];
+        }
+        Bs[kk][jj] = v;
       }
-      Bs[kk][jj] = v;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], bv[4];
+      double a[TM], bv[TN];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][tx + 16 * r];
+      for (int r = 0; r < TM; ++r) a[r] = As[kk][tx + 16 * r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][ty + 16 * c];
+      for (int c = 0; c < TN; ++c) bv[c] = Bs[kk][ty + 16 * c];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < TM; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], bv[c], acc[r][c]);
+        for (int c = 0; c < TN; ++c) acc[r][c] = fma(a[r], bv[c], acc[r][c]);
     }
     __syncthreads();
   }
 
-  double* __restrict__ C = g.C;
+  if (S > 1) {
+    // partial product of slice kb: scratch[kb][i + j * M] (static N)
+    double* part = g.partial + (int64_t)kb * M * g.N;
+#pragma unroll
+    for (int c = 0; c < TN; ++c) {
+      const int j = j0 + ty + 16 * c;
+      if (j >= N) continue;
+#pragma unroll
+      for (int r = 0; r < TM; ++r) {
+        const int i = i0 + tx + 16 * r;
+        if (i < M) part[(int64_t)i + (int64_t)j * M] = acc[r][c];
+      }
+    }
+    return;
+  }
+  double* C = g.C;
   const int ldc = g.ldc;
   const double alpha = g.alpha, beta = g.beta;
-  const bool lowc = flags & GF_LOWER_C;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < TN; ++c) {
     const int j = j0 + ty + 16 * c;
     if (j >= N) continue;
     const int jc = g.colmap ? g.colmap[j] : j;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < TM; ++r) {
       const int i = i0 + tx + 16 * r;
       if (i >= M) continue;
       if (lowc && i < j) continue;
@@ -129,11 +161,54 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restric
   }
 }
 
+// Sums the split-K slices of every problem with splitk > 1 (blockIdx.y).
+__global__ void gemm_reduce_kernel(const GemmDesc* __restrict__ descs) {
+  const GemmDesc& g = descs[blockIdx.y];
+  if (g.splitk <= 1) return;
+  if (g.skip && *g.skip) return;
+  int N = g.N;
+  if (g.dynN) N = min(N, *g.dynN);
+  const int M = g.M, S = g.splitk;
+  const bool lowc = g.flags & GF_LOWER_C;
+  const int64_t total = (int64_t)M * N;
+  const int64_t slice = (int64_t)M * g.N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % M), j = (int)(e / M);
+    if (lowc && i < j) continue;
+    double s = 0.0;
+    for (int q = 0; q < S; ++q) s += g.partial[q * slice + e];
+    const int jc = g.colmap ? g.colmap[j] : j;
+    double* cp = g.C + (int64_t)i + (int64_t)jc * g.ldc;
+    double v = g.alpha * s;
+    if (g.beta != 0.0) v = fma(g.beta, *cp, v);
+    *cp = v;
+  }
+}
+
 }  // namespace
 
-void launch_gemm(const GemmDesc* descs, const int* tile_prefix, int count, int total_tiles, cudaStream_t s) {
+void gemm_tile_shape(int variant, int* bm, int* bn) {
+  switch (variant) {
+    case GEMM_TALL: *bm = 128; *bn = 16; break;
+    case GEMM_SHORT: *bm = 16; *bn = 128; break;
+    default: *bm = 64; *bn = 64; break;
+  }
+}
+
+void launch_gemm(const GemmDesc* descs, const int* tile_prefix, int count, int total_tiles, int variant,
+                 int needs_reduce, int64_t max_mn, cudaStream_t s) {
   if (count <= 0 || total_tiles <= 0) return;
-  gemm_f64_kernel<<<total_tiles, 256, 0, s>>>(descs, tile_prefix, count);
+  switch (variant) {
+    case GEMM_TALL: gemm_f64_kernel<128, 16><<<total_tiles, 256, 0, s>>>(descs, tile_prefix, count); break;
+    case GEMM_SHORT: gemm_f64_kernel<16, 128><<<total_tiles, 256, 0, s>>>(descs, tile_prefix, count); break;
+    default: gemm_f64_kernel<64, 64><<<total_tiles, 256, 0, s>>>(descs, tile_prefix, count); break;
+  }
+  if (needs_reduce) {
+    int gx = (int)((max_mn + 255) / 256);
+    if (gx > 512) gx = 512;
+    if (gx < 1) gx = 1;
+    gemm_reduce_kernel<<<dim3(gx, count), 256, 0, s>>>(descs);
+  }
 }
 
 }  // namespace scs

@@ -46,16 +46,21 @@ struct GemmDesc {
   int lda, ldb, ldc;
   double alpha, beta;
   int flags;
-  int tiles_n;           // tiles along N for the static N
+  int splitk;            // number of K slices (1: no split)
+  double* partial;       // splitk > 1: scratch of splitk * M * N doubles
 };
 
-constexpr int kGemmBM = 64, kGemmBN = 64, kGemmBK = 16;
+constexpr int kGemmBK = 16;
+enum : int { GEMM_SQUARE = 0, GEMM_TALL = 1, GEMM_SHORT = 2 };  // 64x64, 128x16, 16x128 tiles
+
+void gemm_tile_shape(int variant, int* bm, int* bn);
 
 // Launch one grouped GEMM over `count` problems whose descriptors are in
 // device memory (`descs`); tile_prefix[p] = first tile of problem p,
-// tile_prefix[count] = total tiles.
-void launch_gemm(const GemmDesc* descs, const int* tile_prefix, int count, int total_tiles,
-                 cudaStream_t s);
+// tile_prefix[count] = total tiles.  Problems with splitk > 1 are summed by a
+// second kernel (needs_reduce), max_mn = largest M*N of the launch.
+void launch_gemm(const GemmDesc* descs, const int* tile_prefix, int count, int total_tiles, int variant,
+                 int needs_reduce, int64_t max_mn, cudaStream_t s);
 
 // ------------------------------------------------------------------ cones
 // Device view of one cone of the "large" path (n >= 2).
@@ -94,7 +99,9 @@ struct ConeDev {
   double* zhat;     // n     Loewner-corrected z
   double* rot;      // 2n    Givens rotations (c, s) of the deflation
   double* rho;      // n     rank-one weight per merge node (indexed by start)
+  double* unrm;     // n     1 / norm of each secular eigenvector
   int* iperm;       // n     sorted position -> column of the child blocks
+  int* ifp;         // n     sorted position -> column of the merged block (kept first)
   int* irot;        // 2n    rotation column pairs
   int* iorg;        // n     origin pole of each secular root
   int* imap;        // n     output column of each kept eigenvector of a merge
@@ -132,8 +139,13 @@ void launch_dc_loewner(const ConeDev* cones, const MergeNode* nodes, const int* 
                        cudaStream_t s);
 void launch_dc_select(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s);
 void launch_dc_vectors(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total_pos,
-                       cudaStream_t s);
+                       int maxK, cudaStream_t s);
 void launch_dc_copy_deflated(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s);
+void launch_dc_build_qin(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s);
+void launch_dc_apply_rot(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total_pos,
+                         cudaStream_t s);
+void launch_dc_vecnorm(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total_pos,
+                       cudaStream_t s);
 void launch_backtr2(const ConeDev* cones, int ncones, int maxn, int maxk, cudaStream_t s);
 int backtr2_cols(int n);
 size_t panel_smem_bytes(int b, int R);
