@@ -120,6 +120,18 @@ int scs_psd_status(scs_psd_handle h, int32_t* device_status);
 /* Number of kernels the last call enqueued (for launch accounting). */
 int64_t scs_psd_last_launch_count(scs_psd_handle h);
 
+/* Phase timing for profiling.  While enabled, every call records CUDA events
+ * on its stream around each phase of the pipeline; scs_psd_trace_read
+ * synchronises, returns the summed device time in milliseconds and the
+ * number of recorded intervals of each phase (arrays of SCS_PSD_NPHASES
+ * entries, caller-owned), and clears the record.  Phases: 0 svec unpack,
+ * 1 dense->band (panels + trailing GEMMs), 2 band->tridiagonal, 3 tridiagonal
+ * divide and conquer, 4 stage-2 back-transformation, 5 stage-1
+ * back-transformation, 6 reconstruction + svec repack, 7 derivative. */
+#define SCS_PSD_NPHASES 8
+int scs_psd_trace(scs_psd_handle h, int enable);
+int scs_psd_trace_read(scs_psd_handle h, double* ms, int64_t* intervals);
+
 /* Human-readable text for a return code. */
 const char* scs_psd_strerror(int code);
 

@@ -36,15 +36,21 @@ _lock = threading.Lock()
 _handles = {}
 
 EXPORTS = ("scs_psd_create", "scs_psd_destroy", "scs_psd_proj", "scs_psd_proj_batched", "scs_psd_proj_vjp",
-           "scs_psd_reserve", "scs_psd_status", "scs_psd_last_launch_count", "scs_psd_strerror")
+           "scs_psd_reserve", "scs_psd_status", "scs_psd_last_launch_count", "scs_psd_strerror", "scs_psd_trace",
+           "scs_psd_trace_read")
+NPHASES = 8
+PHASES = ("unpack", "dense_to_band", "band_to_tridiag", "tridiag_dc", "backtransform_2", "backtransform_1",
+          "reconstruct", "derivative")
 
 
-def load():
+def load(path: str | None = None):
     """Load the compiled library (raises if it has not been built)."""
-    global _lib
+    global _lib, LIB_PATH
     with _lock:
         if _lib is not None:
             return _lib
+        if path is not None:
+            LIB_PATH = path
         if not os.path.exists(LIB_PATH):
             raise RuntimeError(f"scs_psd CUDA library not built ({LIB_PATH} missing); "
                                "run paper_2606_20519_gb300.build.build() first -- there is no CPU fallback")
@@ -60,6 +66,8 @@ def load():
         lib.scs_psd_status.argtypes = [vp, ctypes.POINTER(i32)]
         lib.scs_psd_last_launch_count.argtypes = [vp]
         lib.scs_psd_last_launch_count.restype = i64
+        lib.scs_psd_trace.argtypes = [vp, ctypes.c_int]
+        lib.scs_psd_trace_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
         lib.scs_psd_strerror.argtypes = [ctypes.c_int]
         lib.scs_psd_strerror.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -185,3 +193,16 @@ def status(device: int = 0) -> int:
 
 def last_launch_count(device: int = 0) -> int:
     return int(load().scs_psd_last_launch_count(handle(device)))
+
+
+def trace(enable: bool, device: int = 0) -> None:
+    """Turn per-phase CUDA-event timing on or off."""
+    _check(load().scs_psd_trace(handle(device), int(bool(enable))), "scs_psd_trace")
+
+
+def trace_read(device: int = 0):
+    """{phase: (ms, intervals)} summed since the last read (synchronises)."""
+    ms = (ctypes.c_double * NPHASES)()
+    cnt = (ctypes.c_int64 * NPHASES)()
+    _check(load().scs_psd_trace_read(handle(device), ms, cnt), "scs_psd_trace_read")
+    return {PHASES[i]: (float(ms[i]), int(cnt[i])) for i in range(NPHASES)}

@@ -101,6 +101,8 @@ struct Plan {
 struct scs_psd_handle_s {
   int device = 0;
   int sms = 0;
+  bool trace = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> trace_ev;
   int* status_word = nullptr;  // device
   cudaStream_t last_stream = nullptr;
   int64_t last_launches = 0;
@@ -178,7 +180,8 @@ struct MetaBuilder {
     g.prefix_off = (int)ints.size();
     int maxM = 0, maxN = 0;
     for (const GemmDesc& p : probs) { maxM = std::max(maxM, p.M); maxN = std::max(maxN, p.N); }
-    g.variant = (maxN <= 16 && maxM > 16) ? GEMM_TALL : (maxM <= 16 && maxN > 16) ? GEMM_SHORT : GEMM_SQUARE;
+    g.variant = (maxM <= 16 && maxN <= 16) ? GEMM_SMALL
+                : (maxN <= 16) ? GEMM_TALL : (maxM <= 16) ? GEMM_SHORT : GEMM_SQUARE;
     int bm, bn;
     gemm_tile_shape(g.variant, &bm, &bn);
     int64_t base = 0;
@@ -192,7 +195,7 @@ struct MetaBuilder {
     int t = 0;
     int64_t off = 0;
     for (GemmDesc& p : probs) {
-      const int Sp = std::max(1, std::min(S, p.K / 64));
+      const int Sp = std::max(1, std::min(S, p.K / 32));
       p.splitk = Sp;
       ints.push_back(t);
       const int tm = (p.M + bm - 1) / bm, tn = (p.N + bn - 1) / bn;
@@ -317,7 +320,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
         maxm = std::max<int>(maxm, (int)cones[c].n - (p + 1) * b);
       }
     ps.njobs = (int)ids.size();
-    ps.cluster = std::min(8, std::max(1, (maxm + 255) / 256));
+    ps.cluster = std::min(16, std::max(1, (maxm + 255) / 256));
     ps.R = (maxm + ps.cluster - 1) / ps.cluster;
     ps.ids_off = (int)mb.ints.size();
     mb.ints.insert(mb.ints.end(), ids.begin(), ids.end());
@@ -549,11 +552,35 @@ int run_gemm(const Plan& P, const GemmLaunch& g, cudaStream_t s, int64_t& n_laun
   return SCS_PSD_OK;
 }
 
+// Phase timing: an event pair per phase interval when tracing is on.
+struct PhaseMark {
+  scs_psd_handle h;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  int phase = -1;
+  void begin(int ph) {
+    if (!h->trace) return;
+    end();
+    phase = ph;
+    cudaEventCreate(&a);
+    cudaEventRecord(a, s);
+  }
+  void end() {
+    if (!h->trace || phase < 0) return;
+    cudaEvent_t b;
+    cudaEventCreate(&b);
+    cudaEventRecord(b, s);
+    h->trace_ev.push_back({phase, {a, b}});
+    phase = -1;
+  }
+};
+
 // The launch sequence of one call.
 int run_plan(scs_psd_handle h, Plan& P, const double* x, double* y, const double* g, double* xbar,
              long long wait_limit, cudaStream_t s) {
   int64_t n_launch = 0;
   int rc;
+  PhaseMark pm{h, s};
   CUDA_TRY(cudaMemsetAsync(P.status_d, 0, sizeof(int) * (P.ncones + 1), s));
   if (P.prog_count) CUDA_TRY(cudaMemsetAsync(P.prog_d, 0, sizeof(int) * P.prog_count, s));
   if (P.ntriv && y) {
@@ -562,14 +589,17 @@ int run_plan(scs_psd_handle h, Plan& P, const double* x, double* y, const double
   }
   if (P.ncones) {
     const int nc = P.ncones;
+    pm.begin(0);
     launch_unpack(P.cones_d, nc, P.maxn * P.maxn, x, s);
     LAUNCH_CHECK();
+    pm.begin(1);
     for (const PanelStep& ps : P.panels) {
       launch_panel(P.cones_d, P.ints_d + ps.ids_off, ps.njobs, ps.panel, P.b, ps.cluster, ps.R, s);
       LAUNCH_CHECK();
       for (int q = 0; q < 6; ++q)
         if ((rc = run_gemm(P, ps.g[q], s, n_launch))) return rc;
     }
+    pm.begin(2);
     launch_band_extract(P.cones_d, nc, P.maxn, s);
     LAUNCH_CHECK();
     for (const BulgeLaunch& bl : P.bulges) {
@@ -580,6 +610,7 @@ int run_plan(scs_psd_handle h, Plan& P, const double* x, double* y, const double
     }
     launch_tridiag_extract(P.cones_d, nc, P.maxn, s);
     LAUNCH_CHECK();
+    pm.begin(3);
     launch_dc_leaves(P.cones_d, nc, P.maxn, s);
     LAUNCH_CHECK();
     for (const Level& lv : P.levels) {
@@ -605,15 +636,19 @@ int run_plan(scs_psd_handle h, Plan& P, const double* x, double* y, const double
       launch_dc_copy_deflated(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
       LAUNCH_CHECK();
     }
-    launch_backtr2(P.cones_d, nc, (int)P.maxn, (int)P.maxn, s);
+    pm.begin(4);
+    launch_backtr2(P.cones_d, nc, (int)P.maxn, (int)P.maxn, P.allv ? (int)P.maxn : (int)(P.maxn + 1) / 2, P.b, s);
     LAUNCH_CHECK();
+    pm.begin(5);
     for (const GemmLaunch& gl : P.bt1)
       if ((rc = run_gemm(P, gl, s, n_launch))) return rc;
     if (y) {
+      pm.begin(6);
       launch_recon(P.cones_d, nc, (int)P.maxn, x, y, s);
       LAUNCH_CHECK();
     }
     if (g && xbar) {
+      pm.begin(7);
       launch_unpack(P.cones_d, nc, P.maxn * P.maxn, g, s);
       LAUNCH_CHECK();
       if ((rc = run_gemm(P, P.vjp[0], s, n_launch))) return rc;
@@ -626,6 +661,7 @@ int run_plan(scs_psd_handle h, Plan& P, const double* x, double* y, const double
       LAUNCH_CHECK();
     }
   }
+  pm.end();
   launch_status_reduce(P.status_d, P.ncones + 1, h->status_word, s);
   LAUNCH_CHECK();
   P.launches = n_launch;
@@ -773,6 +809,30 @@ int scs_psd_status(scs_psd_handle h, int32_t* device_status) {
 }
 
 int64_t scs_psd_last_launch_count(scs_psd_handle h) { return h ? h->last_launches : -1; }
+
+int scs_psd_trace(scs_psd_handle h, int enable) {
+  if (!h) return SCS_PSD_EINVAL;
+  h->trace = enable != 0;
+  return SCS_PSD_OK;
+}
+
+int scs_psd_trace_read(scs_psd_handle h, double* ms, int64_t* intervals) {
+  if (!h || !ms || !intervals) return SCS_PSD_EINVAL;
+  cudaSetDevice(h->device);
+  for (int p = 0; p < SCS_PSD_NPHASES; ++p) { ms[p] = 0.0; intervals[p] = 0; }
+  int rc = SCS_PSD_OK;
+  for (auto& e : h->trace_ev) {
+    float t = 0.f;
+    if (cudaEventSynchronize(e.second.second) != cudaSuccess ||
+        cudaEventElapsedTime(&t, e.second.first, e.second.second) != cudaSuccess)
+      rc = SCS_PSD_ECUDA;
+    if (e.first >= 0 && e.first < SCS_PSD_NPHASES) { ms[e.first] += t; intervals[e.first] += 1; }
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
+  h->trace_ev.clear();
+  return rc;
+}
 
 const char* scs_psd_strerror(int code) {
   switch (code) {

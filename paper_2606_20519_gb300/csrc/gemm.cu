@@ -7,10 +7,10 @@
 // by the FP64 pipe, not by memory: the goal is to keep every SM's FP64 pipe
 // busy with no wasted lanes.  256 threads form a 16 x 16 grid, each owning a
 // (BM/16) x (BN/16) block of independent accumulators; operands are staged
-// through shared memory.  Three tile shapes cover the shapes of this
-// pipeline: 64x64 (square-ish), 128x16 (tall, N = band width) and 16x128
-// (short, M = band width).  Long reductions with few output tiles are split
-// along K (split-K): each slice writes its partial product to scratch and a
+// through shared memory.  Four tile shapes cover the shapes of this
+// pipeline: 64x64 (square-ish), 128x16 (tall, N = band width), 16x128
+// (short, M = band width) and 16x16 (band-width squares).  Long reductions
+// with few output tiles are split along K (split-K): each slice writes its partial product to scratch and a
 // second kernel sums the slices in a fixed order, so results are
 // bit-for-bit repeatable.  Problems of different sizes share one launch (a
 // tile prefix sum maps blockIdx.x to a problem), and sizes that are only
@@ -191,6 +191,7 @@ void gemm_tile_shape(int variant, int* bm, int* bn) {
   switch (variant) {
     case GEMM_TALL: *bm = 128; *bn = 16; break;
     case GEMM_SHORT: *bm = 16; *bn = 128; break;
+    case GEMM_SMALL: *bm = 16; *bn = 16; break;
     default: *bm = 64; *bn = 64; break;
   }
 }
@@ -201,6 +202,7 @@ void launch_gemm(const GemmDesc* descs, const int* tile_prefix, int count, int t
   switch (variant) {
     case GEMM_TALL: gemm_f64_kernel<128, 16><<<total_tiles, 256, 0, s>>>(descs, tile_prefix, count); break;
     case GEMM_SHORT: gemm_f64_kernel<16, 128><<<total_tiles, 256, 0, s>>>(descs, tile_prefix, count); break;
+    case GEMM_SMALL: gemm_f64_kernel<16, 16><<<total_tiles, 256, 0, s>>>(descs, tile_prefix, count); break;
     default: gemm_f64_kernel<64, 64><<<total_tiles, 256, 0, s>>>(descs, tile_prefix, count); break;
   }
   if (needs_reduce) {

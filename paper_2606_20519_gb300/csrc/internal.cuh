@@ -51,7 +51,7 @@ struct GemmDesc {
 };
 
 constexpr int kGemmBK = 16;
-enum : int { GEMM_SQUARE = 0, GEMM_TALL = 1, GEMM_SHORT = 2 };  // 64x64, 128x16, 16x128 tiles
+enum : int { GEMM_SQUARE = 0, GEMM_TALL = 1, GEMM_SHORT = 2, GEMM_SMALL = 3 };  // 64x64, 128x16, 16x128, 16x16
 
 void gemm_tile_shape(int variant, int* bm, int* bn);
 
@@ -73,7 +73,7 @@ struct ConeDev {
   int kmax;         // reflector slots per sweep
   double* A;        // n*n dense matrix (column-major)
   double* band;     // n * (2b) lower band with room for the bulge fill
-  double* refl;     // nsweeps * kmax * (b + 1): tau, v[1..b-1] (v[0] = 1)
+  double* refl;     // nsweeps * kmax * (b + 1): c, u_0 .. u_{L-1} of H = I - c u u^T
   int* prog;        // nsweeps progress counters of the bulge chasing
   double* d;        // n diagonal of the tridiagonal matrix
   double* e;        // n off-diagonal (e[i] couples i and i+1)
@@ -146,8 +146,7 @@ void launch_dc_apply_rot(const ConeDev* cones, const MergeNode* nodes, const int
                          cudaStream_t s);
 void launch_dc_vecnorm(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total_pos,
                        cudaStream_t s);
-void launch_backtr2(const ConeDev* cones, int ncones, int maxn, int maxk, cudaStream_t s);
-int backtr2_cols(int n);
+void launch_backtr2(const ConeDev* cones, int ncones, int maxn, int maxk, int kexp, int band, cudaStream_t s);
 size_t panel_smem_bytes(int b, int R);
 void launch_loewner_scale(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s);
 void launch_pack_lower(const ConeDev* cones, int ncones, int64_t maxn, double* xbar, cudaStream_t s);

@@ -55,12 +55,17 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const ConeDev* __r
   double* taus = part + 8 * kMaxBand;    // [kMaxBand]
   double* Gp = taus + kMaxBand;          // [kMaxBand][kMaxBand] partial Gram
   double* Ts = Gp + kMaxBand * kMaxBand; // [kMaxBand][kMaxBand] T (rank 0)
+  double* Gw = Ts + kMaxBand * kMaxBand; // [8 warps][kMaxBand][kMaxBand] per-warp Gram partials
   __shared__ double wsum[kPanelThreads / 32];
   __shared__ double sh_beta, sh_tau, sh_scal;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int g0 = rank * R;
+  const int BP = (b <= 16) ? 16 : 32;       // lanes per panel row
+  const int tc = lane % BP;                 // column of this lane
+  const int roff = warp * (32 / BP) + lane / BP;
+  const int rstep = (kPanelThreads / 32) * (32 / BP);
   const int nr = skip ? 0 : max(0, min(m - g0, R));
   double* A = cn.A;
 
@@ -122,24 +127,26 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const ConeDev* __r
         else if (gi == j) S[i * bp + j] = beta;
       }
       __syncthreads();
-      // ---- w_c = sum_{gi >= j} v_gi P(gi, c), c > j
-      const int tc = tid & 31, tg = tid >> 5;  // column, row group (8 groups)
+      // ---- w_c = sum_{gi >= j} v_gi P(gi, c), c > j.  Lanes map to columns
+      // (BP = 16 or 32 lanes per row), so a warp covers 32/BP rows at a time
+      // and every lane issues useful FP64 work.
       const bool colok = tc > j && tc < b;
       if (tau != 0.0) {
         double pd = 0.0;
         if (colok)
-          for (int i = tg; i < nr; i += 8) {
+          for (int i = roff; i < nr; i += rstep) {
             const int gi = g0 + i;
             if (gi < j) continue;
             const double v = (gi == j) ? 1.0 : S[i * bp + j];
             pd = fma(v, S[i * bp + tc], pd);
           }
-        part[tg * kMaxBand + tc] = pd;
+        if (BP == 16) pd += __shfl_xor_sync(0xffffffffu, pd, 16);
+        if (lane < BP) part[warp * kMaxBand + lane] = pd;
       }
       __syncthreads();
-      if (tau != 0.0 && tid < 32) {
+      if (tau != 0.0 && tid < BP) {
         double t = 0.0;
-        for (int q = 0; q < 8; ++q) t += part[q * kMaxBand + tid];
+        for (int q = 0; q < kPanelThreads / 32; ++q) t += part[q * kMaxBand + tid];
         red2[slot * kMaxBand + tid] = t;
       }
       cluster.sync();
@@ -149,7 +156,7 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const ConeDev* __r
           for (int r = 0; r < C; ++r) w += cluster.map_shared_rank(red2, r)[slot * kMaxBand + tc];
         const double tw = tau * w;
         if (colok)
-          for (int i = tg; i < nr; i += 8) {
+          for (int i = roff; i < nr; i += rstep) {
             const int gi = g0 + i;
             if (gi < j) continue;
             const double v = (gi == j) ? 1.0 : S[i * bp + j];
@@ -178,18 +185,43 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const ConeDev* __r
         const double v = (gi <= c || c >= bb) ? S[i * bp + c] : 0.0;
         A[(int64_t)(r0 + gi) + (int64_t)(c0 + c) * n] = v;
       }
+    // partial Gram G(a, c) = sum_rows V(i, a) V(i, c): thread = (row subset, column c)
+    double acc[kMaxBand];
+#pragma unroll
+    for (int a = 0; a < kMaxBand; ++a) acc[a] = 0.0;
+    if (tc < bb)
+      for (int i = roff; i < nr; i += rstep) {
+        const int gi = g0 + i;
+        if (gi < tc) continue;  // v_c is zero above row c
+        const double vc = gi == tc ? 1.0 : S[i * bp + tc];
+#pragma unroll
+        for (int a = 0; a < kMaxBand; ++a) {
+          if (a < tc) {
+            const double va = gi == a ? 1.0 : (gi > a ? S[i * bp + a] : 0.0);
+            acc[a] = fma(va, vc, acc[a]);
+          }
+        }
+      }
+#pragma unroll
+    for (int a = 0; a < kMaxBand; ++a) {
+      double v = acc[a];
+      if (BP == 16) v += __shfl_xor_sync(0xffffffffu, v, 16);
+      acc[a] = v;
+    }
+    __syncthreads();
+    // per-warp partials into Ts (free until rank 0 forms T), then sum over warps
+    if (lane < BP) {
+#pragma unroll
+      for (int a = 0; a < kMaxBand; ++a)
+        if (a < bb) Gw[(warp * kMaxBand + a) * kMaxBand + lane] = acc[a];
+    }
+    __syncthreads();
     for (int e = tid; e < bb * bb; e += kPanelThreads) {
       const int a = e % bb, c = e / bb;
-      double acc = 0.0;
-      if (a <= c)
-        for (int i = 0; i < nr; ++i) {
-          const int gi = g0 + i;
-          if (gi < c) continue;  // v_c is zero above row c
-          const double vc = gi == c ? 1.0 : S[i * bp + c];
-          const double va = gi == a ? 1.0 : (gi > a ? S[i * bp + a] : 0.0);
-          acc = fma(va, vc, acc);
-        }
-      Gp[a * kMaxBand + c] = acc;
+      double g = 0.0;
+      if (a < c)
+        for (int q = 0; q < kPanelThreads / 32; ++q) g += Gw[(q * kMaxBand + a) * kMaxBand + c];
+      Gp[a * kMaxBand + c] = g;
     }
   }
   cluster.sync();
@@ -228,7 +260,7 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(const ConeDev* __r
 
 size_t panel_smem_bytes(int b, int R) {
   return sizeof(double) * ((size_t)R * (b + 1) + 4 + 2 * kMaxBand + 8 * kMaxBand + kMaxBand +
-                           2 * kMaxBand * kMaxBand);
+                           2 * kMaxBand * kMaxBand + 8 * kMaxBand * kMaxBand);
 }
 
 void launch_panel(const ConeDev* cones, const int* cone_ids, int njobs, int panel, int b, int cluster, int R,
