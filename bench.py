@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--config", default="admm625",
                    choices=["admm625", "single81", "precision4096", "uneven", "vjp1296"])
     p.add_argument("--band", type=int, default=0)
+    p.add_argument("--precision", default="fp64", choices=["fp64", "split"],
+                   help="fp64: FP64 throughout; split: split-TF32 tensor-core contractions")
     p.add_argument("--no-comparator", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--calls", type=int, default=0,
@@ -247,7 +249,8 @@ def run_ours(args):
     from paper_2606_20519_gb300 import _lib as lib, build
     build.build()
     lib.load()
-    opts = lib.make_opts(band=args.band) if args.band else None
+    prec = lib.SPLIT_TF32 if args.precision == "split" else lib.FP64
+    opts = lib.make_opts(band=args.band, precision=prec) if (args.band or prec != lib.FP64) else None
     b_used = args.band or 16
 
     wl = Workload(args.config, args.calls)
@@ -383,9 +386,10 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "projections/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64 io, tf32x6 split products",
         "data": "synthetic (seeded PCG64), shaped like the paper's SCS iterates; no dataset",
         "config": {"workload": wl.desc, "config": args.config, "cones_per_step": wl.units, "band": b_used,
+                   "precision": args.precision,
                    "parallelism": f"replicas x{world}", "l2": "flushed before every timed step (256 MB write)"},
         "e2e": {"value": e2e_value, "unit": "projections/s", "h2d_bytes_per_step": wl.bytes_in,
                 "d2h_bytes_per_step": wl.bytes_out},

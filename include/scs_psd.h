@@ -60,7 +60,9 @@ enum {
 /* Arithmetic used for the dense contractions. */
 typedef enum {
   SCS_PSD_FP64 = 0,       /* FP64 throughout */
-  SCS_PSD_SPLIT_TF32 = 1  /* reserved: split-TF32 tensor-core contractions */
+  SCS_PSD_SPLIT_TF32 = 1  /* dense contractions as split-TF32 tensor-core products (FP64 operands split
+                             into two TF32 halves, three products, FP32 accumulation); Householder
+                             panels, bulge chasing, secular equations and sign decisions stay FP64 */
 } scs_psd_precision;
 
 /* Options; a NULL pointer means all defaults (zero-initialised struct). */

@@ -32,6 +32,7 @@ constexpr int64_t kMaxSide = 8192;
 struct GemmLaunch {
   int desc_off = 0, count = 0, prefix_off = 0, tiles = 0;
   int variant = GEMM_SQUARE, needs_reduce = 0;
+  int tc = 0;  // 1: split-TF32 tensor-core kernel
   int64_t max_mn = 0;
 };
 
@@ -56,7 +57,8 @@ struct Level {
 struct Plan {
   std::string key;
   int b = kDefaultBand;
-  int allv = 0, side = 0;
+  int allv = 0, side = 0, precision = SCS_PSD_FP64;
+  GemmLaunch recon_tc;  // split mode: S = Z diag(l) Z^T on the tensor cores
   // shapes
   std::vector<int32_t> sides;
   std::vector<int64_t> offsets;
@@ -170,20 +172,31 @@ struct MetaBuilder {
   std::vector<MergeNode> nodes;
   int sms = 148;
   int64_t scratch_doubles = 0;
+  bool split = false;  // use the split-TF32 tensor-core kernel where the shape suits it
 
-  // Picks the tile shape for the launch and a split-K factor per problem so
-  // that the launch has about two CTAs per SM.
+  // Picks the engine and tile shape for the launch and a split-K factor per
+  // problem so that the launch has about two CTAs per SM.
   GemmLaunch add_gemm(std::vector<GemmDesc> probs) {
     GemmLaunch g;
     g.desc_off = (int)descs.size();
     g.count = (int)probs.size();
     g.prefix_off = (int)ints.size();
-    int maxM = 0, maxN = 0;
-    for (const GemmDesc& p : probs) { maxM = std::max(maxM, p.M); maxN = std::max(maxN, p.N); }
-    g.variant = (maxM <= 16 && maxN <= 16) ? GEMM_SMALL
-                : (maxN <= 16) ? GEMM_TALL : (maxM <= 16) ? GEMM_SHORT : GEMM_SQUARE;
+    int maxM = 0, maxN = 0, minK = 1 << 30;
+    for (const GemmDesc& p : probs) {
+      maxM = std::max(maxM, p.M);
+      maxN = std::max(maxN, p.N);
+      minK = std::min(minK, p.K);
+    }
     int bm, bn;
-    gemm_tile_shape(g.variant, &bm, &bn);
+    g.tc = (split && maxM >= 64 && minK >= 32 && !probs.empty()) ? 1 : 0;
+    if (g.tc) {
+      g.variant = (maxN <= 16) ? TC_N16 : TC_N64;
+      tc_tile_shape(g.variant, &bm, &bn);
+    } else {
+      g.variant = (maxM <= 16 && maxN <= 16) ? GEMM_SMALL
+                  : (maxN <= 16) ? GEMM_TALL : (maxM <= 16) ? GEMM_SHORT : GEMM_SQUARE;
+      gemm_tile_shape(g.variant, &bm, &bn);
+    }
     int64_t base = 0;
     for (const GemmDesc& p : probs) {
       int64_t tiles = (int64_t)((p.M + bm - 1) / bm) * ((p.N + bn - 1) / bn);
@@ -195,7 +208,7 @@ struct MetaBuilder {
     int t = 0;
     int64_t off = 0;
     for (GemmDesc& p : probs) {
-      const int Sp = std::max(1, std::min(S, p.K / 32));
+      const int Sp = std::max(1, std::min(S, p.K / (g.tc ? 128 : 32)));
       p.splitk = Sp;
       ints.push_back(t);
       const int tm = (p.M + bm - 1) / bm, tn = (p.N + bn - 1) / bn;
@@ -225,10 +238,12 @@ GemmDesc mk(const double* A, int lda, const double* B, int ldb, double* C, int l
   return g;
 }
 
-int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, int b, int allv, int side) {
+int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, int b, int allv, int side,
+               int precision) {
   P.b = b;
   P.allv = allv;
   P.side = side;
+  P.precision = precision;
   P.sides.assign(sides, sides + count);
   P.offsets.resize(count + 1);
   P.offsets[0] = 0;
@@ -262,6 +277,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   // ---- metadata sizes known up front: status (ncones+1), prog
   MetaBuilder mb;
   mb.sms = h->sms > 0 ? h->sms : 148;
+  mb.split = (precision == SCS_PSD_SPLIT_TF32);
   std::vector<ConeDev> cones(P.ncones);
   size_t prog_total = 0;
   std::vector<size_t> prog_off(P.ncones);
@@ -457,8 +473,15 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
       const int r0 = (p + 1) * b, m = n - r0, bb = std::min(b, m);
       double* V = d.V1 + (int64_t)p * n * b;
       double* T = d.T1 + (int64_t)p * b * b;
-      GemmDesc a = mk(V, m, d.Z + r0, n, d.Y, b, bb, n, m, 1.0, 0.0, GF_TRANS_A, st_ptr(c));
-      a.dynN = d.kinfo;
+      GemmDesc a;
+      if (mb.split) {
+        // (V^T Z)^T = Z^T V: the long dimension (kept columns) becomes M
+        a = mk(d.Z + r0, n, V, m, d.Y, b, n, bb, m, 1.0, 0.0, GF_TRANS_A | GF_TRANS_C, st_ptr(c));
+        a.dynM = d.kinfo;
+      } else {
+        a = mk(V, m, d.Z + r0, n, d.Y, b, bb, n, m, 1.0, 0.0, GF_TRANS_A, st_ptr(c));
+        a.dynN = d.kinfo;
+      }
       GemmDesc b2 = mk(T, b, d.Y, b, d.X, b, bb, n, bb, 1.0, 0.0, 0, st_ptr(c));
       b2.dynN = d.kinfo;
       GemmDesc c3 = mk(V, m, d.X, b, d.Z + r0, n, m, n, bb, -1.0, 1.0, 0, st_ptr(c));
@@ -468,6 +491,20 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
       g[2].push_back(c3);
     }
     for (int q = 0; q < 3; ++q) P.bt1.push_back(mb.add_gemm(g[q]));
+  }
+
+  // ---- split mode: reconstruction S = Z diag(l) Z^T (lower) on the tensor cores
+  if (mb.split && !allv) {
+    std::vector<GemmDesc> g;
+    for (int c = 0; c < P.ncones; ++c) {
+      const ConeDev& d = cones[c];
+      const int n = (int)d.n;
+      GemmDesc q = mk(d.Z, n, d.Z, n, d.QA, n, n, n, n, 1.0, 0.0, GF_TRANS_B | GF_SCALE_B | GF_LOWER_C, st_ptr(c));
+      q.bscale = d.lamk;
+      q.dynK = d.kinfo;
+      g.push_back(q);
+    }
+    P.recon_tc = mb.add_gemm(g);
   }
 
   // ---- derivative contractions
@@ -545,8 +582,13 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
 
 int run_gemm(const Plan& P, const GemmLaunch& g, cudaStream_t s, int64_t& n_launch) {
   if (g.count <= 0 || g.tiles <= 0) return SCS_PSD_OK;
-  launch_gemm(P.descs_d + g.desc_off, P.ints_d + g.prefix_off, g.count, g.tiles, g.variant, g.needs_reduce,
-              g.max_mn, s);
+  if (g.tc) {
+    launch_tc_gemm(P.descs_d + g.desc_off, P.ints_d + g.prefix_off, g.count, g.tiles, g.variant, s);
+    if (g.needs_reduce) launch_gemm_reduce(P.descs_d + g.desc_off, g.count, g.max_mn, s);
+  } else {
+    launch_gemm(P.descs_d + g.desc_off, P.ints_d + g.prefix_off, g.count, g.tiles, g.variant, g.needs_reduce,
+                g.max_mn, s);
+  }
   if (g.needs_reduce) ++n_launch;
   LAUNCH_CHECK();
   return SCS_PSD_OK;
@@ -644,7 +686,12 @@ int run_plan(scs_psd_handle h, Plan& P, const double* x, double* y, const double
       if ((rc = run_gemm(P, gl, s, n_launch))) return rc;
     if (y) {
       pm.begin(6);
-      launch_recon(P.cones_d, nc, (int)P.maxn, x, y, s);
+      if (P.recon_tc.count > 0) {
+        if ((rc = run_gemm(P, P.recon_tc, s, n_launch))) return rc;
+        launch_pack_recon(P.cones_d, nc, P.maxn, x, y, s);
+      } else {
+        launch_recon(P.cones_d, nc, (int)P.maxn, x, y, s);
+      }
       LAUNCH_CHECK();
     }
     if (g && xbar) {
@@ -668,11 +715,11 @@ int run_plan(scs_psd_handle h, Plan& P, const double* x, double* y, const double
   return SCS_PSD_OK;
 }
 
-std::string plan_key(const int32_t* sides, int32_t count, int b, int allv, int side) {
+std::string plan_key(const int32_t* sides, int32_t count, int b, int allv, int side, int precision) {
   std::string k;
   k.reserve(16 + 4 * (size_t)count);
-  char hdr[64];
-  snprintf(hdr, sizeof(hdr), "b%d,a%d,s%d,c%d:", b, allv, side, count);
+  char hdr[80];
+  snprintf(hdr, sizeof(hdr), "b%d,a%d,s%d,p%d,c%d:", b, allv, side, precision, count);
   k += hdr;
   k.append(reinterpret_cast<const char*>(sides), sizeof(int32_t) * (size_t)count);
   return k;
@@ -698,10 +745,11 @@ int do_call(scs_psd_handle h, const double* x, double* y, const double* g, doubl
   if (count == 0 || offsets[count] == 0) return SCS_PSD_OK;
   if (!x || (!y && !xbar)) return SCS_PSD_EINVAL;
   if (allv && (!g || !xbar)) return SCS_PSD_EINVAL;
-  int b = kDefaultBand, side = 0;
+  int b = kDefaultBand, side = 0, precision = SCS_PSD_FP64;
   long long wait = kDefaultWaitCycles;
   if (opts) {
-    if (opts->precision != SCS_PSD_FP64) return SCS_PSD_EINVAL;
+    if (opts->precision != SCS_PSD_FP64 && opts->precision != SCS_PSD_SPLIT_TF32) return SCS_PSD_EINVAL;
+    precision = opts->precision;
     if (opts->band) b = opts->band;
     side = opts->side;
     if (opts->wait_limit_cycles > 0) wait = opts->wait_limit_cycles;
@@ -710,7 +758,7 @@ int do_call(scs_psd_handle h, const double* x, double* y, const double* g, doubl
   std::lock_guard<std::mutex> lock(h->mu);
   if (cudaSetDevice(h->device) != cudaSuccess) return SCS_PSD_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  const std::string key = plan_key(sides, count, b, allv, side);
+  const std::string key = plan_key(sides, count, b, allv, side, precision);
   auto it = h->plans.find(key);
   Plan* P;
   if (it == h->plans.end()) {
@@ -720,7 +768,7 @@ int do_call(scs_psd_handle h, const double* x, double* y, const double* g, doubl
     }
     auto np = std::make_unique<Plan>();
     np->key = key;
-    rc = build_plan(h, *np, sides, count, b, allv, side);
+    rc = build_plan(h, *np, sides, count, b, allv, side, precision);
     if (rc) return rc;
     P = np.get();
     h->plans[key] = std::move(np);

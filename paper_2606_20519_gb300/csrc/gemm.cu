@@ -47,9 +47,10 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restric
   int N = g.N, K = g.K;
   if (g.dynN) N = min(N, *g.dynN);
   if (g.dynK) K = min(K, *g.dynK);
-  const int M = g.M;
+  const int Ms = g.M;
+  const int M = g.dynM ? min(Ms, *g.dynM) : Ms;
   const int S = g.splitk;
-  const int tiles_m = (M + BM - 1) / BM;
+  const int tiles_m = (Ms + BM - 1) / BM;
   int local = tile - prefix[p];
   const int kb = local % S;
   local /= S;
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restric
 
   if (S > 1) {
     // partial product of slice kb: scratch[kb][i + j * M] (static N)
-    double* part = g.partial + (int64_t)kb * M * g.N;
+    double* part = g.partial + (int64_t)kb * Ms * g.N;
 #pragma unroll
     for (int c = 0; c < TN; ++c) {
       const int j = j0 + ty + 16 * c;
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restric
 #pragma unroll
       for (int r = 0; r < TM; ++r) {
         const int i = i0 + tx + 16 * r;
-        if (i < M) part[(int64_t)i + (int64_t)j * M] = acc[r][c];
+        if (i < M) part[(int64_t)i + (int64_t)j * Ms] = acc[r][c];
       }
     }
     return;
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restric
       const int i = i0 + tx + 16 * r;
       if (i >= M) continue;
       if (lowc && i < j) continue;
-      double* cp = C + (int64_t)i + (int64_t)jc * ldc;
+      double* cp = (flags & GF_TRANS_C) ? C + (int64_t)jc + (int64_t)i * ldc : C + (int64_t)i + (int64_t)jc * ldc;
       double v = alpha * acc[r][c];
       if (beta != 0.0) v = fma(beta, *cp, v);
       *cp = v;
@@ -168,17 +169,19 @@ __global__ void gemm_reduce_kernel(const GemmDesc* __restrict__ descs) {
   if (g.skip && *g.skip) return;
   int N = g.N;
   if (g.dynN) N = min(N, *g.dynN);
-  const int M = g.M, S = g.splitk;
+  const int Ms = g.M, S = g.splitk;
+  const int M = g.dynM ? min(Ms, *g.dynM) : Ms;
   const bool lowc = g.flags & GF_LOWER_C;
-  const int64_t total = (int64_t)M * N;
-  const int64_t slice = (int64_t)M * g.N;
+  const int64_t total = (int64_t)Ms * N;
+  const int64_t slice = (int64_t)Ms * g.N;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e % M), j = (int)(e / M);
+    const int i = (int)(e % Ms), j = (int)(e / Ms);
+    if (i >= M) continue;
     if (lowc && i < j) continue;
     double s = 0.0;
     for (int q = 0; q < S; ++q) s += g.partial[q * slice + e];
     const int jc = g.colmap ? g.colmap[j] : j;
-    double* cp = g.C + (int64_t)i + (int64_t)jc * g.ldc;
+    double* cp = (g.flags & GF_TRANS_C) ? g.C + (int64_t)jc + (int64_t)i * g.ldc : g.C + (int64_t)i + (int64_t)jc * g.ldc;
     double v = g.alpha * s;
     if (g.beta != 0.0) v = fma(g.beta, *cp, v);
     *cp = v;
@@ -205,12 +208,14 @@ void launch_gemm(const GemmDesc* descs, const int* tile_prefix, int count, int t
     case GEMM_SMALL: gemm_f64_kernel<16, 16><<<total_tiles, 256, 0, s>>>(descs, tile_prefix, count); break;
     default: gemm_f64_kernel<64, 64><<<total_tiles, 256, 0, s>>>(descs, tile_prefix, count); break;
   }
-  if (needs_reduce) {
-    int gx = (int)((max_mn + 255) / 256);
-    if (gx > 512) gx = 512;
-    if (gx < 1) gx = 1;
-    gemm_reduce_kernel<<<dim3(gx, count), 256, 0, s>>>(descs);
-  }
+  if (needs_reduce) launch_gemm_reduce(descs, count, max_mn, s);
+}
+
+void launch_gemm_reduce(const GemmDesc* descs, int count, int64_t max_mn, cudaStream_t s) {
+  int gx = (int)((max_mn + 255) / 256);
+  if (gx > 512) gx = 512;
+  if (gx < 1) gx = 1;
+  gemm_reduce_kernel<<<dim3(gx, count), 256, 0, s>>>(descs);
 }
 
 }  // namespace scs

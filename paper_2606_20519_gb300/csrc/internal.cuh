@@ -31,6 +31,7 @@ enum : int {
   GF_SYM_A = 4,     // A is square symmetric, only its lower triangle is read
   GF_LOWER_C = 8,   // only the lower triangle (i >= j) of C is computed
   GF_SCALE_B = 16,  // op(B)(k, j) is multiplied by bscale[k]
+  GF_TRANS_C = 32,  // result element (i, j) is stored at C[j + i * ldc]
 };
 
 struct GemmDesc {
@@ -38,6 +39,7 @@ struct GemmDesc {
   const double* B;
   double* C;
   const double* bscale;  // GF_SCALE_B
+  const int* dynM;       // if set: M = min(M, *dynM) (bounds only; layouts use the static M)
   const int* dynN;       // if set: N = min(N, *dynN)
   const int* dynK;       // if set: K = min(K, *dynK)
   const int* colmap;     // if set: column j of the result goes to column colmap[j] of C
@@ -54,6 +56,13 @@ constexpr int kGemmBK = 16;
 enum : int { GEMM_SQUARE = 0, GEMM_TALL = 1, GEMM_SHORT = 2, GEMM_SMALL = 3 };  // 64x64, 128x16, 16x128, 16x16
 
 void gemm_tile_shape(int variant, int* bm, int* bn);
+
+// Split-TF32 tensor-core GEMM (tcgen05), same descriptors; tile 128 x 16 or 128 x 64.
+enum : int { TC_N16 = 16, TC_N64 = 64 };
+void tc_tile_shape(int variant, int* bm, int* bn);
+void launch_tc_gemm(const GemmDesc* descs, const int* tile_prefix, int count, int total_tiles, int variant,
+                    cudaStream_t s);
+void launch_gemm_reduce(const GemmDesc* descs, int count, int64_t max_mn, cudaStream_t s);
 
 // Launch one grouped GEMM over `count` problems whose descriptors are in
 // device memory (`descs`); tile_prefix[p] = first tile of problem p,
@@ -151,6 +160,8 @@ size_t panel_smem_bytes(int b, int R);
 void launch_loewner_scale(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s);
 void launch_pack_lower(const ConeDev* cones, int ncones, int64_t maxn, double* xbar, cudaStream_t s);
 void launch_recon(const ConeDev* cones, int ncones, int maxn, const double* x, double* y, cudaStream_t s);
+// y = svec(S) or x - svec(S) from the lower triangle of S = Z diag(l) Z^T held in QA (split mode)
+void launch_pack_recon(const ConeDev* cones, int ncones, int64_t maxn, const double* x, double* y, cudaStream_t s);
 void launch_status_reduce(const int* status, int count, int* out, cudaStream_t s);
 
 }  // namespace scs

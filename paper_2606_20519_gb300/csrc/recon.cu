@@ -98,7 +98,40 @@ __global__ void __launch_bounds__(256) recon_kernel(const ConeDev* __restrict__ 
   }
 }
 
+// Split mode: S = Z diag(l) Z^T was formed (lower triangle) in QA by the
+// tensor-core GEMM; write svec(S) (positive part) or x - svec(S).
+__global__ void pack_recon_kernel(const ConeDev* __restrict__ cones, const double* x, double* y) {
+  const ConeDev& c = cones[blockIdx.y];
+  const int64_t n = c.n;
+  const int64_t len = n * (n + 1) / 2;
+  const bool bad = *c.status != 0;
+  const int route = c.kinfo[1];
+  const double* xs = x + c.xoff;
+  double* ys = y + c.xoff;
+  for (int64_t j = blockIdx.x; j < n; j += gridDim.x) {
+    const int64_t colo = j * n - (j * (j - 1)) / 2;
+    const int kk = c.kinfo[0];
+    for (int64_t i = j + threadIdx.x; i < n; i += blockDim.x) {
+      const int64_t idx = colo + (i - j);
+      if (idx >= len) continue;
+      const double s = kk > 0 ? c.QA[i + j * n] : 0.0;
+      const double sc = (i == j) ? 1.0 : M_SQRT2;
+      double v;
+      if (bad) v = nan("");
+      else if (route == 0) v = sc * s;
+      else v = fma(-sc, s, xs[idx]);
+      ys[idx] = v;
+    }
+  }
+}
+
 }  // namespace
+
+void launch_pack_recon(const ConeDev* cones, int ncones, int64_t maxn, const double* x, double* y, cudaStream_t s) {
+  if (ncones <= 0) return;
+  int gx = (int)(maxn < 2048 ? maxn : 2048);
+  pack_recon_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones, x, y);
+}
 
 void launch_recon(const ConeDev* cones, int ncones, int maxn, const double* x, double* y, cudaStream_t s) {
   if (ncones <= 0) return;
