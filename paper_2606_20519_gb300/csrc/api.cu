@@ -26,6 +26,7 @@ using namespace scs;
 namespace {
 
 constexpr int kDefaultBand = 16;
+constexpr int64_t kOneStageMax = 2048;  // auto: one-stage tridiagonalisation up to this side
 constexpr long long kDefaultWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 constexpr int64_t kMaxSide = 8192;
 
@@ -44,6 +45,11 @@ struct PanelStep {
 
 struct BulgeLaunch {
   int nctas = 0, ncones = 0;
+  int cone_off = 0, rank_off = 0, count_off = 0;
+};
+
+struct Sytrd1Launch {
+  int nctas = 0, maxn = 0;
   int cone_off = 0, rank_off = 0, count_off = 0;
 };
 
@@ -81,6 +87,8 @@ struct Plan {
   // steps
   std::vector<PanelStep> panels;
   std::vector<BulgeLaunch> bulges;
+  std::vector<Sytrd1Launch> sytrd1;
+  int nlarft = 0, larft_cone_off = 0, larft_idx_off = 0;
   std::vector<Level> levels;
   std::vector<GemmLaunch> bt1;  // 3 per panel, reverse order
   GemmLaunch vjp[4];
@@ -138,15 +146,21 @@ enum Field {
   F_KINFO, F_NFIELDS
 };
 
-ConeLayout cone_layout(int64_t n, int b) {
+int num_blocks1(int64_t n) { return n >= 3 ? (int)((n - 2 + kSy1Block - 1) / kSy1Block) : 0; }
+
+ConeLayout cone_layout(int64_t n, int b, int path) {
   ConeLayout L{};
-  const int P = num_panels(n, b);
-  const int64_t nsw = std::max<int64_t>(0, n - 2);
+  const int P = path ? 0 : num_panels(n, b);
+  const int Q = path ? num_blocks1(n) : 0;
+  const int bw = std::max(b, kSy1Block);
+  const int64_t nsw = path ? 0 : std::max<int64_t>(0, n - 2);
   const int64_t kmax = (n >= 3 ? (n - 3) / b + 1 : 0) + 1;
   const size_t d = sizeof(double), i4 = sizeof(int);
   const size_t sz[F_NFIELDS] = {
-      d * n * n, d * n * 2 * b, d * nsw * kmax * (b + 1), d * n, d * n, d * P * n * b, d * P * b * b,
-      d * n * b, d * n * b, d * n * 3 * b, d * b * b, d * b * b, d * n * n, d * n * n, d * n, d * n,
+      d * n * n, d * n * 2 * b, d * nsw * kmax * (b + 1), d * n, d * n,
+      d * std::max<int64_t>((int64_t)P * n * b, (int64_t)Q * n * kSy1Block),
+      d * std::max<int64_t>((int64_t)P * b * b, (int64_t)Q * kSy1Block * kSy1Block),
+      d * n * bw, d * n * bw + d * 2048, d * n * 3 * b, d * b * b, d * b * b, d * n * n, d * n * n, d * n, d * n,
       d * n * n, d * n * n, d * n * n, d * n, d * n, d * n, d * n, d * n, d * n, d * 2 * n, d * n, d * n,
       i4 * n, i4 * n, i4 * 2 * n, i4 * n, i4 * n, i4 * 4 * n, i4 * 8};
   size_t o = 0;
@@ -239,7 +253,7 @@ GemmDesc mk(const double* A, int lda, const double* B, int ldb, double* C, int l
 }
 
 int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, int b, int allv, int side,
-               int precision) {
+               int precision, int onestage) {
   P.b = b;
   P.allv = allv;
   P.side = side;
@@ -260,12 +274,14 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   P.ncones = (int)big.size();
   P.ntriv = (int)triv_offs.size();
   std::vector<ConeLayout> lay(P.ncones);
+  std::vector<int> path(P.ncones);
   size_t cone_bytes = 0;
   std::vector<size_t> cone_base(P.ncones);
   for (int c = 0; c < P.ncones; ++c) {
     const int64_t n = sides[big[c]];
     P.maxn = std::max(P.maxn, n);
-    lay[c] = cone_layout(n, b);
+    path[c] = (onestage == 1) ? 1 : (onestage == 0 ? 0 : (n <= kOneStageMax ? 1 : 0));
+    lay[c] = cone_layout(n, b, path[c]);
     cone_base[c] = cone_bytes;
     cone_bytes += lay[c].bytes;
   }
@@ -298,9 +314,10 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
     ConeDev& d = cones[c];
     d.n = n;
     d.xoff = P.offsets[big[c]];
+    d.path = path[c];
     d.b = b;
-    d.npanels = num_panels(n, b);
-    d.nsweeps = (int)std::max<int64_t>(0, n - 2);
+    d.npanels = path[c] ? 0 : num_panels(n, b);
+    d.nsweeps = path[c] ? 0 : (int)std::max<int64_t>(0, n - 2);
     d.kmax = (int)((n >= 3 ? (n - 3) / b + 1 : 0) + 1);
 #define FLD(T, f) reinterpret_cast<T*>(cb + L.off[f])
     d.A = FLD(double, F_A); d.band = FLD(double, F_BAND); d.refl = FLD(double, F_REFL);
@@ -365,19 +382,23 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   {
     int cap = bulge_max_ctas(b);
     if (cap <= 0) cap = 1;
-    std::vector<int> want(P.ncones);
-    for (int c = 0; c < P.ncones; ++c) {
-      const int64_t n = cones[c].n;
-      const int nsw = cones[c].nsweeps;
+    std::vector<int> two;
+    for (int c = 0; c < P.ncones; ++c)
+      if (cones[c].path == 0 && cones[c].nsweeps > 0) two.push_back(c);
+    std::vector<int> want(two.size());
+    for (size_t q = 0; q < two.size(); ++q) {
+      const int64_t n = cones[two[q]].n;
+      const int nsw = cones[two[q]].nsweeps;
       int w = (int)std::max<int64_t>(1, n / (3 * b) + 1);
       w = std::min(w, std::max(1, nsw));
-      want[c] = w;
+      want[q] = w;
     }
     int c = 0;
-    while (c < P.ncones) {
+    const int ntwo = (int)two.size();
+    while (c < ntwo) {
       // pack cones into one launch while the CTA cap allows at least 1 each
       int first = c, total_want = 0;
-      while (c < P.ncones && (c - first) < cap) { total_want += want[c]; ++c; }
+      while (c < ntwo && (c - first) < cap) { total_want += want[c]; ++c; }
       const int nc = c - first;
       std::vector<int> give(nc);
       if (total_want <= cap) {
@@ -395,12 +416,70 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
       bl.ncones = nc;
       std::vector<int> cc, rr, gg;
       for (int q = 0; q < nc; ++q)
-        for (int r = 0; r < give[q]; ++r) { cc.push_back(first + q); rr.push_back(r); gg.push_back(give[q]); }
+        for (int r = 0; r < give[q]; ++r) { cc.push_back(two[first + q]); rr.push_back(r); gg.push_back(give[q]); }
       bl.nctas = (int)cc.size();
       bl.cone_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), cc.begin(), cc.end());
       bl.rank_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), rr.begin(), rr.end());
       bl.count_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), gg.begin(), gg.end());
       P.bulges.push_back(bl);
+    }
+  }
+
+  // ---- one-stage tridiagonalisation: CTA groups per cone (cooperative launches)
+  {
+    std::vector<int> one;
+    int64_t maxn1 = 0;
+    for (int c = 0; c < P.ncones; ++c)
+      if (cones[c].path == 1) { one.push_back(c); maxn1 = std::max(maxn1, cones[c].n); }
+    if (!one.empty()) {
+      // at most one CTA per SM for a cone: a step's work is small and the
+      // group barrier's cost grows with the number of CTAs
+      const int cap = std::max(1, sytrd1_max_ctas((int)maxn1));
+      const int sm_cap = std::max(1, h->sms);
+      // large cones (n >= 256) share the GPU in one launch, small cones get one CTA each
+      std::vector<int> large, small;
+      for (int c : one) (cones[c].n >= 256 ? large : small).push_back(c);
+      auto emit = [&](const std::vector<int>& list, bool spread) {
+        size_t i = 0;
+        while (i < list.size()) {
+          std::vector<int> grp;
+          double work = 0.0;
+          while (i < list.size() && (int)grp.size() < cap) {
+            grp.push_back(list[i]);
+            work += std::pow((double)cones[list[i]].n, 3.0);
+            ++i;
+          }
+          std::vector<int> give(grp.size(), 1);
+          if (spread) {
+            int left = cap - (int)grp.size();
+            for (size_t q = 0; q < grp.size(); ++q) {
+              const double share = std::pow((double)cones[grp[q]].n, 3.0) / work;
+              int extra = (int)(share * left);
+              extra = std::min<int64_t>(extra, std::max<int64_t>(0, cones[grp[q]].n / 4 - 1));
+              extra = std::min(extra, sm_cap - 1);
+              give[q] += extra;
+            }
+          }
+          Sytrd1Launch sl;
+          sl.maxn = (int)maxn1;
+          std::vector<int> cc, rr, gg;
+          for (size_t q = 0; q < grp.size(); ++q)
+            for (int r = 0; r < give[q]; ++r) { cc.push_back(grp[q]); rr.push_back(r); gg.push_back(give[q]); }
+          sl.nctas = (int)cc.size();
+          sl.cone_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), cc.begin(), cc.end());
+          sl.rank_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), rr.begin(), rr.end());
+          sl.count_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), gg.begin(), gg.end());
+          P.sytrd1.push_back(sl);
+        }
+      };
+      emit(large, true);
+      emit(small, false);
+      std::vector<int> bc, bi;
+      for (int c : one)
+        for (int q = 0; q < num_blocks1(cones[c].n); ++q) { bc.push_back(c); bi.push_back(q); }
+      P.nlarft = (int)bc.size();
+      P.larft_cone_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), bc.begin(), bc.end());
+      P.larft_idx_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), bi.begin(), bi.end());
     }
   }
 
@@ -463,30 +542,44 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
     }
   }
 
-  // ---- stage-1 back-transformation, reverse panel order
-  for (int p = maxP - 1; p >= 0; --p) {
+  // ---- stage-1 back-transformation (two-stage cones: band-reduction panels;
+  // one-stage cones: 32-reflector blocks), last block first
+  int maxQ = 0;
+  for (int c = 0; c < P.ncones; ++c)
+    if (cones[c].path == 1) maxQ = std::max(maxQ, num_blocks1(cones[c].n));
+  for (int p = std::max(maxP, maxQ) - 1; p >= 0; --p) {
     std::vector<GemmDesc> g[3];
     for (int c = 0; c < P.ncones; ++c) {
       const ConeDev& d = cones[c];
-      if (p >= d.npanels) continue;
       const int n = (int)d.n;
-      const int r0 = (p + 1) * b, m = n - r0, bb = std::min(b, m);
-      double* V = d.V1 + (int64_t)p * n * b;
-      double* T = d.T1 + (int64_t)p * b * b;
-      GemmDesc a;
+      int r0, m, bb, wb;
+      double *V, *T;
+      if (d.path == 0) {
+        if (p >= d.npanels) continue;
+        r0 = (p + 1) * b; m = n - r0; bb = std::min(b, m); wb = b;
+        V = d.V1 + (int64_t)p * n * b;
+        T = d.T1 + (int64_t)p * b * b;
+      } else {
+        if (p >= num_blocks1(n)) continue;
+        r0 = p * kSy1Block + 1; m = n - r0; bb = std::min<int>(kSy1Block, n - 2 - p * kSy1Block);
+        wb = kSy1Block;
+        V = d.V1 + (int64_t)p * n * kSy1Block;
+        T = d.T1 + (int64_t)p * kSy1Block * kSy1Block;
+      }
+      GemmDesc a1;
       if (mb.split) {
         // (V^T Z)^T = Z^T V: the long dimension (kept columns) becomes M
-        a = mk(d.Z + r0, n, V, m, d.Y, b, n, bb, m, 1.0, 0.0, GF_TRANS_A | GF_TRANS_C, st_ptr(c));
-        a.dynM = d.kinfo;
+        a1 = mk(d.Z + r0, n, V, m, d.Y, wb, n, bb, m, 1.0, 0.0, GF_TRANS_A | GF_TRANS_C, st_ptr(c));
+        a1.dynM = d.kinfo;
       } else {
-        a = mk(V, m, d.Z + r0, n, d.Y, b, bb, n, m, 1.0, 0.0, GF_TRANS_A, st_ptr(c));
-        a.dynN = d.kinfo;
+        a1 = mk(V, m, d.Z + r0, n, d.Y, wb, bb, n, m, 1.0, 0.0, GF_TRANS_A, st_ptr(c));
+        a1.dynN = d.kinfo;
       }
-      GemmDesc b2 = mk(T, b, d.Y, b, d.X, b, bb, n, bb, 1.0, 0.0, 0, st_ptr(c));
+      GemmDesc b2 = mk(T, wb, d.Y, wb, d.X, wb, bb, n, bb, 1.0, 0.0, 0, st_ptr(c));
       b2.dynN = d.kinfo;
-      GemmDesc c3 = mk(V, m, d.X, b, d.Z + r0, n, m, n, bb, -1.0, 1.0, 0, st_ptr(c));
+      GemmDesc c3 = mk(V, m, d.X, wb, d.Z + r0, n, m, n, bb, -1.0, 1.0, 0, st_ptr(c));
       c3.dynN = d.kinfo;
-      g[0].push_back(a);
+      g[0].push_back(a1);
       g[1].push_back(b2);
       g[2].push_back(c3);
     }
@@ -641,6 +734,18 @@ int run_plan(scs_psd_handle h, Plan& P, const double* x, double* y, const double
       for (int q = 0; q < 6; ++q)
         if ((rc = run_gemm(P, ps.g[q], s, n_launch))) return rc;
     }
+    if (!P.sytrd1.empty()) {
+      pm.begin(1);
+      for (const Sytrd1Launch& sl : P.sytrd1) {
+        if (launch_sytrd1(P.cones_d, P.ints_d + sl.cone_off, P.ints_d + sl.rank_off, P.ints_d + sl.count_off,
+                          sl.nctas, sl.maxn, wait_limit, s))
+          return SCS_PSD_ECUDA;
+        LAUNCH_CHECK();
+      }
+      pm.begin(5);
+      launch_larft1(P.cones_d, P.ints_d + P.larft_cone_off, P.ints_d + P.larft_idx_off, P.nlarft, s);
+      LAUNCH_CHECK();
+    }
     pm.begin(2);
     launch_band_extract(P.cones_d, nc, P.maxn, s);
     LAUNCH_CHECK();
@@ -754,11 +859,14 @@ int do_call(scs_psd_handle h, const double* x, double* y, const double* g, doubl
     side = opts->side;
     if (opts->wait_limit_cycles > 0) wait = opts->wait_limit_cycles;
   }
+  int onestage = -1;  // auto
+  if (b == 1) { onestage = 1; b = kDefaultBand; }
+  else if (opts && opts->band >= 2) onestage = 0;
   if (b < 2 || b > kMaxBand || side < 0 || side > 2) return SCS_PSD_EINVAL;
   std::lock_guard<std::mutex> lock(h->mu);
   if (cudaSetDevice(h->device) != cudaSuccess) return SCS_PSD_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  const std::string key = plan_key(sides, count, b, allv, side, precision);
+  const std::string key = plan_key(sides, count, b, allv, side, precision) + (char)('A' + onestage + 1);
   auto it = h->plans.find(key);
   Plan* P;
   if (it == h->plans.end()) {
@@ -768,7 +876,7 @@ int do_call(scs_psd_handle h, const double* x, double* y, const double* g, doubl
     }
     auto np = std::make_unique<Plan>();
     np->key = key;
-    rc = build_plan(h, *np, sides, count, b, allv, side, precision);
+    rc = build_plan(h, *np, sides, count, b, allv, side, precision, onestage);
     if (rc) return rc;
     P = np.get();
     h->plans[key] = std::move(np);

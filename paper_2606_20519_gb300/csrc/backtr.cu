@@ -20,7 +20,7 @@ __device__ __forceinline__ int srow(int r) { return r + r / B; }
 template <int B>
 __global__ void __launch_bounds__(kBtThreads) backtr2_kernel(const ConeDev* __restrict__ cones, int cs) {
   const ConeDev& c = cones[blockIdx.y];
-  if (*c.status != 0) return;
+  if (*c.status != 0 || c.nsweeps == 0) return;
   const int n = (int)c.n;
   const int kcols = c.kinfo[0];
   const int j0 = blockIdx.x * cs;

@@ -22,6 +22,7 @@ namespace scs {
 enum : int { ST_NONFINITE = 1, ST_NOCONV = 2, ST_TIMEOUT = 4, ST_BADARG = 8 };
 
 constexpr int kMaxBand = 32;  // largest supported bandwidth b
+constexpr int kSy1Block = 32; // reflectors per block of the one-stage back-transformation
 
 // ------------------------------------------------------------------ GEMM
 // C = alpha * op(A) op(B) + beta * C on column-major FP64 operands.
@@ -76,6 +77,7 @@ void launch_gemm(const GemmDesc* descs, const int* tile_prefix, int count, int t
 struct ConeDev {
   int64_t n;
   int64_t xoff;     // offset of the cone in the svec buffers
+  int path;         // 0: two-stage (dense -> band -> tridiagonal), 1: one-stage tridiagonalisation
   int b;            // bandwidth of stage 1 / 2
   int npanels;
   int nsweeps;      // number of bulge-chasing sweeps (n - 2, at least 0)
@@ -160,6 +162,10 @@ size_t panel_smem_bytes(int b, int R);
 void launch_loewner_scale(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s);
 void launch_pack_lower(const ConeDev* cones, int ncones, int64_t maxn, double* xbar, cudaStream_t s);
 void launch_recon(const ConeDev* cones, int ncones, int maxn, const double* x, double* y, cudaStream_t s);
+int sytrd1_max_ctas(int maxn);
+int launch_sytrd1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,
+                  int maxn, long long wait_limit, cudaStream_t s);
+void launch_larft1(const ConeDev* cones, const int* blk_cone, const int* blk_index, int nblocks, cudaStream_t s);
 // y = svec(S) or x - svec(S) from the lower triangle of S = Z diag(l) Z^T held in QA (split mode)
 void launch_pack_recon(const ConeDev* cones, int ncones, int64_t maxn, const double* x, double* y, cudaStream_t s);
 void launch_status_reduce(const int* status, int count, int* out, cudaStream_t s);

@@ -50,6 +50,7 @@ __global__ void trivial_kernel(const int64_t* __restrict__ offs, const int* __re
 // extra diagonals hold the bulge fill and start at zero.
 __global__ void band_extract_kernel(const ConeDev* __restrict__ cones) {
   const ConeDev& c = cones[blockIdx.y];
+  if (c.path != 0) return;
   const int64_t n = c.n;
   const int ldb = 2 * c.b;
   const int64_t total = n * ldb;
@@ -64,6 +65,7 @@ __global__ void band_extract_kernel(const ConeDev* __restrict__ cones) {
 
 __global__ void tridiag_extract_kernel(const ConeDev* __restrict__ cones) {
   const ConeDev& c = cones[blockIdx.y];
+  if (c.path != 0) return;
   const int64_t n = c.n;
   const int ldb = 2 * c.b;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
