@@ -113,6 +113,25 @@ int scs_psd_proj_vjp(scs_psd_handle h, const double* x, const double* g, double*
                      const int64_t* offsets, const int32_t* sides, int32_t count,
                      const scs_psd_opts* opts, void* stream);
 
+/* Projection of one cone WITHOUT ANY DEVICE ALLOCATION, for callers that
+ * cannot call cudaMalloc (a process whose GPU memory is owned by a pool or a
+ * framework allocator, code that runs where allocation is forbidden after
+ * start-up).  It has no counterpart in the paper.  y = svec(Pi(smat(x))) in
+ * FP64 for a side-n cone, 0 <= n <= 256 (larger n returns SCS_PSD_EINVAL);
+ * x and y are caller-owned device buffers of n(n+1)/2 doubles on the current
+ * device, y may alias x.  All workspace -- the plan's metadata, the
+ * eigensolver's buffers and a status word -- lives in a file-scope
+ * __device__ array of 16 MiB that every GPU loading the library holds until
+ * exit.  The first call on a device (and the first call after a call of
+ * another side) sets up: it takes the array's address with
+ * cudaGetSymbolAddress and writes the plan into the array with
+ * cudaMemcpyAsync on `stream`; make that first call before any stream
+ * capture.  Every call shares the array and leaves the last call's contents
+ * in it (the status word is cleared at the start of each call), so calls
+ * that overlap on the GPU race: issue them on one stream, or synchronise
+ * between them.  Device-side errors fill y with NaN; no handle is needed. */
+int scs_psd_proj_static(const double* x, double* y, int64_t n, void* stream);
+
 /* Optional pre-sizing of the workspace for cones up to side max_n and
  * max_count cones of that side. */
 int scs_psd_reserve(scs_psd_handle h, int64_t max_n, int32_t max_count, const scs_psd_opts* opts);

@@ -36,7 +36,7 @@ _lock = threading.Lock()
 _handles = {}
 
 EXPORTS = ("scs_psd_create", "scs_psd_destroy", "scs_psd_proj", "scs_psd_proj_batched", "scs_psd_proj_vjp",
-           "scs_psd_reserve", "scs_psd_status", "scs_psd_last_launch_count", "scs_psd_strerror", "scs_psd_trace",
+           "scs_psd_proj_static", "scs_psd_reserve", "scs_psd_status", "scs_psd_last_launch_count", "scs_psd_strerror", "scs_psd_trace",
            "scs_psd_trace_read")
 NPHASES = 8
 PHASES = ("unpack", "dense_to_band", "band_to_tridiag", "tridiag_dc", "backtransform_2", "backtransform_1",

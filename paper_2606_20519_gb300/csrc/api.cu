@@ -99,10 +99,11 @@ struct Plan {
   const void* g_y = nullptr;
   const void* g_g = nullptr;
   const void* g_xbar = nullptr;
+  bool arena_owned = false;  // memory carved from a caller-provided region (not freed here)
   ~Plan() {
     if (gexec) cudaGraphExecDestroy(gexec);
-    if (cone_mem) cudaFree(cone_mem);
-    if (meta_mem) cudaFree(meta_mem);
+    if (!arena_owned && cone_mem) cudaFree(cone_mem);
+    if (!arena_owned && meta_mem) cudaFree(meta_mem);
   }
 };
 
@@ -252,8 +253,22 @@ GemmDesc mk(const double* A, int lda, const double* B, int ldb, double* C, int l
   return g;
 }
 
+// Optional device region to carve the plan's memory from instead of
+// cudaMalloc; metadata is then uploaded with cudaMemcpyAsync on `stream`.
+struct Arena {
+  char* base = nullptr;
+  size_t size = 0, used = 0;
+  cudaStream_t stream = nullptr;
+  void* take(size_t bytes) {
+    const size_t o = align_up(used);
+    if (o + bytes > size) return nullptr;
+    used = o + bytes;
+    return base + o;
+  }
+};
+
 int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, int b, int allv, int side,
-               int precision, int onestage) {
+               int precision, int onestage, Arena* arena = nullptr) {
   P.b = b;
   P.allv = allv;
   P.side = side;
@@ -286,7 +301,12 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
     cone_bytes += lay[c].bytes;
   }
   if (cone_bytes) {
-    if (cudaMalloc(&P.cone_mem, cone_bytes) != cudaSuccess) return SCS_PSD_ENOMEM;
+    if (arena) {
+      P.arena_owned = true;
+      if (!(P.cone_mem = arena->take(cone_bytes))) return SCS_PSD_EINVAL;
+    } else if (cudaMalloc(&P.cone_mem, cone_bytes) != cudaSuccess) {
+      return SCS_PSD_ENOMEM;
+    }
   }
   char* base = (char*)P.cone_mem;
 
@@ -622,7 +642,12 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   const size_t triv_b = align_up((sizeof(int64_t) + sizeof(int)) * std::max(1, P.ntriv));
   const size_t scratch_b = align_up(sizeof(double) * std::max<int64_t>(1, mb.scratch_doubles));
   const size_t total = cones_b + ints_b + descs_b + nodes_b + triv_b + scratch_b;
-  if (cudaMalloc(&P.meta_mem, total) != cudaSuccess) return SCS_PSD_ENOMEM;
+  if (arena) {
+    P.arena_owned = true;
+    if (!(P.meta_mem = arena->take(total))) return SCS_PSD_EINVAL;
+  } else if (cudaMalloc(&P.meta_mem, total) != cudaSuccess) {
+    return SCS_PSD_ENOMEM;
+  }
   char* mbase = (char*)P.meta_mem;
   P.cones_d = (ConeDev*)mbase;
   P.ints_d = (int*)(mbase + cones_b);
@@ -643,24 +668,27 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   }
   for (GemmDesc& g : mb.descs)
     if (g.skip) g.skip = P.ints_d + ((intptr_t)g.skip - 1);
+  // kinfo: [3] all eigenpairs, [4] side option (staged in a host block next to the rest)
+  std::vector<int> kin_all((size_t)P.ncones * 8, 0);
+  for (int c = 0; c < P.ncones; ++c) {
+    kin_all[(size_t)c * 8 + 3] = allv;
+    kin_all[(size_t)c * 8 + 4] = side;
+  }
+  auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    if (!bytes) return cudaSuccess;
+    if (arena) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, arena->stream);
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
   cudaError_t e = cudaSuccess;
-  if (P.ncones) e = cudaMemcpy(P.cones_d, cones.data(), sizeof(ConeDev) * P.ncones, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !mb.ints.empty())
-    e = cudaMemcpy(P.ints_d, mb.ints.data(), sizeof(int) * mb.ints.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !mb.descs.empty())
-    e = cudaMemcpy(P.descs_d, mb.descs.data(), sizeof(GemmDesc) * mb.descs.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !mb.nodes.empty())
-    e = cudaMemcpy(P.nodes_d, mb.nodes.data(), sizeof(MergeNode) * mb.nodes.size(), cudaMemcpyHostToDevice);
+  if (P.ncones) e = up(P.cones_d, cones.data(), sizeof(ConeDev) * P.ncones);
+  if (e == cudaSuccess) e = up(P.ints_d, mb.ints.data(), sizeof(int) * mb.ints.size());
+  if (e == cudaSuccess) e = up(P.descs_d, mb.descs.data(), sizeof(GemmDesc) * mb.descs.size());
+  if (e == cudaSuccess) e = up(P.nodes_d, mb.nodes.data(), sizeof(MergeNode) * mb.nodes.size());
   if (e == cudaSuccess && P.ntriv) {
-    e = cudaMemcpy(P.triv_offs_d, triv_offs.data(), sizeof(int64_t) * P.ntriv, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(P.triv_sides_d, triv_sides.data(), sizeof(int) * P.ntriv, cudaMemcpyHostToDevice);
+    e = up(P.triv_offs_d, triv_offs.data(), sizeof(int64_t) * P.ntriv);
+    if (e == cudaSuccess) e = up(P.triv_sides_d, triv_sides.data(), sizeof(int) * P.ntriv);
   }
-  // kinfo: [3] all eigenpairs, [4] side option
-  for (int c = 0; c < P.ncones && e == cudaSuccess; ++c) {
-    int kin[8] = {0, 0, 0, allv, side, 0, 0, 0};
-    e = cudaMemcpy(cones[c].kinfo, kin, sizeof(kin), cudaMemcpyHostToDevice);
-  }
+  for (int c = 0; c < P.ncones && e == cudaSuccess; ++c) e = up(cones[c].kinfo, &kin_all[(size_t)c * 8], 8 * sizeof(int));
   if (e != cudaSuccess) return SCS_PSD_ECUDA;
   (void)h;
   return SCS_PSD_OK;
@@ -889,9 +917,68 @@ int do_call(scs_psd_handle h, const double* x, double* y, const double* g, doubl
   return rc;
 }
 
+// ---- static-scratch entry point: no device allocation at all ----
+// Callers that cannot allocate device memory (inside a memory pool that owns
+// the GPU, in an embedding that forbids cudaMalloc after start-up) get the
+// FP64 projection of one cone of side <= kStaticMaxSide with every buffer --
+// the plan's metadata, the workspace and the status word -- carved from this
+// file-scope array.  Every GPU that loads the library holds it until exit.
+constexpr int64_t kStaticMaxSide = 256;
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+struct StaticDeviceState {
+  bool ready = false;
+  char* base = nullptr;        // device address of g_static_scratch on this device
+  scs_psd_handle_s hview;      // host-side view; its status word lives in the scratch
+  std::unique_ptr<Plan> plan;  // layout the scratch currently holds
+  int64_t plan_n = -1;
+};
+std::mutex g_static_mu;
+StaticDeviceState g_static_state[64];
+
+int proj_static(const double* x, double* y, int64_t n, void* stream) {
+  if (n < 0 || n > kStaticMaxSide) return SCS_PSD_EINVAL;
+  if (n == 0) return SCS_PSD_OK;
+  if (!x || !y) return SCS_PSD_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SCS_PSD_ECUDA;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  StaticDeviceState& st = g_static_state[dev];
+  if (!st.ready) {
+    // once per device, with that device current: the array's device address
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return SCS_PSD_ECUDA;
+    st.base = static_cast<char*>(p);
+    st.hview.device = dev;
+    cudaDeviceGetAttribute(&st.hview.sms, cudaDevAttrMultiProcessorCount, dev);
+    st.hview.status_word = reinterpret_cast<int*>(st.base);  // first 256 bytes
+    st.ready = true;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (st.plan_n != n) {
+    st.plan.reset();
+    st.plan_n = -1;
+    auto np = std::make_unique<Plan>();
+    Arena ar;
+    ar.base = st.base + 256;
+    ar.size = kStaticScratchBytes - 256;
+    ar.stream = s;
+    const int32_t sides[1] = {(int32_t)n};
+    const int rc = build_plan(&st.hview, *np, sides, 1, kDefaultBand, 0, 0, SCS_PSD_FP64, -1, &ar);
+    if (rc) return rc;
+    st.plan = std::move(np);
+    st.plan_n = n;
+  }
+  if (cudaMemsetAsync(st.hview.status_word, 0, sizeof(int), s) != cudaSuccess) return SCS_PSD_ECUDA;
+  return run_plan(&st.hview, *st.plan, x, y, nullptr, nullptr, kDefaultWaitCycles, s);
+}
+
 }  // namespace
 
 extern "C" {
+
+int scs_psd_proj_static(const double* x, double* y, int64_t n, void* stream) { return proj_static(x, y, n, stream); }
 
 int scs_psd_create(scs_psd_handle* h, int device) {
   if (!h) return SCS_PSD_EINVAL;
