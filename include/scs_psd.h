@@ -60,9 +60,11 @@ enum {
 /* Arithmetic used for the dense contractions. */
 typedef enum {
   SCS_PSD_FP64 = 0,       /* FP64 throughout */
-  SCS_PSD_SPLIT_TF32 = 1  /* dense contractions as split-TF32 tensor-core products (FP64 operands split
-                             into two TF32 halves, three products, FP32 accumulation); Householder
-                             panels, bulge chasing, secular equations and sign decisions stay FP64 */
+  SCS_PSD_SPLIT_TF32 = 1  /* dense contractions as split-TF32 tensor-core products (FP64 operands
+                             rounded to FP32 and split into three TF32 parts, the six products above
+                             the lowest order, FP32 accumulation per 8-wide K step, compensated
+                             FP32 sums across steps); Householder panels, bulge chasing, secular
+                             equations and sign decisions stay FP64 */
 } scs_psd_precision;
 
 /* Options; a NULL pointer means all defaults (zero-initialised struct). */
@@ -75,6 +77,9 @@ typedef struct {
                                2..32 = two-stage with this band width for every cone */
   int64_t mem_budget_bytes; /* VJP: workspace budget that triggers recompute; 0 = no limit */
   int64_t wait_limit_cycles;/* bound on device spin-waits; 0 = default */
+  int32_t graphs;           /* 0 = replay a recorded CUDA graph from the second call with the same
+                               shapes and options on, 1 = always launch kernel by kernel */
+  int32_t reserved;         /* must be 0 */
 } scs_psd_opts;
 
 /* Create a handle on CUDA device `device`.  Allocates no device memory yet. */
@@ -94,8 +99,11 @@ int scs_psd_proj(scs_psd_handle h, const double* x, double* y, int64_t n,
  * x[offsets[i] .. offsets[i+1]) and has side sides[i], with
  * offsets[i+1] - offsets[i] == sides[i](sides[i]+1)/2 and offsets[0] == 0.
  * offsets (count+1 entries) and sides (count entries) are HOST arrays.
- * The launch sequence for a given shape list is recorded once as a CUDA
- * graph and replayed on later calls with the same shapes.
+ * The first call for a shape list (with given options) launches kernel by
+ * kernel; the second records that launch sequence once as a CUDA graph and
+ * every later call replays it, after one small launch that hands the graph
+ * this call's x and y.  A call issued while `stream` is itself being
+ * captured is launched kernel by kernel into the caller's capture.
  * Operation: App. D.2, applied block by block (the PSD constraint split into
  * smaller blocks, as the paper's outlook on symmetry reduction proposes). */
 int scs_psd_proj_batched(scs_psd_handle h, const double* x, double* y, const int64_t* offsets,
@@ -112,6 +120,26 @@ int scs_psd_proj_batched(scs_psd_handle h, const double* x, double* y, const int
 int scs_psd_proj_vjp(scs_psd_handle h, const double* x, const double* g, double* xbar, double* y,
                      const int64_t* offsets, const int32_t* sides, int32_t count,
                      const scs_psd_opts* opts, void* stream);
+
+/* Forward pass that keeps the eigendecomposition for a later VJP (the
+ * "store" side of the store-or-recompute choice for the derivative of App. E):
+ * y = Pi(x) as scs_psd_proj_batched (y may be NULL), and every eigenpair of
+ * every cone, X_i = V_i diag(lam_i) V_i^T.  V and lam are caller-owned device
+ * buffers of sum_i sides[i]^2 and sum_i sides[i] doubles; cone i's V_i is
+ * the column-major sides[i] x sides[i] block at sum_{j<i} sides[j]^2 and its
+ * lam_i starts at sum_{j<i} sides[j].  The columns come in no particular
+ * order.  A bad cone's V_i and lam_i are NaN. */
+int scs_psd_proj_store(scs_psd_handle h, const double* x, double* y, double* V, double* lam,
+                       const int64_t* offsets, const int32_t* sides, int32_t count,
+                       const scs_psd_opts* opts, void* stream);
+
+/* xbar = DPi(X)[smat(g)] (as scs_psd_proj_vjp) from an eigendecomposition
+ * stored by scs_psd_proj_store instead of recomputing it; V, lam as there.
+ * With the same shapes and options the result is bit-identical to
+ * scs_psd_proj_vjp's, since the same kernels produce V and lam. */
+int scs_psd_vjp_stored(scs_psd_handle h, const double* V, const double* lam, const double* g, double* xbar,
+                       const int64_t* offsets, const int32_t* sides, int32_t count,
+                       const scs_psd_opts* opts, void* stream);
 
 /* Projection of one cone WITHOUT ANY DEVICE ALLOCATION, for callers that
  * cannot call cudaMalloc (a process whose GPU memory is owned by a pool or a
@@ -140,8 +168,13 @@ int scs_psd_reserve(scs_psd_handle h, int64_t max_n, int32_t max_count, const sc
  * work enqueued since the previous call (an SCS_PSD_* code, OK if none). */
 int scs_psd_status(scs_psd_handle h, int32_t* device_status);
 
-/* Number of kernels the last call enqueued (for launch accounting). */
+/* Number of kernels the last call enqueued (for launch accounting), counting
+ * each kernel of a replayed graph. */
 int64_t scs_psd_last_launch_count(scs_psd_handle h);
+
+/* 1 if the last call replayed a recorded graph, 0 if it launched kernel by
+ * kernel, -1 for a NULL handle. */
+int scs_psd_last_replayed(scs_psd_handle h);
 
 /* Phase timing for profiling.  While enabled, every call records CUDA events
  * on its stream around each phase of the pipeline; scs_psd_trace_read

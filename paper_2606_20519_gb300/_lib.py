@@ -28,7 +28,7 @@ class ScsPsdError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("side", ctypes.c_int32), ("recompute", ctypes.c_int32),
                 ("band", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64),
-                ("wait_limit_cycles", ctypes.c_int64)]
+                ("wait_limit_cycles", ctypes.c_int64), ("graphs", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -36,8 +36,8 @@ _lock = threading.Lock()
 _handles = {}
 
 EXPORTS = ("scs_psd_create", "scs_psd_destroy", "scs_psd_proj", "scs_psd_proj_batched", "scs_psd_proj_vjp",
-           "scs_psd_proj_static", "scs_psd_reserve", "scs_psd_status", "scs_psd_last_launch_count", "scs_psd_strerror", "scs_psd_trace",
-           "scs_psd_trace_read")
+           "scs_psd_proj_store", "scs_psd_vjp_stored", "scs_psd_proj_static", "scs_psd_reserve", "scs_psd_status", "scs_psd_last_launch_count",
+           "scs_psd_last_replayed", "scs_psd_strerror", "scs_psd_trace", "scs_psd_trace_read")
 NPHASES = 8
 PHASES = ("unpack", "dense_to_band", "band_to_tridiag", "tridiag_dc", "backtransform_2", "backtransform_1",
           "reconstruct", "derivative")
@@ -62,10 +62,14 @@ def load(path: str | None = None):
         lib.scs_psd_proj.argtypes = [vp, vp, vp, i64, op, vp]
         lib.scs_psd_proj_batched.argtypes = [vp, vp, vp, vp, vp, i32, op, vp]
         lib.scs_psd_proj_vjp.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, op, vp]
+        lib.scs_psd_proj_store.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, op, vp]
+        lib.scs_psd_vjp_stored.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, op, vp]
         lib.scs_psd_reserve.argtypes = [vp, i64, i32, op]
         lib.scs_psd_status.argtypes = [vp, ctypes.POINTER(i32)]
         lib.scs_psd_last_launch_count.argtypes = [vp]
         lib.scs_psd_last_launch_count.restype = i64
+        lib.scs_psd_last_replayed.argtypes = [vp]
+        lib.scs_psd_last_replayed.restype = ctypes.c_int
         lib.scs_psd_trace.argtypes = [vp, ctypes.c_int]
         lib.scs_psd_trace_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
         lib.scs_psd_strerror.argtypes = [ctypes.c_int]
@@ -102,8 +106,8 @@ def handle(device: int):
 
 
 def make_opts(precision: int = FP64, side: int = 0, band: int = 0, wait_limit_cycles: int = 0,
-              recompute: int = 0, mem_budget_bytes: int = 0) -> Opts:
-    return Opts(precision, side, recompute, band, mem_budget_bytes, wait_limit_cycles)
+              recompute: int = 0, mem_budget_bytes: int = 0, graphs: bool = True) -> Opts:
+    return Opts(precision, side, recompute, band, mem_budget_bytes, wait_limit_cycles, 0 if graphs else 1, 0)
 
 
 def _ptr(t):
@@ -184,6 +188,64 @@ def proj_vjp(x, g, sides, xbar=None, y=None, opts: Opts | None = None, offsets=N
     return xbar
 
 
+def _shape_arrays(sides, offsets):
+    if offsets is None:
+        return shapes(sides)
+    return (np.ascontiguousarray(np.asarray(offsets, dtype=np.int64)),
+            np.ascontiguousarray(np.asarray(sides, dtype=np.int32)))
+
+
+def eig_sizes(sides) -> tuple[int, int]:
+    """Doubles of a stored eigendecomposition: (sum n^2 for V, sum n for lam)."""
+    s = np.asarray(sides, dtype=np.int64)
+    return int((s * s).sum()), int(s.sum())
+
+
+def proj_store(x, sides, y=None, V=None, lam=None, opts: Opts | None = None, offsets=None, want_y=True):
+    """y = Pi(x) and every eigenpair (V, lam) of every cone (C-ABI scs_psd_proj_store).
+    Returns (y or None, V, lam)."""
+    import torch
+    _check_tensor(x, "x")
+    offsets, sides = _shape_arrays(sides, offsets)
+    nv, nl = eig_sizes(sides)
+    if want_y and y is None:
+        y = torch.empty_like(x)
+    if V is None:
+        V = torch.empty(nv, dtype=torch.float64, device=x.device)
+    if lam is None:
+        lam = torch.empty(nl, dtype=torch.float64, device=x.device)
+    _check_tensor(V, "V")
+    _check_tensor(lam, "lam")
+    if V.numel() < nv or lam.numel() < nl:
+        raise ValueError("V or lam too small for the shapes")
+    rc = load().scs_psd_proj_store(handle(x.device.index), _ptr(x), _ptr(y), _ptr(V), _ptr(lam),
+                                   offsets.ctypes.data_as(ctypes.c_void_p), sides.ctypes.data_as(ctypes.c_void_p),
+                                   int(sides.size), ctypes.byref(opts) if opts is not None else None,
+                                   _stream_ptr(x))
+    _check(rc, "scs_psd_proj_store")
+    return y, V, lam
+
+
+def vjp_stored(V, lam, g, sides, xbar=None, opts: Opts | None = None, offsets=None):
+    """xbar = DPi(X)^T g from an eigendecomposition kept by proj_store (C-ABI scs_psd_vjp_stored)."""
+    import torch
+    _check_tensor(V, "V")
+    _check_tensor(lam, "lam")
+    _check_tensor(g, "g")
+    offsets, sides = _shape_arrays(sides, offsets)
+    nv, nl = eig_sizes(sides)
+    if V.numel() < nv or lam.numel() < nl:
+        raise ValueError("V or lam too small for the shapes")
+    if xbar is None:
+        xbar = torch.empty_like(g)
+    rc = load().scs_psd_vjp_stored(handle(g.device.index), _ptr(V), _ptr(lam), _ptr(g), _ptr(xbar),
+                                   offsets.ctypes.data_as(ctypes.c_void_p), sides.ctypes.data_as(ctypes.c_void_p),
+                                   int(sides.size), ctypes.byref(opts) if opts is not None else None,
+                                   _stream_ptr(g))
+    _check(rc, "scs_psd_vjp_stored")
+    return xbar
+
+
 def status(device: int = 0) -> int:
     """Synchronise and return the device status of the work since the last query."""
     v = ctypes.c_int32(0)
@@ -193,6 +255,11 @@ def status(device: int = 0) -> int:
 
 def last_launch_count(device: int = 0) -> int:
     return int(load().scs_psd_last_launch_count(handle(device)))
+
+
+def last_replayed(device: int = 0) -> bool:
+    """True if the last call on the device replayed a recorded CUDA graph."""
+    return load().scs_psd_last_replayed(handle(device)) == 1
 
 
 def trace(enable: bool, device: int = 0) -> None:

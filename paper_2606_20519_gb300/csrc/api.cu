@@ -79,8 +79,8 @@ struct Plan {
   int* ints_d = nullptr;
   GemmDesc* descs_d = nullptr;
   MergeNode* nodes_d = nullptr;
-  int64_t* triv_offs_d = nullptr;
-  int* triv_sides_d = nullptr;
+  int64_t* triv_offs_d = nullptr;  // 3 * ntriv: svec, V and lam offsets of the side-1 cones
+  int64_t vtotal = 0, ltotal = 0;   // doubles of a stored eigendecomposition (sum n^2, sum n)
   int* status_d = nullptr;  // ncones + 1 (last: trivial cones)
   int* prog_d = nullptr;
   size_t prog_count = 0;
@@ -93,15 +93,18 @@ struct Plan {
   std::vector<GemmLaunch> bt1;  // 3 per panel, reverse order
   GemmLaunch vjp[4];
   int64_t launches = 0;
-  // graph
-  cudaGraphExec_t gexec = nullptr;
-  const void* g_x = nullptr;
-  const void* g_y = nullptr;
-  const void* g_g = nullptr;
-  const void* g_xbar = nullptr;
+  IoSlot* io_d = nullptr;  // the caller's buffers of the current call
+  // Recorded launch sequences, one per output mode (MODE_* bits),
+  // with the wait limit they were recorded with.
+  int64_t eager_runs = 0;
+  cudaGraphExec_t gexec[16] = {};
+  long long gwait[16] = {};
+  int64_t glaunches[16] = {};
+  bool gfailed[16] = {};
   bool arena_owned = false;  // memory carved from a caller-provided region (not freed here)
   ~Plan() {
-    if (gexec) cudaGraphExecDestroy(gexec);
+    for (cudaGraphExec_t ge : gexec)
+      if (ge) cudaGraphExecDestroy(ge);
     if (!arena_owned && cone_mem) cudaFree(cone_mem);
     if (!arena_owned && meta_mem) cudaFree(meta_mem);
   }
@@ -113,6 +116,8 @@ struct scs_psd_handle_s {
   int device = 0;
   int sms = 0;
   bool trace = false;
+  bool last_replayed = false;
+  cudaStream_t capture_stream = nullptr;  // records graphs; never executes work
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> trace_ev;
   int* status_word = nullptr;  // device
   cudaStream_t last_stream = nullptr;
@@ -280,14 +285,26 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
 
   // ---- cones of the main path (n >= 2) and trivial ones
   std::vector<int> big;
-  std::vector<int64_t> triv_offs;
-  std::vector<int> triv_sides;
+  std::vector<int64_t> triv_offs, triv_voff, triv_loff;
+  std::vector<int64_t> voff(count + 1, 0), loff(count + 1, 0);
+  for (int i = 0; i < count; ++i) {
+    voff[i + 1] = voff[i] + (int64_t)sides[i] * sides[i];
+    loff[i + 1] = loff[i] + sides[i];
+  }
+  P.vtotal = voff[count];
+  P.ltotal = loff[count];
   for (int i = 0; i < count; ++i) {
     if (sides[i] >= 2) big.push_back(i);
-    else if (sides[i] == 1) { triv_offs.push_back(P.offsets[i]); triv_sides.push_back(1); }
+    else if (sides[i] == 1) {
+      triv_offs.push_back(P.offsets[i]);
+      triv_voff.push_back(voff[i]);
+      triv_loff.push_back(loff[i]);
+    }
   }
   P.ncones = (int)big.size();
   P.ntriv = (int)triv_offs.size();
+  triv_offs.insert(triv_offs.end(), triv_voff.begin(), triv_voff.end());
+  triv_offs.insert(triv_offs.end(), triv_loff.begin(), triv_loff.end());
   std::vector<ConeLayout> lay(P.ncones);
   std::vector<int> path(P.ncones);
   size_t cone_bytes = 0;
@@ -334,6 +351,8 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
     ConeDev& d = cones[c];
     d.n = n;
     d.xoff = P.offsets[big[c]];
+    d.voff = voff[big[c]];
+    d.loff = loff[big[c]];
     d.path = path[c];
     d.b = b;
     d.npanels = path[c] ? 0 : num_panels(n, b);
@@ -639,9 +658,10 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   const size_t ints_b = align_up(sizeof(int) * std::max<size_t>(1, mb.ints.size()));
   const size_t descs_b = align_up(sizeof(GemmDesc) * std::max<size_t>(1, mb.descs.size()));
   const size_t nodes_b = align_up(sizeof(MergeNode) * std::max<size_t>(1, mb.nodes.size()));
-  const size_t triv_b = align_up((sizeof(int64_t) + sizeof(int)) * std::max(1, P.ntriv));
+  const size_t triv_b = align_up(3 * sizeof(int64_t) * std::max(1, P.ntriv));
   const size_t scratch_b = align_up(sizeof(double) * std::max<int64_t>(1, mb.scratch_doubles));
-  const size_t total = cones_b + ints_b + descs_b + nodes_b + triv_b + scratch_b;
+  const size_t io_b = align_up(sizeof(IoSlot));
+  const size_t total = cones_b + ints_b + descs_b + nodes_b + triv_b + scratch_b + io_b;
   if (arena) {
     P.arena_owned = true;
     if (!(P.meta_mem = arena->take(total))) return SCS_PSD_EINVAL;
@@ -654,8 +674,8 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   P.descs_d = (GemmDesc*)(mbase + cones_b + ints_b);
   P.nodes_d = (MergeNode*)(mbase + cones_b + ints_b + descs_b);
   P.triv_offs_d = (int64_t*)(mbase + cones_b + ints_b + descs_b + nodes_b);
-  P.triv_sides_d = (int*)(P.triv_offs_d + std::max(1, P.ntriv));
   double* scratch = (double*)(mbase + cones_b + ints_b + descs_b + nodes_b + triv_b);
+  P.io_d = (IoSlot*)(mbase + cones_b + ints_b + descs_b + nodes_b + triv_b + scratch_b);
   for (size_t q = 0; q < mb.descs.size(); ++q)
     mb.descs[q].partial = mb.part_off[q] >= 0 ? scratch + mb.part_off[q] : nullptr;
   P.status_d = P.ints_d + status_off;
@@ -685,8 +705,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   if (e == cudaSuccess) e = up(P.descs_d, mb.descs.data(), sizeof(GemmDesc) * mb.descs.size());
   if (e == cudaSuccess) e = up(P.nodes_d, mb.nodes.data(), sizeof(MergeNode) * mb.nodes.size());
   if (e == cudaSuccess && P.ntriv) {
-    e = up(P.triv_offs_d, triv_offs.data(), sizeof(int64_t) * P.ntriv);
-    if (e == cudaSuccess) e = up(P.triv_sides_d, triv_sides.data(), sizeof(int) * P.ntriv);
+    e = up(P.triv_offs_d, triv_offs.data(), sizeof(int64_t) * 3 * P.ntriv);
   }
   for (int c = 0; c < P.ncones && e == cudaSuccess; ++c) e = up(cones[c].kinfo, &kin_all[(size_t)c * 8], 8 * sizeof(int));
   if (e != cudaSuccess) return SCS_PSD_ECUDA;
@@ -738,98 +757,108 @@ struct PhaseMark {
   }
 };
 
-// The launch sequence of one call.
-int run_plan(scs_psd_handle h, Plan& P, const double* x, double* y, const double* g, double* xbar,
-             long long wait_limit, cudaStream_t s) {
-  int64_t n_launch = 0;
+// The launch sequence of one call (MODE_* bits) after the caller's buffers
+// are in P.io_d.
+int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStream_t s, int64_t& n_launch) {
   int rc;
+  const bool want_y = (mode & MODE_Y) != 0, want_vjp = (mode & MODE_VJP) != 0;
+  const IoSlot* io = P.io_d;
   PhaseMark pm{h, s};
   CUDA_TRY(cudaMemsetAsync(P.status_d, 0, sizeof(int) * (P.ncones + 1), s));
   if (P.prog_count) CUDA_TRY(cudaMemsetAsync(P.prog_d, 0, sizeof(int) * P.prog_count, s));
-  if (P.ntriv && y) {
-    launch_trivial(P.triv_offs_d, P.triv_sides_d, P.ntriv, x, y, P.status_d, s);
+  if (P.ntriv) {
+    launch_trivial(P.triv_offs_d, P.ntriv, io, mode, P.status_d, s);
     LAUNCH_CHECK();
   }
   if (P.ncones) {
     const int nc = P.ncones;
-    pm.begin(0);
-    launch_unpack(P.cones_d, nc, P.maxn * P.maxn, x, s);
-    LAUNCH_CHECK();
-    pm.begin(1);
-    for (const PanelStep& ps : P.panels) {
-      launch_panel(P.cones_d, P.ints_d + ps.ids_off, ps.njobs, ps.panel, P.b, ps.cluster, ps.R, s);
+    if (mode & MODE_IMPORT) {
+      launch_import_eig(P.cones_d, nc, P.maxn, io, s);
       LAUNCH_CHECK();
-      for (int q = 0; q < 6; ++q)
-        if ((rc = run_gemm(P, ps.g[q], s, n_launch))) return rc;
-    }
-    if (!P.sytrd1.empty()) {
+    } else {
+      pm.begin(0);
+      launch_unpack(P.cones_d, nc, P.maxn * P.maxn, io, 0, s);
+      LAUNCH_CHECK();
       pm.begin(1);
-      for (const Sytrd1Launch& sl : P.sytrd1) {
-        if (launch_sytrd1(P.cones_d, P.ints_d + sl.cone_off, P.ints_d + sl.rank_off, P.ints_d + sl.count_off,
-                          sl.nctas, sl.maxn, wait_limit, s))
+      for (const PanelStep& ps : P.panels) {
+        launch_panel(P.cones_d, P.ints_d + ps.ids_off, ps.njobs, ps.panel, P.b, ps.cluster, ps.R, s);
+        LAUNCH_CHECK();
+        for (int q = 0; q < 6; ++q)
+          if ((rc = run_gemm(P, ps.g[q], s, n_launch))) return rc;
+      }
+      if (!P.sytrd1.empty()) {
+        pm.begin(1);
+        for (const Sytrd1Launch& sl : P.sytrd1) {
+          if (launch_sytrd1(P.cones_d, P.ints_d + sl.cone_off, P.ints_d + sl.rank_off, P.ints_d + sl.count_off,
+                            sl.nctas, sl.maxn, wait_limit, s))
+            return SCS_PSD_ECUDA;
+          LAUNCH_CHECK();
+        }
+        pm.begin(5);
+        launch_larft1(P.cones_d, P.ints_d + P.larft_cone_off, P.ints_d + P.larft_idx_off, P.nlarft, s);
+        LAUNCH_CHECK();
+      }
+      pm.begin(2);
+      launch_band_extract(P.cones_d, nc, P.maxn, s);
+      LAUNCH_CHECK();
+      for (const BulgeLaunch& bl : P.bulges) {
+        if (launch_bulge(P.cones_d, bl.ncones, P.ints_d + bl.cone_off, P.ints_d + bl.rank_off,
+                         P.ints_d + bl.count_off, bl.nctas, P.b, wait_limit, s))
           return SCS_PSD_ECUDA;
         LAUNCH_CHECK();
       }
-      pm.begin(5);
-      launch_larft1(P.cones_d, P.ints_d + P.larft_cone_off, P.ints_d + P.larft_idx_off, P.nlarft, s);
+      launch_tridiag_extract(P.cones_d, nc, P.maxn, s);
       LAUNCH_CHECK();
-    }
-    pm.begin(2);
-    launch_band_extract(P.cones_d, nc, P.maxn, s);
-    LAUNCH_CHECK();
-    for (const BulgeLaunch& bl : P.bulges) {
-      if (launch_bulge(P.cones_d, bl.ncones, P.ints_d + bl.cone_off, P.ints_d + bl.rank_off,
-                       P.ints_d + bl.count_off, bl.nctas, P.b, wait_limit, s))
-        return SCS_PSD_ECUDA;
+      pm.begin(3);
+      launch_dc_leaves(P.cones_d, nc, P.maxn, s);
       LAUNCH_CHECK();
-    }
-    launch_tridiag_extract(P.cones_d, nc, P.maxn, s);
-    LAUNCH_CHECK();
-    pm.begin(3);
-    launch_dc_leaves(P.cones_d, nc, P.maxn, s);
-    LAUNCH_CHECK();
-    for (const Level& lv : P.levels) {
-      const MergeNode* nodes = P.nodes_d + lv.nodes_off;
-      const int* pos = P.ints_d + lv.pos_off;
-      launch_dc_prepare(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
-      LAUNCH_CHECK();
-      launch_dc_build_qin(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
-      LAUNCH_CHECK();
-      launch_dc_apply_rot(P.cones_d, nodes, pos, P.total_pos, s);
-      LAUNCH_CHECK();
-      launch_dc_secular(P.cones_d, nodes, pos, P.total_pos, s);
-      LAUNCH_CHECK();
-      launch_dc_loewner(P.cones_d, nodes, pos, P.total_pos, s);
-      LAUNCH_CHECK();
-      launch_dc_select(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
-      LAUNCH_CHECK();
-      launch_dc_vecnorm(P.cones_d, nodes, pos, P.total_pos, s);
-      LAUNCH_CHECK();
-      launch_dc_vectors(P.cones_d, nodes, pos, P.total_pos, lv.maxK, s);
-      LAUNCH_CHECK();
-      if ((rc = run_gemm(P, lv.g, s, n_launch))) return rc;
-      launch_dc_copy_deflated(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
-      LAUNCH_CHECK();
-    }
-    pm.begin(4);
-    launch_backtr2(P.cones_d, nc, (int)P.maxn, (int)P.maxn, P.allv ? (int)P.maxn : (int)(P.maxn + 1) / 2, P.b, s);
-    LAUNCH_CHECK();
-    pm.begin(5);
-    for (const GemmLaunch& gl : P.bt1)
-      if ((rc = run_gemm(P, gl, s, n_launch))) return rc;
-    if (y) {
-      pm.begin(6);
-      if (P.recon_tc.count > 0) {
-        if ((rc = run_gemm(P, P.recon_tc, s, n_launch))) return rc;
-        launch_pack_recon(P.cones_d, nc, P.maxn, x, y, s);
-      } else {
-        launch_recon(P.cones_d, nc, (int)P.maxn, x, y, s);
+      for (const Level& lv : P.levels) {
+        const MergeNode* nodes = P.nodes_d + lv.nodes_off;
+        const int* pos = P.ints_d + lv.pos_off;
+        launch_dc_prepare(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
+        LAUNCH_CHECK();
+        launch_dc_build_qin(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
+        LAUNCH_CHECK();
+        launch_dc_apply_rot(P.cones_d, nodes, pos, P.total_pos, s);
+        LAUNCH_CHECK();
+        launch_dc_secular(P.cones_d, nodes, pos, P.total_pos, s);
+        LAUNCH_CHECK();
+        launch_dc_loewner(P.cones_d, nodes, pos, P.total_pos, s);
+        LAUNCH_CHECK();
+        launch_dc_select(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
+        LAUNCH_CHECK();
+        launch_dc_vecnorm(P.cones_d, nodes, pos, P.total_pos, s);
+        LAUNCH_CHECK();
+        launch_dc_vectors(P.cones_d, nodes, pos, P.total_pos, lv.maxK, s);
+        LAUNCH_CHECK();
+        if ((rc = run_gemm(P, lv.g, s, n_launch))) return rc;
+        launch_dc_copy_deflated(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
+        LAUNCH_CHECK();
       }
+      pm.begin(4);
+      launch_backtr2(P.cones_d, nc, (int)P.maxn, (int)P.maxn, P.allv ? (int)P.maxn : (int)(P.maxn + 1) / 2, P.b, s);
       LAUNCH_CHECK();
+      pm.begin(5);
+      for (const GemmLaunch& gl : P.bt1)
+        if ((rc = run_gemm(P, gl, s, n_launch))) return rc;
+      if (mode & MODE_EXPORT) {
+        launch_export_eig(P.cones_d, nc, P.maxn, io, s);
+        LAUNCH_CHECK();
+      }
+      if (want_y) {
+        pm.begin(6);
+        if (P.recon_tc.count > 0) {
+          if ((rc = run_gemm(P, P.recon_tc, s, n_launch))) return rc;
+          launch_pack_recon(P.cones_d, nc, P.maxn, io, s);
+        } else {
+          launch_recon(P.cones_d, nc, (int)P.maxn, io, s);
+        }
+        LAUNCH_CHECK();
+      }
     }
-    if (g && xbar) {
+    if (want_vjp) {
       pm.begin(7);
-      launch_unpack(P.cones_d, nc, P.maxn * P.maxn, g, s);
+      launch_unpack(P.cones_d, nc, P.maxn * P.maxn, io, 1, s);
       LAUNCH_CHECK();
       if ((rc = run_gemm(P, P.vjp[0], s, n_launch))) return rc;
       if ((rc = run_gemm(P, P.vjp[1], s, n_launch))) return rc;
@@ -837,13 +866,76 @@ int run_plan(scs_psd_handle h, Plan& P, const double* x, double* y, const double
       LAUNCH_CHECK();
       if ((rc = run_gemm(P, P.vjp[2], s, n_launch))) return rc;
       if ((rc = run_gemm(P, P.vjp[3], s, n_launch))) return rc;
-      launch_pack_lower(P.cones_d, nc, P.maxn, xbar, s);
+      launch_pack_lower(P.cones_d, nc, P.maxn, io, s);
       LAUNCH_CHECK();
     }
   }
   pm.end();
   launch_status_reduce(P.status_d, P.ncones + 1, h->status_word, s);
   LAUNCH_CHECK();
+  return SCS_PSD_OK;
+}
+
+// Records the launch sequence of `mode` as a graph on the handle's capture
+// stream (recording executes nothing).  A sequence that cannot be recorded
+// is marked and stays eager.
+void record_graph(scs_psd_handle h, Plan& P, int mode, long long wait_limit) {
+  if (P.gexec[mode]) {
+    cudaGraphExecDestroy(P.gexec[mode]);
+    P.gexec[mode] = nullptr;
+  }
+  if (!h->capture_stream && cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    h->capture_stream = nullptr;
+    P.gfailed[mode] = true;
+    return;
+  }
+  cudaStream_t cs = h->capture_stream;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    P.gfailed[mode] = true;
+    return;
+  }
+  int64_t n_launch = 0;
+  const int rc = run_body(h, P, mode, wait_limit, cs, n_launch);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  cudaGraphExec_t ge = nullptr;
+  if (rc == SCS_PSD_OK && e == cudaSuccess && graph && cudaGraphInstantiate(&ge, graph, 0) == cudaSuccess) {
+    P.gexec[mode] = ge;
+    P.gwait[mode] = wait_limit;
+    P.glaunches[mode] = n_launch;
+  } else {
+    P.gfailed[mode] = true;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+}
+
+// One call: publish the caller's buffers, then run the launch sequence --
+// eagerly on the first call of a plan (and whenever tracing, or when the
+// caller's stream is itself being captured), as a recorded graph after that.
+int run_plan(scs_psd_handle h, Plan& P, const IoSlot& io, int mode, long long wait_limit, cudaStream_t s,
+             bool allow_graph) {
+  int64_t n_launch = 0;
+  launch_set_io(P.io_d, io, s);
+  LAUNCH_CHECK();
+  h->last_replayed = false;
+  if (allow_graph && !h->trace && P.eager_runs > 0 && !P.gfailed[mode]) {
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cst) == cudaSuccess && cst == cudaStreamCaptureStatusNone) {
+      if (!P.gexec[mode] || P.gwait[mode] != wait_limit) record_graph(h, P, mode, wait_limit);
+      if (P.gexec[mode]) {
+        CUDA_TRY(cudaGraphLaunch(P.gexec[mode], s));
+        P.launches = n_launch + P.glaunches[mode];
+        h->last_replayed = true;
+        return SCS_PSD_OK;
+      }
+    }
+    cudaGetLastError();
+  }
+  const int rc = run_body(h, P, mode, wait_limit, s, n_launch);
+  if (rc) return rc;
+  ++P.eager_runs;
   P.launches = n_launch;
   return SCS_PSD_OK;
 }
@@ -870,18 +962,25 @@ int check_shapes(const int64_t* offsets, const int32_t* sides, int32_t count) {
   return SCS_PSD_OK;
 }
 
-int do_call(scs_psd_handle h, const double* x, double* y, const double* g, double* xbar, const int64_t* offsets,
-            const int32_t* sides, int32_t count, const scs_psd_opts* opts, void* stream, int allv) {
+// One call of any entry point: `mode` (MODE_* bits) says which of io's
+// buffers are read and written; every one it names must be non-NULL.
+int do_call(scs_psd_handle h, const IoSlot& io, int mode, const int64_t* offsets, const int32_t* sides,
+            int32_t count, const scs_psd_opts* opts, void* stream) {
   if (!h) return SCS_PSD_EINVAL;
   int rc = check_shapes(offsets, sides, count);
   if (rc) return rc;
   if (count == 0 || offsets[count] == 0) return SCS_PSD_OK;
-  if (!x || (!y && !xbar)) return SCS_PSD_EINVAL;
-  if (allv && (!g || !xbar)) return SCS_PSD_EINVAL;
+  if (!(mode & MODE_IMPORT) && !io.x) return SCS_PSD_EINVAL;
+  if ((mode & MODE_Y) && !io.y) return SCS_PSD_EINVAL;
+  if ((mode & MODE_VJP) && (!io.g || !io.xbar)) return SCS_PSD_EINVAL;
+  if ((mode & (MODE_EXPORT | MODE_IMPORT)) && (!io.V || !io.lam)) return SCS_PSD_EINVAL;
+  // every mode but the plain projection needs all n eigenpairs of each cone
+  const int allv = (mode & (MODE_VJP | MODE_EXPORT | MODE_IMPORT)) ? 1 : 0;
   int b = kDefaultBand, side = 0, precision = SCS_PSD_FP64;
   long long wait = kDefaultWaitCycles;
   if (opts) {
     if (opts->precision != SCS_PSD_FP64 && opts->precision != SCS_PSD_SPLIT_TF32) return SCS_PSD_EINVAL;
+    if (opts->graphs < 0 || opts->graphs > 1 || opts->reserved != 0) return SCS_PSD_EINVAL;
     precision = opts->precision;
     if (opts->band) b = opts->band;
     side = opts->side;
@@ -911,7 +1010,7 @@ int do_call(scs_psd_handle h, const double* x, double* y, const double* g, doubl
   } else {
     P = it->second.get();
   }
-  rc = run_plan(h, *P, x, y, g, xbar, wait, s);
+  rc = run_plan(h, *P, io, mode, wait, s, !(opts && opts->graphs == 1));
   h->last_stream = s;
   h->last_launches = P->launches;
   return rc;
@@ -971,7 +1070,8 @@ int proj_static(const double* x, double* y, int64_t n, void* stream) {
     st.plan_n = n;
   }
   if (cudaMemsetAsync(st.hview.status_word, 0, sizeof(int), s) != cudaSuccess) return SCS_PSD_ECUDA;
-  return run_plan(&st.hview, *st.plan, x, y, nullptr, nullptr, kDefaultWaitCycles, s);
+  const IoSlot io{x, y, nullptr, nullptr, nullptr, nullptr};
+  return run_plan(&st.hview, *st.plan, io, MODE_Y, kDefaultWaitCycles, s, false);
 }
 
 }  // namespace
@@ -1004,6 +1104,7 @@ int scs_psd_destroy(scs_psd_handle h) {
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
   h->plans.clear();
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   cudaFree(h->status_word);
   delete h;
   return SCS_PSD_OK;
@@ -1015,19 +1116,34 @@ int scs_psd_proj(scs_psd_handle h, const double* x, double* y, int64_t n, const 
   const int64_t offs[2] = {0, svec_len(n)};
   const int32_t sides[1] = {(int32_t)n};
   if (!y) return SCS_PSD_EINVAL;
-  return do_call(h, x, y, nullptr, nullptr, offs, sides, 1, opts, stream, 0);
+  const IoSlot io{x, y, nullptr, nullptr, nullptr, nullptr};
+  return do_call(h, io, MODE_Y, offs, sides, 1, opts, stream);
 }
 
 int scs_psd_proj_batched(scs_psd_handle h, const double* x, double* y, const int64_t* offsets, const int32_t* sides,
                          int32_t count, const scs_psd_opts* opts, void* stream) {
-  if (!y && count > 0) return SCS_PSD_EINVAL;
-  return do_call(h, x, y, nullptr, nullptr, offsets, sides, count, opts, stream, 0);
+  const IoSlot io{x, y, nullptr, nullptr, nullptr, nullptr};
+  return do_call(h, io, MODE_Y, offsets, sides, count, opts, stream);
 }
 
 int scs_psd_proj_vjp(scs_psd_handle h, const double* x, const double* g, double* xbar, double* y,
                      const int64_t* offsets, const int32_t* sides, int32_t count, const scs_psd_opts* opts,
                      void* stream) {
-  return do_call(h, x, y, g, xbar, offsets, sides, count, opts, stream, 1);
+  const IoSlot io{x, y, g, xbar, nullptr, nullptr};
+  return do_call(h, io, MODE_VJP | (y ? MODE_Y : 0), offsets, sides, count, opts, stream);
+}
+
+int scs_psd_proj_store(scs_psd_handle h, const double* x, double* y, double* V, double* lam, const int64_t* offsets,
+                       const int32_t* sides, int32_t count, const scs_psd_opts* opts, void* stream) {
+  const IoSlot io{x, y, nullptr, nullptr, V, lam};
+  return do_call(h, io, MODE_EXPORT | (y ? MODE_Y : 0), offsets, sides, count, opts, stream);
+}
+
+int scs_psd_vjp_stored(scs_psd_handle h, const double* V, const double* lam, const double* g, double* xbar,
+                       const int64_t* offsets, const int32_t* sides, int32_t count, const scs_psd_opts* opts,
+                       void* stream) {
+  const IoSlot io{nullptr, nullptr, g, xbar, const_cast<double*>(V), const_cast<double*>(lam)};
+  return do_call(h, io, MODE_IMPORT | MODE_VJP, offsets, sides, count, opts, stream);
 }
 
 int scs_psd_reserve(scs_psd_handle h, int64_t max_n, int32_t max_count, const scs_psd_opts* opts) {
@@ -1052,6 +1168,8 @@ int scs_psd_status(scs_psd_handle h, int32_t* device_status) {
 }
 
 int64_t scs_psd_last_launch_count(scs_psd_handle h) { return h ? h->last_launches : -1; }
+
+int scs_psd_last_replayed(scs_psd_handle h) { return h ? (h->last_replayed ? 1 : 0) : -1; }
 
 int scs_psd_trace(scs_psd_handle h, int enable) {
   if (!h) return SCS_PSD_EINVAL;

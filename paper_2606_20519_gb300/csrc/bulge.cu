@@ -232,9 +232,17 @@ int bulge_max_ctas(int b) {
 int launch_bulge(const ConeDev* cones, int ncones, const int* cta_cone, const int* cta_rank, const int* cta_count,
                  int nctas, int b, long long wait_limit, cudaStream_t s) {
   if (ncones <= 0 || nctas <= 0) return 0;
-  void* args[] = {(void*)&cones, (void*)&cta_cone, (void*)&cta_rank, (void*)&cta_count, (void*)&b,
-                  (void*)&wait_limit};
-  return (int)cudaLaunchCooperativeKernel((void*)bulge_kernel, dim3(nctas), dim3(kBulgeThreads), args, 0, s);
+  // co-resident CTAs (they wait on one another); the attribute also survives graph recording
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nctas);
+  cfg.blockDim = dim3(kBulgeThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&cfg, bulge_kernel, cones, cta_cone, cta_rank, cta_count, b, wait_limit);
 }
 
 }  // namespace scs

@@ -77,6 +77,8 @@ void launch_gemm(const GemmDesc* descs, const int* tile_prefix, int count, int t
 struct ConeDev {
   int64_t n;
   int64_t xoff;     // offset of the cone in the svec buffers
+  int64_t voff;     // offset of the cone's n x n eigenvector block in IoSlot::V
+  int64_t loff;     // offset of the cone's n eigenvalues in IoSlot::lam
   int path;         // 0: two-stage (dense -> band -> tridiagonal), 1: one-stage tridiagonalisation
   int b;            // bandwidth of stage 1 / 2
   int npanels;
@@ -131,10 +133,33 @@ struct MergeNode {
   int level;   // tree level (selects the ping-pong buffers)
 };
 
+// The caller's buffers of one call.  Kernels read them from this device slot
+// (written by launch_set_io at the start of every call), so the rest of a
+// call's launch sequence does not depend on them and can be replayed as a
+// recorded graph.
+struct IoSlot {
+  const double* x;
+  double* y;
+  const double* g;
+  double* xbar;
+  double* V;    // all eigenvectors, cone i at voff (n x n column-major): written or read
+  double* lam;  // all eigenvalues, cone i at loff
+};
+
+// Output modes of one call (bits).
+enum : int {
+  MODE_Y = 1,       // y = Pi(x)
+  MODE_VJP = 2,     // xbar = DPi(X)[smat(g)]
+  MODE_EXPORT = 4,  // write the eigendecomposition to io->V, io->lam
+  MODE_IMPORT = 8,  // take the eigendecomposition from io->V, io->lam instead of computing it
+};
+
 // ------------------------------------------------------------------ kernels
-void launch_unpack(const ConeDev* cones, int ncones, int64_t maxn2, const double* x, cudaStream_t s);
-void launch_trivial(const int64_t* offs, const int* sides, int count, const double* x, double* y,
-                    int* status, cudaStream_t s);
+void launch_set_io(IoSlot* slot, const IoSlot& v, cudaStream_t s);
+// which = 0: unpack io->x, 1: unpack io->g
+void launch_unpack(const ConeDev* cones, int ncones, int64_t maxn2, const IoSlot* io, int which, cudaStream_t s);
+// Cones of side 1: y, xbar, (V, lam) by `mode`; offs holds count svec, V and lam offsets each
+void launch_trivial(const int64_t* offs, int count, const IoSlot* io, int mode, int* status, cudaStream_t s);
 void launch_panel(const ConeDev* cones, const int* cone_ids, int njobs, int panel, int b,
                   int cluster, int rows_per_cta, cudaStream_t s);
 void launch_band_extract(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s);
@@ -159,15 +184,18 @@ void launch_dc_vecnorm(const ConeDev* cones, const MergeNode* nodes, const int* 
                        cudaStream_t s);
 void launch_backtr2(const ConeDev* cones, int ncones, int maxn, int maxk, int kexp, int band, cudaStream_t s);
 size_t panel_smem_bytes(int b, int R);
+// Z, lamk (all n eigenpairs) <-> io->V, io->lam
+void launch_export_eig(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s);
+void launch_import_eig(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s);
 void launch_loewner_scale(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s);
-void launch_pack_lower(const ConeDev* cones, int ncones, int64_t maxn, double* xbar, cudaStream_t s);
-void launch_recon(const ConeDev* cones, int ncones, int maxn, const double* x, double* y, cudaStream_t s);
+void launch_pack_lower(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s);
+void launch_recon(const ConeDev* cones, int ncones, int maxn, const IoSlot* io, cudaStream_t s);
 int sytrd1_max_ctas(int maxn);
 int launch_sytrd1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,
                   int maxn, long long wait_limit, cudaStream_t s);
 void launch_larft1(const ConeDev* cones, const int* blk_cone, const int* blk_index, int nblocks, cudaStream_t s);
 // y = svec(S) or x - svec(S) from the lower triangle of S = Z diag(l) Z^T held in QA (split mode)
-void launch_pack_recon(const ConeDev* cones, int ncones, int64_t maxn, const double* x, double* y, cudaStream_t s);
+void launch_pack_recon(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s);
 void launch_status_reduce(const int* status, int count, int* out, cudaStream_t s);
 
 }  // namespace scs

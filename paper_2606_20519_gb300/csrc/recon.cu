@@ -19,7 +19,9 @@ namespace {
 
 constexpr int BM = 64, BK = 16;
 
-__global__ void __launch_bounds__(256) recon_kernel(const ConeDev* __restrict__ cones, const double* x, double* y) {
+__global__ void __launch_bounds__(256) recon_kernel(const ConeDev* __restrict__ cones, const IoSlot* __restrict__ io) {
+  const double* x = io->x;
+  double* y = io->y;
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BM + 1];
   const ConeDev& c = cones[blockIdx.y];
@@ -100,7 +102,9 @@ __global__ void __launch_bounds__(256) recon_kernel(const ConeDev* __restrict__ 
 
 // Split mode: S = Z diag(l) Z^T was formed (lower triangle) in QA by the
 // tensor-core GEMM; write svec(S) (positive part) or x - svec(S).
-__global__ void pack_recon_kernel(const ConeDev* __restrict__ cones, const double* x, double* y) {
+__global__ void pack_recon_kernel(const ConeDev* __restrict__ cones, const IoSlot* __restrict__ io) {
+  const double* x = io->x;
+  double* y = io->y;
   const ConeDev& c = cones[blockIdx.y];
   const int64_t n = c.n;
   const int64_t len = n * (n + 1) / 2;
@@ -127,16 +131,16 @@ __global__ void pack_recon_kernel(const ConeDev* __restrict__ cones, const doubl
 
 }  // namespace
 
-void launch_pack_recon(const ConeDev* cones, int ncones, int64_t maxn, const double* x, double* y, cudaStream_t s) {
+void launch_pack_recon(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s) {
   if (ncones <= 0) return;
   int gx = (int)(maxn < 2048 ? maxn : 2048);
-  pack_recon_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones, x, y);
+  pack_recon_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones, io);
 }
 
-void launch_recon(const ConeDev* cones, int ncones, int maxn, const double* x, double* y, cudaStream_t s) {
+void launch_recon(const ConeDev* cones, int ncones, int maxn, const IoSlot* io, cudaStream_t s) {
   if (ncones <= 0) return;
   const int tiles = (maxn + BM - 1) / BM;
-  recon_kernel<<<dim3(tiles * (tiles + 1) / 2, ncones), 256, 0, s>>>(cones, x, y);
+  recon_kernel<<<dim3(tiles * (tiles + 1) / 2, ncones), 256, 0, s>>>(cones, io);
 }
 
 }  // namespace scs

@@ -14,8 +14,9 @@ namespace {
 __device__ __forceinline__ int64_t svec_col_offset(int64_t n, int64_t j) { return j * n - (j * (j - 1)) / 2; }
 
 // Dense symmetric A (column-major, both triangles) from the svec input.
-__global__ void unpack_kernel(const ConeDev* __restrict__ cones, const double* __restrict__ x) {
+__global__ void unpack_kernel(const ConeDev* __restrict__ cones, const IoSlot* __restrict__ io, int which) {
   const ConeDev& c = cones[blockIdx.y];
+  const double* __restrict__ x = which ? io->g : io->x;
   const int64_t n = c.n;
   const int64_t nn = n * n;
   const double* xs = x + c.xoff;
@@ -31,18 +32,22 @@ __global__ void unpack_kernel(const ConeDev* __restrict__ cones, const double* _
   if (bad) atomicOr(c.status, ST_NONFINITE);
 }
 
-// Cones of side 0 or 1: Pi(x) = max(x, 0).
-__global__ void trivial_kernel(const int64_t* __restrict__ offs, const int* __restrict__ sides, int count,
-                               const double* __restrict__ x, double* __restrict__ y, int* status) {
+// Cones of side 1: X = (x) has V = (1), l = x, so Pi(x) = max(x, 0) and
+// DPi(x)[g] = g for x > 0, 0 otherwise (the derivative taken as 0 at 0).
+// offs: [0, count) svec offsets, [count, 2 count) V offsets, [2 count, 3 count) lam offsets.
+__global__ void trivial_kernel(const int64_t* __restrict__ offs, int count, const IoSlot* __restrict__ io, int mode,
+                               int* status) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
-  if (sides[t] != 1) return;
-  const double v = x[offs[t]];
-  if (!isfinite(v)) {
-    y[offs[t]] = nan("");
-    atomicOr(status, ST_NONFINITE);
-  } else {
-    y[offs[t]] = v > 0.0 ? v : 0.0;
+  const int64_t o = offs[t], ov = offs[count + t], ol = offs[2 * count + t];
+  const double v = (mode & MODE_IMPORT) ? io->lam[ol] : io->x[o];
+  const bool bad = !isfinite(v) || ((mode & MODE_IMPORT) && !isfinite(io->V[ov]));
+  if (bad) atomicOr(status, ST_NONFINITE);
+  if (mode & MODE_Y) io->y[o] = bad ? nan("") : (v > 0.0 ? v : 0.0);
+  if (mode & MODE_VJP) io->xbar[o] = bad ? nan("") : (v > 0.0 ? io->g[o] : 0.0);
+  if (mode & MODE_EXPORT) {
+    io->V[ov] = bad ? nan("") : 1.0;
+    io->lam[ol] = bad ? nan("") : v;
   }
 }
 
@@ -74,6 +79,8 @@ __global__ void tridiag_extract_kernel(const ConeDev* __restrict__ cones) {
   }
 }
 
+__global__ void set_io_kernel(IoSlot* slot, IoSlot v) { *slot = v; }
+
 __global__ void status_reduce_kernel(const int* __restrict__ status, int count, int* out) {
   int v = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) v |= status[i];
@@ -83,17 +90,18 @@ __global__ void status_reduce_kernel(const int* __restrict__ status, int count, 
 
 }  // namespace
 
-void launch_unpack(const ConeDev* cones, int ncones, int64_t maxn2, const double* x, cudaStream_t s) {
+void launch_set_io(IoSlot* slot, const IoSlot& v, cudaStream_t s) { set_io_kernel<<<1, 1, 0, s>>>(slot, v); }
+
+void launch_unpack(const ConeDev* cones, int ncones, int64_t maxn2, const IoSlot* io, int which, cudaStream_t s) {
   if (ncones <= 0) return;
   int gx = (int)((maxn2 + 255) / 256);
   if (gx > 1024) gx = 1024;
-  unpack_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones, x);
+  unpack_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones, io, which);
 }
 
-void launch_trivial(const int64_t* offs, const int* sides, int count, const double* x, double* y, int* status,
-                    cudaStream_t s) {
+void launch_trivial(const int64_t* offs, int count, const IoSlot* io, int mode, int* status, cudaStream_t s) {
   if (count <= 0) return;
-  trivial_kernel<<<(count + 255) / 256, 256, 0, s>>>(offs, sides, count, x, y, status);
+  trivial_kernel<<<(count + 255) / 256, 256, 0, s>>>(offs, count, io, mode, status);
 }
 
 void launch_band_extract(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s) {

@@ -357,8 +357,18 @@ int launch_sytrd1(const ConeDev* cones, const int* cta_cone, const int* cta_rank
                   int maxn, long long wait_limit, cudaStream_t s) {
   if (nctas <= 0) return 0;
   const size_t smem = ((size_t)2 * maxn + kPartMax) * sizeof(double);
-  void* args[] = {(void*)&cones, (void*)&cta_cone, (void*)&cta_rank, (void*)&cta_count, (void*)&wait_limit};
-  return (int)cudaLaunchCooperativeKernel((void*)sytrd1_kernel, dim3(nctas), dim3(kSyThreads), args, smem, s);
+  // co-resident CTAs (they wait on one another); the attribute also survives graph recording
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nctas);
+  cfg.blockDim = dim3(kSyThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&cfg, sytrd1_kernel, cones, cta_cone, cta_rank, cta_count, wait_limit);
 }
 
 void launch_larft1(const ConeDev* cones, const int* blk_cone, const int* blk_index, int nblocks, cudaStream_t s) {

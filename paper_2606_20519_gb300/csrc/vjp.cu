@@ -36,11 +36,44 @@ __global__ void loewner_scale_kernel(const ConeDev* __restrict__ cones) {
   }
 }
 
-// xbar = svec of the lower triangle of H (H = QB here), NaN on a bad cone.
-__global__ void pack_lower_kernel(const ConeDev* __restrict__ cones, const double* __restrict__ H_unused,
-                                  double* xbar) {
-  (void)H_unused;
+// Stored eigendecomposition out: V block = Z (all n columns), lam = lamk;
+// NaN for a cone whose status is bad.
+__global__ void export_eig_kernel(const ConeDev* __restrict__ cones, const IoSlot* __restrict__ io) {
   const ConeDev& c = cones[blockIdx.y];
+  const int64_t n = c.n, nn = n * n;
+  const bool bad = *c.status != 0;
+  double* V = io->V + c.voff;
+  double* lam = io->lam + c.loff;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
+    V[e] = bad ? nan("") : c.Z[e];
+    if (e < n) lam[e] = bad ? nan("") : c.lamk[e];
+  }
+}
+
+// Stored eigendecomposition in, in place of the eigensolver's output.
+__global__ void import_eig_kernel(const ConeDev* __restrict__ cones, const IoSlot* __restrict__ io) {
+  const ConeDev& c = cones[blockIdx.y];
+  const int64_t n = c.n, nn = n * n;
+  const double* V = io->V + c.voff;
+  const double* lam = io->lam + c.loff;
+  bool bad = false;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = V[e];
+    bad |= !isfinite(v);
+    c.Z[e] = v;
+    if (e < n) {
+      const double l = lam[e];
+      bad |= !isfinite(l);
+      c.lamk[e] = l;
+    }
+  }
+  if (bad) atomicOr(c.status, ST_NONFINITE);
+}
+
+// xbar = svec of the lower triangle of H (H = QB here), NaN on a bad cone.
+__global__ void pack_lower_kernel(const ConeDev* __restrict__ cones, const IoSlot* __restrict__ io) {
+  const ConeDev& c = cones[blockIdx.y];
+  double* xbar = io->xbar;
   const int64_t n = c.n;
   const int64_t len = n * (n + 1) / 2;
   const bool bad = *c.status != 0;
@@ -68,11 +101,25 @@ void launch_loewner_scale(const ConeDev* cones, int ncones, int64_t maxn, cudaSt
   loewner_scale_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones);
 }
 
-void launch_pack_lower(const ConeDev* cones, int ncones, int64_t maxn, double* xbar, cudaStream_t s) {
+void launch_export_eig(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s) {
+  if (ncones <= 0) return;
+  int gx = (int)((maxn * maxn + 255) / 256);
+  if (gx > 2048) gx = 2048;
+  export_eig_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones, io);
+}
+
+void launch_import_eig(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s) {
+  if (ncones <= 0) return;
+  int gx = (int)((maxn * maxn + 255) / 256);
+  if (gx > 2048) gx = 2048;
+  import_eig_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones, io);
+}
+
+void launch_pack_lower(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s) {
   if (ncones <= 0) return;
   int gx = (int)((maxn * (maxn + 1) / 2 + 255) / 256);
   if (gx > 2048) gx = 2048;
-  pack_lower_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones, nullptr, xbar);
+  pack_lower_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones, io);
 }
 
 }  // namespace scs
