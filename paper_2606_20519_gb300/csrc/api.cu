@@ -91,6 +91,7 @@ struct Plan {
   int nlarft = 0, larft_cone_off = 0, larft_idx_off = 0;
   std::vector<Level> levels;
   std::vector<GemmLaunch> bt1;  // 3 per panel, reverse order
+  int bt1k_nctas = 0, bt1k_cone_off = 0, bt1k_rank_off = 0, bt1k_count_off = 0, bt1k_maxn = 0;  // fused kernel
   GemmLaunch vjp[4];
   int64_t launches = 0;
   IoSlot* io_d = nullptr;  // the caller's buffers of the current call
@@ -582,10 +583,48 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   }
 
   // ---- stage-1 back-transformation (two-stage cones: band-reduction panels;
-  // one-stage cones: 32-reflector blocks), last block first
+  // one-stage cones: 32-reflector blocks), last block first.  FP64 one-stage
+  // cones use the fused kernel (a slab of columns per CTA, CTAs given to the
+  // cones in proportion to their work n^2 k); the rest use grouped GEMMs.
+  auto fused_bt1 = [&](const ConeDev& d) {
+    return !mb.split && d.path == 1 && d.n >= 3 && d.n <= bt1_max_side();
+  };
+  {
+    std::vector<int> fc;
+    double wsum = 0.0;
+    for (int c = 0; c < P.ncones; ++c)
+      if (fused_bt1(cones[c])) {
+        fc.push_back(c);
+        const double n = (double)cones[c].n;
+        wsum += n * n * (allv ? n : 0.5 * n);
+      }
+    if (!fc.empty()) {
+      const double budget = std::max<double>(2.0 * mb.sms, (double)fc.size());
+      std::vector<int> cc, cr, cn;
+      for (int c : fc) {
+        const int64_t n = cones[c].n;
+        const double w = (double)n * n * (allv ? n : 0.5 * n);
+        // columns per CTA: a power of two (the slab widths of the kernel)
+        const int bud = std::max(1, (int)(budget * w / wsum));
+        const int kest = allv ? (int)n : (int)(n + 1) / 2;
+        int per = 1;
+        while (per < 8 && (kest + per - 1) / per > bud) per *= 2;
+        const int g = std::max(1, (kest + per - 1) / per);
+        for (int r = 0; r < g; ++r) { cc.push_back(c); cr.push_back(r); cn.push_back(g); }
+        P.bt1k_maxn = std::max<int>(P.bt1k_maxn, (int)n);
+      }
+      P.bt1k_nctas = (int)cc.size();
+      P.bt1k_cone_off = (int)mb.ints.size();
+      mb.ints.insert(mb.ints.end(), cc.begin(), cc.end());
+      P.bt1k_rank_off = (int)mb.ints.size();
+      mb.ints.insert(mb.ints.end(), cr.begin(), cr.end());
+      P.bt1k_count_off = (int)mb.ints.size();
+      mb.ints.insert(mb.ints.end(), cn.begin(), cn.end());
+    }
+  }
   int maxQ = 0;
   for (int c = 0; c < P.ncones; ++c)
-    if (cones[c].path == 1) maxQ = std::max(maxQ, num_blocks1(cones[c].n));
+    if (cones[c].path == 1 && !fused_bt1(cones[c])) maxQ = std::max(maxQ, num_blocks1(cones[c].n));
   for (int p = std::max(maxP, maxQ) - 1; p >= 0; --p) {
     std::vector<GemmDesc> g[3];
     for (int c = 0; c < P.ncones; ++c) {
@@ -599,7 +638,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
         V = d.V1 + (int64_t)p * n * b;
         T = d.T1 + (int64_t)p * b * b;
       } else {
-        if (p >= num_blocks1(n)) continue;
+        if (fused_bt1(d) || p >= num_blocks1(n)) continue;
         r0 = p * kSy1Block + 1; m = n - r0; bb = std::min<int>(kSy1Block, n - 2 - p * kSy1Block);
         wb = kSy1Block;
         V = d.V1 + (int64_t)p * n * kSy1Block;
@@ -839,6 +878,11 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
       launch_backtr2(P.cones_d, nc, (int)P.maxn, (int)P.maxn, P.allv ? (int)P.maxn : (int)(P.maxn + 1) / 2, P.b, s);
       LAUNCH_CHECK();
       pm.begin(5);
+      if (P.bt1k_nctas) {
+        launch_bt1(P.cones_d, P.ints_d + P.bt1k_cone_off, P.ints_d + P.bt1k_rank_off, P.ints_d + P.bt1k_count_off,
+                   P.bt1k_nctas, P.bt1k_maxn, s);
+        LAUNCH_CHECK();
+      }
       for (const GemmLaunch& gl : P.bt1)
         if ((rc = run_gemm(P, gl, s, n_launch))) return rc;
       if (mode & MODE_EXPORT) {

@@ -141,4 +141,210 @@ void launch_backtr2(const ConeDev* cones, int ncones, int maxn, int maxk, int ke
   }
 }
 
+// ------------------------------------------------------------------------
+// Stage-1 back-transformation in one launch: Z <- Q1 Z with
+// Q1 = (I - V_0 T_0 V_0^T) ... (I - V_{B-1} T_{B-1} V_{B-1}^T), the blocks of
+// the one-stage tridiagonalisation (32 reflectors each) or the band
+// reduction's panels, applied last block first.  A CTA holds a slab of up to
+// KC kept columns in shared memory for the whole pass; per block it forms
+// W = V^T Z (lanes over rows, four reflectors per warp, then a warp
+// reduce-scatter), W' = T W and Z -= V W'.  The reflector blocks are read
+// from L2 (every CTA streams them), the slab never leaves the SM.  CTA ->
+// (cone, rank in the cone's group, group size) comes from tables, so big
+// cones get many CTAs and small ones one.
+namespace {
+
+constexpr int kB1Threads = 256;
+constexpr int kB1MaxCols = 8;
+constexpr size_t kB1SmemMax = 200 * 1024;
+
+struct Stage1Block {
+  int r0, mq, bb, wb;
+  const double* V;
+  const double* T;
+};
+
+__device__ __forceinline__ int stage1_nblocks(const ConeDev& c) {
+  const int n = (int)c.n;
+  if (c.path == 0) return c.npanels;
+  return n >= 3 ? (n - 2 + kSy1Block - 1) / kSy1Block : 0;
+}
+
+__device__ __forceinline__ Stage1Block stage1_block(const ConeDev& c, int q) {
+  const int n = (int)c.n;
+  Stage1Block k;
+  if (c.path == 0) {
+    k.wb = c.b;
+    k.r0 = (q + 1) * c.b;
+    k.mq = n - k.r0;
+    k.bb = min(c.b, k.mq);
+    k.V = c.V1 + (int64_t)q * n * c.b;
+    k.T = c.T1 + (int64_t)q * c.b * c.b;
+  } else {
+    k.wb = kSy1Block;
+    k.r0 = q * kSy1Block + 1;
+    k.mq = n - k.r0;
+    k.bb = min(kSy1Block, n - 2 - q * kSy1Block);
+    k.V = c.V1 + (int64_t)q * n * kSy1Block;
+    k.T = c.T1 + (int64_t)q * kSy1Block * kSy1Block;
+  }
+  return k;
+}
+
+// Sum of v over the warp, recursive halving: on return lane l holds the sum
+// of element (l >> (5 - log2 NV)) of v.
+template <int NV>
+__device__ __forceinline__ double warp_reduce_scatter(double (&v)[NV]) {
+  const int lane = threadIdx.x & 31;
+  int cnt = NV;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    if (cnt > 1) {
+      const int half = cnt / 2;
+      const bool up = (lane & off) != 0;
+#pragma unroll
+      for (int i = 0; i < NV / 2; ++i) {
+        if (i < half) {
+          const double send = up ? v[i] : v[i + half];
+          const double keep = up ? v[i + half] : v[i];
+          v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+      }
+      cnt = half;
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+    }
+  }
+  return v[0];
+}
+
+template <int KC>
+__device__ void bt1_slab(const ConeDev& c, int j0, int ncols, double* zs, double* Wsm, double* Wt) {
+  const int n = (int)c.n;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  double* Z = c.Z;
+  // rows 1 .. n-1 of the slab (row 0 is untouched: Q1 = diag(1, Q1'))
+  for (int e = tid; e < KC * n; e += kB1Threads) {
+    const int col = e / n, r = e - col * n;
+    zs[e] = col < ncols ? Z[(int64_t)r + (int64_t)(j0 + col) * n] : 0.0;
+  }
+  __syncthreads();
+  const int nblk = stage1_nblocks(c);
+  for (int q = nblk - 1; q >= 0; --q) {
+    const Stage1Block B = stage1_block(c, q);
+    // ---- W = V^T Z(r0:, slab): warp w takes reflectors 4w .. 4w+3
+    {
+      double acc[4 * KC];
+#pragma unroll
+      for (int i = 0; i < 4 * KC; ++i) acc[i] = 0.0;
+      const int a0 = warp * 4;
+      if (a0 < B.bb) {
+        const double* zr = zs + B.r0;
+#pragma unroll 2
+        for (int r = lane; r < B.mq; r += 32) {
+          double z[KC];
+#pragma unroll
+          for (int col = 0; col < KC; ++col) z[col] = zr[col * n + r];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const double v = (a0 + i < B.bb) ? __ldg(B.V + r + (int64_t)(a0 + i) * B.mq) : 0.0;
+#pragma unroll
+            for (int col = 0; col < KC; ++col) acc[i * KC + col] = fma(v, z[col], acc[i * KC + col]);
+          }
+        }
+      }
+      const double s = warp_reduce_scatter<4 * KC>(acc);
+      constexpr int kShift = (4 * KC == 32) ? 0 : (4 * KC == 16) ? 1 : (4 * KC == 8) ? 2 : 3;
+      if ((lane & ((1 << kShift) - 1)) == 0) {
+        const int idx = lane >> kShift;  // i * KC + col
+        Wsm[(a0 + idx / KC) * KC + (idx % KC)] = s;
+      }
+    }
+    __syncthreads();
+    // ---- W' = T W (T upper triangular)
+    if (tid < kSy1Block * KC) {
+      const int a = tid / KC, col = tid % KC;
+      double s0 = 0.0, s1 = 0.0;
+      if (a < B.bb) {
+        int bq = a;
+        for (; bq + 1 < B.bb; bq += 2) {
+          s0 = fma(__ldg(B.T + a + (int64_t)bq * B.wb), Wsm[bq * KC + col], s0);
+          s1 = fma(__ldg(B.T + a + (int64_t)(bq + 1) * B.wb), Wsm[(bq + 1) * KC + col], s1);
+        }
+        if (bq < B.bb) s0 = fma(__ldg(B.T + a + (int64_t)bq * B.wb), Wsm[bq * KC + col], s0);
+      }
+      Wt[a * KC + col] = s0 + s1;
+    }
+    __syncthreads();
+    // ---- Z(r0:, slab) -= V W'
+    for (int r = tid; r < B.mq; r += kB1Threads) {
+      double s0[KC], s1[KC];
+#pragma unroll
+      for (int col = 0; col < KC; ++col) { s0[col] = 0.0; s1[col] = 0.0; }
+#pragma unroll 8
+      for (int a = 0; a < kSy1Block; a += 2) {
+        if (a < B.bb) {
+          const double v0 = __ldg(B.V + r + (int64_t)a * B.mq);
+          const double v1 = (a + 1 < B.bb) ? __ldg(B.V + r + (int64_t)(a + 1) * B.mq) : 0.0;
+#pragma unroll
+          for (int col = 0; col < KC; ++col) {
+            s0[col] = fma(v0, Wt[a * KC + col], s0[col]);
+            s1[col] = fma(v1, Wt[(a + 1) * KC + col], s1[col]);
+          }
+        }
+      }
+#pragma unroll
+      for (int col = 0; col < KC; ++col) zs[col * n + B.r0 + r] -= s0[col] + s1[col];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < KC * n; e += kB1Threads) {
+    const int col = e / n, r = e - col * n;
+    if (col < ncols && r >= 1) Z[(int64_t)r + (int64_t)(j0 + col) * n] = zs[e];
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kB1Threads) bt1_kernel(const ConeDev* __restrict__ cones,
+                                                         const int* __restrict__ cta_cone,
+                                                         const int* __restrict__ cta_rank,
+                                                         const int* __restrict__ cta_count, int kcmax) {
+  extern __shared__ double b1_smem[];
+  __shared__ double Wsm[kSy1Block * kB1MaxCols];
+  __shared__ double Wt[kSy1Block * kB1MaxCols];
+  const ConeDev& c = cones[cta_cone[blockIdx.x]];
+  if (*c.status != 0) return;
+  const int rank = cta_rank[blockIdx.x], G = cta_count[blockIdx.x];
+  const int k = c.kinfo[0];
+  // columns [lo, hi) of this CTA
+  const int base = k / G, extra = k % G;
+  const int lo = rank * base + min(rank, extra);
+  const int hi = lo + base + (rank < extra ? 1 : 0);
+  for (int j0 = lo; j0 < hi;) {
+    const int left = hi - j0;
+    if (left > 4 && kcmax >= 8) { bt1_slab<8>(c, j0, min(left, 8), b1_smem, Wsm, Wt); j0 += min(left, 8); }
+    else if (left > 2 && kcmax >= 4) { bt1_slab<4>(c, j0, min(left, 4), b1_smem, Wsm, Wt); j0 += min(left, 4); }
+    else if (left >= 2 && kcmax >= 2) { bt1_slab<2>(c, j0, 2, b1_smem, Wsm, Wt); j0 += 2; }
+    else { bt1_slab<1>(c, j0, 1, b1_smem, Wsm, Wt); j0 += 1; }
+  }
+}
+
+}  // namespace
+
+int bt1_max_side() { return (int)(kB1SmemMax / sizeof(double)); }
+
+void launch_bt1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,
+                int maxn, cudaStream_t s) {
+  if (nctas <= 0 || maxn <= 0) return;
+  int kcmax = kB1MaxCols;
+  while (kcmax > 1 && (size_t)kcmax * maxn * sizeof(double) > kB1SmemMax) kcmax /= 2;
+  const size_t smem = (size_t)kcmax * maxn * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(bt1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kB1SmemMax);
+    attr = true;
+  }
+  bt1_kernel<<<nctas, kB1Threads, smem, s>>>(cones, cta_cone, cta_rank, cta_count, kcmax);
+}
+
 }  // namespace scs

@@ -194,6 +194,10 @@ int sytrd1_max_ctas(int maxn);
 int launch_sytrd1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,
                   int maxn, long long wait_limit, cudaStream_t s);
 void launch_larft1(const ConeDev* cones, const int* blk_cone, const int* blk_index, int nblocks, cudaStream_t s);
+// Z <- Q1 Z for the stage-1 blocks in one launch (CTA tables as launch_sytrd1); cones of side <= bt1_max_side()
+void launch_bt1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,
+                int maxn, cudaStream_t s);
+int bt1_max_side();
 // y = svec(S) or x - svec(S) from the lower triangle of S = Z diag(l) Z^T held in QA (split mode)
 void launch_pack_recon(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s);
 void launch_status_reduce(const int* status, int count, int* out, cudaStream_t s);

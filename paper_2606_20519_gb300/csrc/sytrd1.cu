@@ -4,23 +4,20 @@
 //
 // CTA r of a cone's group of G CTAs owns the columns i with i mod G = r for
 // the whole reduction (both triangles are kept, so a column is contiguous).
-// Column j (m = n - j - 1 rows below the diagonal):
-//   A: every CTA waits until the owner of column j has published it (a
-//      single-producer flag), reads its rows j+1 .. n-1 and forms the
-//      reflector H = I - tau v v^T (v_0 = 1, LAPACK convention) redundantly;
-//   B: each CTA computes p_i = tau A(j+1:, i)^T v for its columns and the
-//      partial sum of p_i v_i;                               -- group barrier
-//   C: every CTA forms w = p - (tau/2)(p^T v) v and applies the rank-2 update
-//      A <- A - v w^T - w v^T to its own columns; the owner of column j+1
-//      updates it first and publishes it.
-// Work items are (column, 256-row chunk) pairs spread over all warps, each
-// lane keeping 8 loads in flight (the loop is bound by L2 latency otherwise).
-// The diagonal d, off-diagonal e, tau and the reflectors (packed into
-// 32-column blocks with their unit diagonal and zeros, ready for the blocked
-// back-transformation) are written by the group's first CTA.  Group barriers
-// are counters in global memory with release/acquire ordering and a bounded
-// wait (ST_TIMEOUT on expiry); the launch is cooperative, so every CTA is
-// resident.  Data written by other CTAs is read with ld.global.cg (L2).
+// Per column j there is one group barrier: before it each CTA has written
+// p_i = tau_j A(j+1:, i)^T v_j for its columns; after it every CTA forms
+// w_j, updates column j+1 itself (from its stored value, v_j and w_j) and
+// forms reflector j+1 redundantly -- the same arithmetic in every CTA, so
+// no column has to be handed from its owner -- and then makes one fused
+// pass over its own columns: the rank-2 update of step j and the products
+// p_i of step j+1.  Work items are (column, 256-row chunk) pairs spread over
+// all warps, each lane keeping 8 loads in flight.  d, e, tau and the
+// reflectors (packed into 32-column blocks with their unit diagonal and
+// zeros, ready for the blocked back-transformation) are written as they are
+// formed.  Group barriers are counters in global memory with release/acquire
+// ordering and a bounded wait (ST_TIMEOUT on expiry); the launch is
+// cooperative, so every CTA is resident.  Data written by other CTAs is read
+// with ld.global.cg (L2).
 //
 // larft1_kernel then forms, for every 32-reflector block, the triangular
 // factor T of H_0 ... H_31 = I - V T V^T.
@@ -47,10 +44,9 @@ __device__ double block_sum256(double v, double* red) {
   __syncthreads();
   if (lane == 0) red[w] = v;
   __syncthreads();
-  double t = 0.0;
-#pragma unroll
-  for (int q = 0; q < kSyThreads / 32; ++q) t += red[q];
-  return t;
+  // pairwise (3 dependent adds instead of 7), the same order in every thread
+  static_assert(kSyThreads == 256, "tree below sums 8 warps");
+  return ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
 }
 
 // Barrier over the G CTAs of one cone; returns false when the wait ran out.
@@ -76,6 +72,120 @@ __device__ bool group_barrier(int* counter, int target, long long limit, int* fl
 constexpr int kChunk = 256;   // rows per work item (32 lanes x 8 loads in flight)
 constexpr int kPartMax = 2048; // work items per round (shared-memory partial sums)
 
+// Householder reflector of x[0 .. len-1] in place (every thread of the CTA
+// calls it; x in shared memory): H x = beta e_1 with H = I - tau u u^T,
+// u_0 = 1 (LAPACK convention).  x becomes u; tau and beta are returned.
+__device__ double make_reflector(double* x, int len, double* red, double* sh, double* beta_out) {
+  double ps = 0.0;
+  for (int t = 1 + threadIdx.x; t < len; t += kSyThreads) ps = fma(x[t], x[t], ps);
+  const double sigma = block_sum256(ps, red);
+  if (threadIdx.x == 0) {
+    const double alpha = x[0];
+    double beta = alpha, tau = 0.0, scal = 0.0;
+    if (sigma != 0.0) {
+      const double nrm = sqrt(fma(alpha, alpha, sigma));
+      beta = alpha >= 0.0 ? -nrm : nrm;
+      tau = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    sh[0] = beta; sh[1] = tau; sh[2] = scal;
+  }
+  __syncthreads();
+  const double scal = sh[2];
+  for (int t = 1 + threadIdx.x; t < len; t += kSyThreads) x[t] *= scal;
+  __syncthreads();
+  if (threadIdx.x == 0) x[0] = 1.0;
+  *beta_out = sh[0];
+  return sh[1];
+}
+
+// Reflector j (u indexed from row j+1) into its 32-column block of V1, with
+// the unit diagonal and the zeros above; rows spread over the group.
+__device__ void store_reflector(const ConeDev& c, int n, int j, const double* u, int rank, int G) {
+  const int q = j / kNb, col = j % kNb;
+  const int r0 = q * kNb + 1;               // first row of block q
+  const int mq = n - r0;                    // rows of block q
+  double* Vq = c.V1 + (int64_t)q * n * kNb;  // mq x 32, ld mq
+  for (int r = rank * kSyThreads + threadIdx.x; r < mq; r += G * kSyThreads) {
+    const int row = r0 + r;
+    double val = 0.0;
+    if (row == j + 1) val = 1.0;
+    else if (row > j + 1) val = u[row - j - 1];
+    Vq[(int64_t)r + (int64_t)col * mq] = val;
+  }
+}
+
+// One pass over this CTA's columns i >= r0 (i mod G = rank), rows r0 .. n-1:
+// with UPDATE, first A(r, i) -= v_r w_i + w_r v_i (vu, wu indexed from row
+// r0 - 1); then p_i = tau * sum_r A(r, i) u_r (u indexed from row r0) into
+// pbuf[i].  Returns this CTA's sum of p_i u_i (thread 0 holds it).
+template <bool UPDATE>
+__device__ double column_pass(double* __restrict__ A, int n, int r0, const double* __restrict__ u, double tau,
+                              const double* __restrict__ vu, const double* __restrict__ wu, double* pbuf,
+                              double* psum, double* red, int rank, int G) {
+  const int L = n - r0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int first = r0 + ((rank - r0 % G) + G) % G;
+  const int ncol = first < n ? (n - 1 - first) / G + 1 : 0;
+  const int nch = (L + kChunk - 1) / kChunk;
+  const int per = kPartMax / nch;
+  double mypv = 0.0;
+  for (int k0 = 0; k0 < ncol; k0 += per) {
+    const int kc = min(ncol - k0, per);
+    for (int it = warp; it < kc * nch; it += kSyThreads / 32) {
+      const int k = k0 + it / nch, ch = it % nch;
+      const int i = first + G * k;
+      double* col = A + (int64_t)i * n + r0;
+      const int t0 = ch * kChunk + lane;
+      double a[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int t = t0 + 32 * r;
+        a[r] = t < L ? __ldcg(col + t) : 0.0;
+      }
+      if (UPDATE) {
+        const double vi = vu[i - r0 + 1], wi = wu[i - r0 + 1];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int t = t0 + 32 * r;
+          if (t < L) {
+            a[r] = a[r] - fma(vu[t + 1], wi, wu[t + 1] * vi);
+            __stcg(col + t, a[r]);
+          }
+        }
+      }
+      double acc = 0.0;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int t = t0 + 32 * r;
+        if (t < L) acc = fma(a[r], u[t], acc);
+      }
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) psum[it] = acc;
+    }
+    __syncthreads();
+    for (int kk = tid; kk < kc; kk += kSyThreads) {
+      double p = 0.0;
+      for (int ch = 0; ch < nch; ++ch) p += psum[kk * nch + ch];
+      p *= tau;
+      const int i = first + G * (k0 + kk);
+      __stcg(pbuf + i, p);
+      mypv = fma(p, u[i - r0], mypv);
+    }
+    __syncthreads();
+  }
+  return block_sum256(mypv, red);
+}
+
+// Step j (reflector H_j = I - tau_j v v^T from column j, v indexed from row
+// j+1, m = n - j - 1 entries) with p = tau_j A22 v already in pbuf:
+//   every CTA, after the group barrier:  w = p - (tau_j/2)(p^T v) v, and the
+//     updated column j+1 (rows j+1 ..) from its current value, v and w --
+//     so the next reflector is formed redundantly, with no hand-off;
+//   then one pass over its own columns i >= j+2 applies the rank-2 update
+//     A <- A - v w^T - w v^T to rows j+2 .. and forms the next step's
+//     p_i = tau_{j+1} A(j+2:, i)^T v'  (fused: one read and one write of A).
+// One group barrier per column.
 __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __restrict__ cones,
                                                             const int* __restrict__ cta_cone,
                                                             const int* __restrict__ cta_rank,
@@ -83,201 +193,111 @@ __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __res
                                                             long long wait_limit) {
   extern __shared__ double sy_smem[];
   __shared__ double red[kSyThreads / 32];
-  __shared__ double sh_beta, sh_tau, sh_scal, sh_K;
+  __shared__ double sh[4];
   __shared__ int sh_flag;
   const ConeDev& c = cones[cta_cone[blockIdx.x]];
   const int rank = cta_rank[blockIdx.x], G = cta_count[blockIdx.x];
   const int n = (int)c.n;
   if (*c.status != 0) return;
   double* A = c.A;
-  double* v = sy_smem;               // m values of the current reflector
-  double* w = sy_smem + n;           // p, then w
-  double* psum = sy_smem + 2 * n;    // kPartMax partial dot products
-  // p_i (absolute column index) and the partial sums p^T v, double-buffered by
-  // step parity: a CTA writes step j+2's values only after every CTA has
-  // passed step j+1's barrier, i.e. finished reading step j's values
-  double* pbuf2 = c.X;               // 2 x n
-  double* part2 = c.X + 2 * n;       // 2 x G
-  int* bar = c.prog;                 // barrier counter
-  int* ready = c.prog + 1;           // last column whose update is complete
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* vc = sy_smem;             // v_j (rows j+1 ..)
+  double* w = sy_smem + n;          // p_j, then w_j
+  double* vx = sy_smem + 2 * n;     // updated column j+1 (rows j+1 ..), then v_{j+1} at vx + 1
+  double* psum = sy_smem + 3 * n;   // kPartMax partial dot products
+  // p and the partial sums p^T v, double-buffered by step parity: a CTA
+  // writes step j+2's values only after every CTA has passed step j+1's
+  // barrier, i.e. finished reading step j's values
+  double* pbuf2 = c.X;              // 2 x n
+  double* part2 = c.X + 2 * n;      // 2 x G
+  int* bar = c.prog;
+  const int tid = threadIdx.x;
   int bstep = 0;
-
+  if (n < 3) {
+    if (rank == 0 && tid == 0) {
+      c.d[0] = A[0];
+      c.e[0] = n == 2 ? A[1] : 0.0;
+      if (n == 2) { c.d[1] = A[3]; c.e[1] = 0.0; }
+    }
+    return;
+  }
+  // ---- prologue: reflector 0 from column 0, p_0 for my columns
+  double beta, tau;
+  for (int t = tid; t < n - 1; t += kSyThreads) vc[t] = __ldcg(A + 1 + t);
+  __syncthreads();
+  tau = make_reflector(vc, n - 1, red, sh, &beta);
+  __syncthreads();
+  if (rank == 0 && tid == 0) {
+    c.d[0] = __ldcg(A);
+    c.e[0] = beta;
+    c.rho[0] = tau;
+  }
+  store_reflector(c, n, 0, vc, rank, G);
+  {
+    const double pv = column_pass<false>(A, n, 1, vc, tau, nullptr, nullptr, pbuf2, psum, red, rank, G);
+    if (tid == 0) __stcg(part2 + rank, pv);
+  }
   for (int j = 0; j + 2 < n; ++j) {
     const int m = n - j - 1;
-    double* pbuf = pbuf2 + (j & 1) * n;
-    double* part = part2 + (j & 1) * G;
-    // ---- A: wait until column j is up to date (single producer), then the
-    // reflector from its rows j+1 .. n-1, in every CTA
-    if (j > 0 && ((j % G) != rank)) {
-      if (tid == 0) {
-        int ok = 1;
-        if (ld_acquire(ready) < j) {
-          const long long t0 = clock64();
-          while (ld_acquire(ready) < j) {
-            if (clock64() - t0 > wait_limit) { ok = 0; break; }
-          }
-        }
-        sh_flag = ok;
-      }
-      __syncthreads();
-      if (!sh_flag) {
-        if (tid == 0) atomicOr(c.status, ST_TIMEOUT);
-        return;
-      }
-    }
-    for (int t = tid; t < m; t += kSyThreads) v[t] = __ldcg(A + (int64_t)(j + 1 + t) + (int64_t)j * n);
-    __syncthreads();
-    double ps = 0.0;
-    for (int t = 1 + tid; t < m; t += kSyThreads) ps = fma(v[t], v[t], ps);
-    const double sigma = block_sum256(ps, red);
-    if (tid == 0) {
-      const double alpha = v[0];
-      double beta = alpha, tau = 0.0, scal = 0.0;
-      if (sigma != 0.0) {
-        const double nrm = sqrt(fma(alpha, alpha, sigma));
-        beta = alpha >= 0.0 ? -nrm : nrm;
-        tau = (beta - alpha) / beta;
-        scal = 1.0 / (alpha - beta);
-      }
-      sh_beta = beta; sh_tau = tau; sh_scal = scal;
-    }
-    __syncthreads();
-    const double tau = sh_tau, scal = sh_scal;
-    for (int t = 1 + tid; t < m; t += kSyThreads) v[t] *= scal;
-    if (tid == 0) v[0] = 1.0;
-    __syncthreads();
-    if (rank == 0) {
-      // outputs: d_j, e_j, tau_j and the reflector in its 32-column block
-      const int q = j / kNb, col = j % kNb;
-      const int r0 = q * kNb + 1;               // first row of block q
-      const int mq = n - r0;                    // rows of block q
-      double* Vq = c.V1 + (int64_t)q * n * kNb;  // mq x 32, ld mq
-      for (int r = tid; r < mq; r += kSyThreads) {
-        const int row = r0 + r;
-        double val = 0.0;
-        if (row == j + 1) val = 1.0;
-        else if (row > j + 1) val = v[row - j - 1];
-        Vq[(int64_t)r + (int64_t)col * mq] = val;
-      }
-      if (tid == 0) {
-        c.d[j] = __ldcg(A + (int64_t)j + (int64_t)j * n);
-        c.e[j] = sh_beta;
-        c.rho[j] = tau;  // tau of reflector j (the divide and conquer reuses rho later)
-      }
-    }
-    // my columns: i = first + G * k, i > j (absolute ownership: i mod G == rank)
-    const int first = j + 1 + ((rank - (j + 1) % G) + G) % G;
-    const int ncol = first < n ? (n - 1 - first) / G + 1 : 0;
-    const int nch = (m + kChunk - 1) / kChunk;
-    if (tau == 0.0) {
-      // H = I (same decision in every CTA): column j+1 is already current
-      if (((j + 1) % G) == rank && tid == 0) {
-        __threadfence();
-        asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(ready), "r"(j + 1) : "memory");
-      }
-      continue;
-    }
-    // ---- B: p_i = tau A(j+1:, i)^T v for my columns; items (column, row chunk)
-    double mypv = 0.0;
-    for (int k0 = 0; k0 < ncol; k0 += kPartMax / nch) {
-      const int kc = min(ncol - k0, kPartMax / nch);
-      for (int it = warp; it < kc * nch; it += kSyThreads / 32) {
-        const int k = k0 + it / nch, ch = it % nch;
-        const double* col = A + (int64_t)(first + G * k) * n + (j + 1);
-        const int t0 = ch * kChunk + lane;
-        double a[8];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const int t = t0 + 32 * r;
-          a[r] = t < m ? __ldcg(col + t) : 0.0;
-        }
-        double acc = 0.0;
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const int t = t0 + 32 * r;
-          if (t < m) acc = fma(a[r], v[t], acc);
-        }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) psum[it] = acc;
-      }
-      __syncthreads();
-      for (int kk = tid; kk < kc; kk += kSyThreads) {
-        double p = 0.0;
-        for (int ch = 0; ch < nch; ++ch) p += psum[kk * nch + ch];
-        p *= tau;
-        const int i = first + G * (k0 + kk);
-        __stcg(pbuf + i, p);
-        mypv = fma(p, v[i - j - 1], mypv);
-      }
-      __syncthreads();
-    }
-    const double pv = block_sum256(mypv, red);
-    if (tid == 0) __stcg(part + rank, pv);
+    const double* pbuf = pbuf2 + (j & 1) * n;
+    const double* part = part2 + (j & 1) * G;
     if (!group_barrier(bar, (++bstep) * G, wait_limit, &sh_flag)) {
       if (tid == 0) atomicOr(c.status, ST_TIMEOUT);
       return;
     }
-    // ---- C: w = p - K v, then the rank-2 update of my columns (column j+1 first)
+    // ---- w = p - K v and the updated column j+1, in every CTA
     double pt = 0.0;
     for (int r = tid; r < G; r += kSyThreads) pt += __ldcg(part + r);
+    // all loads of a round first, then the shared-memory stores (one L2 round trip)
+    for (int base = 0; base < m; base += 4 * kSyThreads) {
+      double pr[4], ar[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int t = base + q * kSyThreads + tid;
+        pr[q] = t < m ? __ldcg(pbuf + j + 1 + t) : 0.0;
+        ar[q] = t < m ? __ldcg(A + (int64_t)(j + 1 + t) + (int64_t)(j + 1) * n) : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int t = base + q * kSyThreads + tid;
+        if (t < m) { w[t] = pr[q]; vx[t] = ar[q]; }
+      }
+    }
     const double K = 0.5 * tau * block_sum256(pt, red);
-    for (int t = tid; t < m; t += kSyThreads) w[t] = fma(-K, v[t], __ldcg(pbuf + j + 1 + t));
+    for (int t = tid; t < m; t += kSyThreads) w[t] = fma(-K, vc[t], w[t]);
     __syncthreads();
-    for (int it = warp; it < ncol * nch; it += kSyThreads / 32) {
-      const int k = it / nch, ch = it % nch;
-      const int i = first + G * k;
-      double* col = A + (int64_t)i * n + (j + 1);
-      const double vi = v[i - j - 1], wi = w[i - j - 1];
-      const int t0 = ch * kChunk + lane;
-      double a[8];
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int t = t0 + 32 * r;
-        a[r] = t < m ? __ldcg(col + t) : 0.0;
-      }
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int t = t0 + 32 * r;
-        if (t < m) __stcg(col + t, a[r] - fma(v[t], wi, w[t] * vi));
-      }
+    {
+      const double w0 = w[0];
+      for (int t = tid; t < m; t += kSyThreads) vx[t] = vx[t] - fma(vc[t], w0, w[t] * vc[0]);
     }
-    // the owner of column j+1 publishes it (its first column, updated above)
     __syncthreads();
-    if (((j + 1) % G) == rank && tid == 0) {
-      __threadfence();
-      asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(ready), "r"(j + 1) : "memory");
-    }
-  }
-  // the last 2 x 2 block: wait for its columns, then d and e
-  if (rank == 0) {
-    if (tid == 0) {
-      int ok = 1;
-      if (n >= 3 && ld_acquire(ready) < n - 2) {
-        const long long t0 = clock64();
-        while (ld_acquire(ready) < n - 2) {
-          if (clock64() - t0 > wait_limit) { ok = 0; break; }
-        }
+    if (j + 3 < n) {
+      // ---- reflector j+1 from rows j+2 .. of the updated column
+      const double dj1 = vx[0];
+      double beta1;
+      const double tau1 = make_reflector(vx + 1, m - 1, red, sh, &beta1);
+      __syncthreads();
+      if (rank == 0 && tid == 0) {
+        c.d[j + 1] = dj1;
+        c.e[j + 1] = beta1;
+        c.rho[j + 1] = tau1;
       }
-      if (!ok) atomicOr(c.status, ST_TIMEOUT);
-    }
-    // every column of the last block is owned and updated before the final barrier of step n-3
-    if (!group_barrier(bar, (++bstep) * G, wait_limit, &sh_flag)) {
-      if (tid == 0) atomicOr(c.status, ST_TIMEOUT);
-      return;
-    }
-    if (tid == 0) {
-      if (n >= 2) {
-        c.d[n - 2] = __ldcg(A + (int64_t)(n - 2) + (int64_t)(n - 2) * n);
-        c.e[n - 2] = __ldcg(A + (int64_t)(n - 1) + (int64_t)(n - 2) * n);
+      store_reflector(c, n, j + 1, vx + 1, rank, G);
+      double* pnext = pbuf2 + ((j + 1) & 1) * n;
+      const double pv = column_pass<true>(A, n, j + 2, vx + 1, tau1, vc, w, pnext, psum, red, rank, G);
+      if (tid == 0) __stcg(part2 + ((j + 1) & 1) * G + rank, pv);
+      // v_{j+1} becomes the current reflector
+      for (int t = tid; t < m - 1; t += kSyThreads) vc[t] = vx[1 + t];
+      tau = tau1;
+      __syncthreads();
+    } else {
+      // the last 2 x 2 block (rows n-2, n-1)
+      if (rank == 0 && tid == 0) {
+        const double a = __ldcg(A + (int64_t)(n - 1) + (int64_t)(n - 1) * n);
+        c.d[n - 2] = vx[0];
+        c.e[n - 2] = vx[1];
+        c.d[n - 1] = a - fma(vc[1], w[1], w[1] * vc[1]);
+        c.e[n - 1] = 0.0;
       }
-      c.d[n - 1] = __ldcg(A + (int64_t)(n - 1) + (int64_t)(n - 1) * n);
-      c.e[n - 1] = 0.0;
-    }
-  } else {
-    if (!group_barrier(bar, (++bstep) * G, wait_limit, &sh_flag)) {
-      if (tid == 0) atomicOr(c.status, ST_TIMEOUT);
-      return;
     }
   }
 }
@@ -347,7 +367,7 @@ int sytrd1_max_ctas(int maxn) {
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = ((size_t)2 * maxn + kPartMax) * sizeof(double);
+  const size_t smem = ((size_t)3 * maxn + kPartMax) * sizeof(double);
   cudaFuncSetAttribute(sytrd1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sytrd1_kernel, kSyThreads, smem);
   return per_sm * sms;
@@ -356,7 +376,7 @@ int sytrd1_max_ctas(int maxn) {
 int launch_sytrd1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,
                   int maxn, long long wait_limit, cudaStream_t s) {
   if (nctas <= 0) return 0;
-  const size_t smem = ((size_t)2 * maxn + kPartMax) * sizeof(double);
+  const size_t smem = ((size_t)3 * maxn + kPartMax) * sizeof(double);
   // co-resident CTAs (they wait on one another); the attribute also survives graph recording
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nctas);
