@@ -818,7 +818,7 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
       pm.begin(0);
       launch_unpack(P.cones_d, nc, P.maxn * P.maxn, io, 0, s);
       LAUNCH_CHECK();
-      pm.begin(1);
+      if (!P.panels.empty()) pm.begin(1);
       for (const PanelStep& ps : P.panels) {
         launch_panel(P.cones_d, P.ints_d + ps.ids_off, ps.njobs, ps.panel, P.b, ps.cluster, ps.R, s);
         LAUNCH_CHECK();

@@ -156,50 +156,114 @@ __global__ void __launch_bounds__(kDcThreads) dc_prepare_kernel(const ConeDev* _
   for (int t = tid; t < K; t += kDcThreads) zv[t] *= inv;
   __syncthreads();
 
-  // ---- deflation scan (sequential by nature)
+  // ---- deflation scan.  Sequential by nature (a rotation changes the pole
+  // and z of the survivor, which the next test reads), but almost every
+  // test is negative: warp 0 takes 32 positions at a time, evaluates their
+  // tests against the current predecessors in parallel and walks a chunk
+  // one position at a time only from its first positive test on.
+  // Close-pole test |gap c s| <= tol with c = z_j / t, s = z_p / t,
+  // t = hypot(z_j, z_p), written without the division: |gap z_j z_p| <= tol t^2.
   double* rot = c.rot + 2 * s;
   int* irot = c.irot + 2 * s;
-  if (tid == 0) {
-    const double rho = fabs(beta) * nrm2;
-    const double tol = 8.0 * kEps * fmax(dmax, rho);
+  const double rho = fabs(beta) * nrm2;
+  const double tol = 8.0 * kEps * fmax(dmax, rho);
+  if (tid < 32) {
+    const int lane = tid;
     int last = -1, nrot = 0;
-    // fp[] temporarily holds 1 for kept, 0 for deflated
-    for (int j = 0; j < K; ++j) {
-      if (rho * fabs(zv[j]) <= tol) { fp[j] = 0; continue; }
-      if (last >= 0) {
-        const double sp = zv[last], cj = zv[j];
-        const double tt = hypot(cj, sp);
-        const double cc = cj / tt, sn = sp / tt;
-        const double gap = dv[j] - dv[last];
-        if (fabs(gap * cc * sn) <= tol) {
-          const double dp = dv[last], dj = dv[j];
-          dv[last] = dp * cc * cc + dj * sn * sn;
-          dv[j] = dp * sn * sn + dj * cc * cc;
-          zv[j] = tt;
-          zv[last] = 0.0;
-          fp[last] = 0;
-          rot[2 * nrot] = cc;
-          rot[2 * nrot + 1] = sn;
-          irot[2 * nrot] = last;  // sorted indices for now
-          irot[2 * nrot + 1] = j;
-          ++nrot;
+    for (int base = 0; base < K; base += 32) {
+      const int j = base + lane;
+      const bool keep = j < K && !(rho * fabs(zv[j]) <= tol);
+      const unsigned km = __ballot_sync(0xffffffffu, keep);
+      const unsigned below = km & ((1u << lane) - 1u);
+      const int p = below ? base + 31 - __clz(below) : last;
+      bool trig = false;
+      if (keep && p >= 0) {
+        const double zp = zv[p], zj = zv[j];
+        trig = fabs((dv[j] - dv[p]) * zj * zp) <= tol * fma(zj, zj, zp * zp);
+      }
+      const unsigned tm = __ballot_sync(0xffffffffu, trig);
+      if (tm == 0u) {
+        if (j < K) fp[j] = keep ? 1 : 0;
+        if (km) last = base + 31 - __clz(km);
+        continue;
+      }
+      const int first = __ffs(tm) - 1;
+      if (j < K && lane < first) fp[j] = keep ? 1 : 0;
+      const unsigned pre = km & ((1u << first) - 1u);
+      if (pre) last = base + 31 - __clz(pre);
+      __syncwarp();
+      if (lane == 0) {
+        const int jend = min(K, base + 32);
+        for (int jj = base + first; jj < jend; ++jj) {
+          if (rho * fabs(zv[jj]) <= tol) { fp[jj] = 0; continue; }
+          if (last >= 0) {
+            const double sp = zv[last], cj = zv[jj];
+            const double gap = dv[jj] - dv[last];
+            const double t2 = fma(cj, cj, sp * sp);
+            if (fabs(gap * cj * sp) <= tol * t2) {
+              const double tt = sqrt(t2);
+              const double cc = cj / tt, sn = sp / tt;
+              const double dp = dv[last], dj = dv[jj];
+              dv[last] = dp * cc * cc + dj * sn * sn;
+              dv[jj] = dp * sn * sn + dj * cc * cc;
+              zv[jj] = tt;
+              zv[last] = 0.0;
+              fp[last] = 0;
+              rot[2 * nrot] = cc;
+              rot[2 * nrot + 1] = sn;
+              irot[2 * nrot] = last;  // sorted indices for now
+              irot[2 * nrot + 1] = jj;
+              ++nrot;
+            }
+          }
+          fp[jj] = 1;
+          last = jj;
         }
       }
-      fp[j] = 1;
-      last = j;
+      last = __shfl_sync(0xffffffffu, last, 0);
+      nrot = __shfl_sync(0xffffffffu, nrot, 0);
+      __syncwarp();
     }
-    // final columns: kept first (in order), deflated after (in order)
-    int kk = 0;
-    for (int j = 0; j < K; ++j) kk += fp[j];
-    int pk = 0, pd = kk;
-    for (int j = 0; j < K; ++j) fp[j] = fp[j] ? pk++ : pd++;
-    for (int r = 0; r < nrot; ++r) {
-      irot[2 * r] = fp[irot[2 * r]];
-      irot[2 * r + 1] = fp[irot[2 * r + 1]];
+    if (lane == 0) {
+      sh_rho = rho;
+      sh_nrot = nrot;
     }
-    sh_rho = rho;
-    sh_kk = kk;
-    sh_nrot = nrot;
+  }
+  __syncthreads();
+  // final columns: kept first, deflated after, each in sorted order (block scan of the flags)
+  {
+    __shared__ int wsum[kDcThreads / 32];
+    __shared__ int sh_total;
+    const int per = (K + kDcThreads - 1) / kDcThreads;
+    const int a0 = min(K, tid * per), a1 = min(K, a0 + per);
+    int mine = 0;
+    for (int j = a0; j < a1; ++j) mine += fp[j];
+    const int lane = tid & 31, wid = tid >> 5;
+    int incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (tid == 0) {
+      int run = 0;
+      for (int q = 0; q < kDcThreads / 32; ++q) { const int v = wsum[q]; wsum[q] = run; run += v; }
+      sh_total = run;
+    }
+    __syncthreads();
+    const int kkept = sh_total;
+    int kb = wsum[wid] + incl - mine;  // kept positions before mine
+    for (int j = a0; j < a1; ++j) {
+      if (fp[j]) fp[j] = kb++;
+      else fp[j] = kkept + (j - kb);  // deflated: after all kept, in order
+    }
+    if (tid == 0) sh_kk = kkept;
+  }
+  __syncthreads();
+  for (int r = tid; r < sh_nrot; r += kDcThreads) {
+    irot[2 * r] = fp[irot[2 * r]];
+    irot[2 * r + 1] = fp[irot[2 * r + 1]];
   }
   __syncthreads();
   const int kk = sh_kk;
