@@ -50,6 +50,7 @@ struct BulgeLaunch {
 
 struct Sytrd1Launch {
   int nctas = 0, maxn = 0;
+  size_t smem = 0;
   int cone_off = 0, rank_off = 0, count_off = 0;
 };
 
@@ -480,11 +481,20 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
       std::vector<int> large, small;
       for (int c : one) (cones[c].n >= 256 ? large : small).push_back(c);
       auto emit = [&](const std::vector<int>& list, bool spread) {
+        // one-CTA cones keep their matrix in shared memory when it fits:
+        // group them by the occupancy of that size
+        int gcap = cap;
+        if (!spread && !list.empty()) {
+          int mx = 0;
+          for (int c : list) mx = std::max<int>(mx, (int)cones[c].n);
+          const size_t res = sytrd1_smem_bytes(mx, 1, true);
+          if (res <= 200 * 1024) gcap = std::max(1, sytrd1_max_ctas_for(res));
+        }
         size_t i = 0;
         while (i < list.size()) {
           std::vector<int> grp;
           double work = 0.0;
-          while (i < list.size() && (int)grp.size() < cap) {
+          while (i < list.size() && (int)grp.size() < gcap) {
             grp.push_back(list[i]);
             work += std::pow((double)cones[list[i]].n, 3.0);
             ++i;
@@ -502,6 +512,16 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
           }
           Sytrd1Launch sl;
           sl.maxn = (int)maxn1;
+          // shared-memory-resident columns when every cone of the launch fits and
+          // the launch stays co-resident
+          {
+            size_t need = 0;
+            for (size_t q = 0; q < grp.size(); ++q)
+              need = std::max(need, sytrd1_smem_bytes((int)cones[grp[q]].n, give[q], true));
+            int total = 0;
+            for (int g : give) total += g;
+            if (need <= 200 * 1024 && sytrd1_max_ctas_for(need) >= total) sl.smem = need;
+          }
           std::vector<int> cc, rr, gg;
           for (size_t q = 0; q < grp.size(); ++q)
             for (int r = 0; r < give[q]; ++r) { cc.push_back(grp[q]); rr.push_back(r); gg.push_back(give[q]); }
@@ -829,7 +849,7 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
         pm.begin(1);
         for (const Sytrd1Launch& sl : P.sytrd1) {
           if (launch_sytrd1(P.cones_d, P.ints_d + sl.cone_off, P.ints_d + sl.rank_off, P.ints_d + sl.count_off,
-                            sl.nctas, sl.maxn, wait_limit, s))
+                            sl.nctas, sl.maxn, sl.smem, wait_limit, s))
             return SCS_PSD_ECUDA;
           LAUNCH_CHECK();
         }

@@ -191,8 +191,11 @@ void launch_loewner_scale(const ConeDev* cones, int ncones, int64_t maxn, cudaSt
 void launch_pack_lower(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s);
 void launch_recon(const ConeDev* cones, int ncones, int maxn, const IoSlot* io, cudaStream_t s);
 int sytrd1_max_ctas(int maxn);
+int sytrd1_max_ctas_for(size_t smem_bytes);
+// dynamic shared memory of one CTA for side n in a group of G (resident: its columns in shared memory)
+size_t sytrd1_smem_bytes(int n, int G, bool resident);
 int launch_sytrd1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,
-                  int maxn, long long wait_limit, cudaStream_t s);
+                  int maxn, size_t smem_bytes, long long wait_limit, cudaStream_t s);
 void launch_larft1(const ConeDev* cones, const int* blk_cone, const int* blk_index, int nblocks, cudaStream_t s);
 // Z <- Q1 Z for the stage-1 blocks in one launch (CTA tables as launch_sytrd1); cones of side <= bt1_max_side()
 void launch_bt1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,

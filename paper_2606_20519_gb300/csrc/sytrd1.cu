@@ -71,6 +71,7 @@ __device__ bool group_barrier(int* counter, int target, long long limit, int* fl
 
 constexpr int kChunk = 256;   // rows per work item (32 lanes x 8 loads in flight)
 constexpr int kPartMax = 2048; // work items per round (shared-memory partial sums)
+constexpr size_t kSyResidentMax = 200 * 1024;  // dynamic shared memory of a launch, at most
 
 // Householder reflector of x[0 .. len-1] in place (every thread of the CTA
 // calls it; x in shared memory): H x = beta e_1 with H = I - tau u u^T,
@@ -119,38 +120,49 @@ __device__ void store_reflector(const ConeDev& c, int n, int j, const double* u,
 // with UPDATE, first A(r, i) -= v_r w_i + w_r v_i (vu, wu indexed from row
 // r0 - 1); then p_i = tau * sum_r A(r, i) u_r (u indexed from row r0) into
 // pbuf[i].  Returns this CTA's sum of p_i u_i (thread 0 holds it).
-template <bool UPDATE>
-__device__ double column_pass(double* __restrict__ A, int n, int r0, const double* __restrict__ u, double tau,
-                              const double* __restrict__ vu, const double* __restrict__ wu, double* pbuf,
-                              double* psum, double* red, int rank, int G) {
+// RES: this CTA's columns live in shared memory (cols, column i at
+// ((i - rank) / G) * n); the owner of column r0 -- the next reflector's
+// source -- also writes its updated rows to A for every CTA to read.
+template <bool UPDATE, bool RES>
+__device__ double column_pass(double* __restrict__ A, double* __restrict__ cols, int n, int r0,
+                              const double* __restrict__ u, double tau, const double* __restrict__ vu,
+                              const double* __restrict__ wu, double* pbuf, double* psum, int pcap, double* red,
+                              int rank, int G) {
   const int L = n - r0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int first = r0 + ((rank - r0 % G) + G) % G;
   const int ncol = first < n ? (n - 1 - first) / G + 1 : 0;
   const int nch = (L + kChunk - 1) / kChunk;
-  const int per = kPartMax / nch;
+  const int per = pcap / nch;
   double mypv = 0.0;
   for (int k0 = 0; k0 < ncol; k0 += per) {
     const int kc = min(ncol - k0, per);
     for (int it = warp; it < kc * nch; it += kSyThreads / 32) {
       const int k = k0 + it / nch, ch = it % nch;
       const int i = first + G * k;
-      double* col = A + (int64_t)i * n + r0;
+      double* gcol = A + (int64_t)i * n + r0;
+      double* col = RES ? cols + (int64_t)((i - rank) / G) * n + r0 : gcol;
       const int t0 = ch * kChunk + lane;
       double a[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
         const int t = t0 + 32 * r;
-        a[r] = t < L ? __ldcg(col + t) : 0.0;
+        a[r] = t < L ? (RES ? col[t] : __ldcg(col + t)) : 0.0;
       }
       if (UPDATE) {
         const double vi = vu[i - r0 + 1], wi = wu[i - r0 + 1];
+        const bool publish = RES && i == r0;
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
           const int t = t0 + 32 * r;
           if (t < L) {
             a[r] = a[r] - fma(vu[t + 1], wi, wu[t + 1] * vi);
-            __stcg(col + t, a[r]);
+            if (RES) {
+              col[t] = a[r];
+              if (publish) __stcg(gcol + t, a[r]);
+            } else {
+              __stcg(col + t, a[r]);
+            }
           }
         }
       }
@@ -186,24 +198,29 @@ __device__ double column_pass(double* __restrict__ A, int n, int r0, const doubl
 //     A <- A - v w^T - w v^T to rows j+2 .. and forms the next step's
 //     p_i = tau_{j+1} A(j+2:, i)^T v'  (fused: one read and one write of A).
 // One group barrier per column.
-__global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __restrict__ cones,
-                                                            const int* __restrict__ cta_cone,
-                                                            const int* __restrict__ cta_rank,
-                                                            const int* __restrict__ cta_count,
-                                                            long long wait_limit) {
-  extern __shared__ double sy_smem[];
-  __shared__ double red[kSyThreads / 32];
-  __shared__ double sh[4];
-  __shared__ int sh_flag;
-  const ConeDev& c = cones[cta_cone[blockIdx.x]];
-  const int rank = cta_rank[blockIdx.x], G = cta_count[blockIdx.x];
+// Shared memory of a CTA: v, w, the updated column (3n), the partial sums,
+// and with RES the CTA's own columns (ceil(n / G) of n rows).
+__host__ __device__ inline int sytrd1_pcap(int n, int G) {
+  const int items = ((n + G - 1) / G) * ((n + kChunk - 1) / kChunk);
+  return items < kPartMax ? items : kPartMax;
+}
+__host__ __device__ inline size_t sytrd1_bytes(int n, int G, bool res) {
+  const size_t own = res ? (size_t)((n + G - 1) / G) * n : 0;
+  return ((size_t)3 * n + sytrd1_pcap(n, G) + own) * sizeof(double);
+}
+
+template <bool RES>
+__device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_limit, double* sy_smem, double* red,
+                            double* sh, int* sh_flag_p) {
+  int& sh_flag = *sh_flag_p;
   const int n = (int)c.n;
-  if (*c.status != 0) return;
   double* A = c.A;
+  const int pcap = sytrd1_pcap(n, G);
+  double* cols = sy_smem + 3 * n + pcap;  // RES: own columns
   double* vc = sy_smem;             // v_j (rows j+1 ..)
   double* w = sy_smem + n;          // p_j, then w_j
   double* vx = sy_smem + 2 * n;     // updated column j+1 (rows j+1 ..), then v_{j+1} at vx + 1
-  double* psum = sy_smem + 3 * n;   // kPartMax partial dot products
+  double* psum = sy_smem + 3 * n;   // pcap partial dot products
   // p and the partial sums p^T v, double-buffered by step parity: a CTA
   // writes step j+2's values only after every CTA has passed step j+1's
   // barrier, i.e. finished reading step j's values
@@ -212,6 +229,14 @@ __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __res
   int* bar = c.prog;
   const int tid = threadIdx.x;
   int bstep = 0;
+  if (RES) {
+    for (int i = rank; i < n; i += G) {
+      const double* src = A + (int64_t)i * n;
+      double* dst = cols + (int64_t)((i - rank) / G) * n;
+      for (int r = tid; r < n; r += kSyThreads) dst[r] = __ldcg(src + r);
+    }
+    __syncthreads();
+  }
   if (n < 3) {
     if (rank == 0 && tid == 0) {
       c.d[0] = A[0];
@@ -233,7 +258,7 @@ __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __res
   }
   store_reflector(c, n, 0, vc, rank, G);
   {
-    const double pv = column_pass<false>(A, n, 1, vc, tau, nullptr, nullptr, pbuf2, psum, red, rank, G);
+    const double pv = column_pass<false, RES>(A, cols, n, 1, vc, tau, nullptr, nullptr, pbuf2, psum, pcap, red, rank, G);
     if (tid == 0) __stcg(part2 + rank, pv);
   }
   for (int j = 0; j + 2 < n; ++j) {
@@ -283,23 +308,46 @@ __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __res
       }
       store_reflector(c, n, j + 1, vx + 1, rank, G);
       double* pnext = pbuf2 + ((j + 1) & 1) * n;
-      const double pv = column_pass<true>(A, n, j + 2, vx + 1, tau1, vc, w, pnext, psum, red, rank, G);
+      const double pv = column_pass<true, RES>(A, cols, n, j + 2, vx + 1, tau1, vc, w, pnext, psum, pcap, red, rank, G);
       if (tid == 0) __stcg(part2 + ((j + 1) & 1) * G + rank, pv);
       // v_{j+1} becomes the current reflector
       for (int t = tid; t < m - 1; t += kSyThreads) vc[t] = vx[1 + t];
       tau = tau1;
       __syncthreads();
     } else {
-      // the last 2 x 2 block (rows n-2, n-1)
+      // the last 2 x 2 block (rows n-2, n-1); A(n-1, n-1) is current in its
+      // owner's copy (and in A unless RES)
       if (rank == 0 && tid == 0) {
-        const double a = __ldcg(A + (int64_t)(n - 1) + (int64_t)(n - 1) * n);
         c.d[n - 2] = vx[0];
         c.e[n - 2] = vx[1];
-        c.d[n - 1] = a - fma(vc[1], w[1], w[1] * vc[1]);
         c.e[n - 1] = 0.0;
+      }
+      if (rank == (RES ? (n - 1) % G : 0) && tid == 0) {
+        const double a = RES ? cols[(int64_t)((n - 1 - rank) / G) * n + (n - 1)]
+                             : __ldcg(A + (int64_t)(n - 1) + (int64_t)(n - 1) * n);
+        c.d[n - 1] = a - fma(vc[1], w[1], w[1] * vc[1]);
       }
     }
   }
+}
+
+__global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __restrict__ cones,
+                                                            const int* __restrict__ cta_cone,
+                                                            const int* __restrict__ cta_rank,
+                                                            const int* __restrict__ cta_count,
+                                                            long long wait_limit, int smem_bytes) {
+  extern __shared__ double sy_smem[];
+  __shared__ double red[kSyThreads / 32];
+  __shared__ double sh[4];
+  __shared__ int sh_flag;
+  const ConeDev& c = cones[cta_cone[blockIdx.x]];
+  const int rank = cta_rank[blockIdx.x], G = cta_count[blockIdx.x];
+  if (*c.status != 0) return;
+  // every CTA of a cone takes the same decision (same n, G, launch)
+  if (sytrd1_bytes((int)c.n, G, true) <= (size_t)smem_bytes)
+    sytrd1_body<true>(c, rank, G, wait_limit, sy_smem, red, sh, &sh_flag);
+  else
+    sytrd1_body<false>(c, rank, G, wait_limit, sy_smem, red, sh, &sh_flag);
 }
 
 // T factor of each 32-reflector block (one CTA per block): G = V^T V, then
@@ -363,20 +411,23 @@ __global__ void __launch_bounds__(kSyThreads) larft1_kernel(const ConeDev* __res
 
 }  // namespace
 
-int sytrd1_max_ctas(int maxn) {
+size_t sytrd1_smem_bytes(int n, int G, bool resident) { return sytrd1_bytes(n, G, resident); }
+
+int sytrd1_max_ctas_for(size_t smem) {
   int per_sm = 0, sms = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const size_t smem = ((size_t)3 * maxn + kPartMax) * sizeof(double);
-  cudaFuncSetAttribute(sytrd1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(sytrd1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSyResidentMax);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sytrd1_kernel, kSyThreads, smem);
   return per_sm * sms;
 }
 
+int sytrd1_max_ctas(int maxn) { return sytrd1_max_ctas_for(sytrd1_bytes(maxn, 1, false)); }
+
 int launch_sytrd1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,
-                  int maxn, long long wait_limit, cudaStream_t s) {
+                  int maxn, size_t smem, long long wait_limit, cudaStream_t s) {
   if (nctas <= 0) return 0;
-  const size_t smem = ((size_t)3 * maxn + kPartMax) * sizeof(double);
+  if (smem < sytrd1_bytes(maxn, 1, false)) smem = sytrd1_bytes(maxn, 1, false);
   // co-resident CTAs (they wait on one another); the attribute also survives graph recording
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nctas);
@@ -388,7 +439,7 @@ int launch_sytrd1(const ConeDev* cones, const int* cta_cone, const int* cta_rank
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return (int)cudaLaunchKernelEx(&cfg, sytrd1_kernel, cones, cta_cone, cta_rank, cta_count, wait_limit);
+  return (int)cudaLaunchKernelEx(&cfg, sytrd1_kernel, cones, cta_cone, cta_rank, cta_count, wait_limit, (int)smem);
 }
 
 void launch_larft1(const ConeDev* cones, const int* blk_cone, const int* blk_index, int nblocks, cudaStream_t s) {
