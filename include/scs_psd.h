@@ -60,10 +60,11 @@ enum {
 /* Arithmetic used for the dense contractions. */
 typedef enum {
   SCS_PSD_FP64 = 0,       /* FP64 throughout */
-  SCS_PSD_SPLIT_TF32 = 1  /* dense contractions as split-TF32 tensor-core products (FP64 operands
-                             rounded to FP32 and split into three TF32 parts, the six products above
-                             the lowest order, FP32 accumulation per 8-wide K step, compensated
-                             FP32 sums across steps); Householder panels, bulge chasing, secular
+  SCS_PSD_SPLIT_TF32 = 1  /* dense contractions as split-TF32 tensor-core products: FP64 operands
+                             sliced on a grid shared by each 16-wide K chunk into three TF32 parts
+                             (10 + 11 + 11 bits), six part products, the leading ones summed exactly
+                             in FP32, compensated FP32 sums across chunks (relative error of the
+                             projection about 2e-8); Householder panels, bulge chasing, secular
                              equations and sign decisions stay FP64 */
 } scs_psd_precision;
 

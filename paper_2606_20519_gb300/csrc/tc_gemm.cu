@@ -1,24 +1,36 @@
 // Split-TF32 GEMM on the 5th-generation tensor cores (tcgen05), FP64 in and out.
 //
-// C = alpha op(A) op(B) + beta C with FP64 operands in global memory.  Each
-// operand element x is rounded to FP32 and split exactly into three TF32
-// values x32 = hi + mid + lo, and the product is formed from the six part
-// products whose orders sum to at most 2 (hh, hm, mh, hl, mm, lh), each a
-// tcgen05.mma of kind::tf32 with FP32 accumulation in tensor memory.  The
-// dropped products are below 2^-33 of the result; the operand rounding
-// (2^-24) and the FP32 accumulation bound the accuracy.  The FP64 parts of
-// the eigensolver (Householder panels, bulge chasing, secular equations,
-// sign decisions) stay FP64.
+// C = alpha op(A) op(B) + beta C with FP64 operands in global memory.
+//
+// Operand split on a common grid (the Ozaki idea of error-free slicing):
+// the elements of one row of op(A) (one column of op(B)) within a 16-wide
+// K chunk share the exponent 2^T of their largest magnitude, and each
+// element x is rounded to the 32-bit fixed-point grid 2^(T-32) and cut into
+// three integer slices of 10, 11 and 11 bits,
+//     x ~ hi + mid + lo,  hi on 2^(T-10), mid on 2^(T-21), lo on 2^(T-32),
+// each exactly a TF32 value.  Then every hi*hi product of a chunk is an
+// integer multiple of one unit with at most 20 bits, so a chunk's 16 of them
+// sum EXACTLY in the tensor core's FP32 accumulator (at most 2^24 units).
+// The other retained products (hm, mh, hl, mm, lh) are at most 2^-10 of
+// those and go to a second accumulator, whose FP32 rounding costs 2^-34.
+// The dropped products (ml, lm, ll) and the grid rounding leave an error of
+// about 2^-30 of max|a| max|b| per term, against 2^-24 when the operands
+// were rounded to FP32.  Accumulators are drained per stage into
+// compensated FP32 sums (TwoSum).  The FP64 parts of the eigensolver
+// (Householder panels, bulge chasing, secular equations, sign decisions)
+// stay FP64.
 //
 // Tile 128 x BN (BN = 16 or 64), K-stage 32, two shared-memory stages.  The
-// 128 threads load FP64, split and store the three TF32 parts into the
-// K-major, no-swizzle core-matrix layout (8 rows x 16 bytes per core matrix,
-// K-direction core stride 128 B, 8-row-group stride 1024 B); thread 0 issues
-// the MMAs and a tcgen05.commit per stage to that stage's mbarrier, so the
-// next stage loads while the tensor core works.  The epilogue reads the
-// accumulator with tcgen05.ld (warp w owns rows 32w .. 32w+31).  Every
-// mbarrier wait is bounded; on expiry the cone is flagged ST_TIMEOUT and the
-// tile is skipped, and tensor memory is always released.
+// 128 threads load FP64 into a staging buffer while taking the chunk
+// exponents (shared-memory atomicMax), then slice and store the three TF32
+// parts into the K-major, no-swizzle core-matrix layout (8 rows x 16 bytes
+// per core matrix, K-direction core stride 128 B, 8-row-group stride
+// 1024 B); thread 0 issues the MMAs and a tcgen05.commit per stage to that
+// stage's mbarrier, so the next stage loads while the tensor core works.
+// The epilogue reads tensor memory with tcgen05.ld (warp w owns rows
+// 32w .. 32w+31).  Every mbarrier wait is bounded; on expiry the cone is
+// flagged ST_TIMEOUT and the tile is skipped, and tensor memory is always
+// released.
 #include <stdint.h>
 
 #include "internal.cuh"
@@ -52,34 +64,40 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return r;
 }
 
-// FP64 -> FP32 with round-to-nearest-even by integer operations, so that the
-// conversion of every operand element does not occupy the FP64 pipe (on this
-// part a conversion costs as much as an FP64 FMA); magnitudes below 2^-126
-// become zero (far below the split's resolution).
-__device__ __forceinline__ float f64_to_f32(double v) {
-  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
-  const int e = (int)((hi >> 20) & 0x7FF) - 896;
-  if (e <= 0) return 0.0f;
-  // 52-bit mantissa -> 23 bits, rounding on the 29 dropped bits (ties to even);
-  // a carry out of the mantissa correctly bumps the exponent field
-  uint32_t bits = ((uint32_t)min(e, 254) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
-  const uint32_t rest = lo & 0x1FFFFFFFu, half = 0x10000000u;
-  if (rest > half || (rest == half && (bits & 1u))) ++bits;
-  return __uint_as_float((hi & 0x80000000u) | bits);
+// v * 2^p for an integer 0 <= v < 2^12 (exact unless the result leaves the
+// normal FP32 range, far below the slices' resolution in this solver).
+__device__ __forceinline__ float scaled_int(uint32_t v, int p) {
+  if (v == 0u) return 0.0f;
+  const float f = (float)v;
+  if (p >= -126 && p <= 127) return f * __int_as_float((p + 127) << 23);
+  if (p < -126 && p >= -252) return (f * __int_as_float((p + 126 + 127) << 23)) * __int_as_float(1 << 23);
+  return p > 0 ? __int_as_float(0x7f800000) : 0.0f;
 }
 
-// x ~ hi + mid + lo, three TF32 values that reproduce the FP32 rounding of x
-// exactly (11 + 11 + 2 significant bits).
-__device__ __forceinline__ void split_store(uint8_t* const* parts, uint32_t off, double v) {
-  const float x = f64_to_f32(v);
-  const uint32_t h = to_tf32(x);
-  const float r1 = x - __uint_as_float(h);
-  const uint32_t m = to_tf32(r1);
-  const uint32_t l = to_tf32(r1 - __uint_as_float(m));
-  *(uint32_t*)(parts[0] + off) = h;
-  *(uint32_t*)(parts[1] + off) = m;
-  *(uint32_t*)(parts[2] + off) = l;
+// Slices of v on the grid of its chunk (largest biased exponent eg): v ~
+// sign (qh 2^(T-10) + qm 2^(T-21) + ql 2^(T-32)), T = eg - 1022, with
+// q = round(|v| 2^(32-T)) < 2^32 + 1 taken from the FP64 bits by integer
+// operations only (nothing here occupies the FP64 pipe).
+__device__ __forceinline__ void split_grid(uint8_t* const* parts, uint32_t off, double v, int eg) {
+  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+  const int e = (int)((hi >> 20) & 0x7FF);
+  float fh = 0.0f, fm = 0.0f, fl = 0.0f;
+  if (e != 0 && eg != 0) {
+    const int sh = 21 + (eg - e);  // >= 21
+    const uint64_t mant = ((uint64_t)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
+    const uint64_t q = sh >= 64 ? 0ull : (((mant >> (sh - 1)) + 1ull) >> 1);
+    const int T = eg - 1022;
+    fh = scaled_int((uint32_t)(q >> 22), T - 10);
+    fm = scaled_int((uint32_t)(q >> 11) & 0x7FFu, T - 21);
+    fl = scaled_int((uint32_t)q & 0x7FFu, T - 32);
+    if (hi >> 31) { fh = -fh; fm = -fm; fl = -fl; }
+  }
+  *(float*)(parts[0] + off) = fh;
+  *(float*)(parts[1] + off) = fm;
+  *(float*)(parts[2] + off) = fl;
 }
+
+__device__ __forceinline__ int exp_field(double v) { return (int)(((uint32_t)__double2hiint(v) >> 20) & 0x7FF); }
 
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
   for (long long it = 0; it < kTcWaitIters; ++it) {
@@ -105,10 +123,16 @@ __device__ __forceinline__ int find_problem(const int* prefix, int count, int ti
 
 constexpr int NSPLIT = 3;
 
+constexpr int KCH = 16;  // K chunk sharing one exponent (16 hi*hi products sum exactly)
+
 template <int BN>
 struct TcSmem {
   uint8_t a[2][NSPLIT][TBM * TBK * 4];  // [stage][hi/mid/lo]
   uint8_t b[2][NSPLIT][BN * TBK * 4];
+  double sta[TBM * TBK];                // FP64 staging of the stage being loaded
+  double stb[BN * TBK];
+  int ema[2][TBM][TBK / KCH];           // [stage][row][chunk] largest exponent field
+  int emb[2][BN][TBK / KCH];
   uint64_t mbar[2];
   uint32_t tmem;
   int fail;
@@ -157,9 +181,16 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
     asm volatile("fence.mbarrier_init.release.cluster;");
     sm.fail = 0;
   }
-  // one accumulator per 8-wide K-step and stage: 2 stages x 4 K-steps x BN columns
-  constexpr int NACC = 2 * (TBK / 8);
-  constexpr int TCOLS = (NACC * BN) < 32 ? 32 : NACC * BN;
+  for (int q = tid; q < 2 * (TBM + BN) * (TBK / KCH); q += 128) {
+    if (q < 2 * TBM * (TBK / KCH)) (&sm.ema[0][0][0])[q] = 0;
+    else (&sm.emb[0][0][0])[q - 2 * TBM * (TBK / KCH)] = 0;
+  }
+  // per stage: one exact accumulator per 16-wide K chunk (hi*hi) and one for
+  // the smaller products: 2 stages x 3 accumulators x BN columns
+  constexpr int NACC = 2 * (TBK / KCH + 1);
+  constexpr int ACC_PER_STAGE = TBK / KCH + 1;
+  constexpr int TCOLS = (NACC * BN) <= 32 ? 32 : (NACC * BN) <= 64 ? 64 : (NACC * BN) <= 128 ? 128
+                        : (NACC * BN) <= 256 ? 256 : 512;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem)),
                  "r"(TCOLS));
@@ -172,19 +203,18 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
   // idesc: D f32, A/B tf32, both K-major, N >> 3 at bit 17, M >> 4 at bit 24
   const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
 
-  // Short accumulations: the MMAs of K-step ks of stage kt write accumulator
-  // (kt & 1, ks), fresh each time; two stages later all threads read the
-  // stage's four accumulators and add them into compensated FP32 register
-  // sums (TwoSum), so the tensor core's FP32 accumulation never spans more
-  // than 8 products of the leading parts.
+  // Accumulators of stage kt: (kt & 1, chunk) for the exact hi*hi sums and
+  // (kt & 1, rest) for the others, fresh each time; two stages later all
+  // threads read them and add them into compensated FP32 register sums
+  // (TwoSum).
   float acc_hi[BN], acc_lo[BN];
 #pragma unroll
   for (int q = 0; q < BN; ++q) { acc_hi[q] = 0.0f; acc_lo[q] = 0.0f; }
   bool ok = true;
   auto drain = [&](int stage) {
 #pragma unroll
-    for (int ks = 0; ks < TBK / 8; ++ks) {
-    const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(((stage & 1) * (TBK / 8) + ks) * BN);
+    for (int ks = 0; ks < ACC_PER_STAGE; ++ks) {
+    const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(((stage & 1) * ACC_PER_STAGE + ks) * BN);
 #pragma unroll
     for (int c0 = 0; c0 < BN; c0 += 16) {
       uint32_t r[16];
@@ -214,7 +244,8 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
       if (ok) drain(kt - 2);
     }
     const int k0 = kbeg + kt * TBK;
-    // ---- A tile: op(A)(i0 + r, k0 + k), 128 x 32
+    // ---- pass 1: FP64 values into staging, chunk exponents
+    // A tile: op(A)(i0 + r, k0 + k), 128 x 32
 #pragma unroll 4
     for (int q = 0; q < (TBM * TBK) / 128; ++q) {
       const int e = tid + q * 128;
@@ -227,10 +258,11 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
         else if (ta) v = A[(int64_t)kk + (int64_t)i * lda];
         else v = A[(int64_t)i + (int64_t)kk * lda];
       }
-      uint8_t* pa[3] = {sm.a[s][0], sm.a[s][1], sm.a[s][2]};
-      split_store(pa, tile_off(r, k), v);
+      sm.sta[e] = v;
+      const int ex = exp_field(v);
+      if (ex) atomicMax(&sm.ema[s][r][k / KCH], ex);
     }
-    // ---- B tile: op(B)(k0 + k, j0 + c) stored as BN rows (c) x 32 (k), K-major
+    // B tile: op(B)(k0 + k, j0 + c) stored as BN rows (c) x 32 (k), K-major
 #pragma unroll 4
     for (int q = 0; q < (BN * TBK + 127) / 128; ++q) {
       const int e = tid + q * 128;
@@ -243,8 +275,35 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
           v = tb ? B[(int64_t)j + (int64_t)kk * ldb] : B[(int64_t)kk + (int64_t)j * ldb];
           if (scl) v *= g.bscale[kk];
         }
-        uint8_t* pb[3] = {sm.b[s][0], sm.b[s][1], sm.b[s][2]};
-        split_store(pb, tile_off(c, k), v);
+        sm.stb[e] = v;
+        const int ex = exp_field(v);
+        if (ex) atomicMax(&sm.emb[s][c][k / KCH], ex);
+      }
+    }
+    __syncthreads();
+    // ---- pass 2: slices on the chunk grids; clear the other stage's exponents
+    {
+      uint8_t* pa[3] = {sm.a[s][0], sm.a[s][1], sm.a[s][2]};
+#pragma unroll 4
+      for (int q = 0; q < (TBM * TBK) / 128; ++q) {
+        const int e = tid + q * 128;
+        int r, k;
+        if (ta) { k = e % TBK; r = e / TBK; } else { r = e % TBM; k = e / TBM; }
+        split_grid(pa, tile_off(r, k), sm.sta[e], sm.ema[s][r][k / KCH]);
+      }
+      uint8_t* pb[3] = {sm.b[s][0], sm.b[s][1], sm.b[s][2]};
+#pragma unroll 4
+      for (int q = 0; q < (BN * TBK + 127) / 128; ++q) {
+        const int e = tid + q * 128;
+        if ((BN * TBK) % 128 == 0 || e < BN * TBK) {
+          int c, k;
+          if (tb) { c = e % BN; k = e / BN; } else { k = e % TBK; c = e / TBK; }
+          split_grid(pb, tile_off(c, k), sm.stb[e], sm.emb[s][c][k / KCH]);
+        }
+      }
+      for (int q = tid; q < (TBM + BN) * (TBK / KCH); q += 128) {
+        if (q < TBM * (TBK / KCH)) (&sm.ema[s ^ 1][0][0])[q] = 0;
+        else (&sm.emb[s ^ 1][0][0])[q - TBM * (TBK / KCH)] = 0;
       }
     }
     asm volatile("fence.proxy.async.shared::cta;");
@@ -252,7 +311,8 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      // products with i + j <= 2 of the three parts: hh, hm, mh, hl, mm, lh
+      // products with i + j <= 2 of the three parts: hh (exact, per 16-wide
+      // chunk), then hm, mh, hl, mm, lh (one accumulator per stage)
       constexpr int PA[6] = {0, 0, 1, 0, 1, 2};
       constexpr int PB[6] = {0, 1, 0, 2, 1, 0};
 #pragma unroll
@@ -261,11 +321,12 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
         for (int q = 0; q < 6; ++q) {
           const uint64_t da = make_desc(smem_u32(sm.a[s][PA[q]]) + ks * 256);
           const uint64_t db = make_desc(smem_u32(sm.b[s][PB[q]]) + ks * 256);
-          const uint32_t acc = (q > 0) ? 1u : 0u;
+          const int slot = (q == 0) ? (ks * 8) / KCH : TBK / KCH;
+          const uint32_t acc = (q == 0) ? (((ks * 8) % KCH) != 0 ? 1u : 0u) : ((ks == 0 && q == 1) ? 0u : 1u);
           asm volatile(
               "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
               "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
-                  tmem + (uint32_t)((s * (TBK / 8) + ks) * BN)),
+                  tmem + (uint32_t)((s * ACC_PER_STAGE + slot) * BN)),
               "l"(da), "l"(db), "r"(idesc), "r"(acc));
         }
       }
