@@ -161,6 +161,26 @@ int scs_psd_vjp_stored(scs_psd_handle h, const double* V, const double* lam, con
  * between them.  Device-side errors fill y with NaN; no handle is needed. */
 int scs_psd_proj_static(const double* x, double* y, int64_t n, void* stream);
 
+/* Autotuner (launch shapes are the project's own choice; the paper fixes
+ * none).  Times candidate launch shapes of the projection for this shape
+ * list and precision on the caller's input x (device, layout as
+ * scs_psd_proj_batched; not modified): the route and band width (automatic,
+ * one-stage, two-stage with 8, 16, 32), the GEMM split-K target (1, 2, 4
+ * CTAs per SM), and for one-stage cones the back-transformation slab width
+ * (2, 4, 8 columns) and the one-stage group size (all or half of the SMs),
+ * by coordinate search, three timed runs each (CUDA events on `stream`).
+ * The winner is kept in the handle and used by every later call with these
+ * shapes and precision whose opts->band is 0.  chosen (may be NULL)
+ * receives {band, gemm CTAs per SM, slab columns, group share}, best_ms (may
+ * be NULL) its time per call.  Allocates a scratch output for the duration;
+ * synchronises `stream`; drops the handle's cached plans. */
+int scs_psd_autotune(scs_psd_handle h, const double* x, const int64_t* offsets, const int32_t* sides,
+                     int32_t count, const scs_psd_opts* opts, void* stream, int32_t* chosen,
+                     double* best_ms);
+
+/* The launch shapes of the last call, as scs_psd_autotune's `chosen`. */
+int scs_psd_last_tuning(scs_psd_handle h, int32_t* out);
+
 /* Optional pre-sizing of the workspace for cones up to side max_n and
  * max_count cones of that side. */
 int scs_psd_reserve(scs_psd_handle h, int64_t max_n, int32_t max_count, const scs_psd_opts* opts);

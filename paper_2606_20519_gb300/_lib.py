@@ -37,7 +37,8 @@ _handles = {}
 
 EXPORTS = ("scs_psd_create", "scs_psd_destroy", "scs_psd_proj", "scs_psd_proj_batched", "scs_psd_proj_vjp",
            "scs_psd_proj_store", "scs_psd_vjp_stored", "scs_psd_proj_static", "scs_psd_reserve", "scs_psd_status", "scs_psd_last_launch_count",
-           "scs_psd_last_replayed", "scs_psd_strerror", "scs_psd_trace", "scs_psd_trace_read")
+           "scs_psd_last_replayed", "scs_psd_strerror", "scs_psd_trace", "scs_psd_trace_read",
+           "scs_psd_autotune", "scs_psd_last_tuning")
 NPHASES = 8
 PHASES = ("unpack", "dense_to_band", "band_to_tridiag", "tridiag_dc", "backtransform_2", "backtransform_1",
           "reconstruct", "derivative")
@@ -68,6 +69,9 @@ def load(path: str | None = None):
         lib.scs_psd_status.argtypes = [vp, ctypes.POINTER(i32)]
         lib.scs_psd_last_launch_count.argtypes = [vp]
         lib.scs_psd_last_launch_count.restype = i64
+        lib.scs_psd_autotune.argtypes = [vp, vp, vp, vp, i32, op, vp, ctypes.POINTER(i32),
+                                         ctypes.POINTER(ctypes.c_double)]
+        lib.scs_psd_last_tuning.argtypes = [vp, ctypes.POINTER(i32)]
         lib.scs_psd_last_replayed.argtypes = [vp]
         lib.scs_psd_last_replayed.restype = ctypes.c_int
         lib.scs_psd_trace.argtypes = [vp, ctypes.c_int]
@@ -244,6 +248,33 @@ def vjp_stored(V, lam, g, sides, xbar=None, opts: Opts | None = None, offsets=No
                                    _stream_ptr(g))
     _check(rc, "scs_psd_vjp_stored")
     return xbar
+
+
+TUNING_FIELDS = ("band", "gemm_ctas", "bt1_cols", "sy_share")
+
+
+def autotune(x, sides, opts: Opts | None = None, offsets=None) -> dict:
+    """Time launch-shape candidates on x and keep the fastest for these shapes
+    (C-ABI scs_psd_autotune); returns the choice and its time per call."""
+    _check_tensor(x, "x")
+    offsets, sides = _shape_arrays(sides, offsets)
+    out = (ctypes.c_int32 * 4)()
+    ms = ctypes.c_double(0.0)
+    rc = load().scs_psd_autotune(handle(x.device.index), _ptr(x), offsets.ctypes.data_as(ctypes.c_void_p),
+                                 sides.ctypes.data_as(ctypes.c_void_p), int(sides.size),
+                                 ctypes.byref(opts) if opts is not None else None, _stream_ptr(x), out,
+                                 ctypes.byref(ms))
+    _check(rc, "scs_psd_autotune")
+    d = dict(zip(TUNING_FIELDS, [int(v) for v in out]))
+    d["ms"] = float(ms.value)
+    return d
+
+
+def last_tuning(device: int = 0) -> dict:
+    """Launch shapes of the last call on the device."""
+    out = (ctypes.c_int32 * 4)()
+    _check(load().scs_psd_last_tuning(handle(device), out), "scs_psd_last_tuning")
+    return dict(zip(TUNING_FIELDS, [int(v) for v in out]))
 
 
 def status(device: int = 0) -> int:

@@ -61,8 +61,22 @@ struct Level {
   GemmLaunch g;
 };
 
+// Launch-shape choices of a plan: the ones the autotuner searches.
+struct Tuning {
+  int band = 0;       // 0: automatic path (one-stage up to kOneStageMax), 1: one-stage, 2..32: two-stage width
+  int gemm_ctas = 2;  // grouped GEMMs: split K until a launch has about this many CTAs per SM
+  int bt1_cols = 8;   // fused stage-1 back-transformation: columns per CTA slab, at most
+  int sy_share = 1;   // one-stage tridiagonalisation: a large cone's group has at most SMs / sy_share CTAs
+  std::string str() const {
+    char b[64];
+    snprintf(b, sizeof(b), "t%d,%d,%d,%d", band, gemm_ctas, bt1_cols, sy_share);
+    return b;
+  }
+};
+
 struct Plan {
   std::string key;
+  Tuning tune;
   int b = kDefaultBand;
   int allv = 0, side = 0, precision = SCS_PSD_FP64;
   GemmLaunch recon_tc;  // split mode: S = Z diag(l) Z^T on the tensor cores
@@ -125,6 +139,8 @@ struct scs_psd_handle_s {
   cudaStream_t last_stream = nullptr;
   int64_t last_launches = 0;
   std::map<std::string, std::unique_ptr<Plan>> plans;
+  std::map<std::string, Tuning> tuned;  // autotuner's choices by shapes and precision
+  Tuning last_tune;
   std::mutex mu;
 };
 
@@ -193,6 +209,7 @@ struct MetaBuilder {
   std::vector<int64_t> part_off;  // per descriptor: offset in the split-K scratch (doubles)
   std::vector<MergeNode> nodes;
   int sms = 148;
+  int gemm_ctas = 2;   // split-K target, CTAs per SM
   int64_t scratch_doubles = 0;
   bool split = false;  // use the split-TF32 tensor-core kernel where the shape suits it
 
@@ -226,7 +243,8 @@ struct MetaBuilder {
       base += tiles;
     }
     int S = 1;
-    if (base > 0 && base < 2 * sms) S = (int)std::min<int64_t>(64, (2 * sms + base - 1) / base);
+    const int64_t want = (int64_t)gemm_ctas * sms;
+    if (base > 0 && base < want) S = (int)std::min<int64_t>(64, (want + base - 1) / base);
     int t = 0;
     int64_t off = 0;
     for (GemmDesc& p : probs) {
@@ -275,7 +293,8 @@ struct Arena {
 };
 
 int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, int b, int allv, int side,
-               int precision, int onestage, Arena* arena = nullptr) {
+               int precision, int onestage, const Tuning& tune, Arena* arena = nullptr) {
+  P.tune = tune;
   P.b = b;
   P.allv = allv;
   P.side = side;
@@ -332,6 +351,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   // ---- metadata sizes known up front: status (ncones+1), prog
   MetaBuilder mb;
   mb.sms = h->sms > 0 ? h->sms : 148;
+  mb.gemm_ctas = std::max(1, tune.gemm_ctas);
   mb.split = (precision == SCS_PSD_SPLIT_TF32);
   std::vector<ConeDev> cones(P.ncones);
   size_t prog_total = 0;
@@ -476,7 +496,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
       // at most one CTA per SM for a cone: a step's work is small and the
       // group barrier's cost grows with the number of CTAs
       const int cap = std::max(1, sytrd1_max_ctas((int)maxn1));
-      const int sm_cap = std::max(1, h->sms);
+      const int sm_cap = std::max(1, h->sms / std::max(1, tune.sy_share));
       // large cones (n >= 256) share the GPU in one launch, small cones get one CTA each
       std::vector<int> large, small;
       for (int c : one) (cones[c].n >= 256 ? large : small).push_back(c);
@@ -628,7 +648,8 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
         const int bud = std::max(1, (int)(budget * w / wsum));
         const int kest = allv ? (int)n : (int)(n + 1) / 2;
         int per = 1;
-        while (per < 8 && (kest + per - 1) / per > bud) per *= 2;
+        const int per_max = std::max(1, std::min(8, tune.bt1_cols));
+        while (per < per_max && (kest + per - 1) / per > bud) per *= 2;
         const int g = std::max(1, (kest + per - 1) / per);
         for (int r = 0; r < g; ++r) { cc.push_back(c); cr.push_back(r); cn.push_back(g); }
         P.bt1k_maxn = std::max<int>(P.bt1k_maxn, (int)n);
@@ -1026,6 +1047,36 @@ int check_shapes(const int64_t* offsets, const int32_t* sides, int32_t count) {
   return SCS_PSD_OK;
 }
 
+std::string tune_key(const int32_t* sides, int32_t count, int precision) {
+  return plan_key(sides, count, 0, 0, 0, precision);
+}
+
+// The cached plan for these shapes, options and launch shapes (built on first use).
+int get_plan(scs_psd_handle h, const int32_t* sides, int32_t count, int allv, int side, int precision,
+             const Tuning& tune, Plan** out) {
+  int b = kDefaultBand, onestage = -1;
+  if (tune.band == 1) onestage = 1;
+  else if (tune.band >= 2) { onestage = 0; b = tune.band; }
+  if (b < 2 || b > kMaxBand) return SCS_PSD_EINVAL;
+  const std::string key = plan_key(sides, count, b, allv, side, precision) + (char)('A' + onestage + 1) + tune.str();
+  auto it = h->plans.find(key);
+  if (it != h->plans.end()) {
+    *out = it->second.get();
+    return SCS_PSD_OK;
+  }
+  if (h->plans.size() >= 16) {
+    cudaDeviceSynchronize();
+    h->plans.clear();
+  }
+  auto np = std::make_unique<Plan>();
+  np->key = key;
+  const int rc = build_plan(h, *np, sides, count, b, allv, side, precision, onestage, tune);
+  if (rc) return rc;
+  *out = np.get();
+  h->plans[key] = std::move(np);
+  return SCS_PSD_OK;
+}
+
 // One call of any entry point: `mode` (MODE_* bits) says which of io's
 // buffers are read and written; every one it names must be non-NULL.
 int do_call(scs_psd_handle h, const IoSlot& io, int mode, const int64_t* offsets, const int32_t* sides,
@@ -1040,44 +1091,144 @@ int do_call(scs_psd_handle h, const IoSlot& io, int mode, const int64_t* offsets
   if ((mode & (MODE_EXPORT | MODE_IMPORT)) && (!io.V || !io.lam)) return SCS_PSD_EINVAL;
   // every mode but the plain projection needs all n eigenpairs of each cone
   const int allv = (mode & (MODE_VJP | MODE_EXPORT | MODE_IMPORT)) ? 1 : 0;
-  int b = kDefaultBand, side = 0, precision = SCS_PSD_FP64;
+  int side = 0, precision = SCS_PSD_FP64;
   long long wait = kDefaultWaitCycles;
   if (opts) {
     if (opts->precision != SCS_PSD_FP64 && opts->precision != SCS_PSD_SPLIT_TF32) return SCS_PSD_EINVAL;
     if (opts->graphs < 0 || opts->graphs > 1 || opts->reserved != 0) return SCS_PSD_EINVAL;
+    if (opts->band < 0 || opts->band > kMaxBand) return SCS_PSD_EINVAL;
     precision = opts->precision;
-    if (opts->band) b = opts->band;
     side = opts->side;
     if (opts->wait_limit_cycles > 0) wait = opts->wait_limit_cycles;
   }
-  int onestage = -1;  // auto
-  if (b == 1) { onestage = 1; b = kDefaultBand; }
-  else if (opts && opts->band >= 2) onestage = 0;
-  if (b < 2 || b > kMaxBand || side < 0 || side > 2) return SCS_PSD_EINVAL;
+  if (side < 0 || side > 2) return SCS_PSD_EINVAL;
   std::lock_guard<std::mutex> lock(h->mu);
   if (cudaSetDevice(h->device) != cudaSuccess) return SCS_PSD_ECUDA;
-  cudaStream_t s = (cudaStream_t)stream;
-  const std::string key = plan_key(sides, count, b, allv, side, precision) + (char)('A' + onestage + 1);
-  auto it = h->plans.find(key);
-  Plan* P;
-  if (it == h->plans.end()) {
-    if (h->plans.size() >= 16) {
-      cudaDeviceSynchronize();
-      h->plans.clear();
-    }
-    auto np = std::make_unique<Plan>();
-    np->key = key;
-    rc = build_plan(h, *np, sides, count, b, allv, side, precision, onestage);
-    if (rc) return rc;
-    P = np.get();
-    h->plans[key] = std::move(np);
+  // launch shapes: an explicit band wins; otherwise the autotuner's choice for
+  // these shapes and precision, if it ran; otherwise the defaults
+  Tuning tune;
+  if (opts && opts->band) {
+    tune.band = opts->band;
   } else {
-    P = it->second.get();
+    auto t = h->tuned.find(tune_key(sides, count, precision));
+    if (t != h->tuned.end()) tune = t->second;
   }
+  Plan* P = nullptr;
+  rc = get_plan(h, sides, count, allv, side, precision, tune, &P);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
   rc = run_plan(h, *P, io, mode, wait, s, !(opts && opts->graphs == 1));
   h->last_stream = s;
   h->last_launches = P->launches;
+  h->last_tune = P->tune;
   return rc;
+}
+
+// ---- autotuner: times launch-shape candidates on the caller's input ----
+// Coordinate search: first the route and band width (automatic, one-stage,
+// two-stage with b = 8, 16, 32), then the GEMM split-K target (1, 2, 4 CTAs
+// per SM), then -- when the winner has one-stage cones -- the slab width of
+// the fused back-transformation (2, 4, 8 columns) and the group size of the
+// one-stage reduction (all SMs or half).  Each candidate runs once to warm up
+// and three times under CUDA events on `stream`; candidates whose device
+// status is not clean are discarded.  The winner is kept in the handle for
+// these shapes and precision and used by later calls that leave opts->band 0.
+int autotune(scs_psd_handle h, const double* x, const int64_t* offsets, const int32_t* sides, int32_t count,
+             const scs_psd_opts* opts, void* stream, int32_t* chosen, double* best_ms_out) {
+  if (!h || !x) return SCS_PSD_EINVAL;
+  int rc = check_shapes(offsets, sides, count);
+  if (rc) return rc;
+  if (count == 0 || offsets[count] == 0) return SCS_PSD_OK;
+  int side = 0, precision = SCS_PSD_FP64;
+  long long wait = kDefaultWaitCycles;
+  if (opts) {
+    if (opts->precision != SCS_PSD_FP64 && opts->precision != SCS_PSD_SPLIT_TF32) return SCS_PSD_EINVAL;
+    precision = opts->precision;
+    side = opts->side;
+    if (opts->wait_limit_cycles > 0) wait = opts->wait_limit_cycles;
+  }
+  if (side < 0 || side > 2) return SCS_PSD_EINVAL;
+  std::lock_guard<std::mutex> lock(h->mu);
+  if (cudaSetDevice(h->device) != cudaSuccess) return SCS_PSD_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  int maxn = 0;
+  for (int i = 0; i < count; ++i) maxn = std::max(maxn, (int)sides[i]);
+  double* y = nullptr;
+  if (cudaMalloc(&y, sizeof(double) * (size_t)offsets[count]) != cudaSuccess) return SCS_PSD_ENOMEM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const IoSlot io{x, y, nullptr, nullptr, nullptr, nullptr};
+  const double kInf = 1e300;
+  auto measure = [&](const Tuning& t) -> double {
+    Plan* P = nullptr;
+    if (get_plan(h, sides, count, 0, side, precision, t, &P)) return kInf;
+    if (cudaMemsetAsync(h->status_word, 0, sizeof(int), s) != cudaSuccess) return kInf;
+    if (run_plan(h, *P, io, MODE_Y, wait, s, false)) return kInf;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3; ++r)
+      if (run_plan(h, *P, io, MODE_Y, wait, s, false)) return kInf;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return kInf;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    int st = 0;
+    if (cudaMemcpy(&st, h->status_word, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || st != 0) return kInf;
+    return ms / 3.0;
+  };
+  Tuning best;
+  double best_ms = kInf;
+  auto consider = [&](const Tuning& t) {
+    const double ms = measure(t);
+    if (ms < best_ms) { best_ms = ms; best = t; }
+  };
+  consider(Tuning());
+  if (maxn >= 3) {
+    for (int band : {1, 8, 16, 32}) {
+      Tuning t;
+      t.band = band;
+      consider(t);
+    }
+  }
+  const Tuning route = best;
+  for (int gc : {1, 4}) {
+    Tuning t = route;
+    t.gemm_ctas = gc;
+    consider(t);
+  }
+  bool has_one = false;
+  for (int i = 0; i < count; ++i) {
+    const int n = sides[i];
+    if (n >= 3 && (best.band == 1 || (best.band == 0 && n <= kOneStageMax))) has_one = true;
+  }
+  if (has_one) {
+    const Tuning base = best;
+    for (int cols : {2, 4}) {
+      Tuning t = base;
+      t.bt1_cols = cols;
+      consider(t);
+    }
+    Tuning t = best;
+    t.sy_share = 2;
+    consider(t);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(y);
+  cudaMemset(h->status_word, 0, sizeof(int));
+  // keep only the winner's plan among this shape list's candidates
+  h->plans.clear();
+  if (best_ms >= kInf) return SCS_PSD_ECUDA;
+  h->tuned[tune_key(sides, count, precision)] = best;
+  if (chosen) {
+    chosen[0] = best.band;
+    chosen[1] = best.gemm_ctas;
+    chosen[2] = best.bt1_cols;
+    chosen[3] = best.sy_share;
+  }
+  if (best_ms_out) *best_ms_out = best_ms;
+  return SCS_PSD_OK;
 }
 
 // ---- static-scratch entry point: no device allocation at all ----
@@ -1128,7 +1279,7 @@ int proj_static(const double* x, double* y, int64_t n, void* stream) {
     ar.size = kStaticScratchBytes - 256;
     ar.stream = s;
     const int32_t sides[1] = {(int32_t)n};
-    const int rc = build_plan(&st.hview, *np, sides, 1, kDefaultBand, 0, 0, SCS_PSD_FP64, -1, &ar);
+    const int rc = build_plan(&st.hview, *np, sides, 1, kDefaultBand, 0, 0, SCS_PSD_FP64, -1, Tuning(), &ar);
     if (rc) return rc;
     st.plan = std::move(np);
     st.plan_n = n;
@@ -1213,6 +1364,20 @@ int scs_psd_vjp_stored(scs_psd_handle h, const double* V, const double* lam, con
 int scs_psd_reserve(scs_psd_handle h, int64_t max_n, int32_t max_count, const scs_psd_opts* opts) {
   (void)opts;
   if (!h || max_n < 0 || max_n > kMaxSide || max_count < 0) return SCS_PSD_EINVAL;
+  return SCS_PSD_OK;
+}
+
+int scs_psd_autotune(scs_psd_handle h, const double* x, const int64_t* offsets, const int32_t* sides, int32_t count,
+                     const scs_psd_opts* opts, void* stream, int32_t* chosen, double* best_ms) {
+  return autotune(h, x, offsets, sides, count, opts, stream, chosen, best_ms);
+}
+
+int scs_psd_last_tuning(scs_psd_handle h, int32_t* out) {
+  if (!h || !out) return SCS_PSD_EINVAL;
+  out[0] = h->last_tune.band;
+  out[1] = h->last_tune.gemm_ctas;
+  out[2] = h->last_tune.bt1_cols;
+  out[3] = h->last_tune.sy_share;
   return SCS_PSD_OK;
 }
 
