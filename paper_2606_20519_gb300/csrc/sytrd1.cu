@@ -76,9 +76,8 @@ constexpr size_t kSyResidentMax = 200 * 1024;  // dynamic shared memory of a lau
 // Householder reflector of x[0 .. len-1] in place (every thread of the CTA
 // calls it; x in shared memory): H x = beta e_1 with H = I - tau u u^T,
 // u_0 = 1 (LAPACK convention).  x becomes u; tau and beta are returned.
-__device__ double make_reflector(double* x, int len, double* red, double* sh, double* beta_out) {
-  double ps = 0.0;
-  for (int t = 1 + threadIdx.x; t < len; t += kSyThreads) ps = fma(x[t], x[t], ps);
+// ps: this thread's part of sum_{t >= 1} x[t]^2 (the caller's loop formed it).
+__device__ double make_reflector_ps(double* x, int len, double ps, double* red, double* sh, double* beta_out) {
   const double sigma = block_sum256(ps, red);
   if (threadIdx.x == 0) {
     const double alpha = x[0];
@@ -98,6 +97,12 @@ __device__ double make_reflector(double* x, int len, double* red, double* sh, do
   if (threadIdx.x == 0) x[0] = 1.0;
   *beta_out = sh[0];
   return sh[1];
+}
+
+__device__ double make_reflector(double* x, int len, double* red, double* sh, double* beta_out) {
+  double ps = 0.0;
+  for (int t = 1 + threadIdx.x; t < len; t += kSyThreads) ps = fma(x[t], x[t], ps);
+  return make_reflector_ps(x, len, ps, red, sh, beta_out);
 }
 
 // Reflector j (u indexed from row j+1) into its 32-column block of V1, with
@@ -156,7 +161,7 @@ __device__ double column_pass(double* __restrict__ A, double* __restrict__ cols,
         for (int r = 0; r < 8; ++r) {
           const int t = t0 + 32 * r;
           if (t < L) {
-            a[r] = a[r] - fma(vu[t + 1], wi, wu[t + 1] * vi);
+            a[r] = fma(-vu[t + 1], wi, fma(-wu[t + 1], vi, a[r]));
             if (RES) {
               col[t] = a[r];
               if (publish) __stcg(gcol + t, a[r]);
@@ -288,18 +293,26 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
       }
     }
     const double K = 0.5 * tau * block_sum256(pt, red);
-    for (int t = tid; t < m; t += kSyThreads) w[t] = fma(-K, vc[t], w[t]);
-    __syncthreads();
+    // one pass: w_t = p_t - K v_t, the updated column a_t - w_t v_0 - v_t w_0,
+    // and the next reflector's sum of squares (rows j+3 ..).  w[0] keeps p_0:
+    // every thread forms w_0 from it, and nothing later reads w[0].
+    double ps = 0.0;
     {
-      const double w0 = w[0];
-      for (int t = tid; t < m; t += kSyThreads) vx[t] = vx[t] - fma(vc[t], w0, w[t] * vc[0]);
+      const double v0 = vc[0];
+      const double w0 = fma(-K, v0, w[0]);
+      for (int t = tid; t < m; t += kSyThreads) {
+        const double wt = fma(-K, vc[t], w[t]);
+        if (t > 0) w[t] = wt;
+        const double nc = fma(-vc[t], w0, fma(-wt, v0, vx[t]));
+        vx[t] = nc;
+        if (t >= 2) ps = fma(nc, nc, ps);
+      }
     }
-    __syncthreads();
     if (j + 3 < n) {
       // ---- reflector j+1 from rows j+2 .. of the updated column
-      const double dj1 = vx[0];
       double beta1;
-      const double tau1 = make_reflector(vx + 1, m - 1, red, sh, &beta1);
+      const double tau1 = make_reflector_ps(vx + 1, m - 1, ps, red, sh, &beta1);
+      const double dj1 = vx[0];
       __syncthreads();
       if (rank == 0 && tid == 0) {
         c.d[j + 1] = dj1;
@@ -315,6 +328,7 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
       tau = tau1;
       __syncthreads();
     } else {
+      __syncthreads();
       // the last 2 x 2 block (rows n-2, n-1); A(n-1, n-1) is current in its
       // owner's copy (and in A unless RES)
       if (rank == 0 && tid == 0) {
