@@ -623,12 +623,11 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   }
 
   // ---- stage-1 back-transformation (two-stage cones: band-reduction panels;
-  // one-stage cones: 32-reflector blocks), last block first.  FP64 one-stage
-  // cones use the fused kernel (a slab of columns per CTA, CTAs given to the
-  // cones in proportion to their work n^2 k); the rest use grouped GEMMs.
-  auto fused_bt1 = [&](const ConeDev& d) {
-    return !mb.split && d.path == 1 && d.n >= 3 && d.n <= bt1_max_side();
-  };
+  // one-stage cones: 32-reflector blocks), last block first.  One-stage cones
+  // use the fused FP64 kernel (a slab of columns per CTA, CTAs given to the
+  // cones in proportion to their work n^2 k; at these sides it beats the
+  // split products, whose K is only 32); the rest use grouped GEMMs.
+  auto fused_bt1 = [&](const ConeDev& d) { return d.path == 1 && d.n >= 3 && d.n <= bt1_max_side(); };
   {
     std::vector<int> fc;
     double wsum = 0.0;

@@ -20,7 +20,8 @@
 // (Householder panels, bulge chasing, secular equations, sign decisions)
 // stay FP64.
 //
-// Tile 128 x BN (BN = 16 or 64), K-stage 32, two shared-memory stages.  The
+// Tile 128 x BN (BN = 16 or 64), K-stage 16, two shared-memory stages (about
+// 100 KB of shared memory, so two CTAs share an SM).  The
 // 128 threads load FP64 into a staging buffer while taking the chunk
 // exponents (shared-memory atomicMax), then slice and store the three TF32
 // parts into the K-major, no-swizzle core-matrix layout (8 rows x 16 bytes
@@ -39,7 +40,7 @@ namespace scs {
 
 namespace {
 
-constexpr int TBM = 128, TBK = 32;
+constexpr int TBM = 128, TBK = 16;
 constexpr int KG = TBK / 4;  // 16-byte K groups per row
 constexpr long long kTcWaitIters = 4000000LL;
 
@@ -48,8 +49,8 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;   // K-direction core-matrix stride
-  d |= (uint64_t)((1024u >> 4) & 0x3FFF) << 32;  // 8-row-group stride
+  d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;             // K-direction core-matrix stride
+  d |= (uint64_t)(((uint32_t)(KG * 128) >> 4) & 0x3FFF) << 32;  // 8-row-group stride
   d |= (uint64_t)1 << 46;                        // descriptor version for tcgen05
   return d;                                      // no swizzle, base offset 0
 }
@@ -95,6 +96,19 @@ __device__ __forceinline__ void split_grid(uint8_t* const* parts, uint32_t off, 
   *(float*)(parts[0] + off) = fh;
   *(float*)(parts[1] + off) = fm;
   *(float*)(parts[2] + off) = fl;
+}
+
+// FP32 -> FP64 by integer operations (exact; FP32 subnormals become zero,
+// below 2^-126 of nothing that matters here), so that the epilogue does not
+// spend FP64-pipe conversions.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0u) return 0.0;
+  const uint32_t m = u & 0x7FFFFFu;
+  const uint32_t ex = (e == 0xFFu) ? 0x7FFu : e + 896u;
+  const uint32_t hi = (u & 0x80000000u) | (ex << 20) | (m >> 3);
+  return __hiloint2double((int)hi, (int)(m << 29));
 }
 
 __device__ __forceinline__ int exp_field(double v) { return (int)(((uint32_t)__double2hiint(v) >> 20) & 0x7FF); }
@@ -244,13 +258,17 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
       if (ok) drain(kt - 2);
     }
     const int k0 = kbeg + kt * TBK;
+    // element -> (r, k) so that consecutive threads read consecutive memory:
+    // k fastest for op(A) = A^T and for a symmetric tile wholly above the
+    // diagonal (read from the lower triangle, i.e. transposed)
+    const bool kfast = ta || (sa && i0 + TBM <= k0);
     // ---- pass 1: FP64 values into staging, chunk exponents
-    // A tile: op(A)(i0 + r, k0 + k), 128 x 32
+    // A tile: op(A)(i0 + r, k0 + k), 128 x TBK
 #pragma unroll 4
     for (int q = 0; q < (TBM * TBK) / 128; ++q) {
       const int e = tid + q * 128;
       int r, k;
-      if (ta) { k = e % TBK; r = e / TBK; } else { r = e % TBM; k = e / TBM; }
+      if (kfast) { k = e % TBK; r = e / TBK; } else { r = e % TBM; k = e / TBM; }
       const int i = i0 + r, kk = k0 + k;
       double v = 0.0;
       if (i < M && kk < kend) {
@@ -288,7 +306,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
       for (int q = 0; q < (TBM * TBK) / 128; ++q) {
         const int e = tid + q * 128;
         int r, k;
-        if (ta) { k = e % TBK; r = e / TBK; } else { r = e % TBM; k = e / TBM; }
+        if (kfast) { k = e % TBK; r = e / TBK; } else { r = e % TBM; k = e / TBM; }
         split_grid(pa, tile_off(r, k), sm.sta[e], sm.ema[s][r][k / KCH]);
       }
       uint8_t* pb[3] = {sm.b[s][0], sm.b[s][1], sm.b[s][2]};
@@ -348,6 +366,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
   if (fail && tid == 0 && g.skip) atomicOr(const_cast<int*>(g.skip), ST_TIMEOUT);
 
   if (!fail) {
+    const bool alpha_one = g.alpha == 1.0, alpha_mone = g.alpha == -1.0, beta_one = g.beta == 1.0;
     const int row = i0 + warp * 32 + lane;
     double* part = (S > 1) ? g.partial + (int64_t)kb * Ms * g.N : nullptr;
     if (row < M) {
@@ -355,17 +374,22 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
       for (int q = 0; q < BN; ++q) {
         const int j = j0 + q;
         if (j >= N) continue;
-        const double acc = (double)acc_hi[q] + (double)acc_lo[q];
+        if (lowc && !part && row < j) continue;
+        double acc = f32_to_f64(acc_hi[q]) + f32_to_f64(acc_lo[q]);
         if (part) {
           part[(int64_t)row + (int64_t)j * Ms] = acc;
           continue;
         }
-        if (lowc && row < j) continue;
         const int jc = g.colmap ? g.colmap[j] : j;
         double* cp = (flags & GF_TRANS_C) ? g.C + (int64_t)jc + (int64_t)row * g.ldc
                                           : g.C + (int64_t)row + (int64_t)jc * g.ldc;
-        double v = g.alpha * acc;
-        if (g.beta != 0.0) v = fma(g.beta, *cp, v);
+        // alpha = +-1 and beta in {0, 1} (every contraction of the solver) without extra FP64 work
+        double v;
+        if (alpha_one) v = acc;
+        else if (alpha_mone) v = __longlong_as_double(__double_as_longlong(acc) ^ (long long)0x8000000000000000ULL);
+        else v = g.alpha * acc;
+        if (beta_one) v = *cp + v;
+        else if (g.beta != 0.0) v = fma(g.beta, *cp, v);
         *cp = v;
       }
     }
