@@ -42,7 +42,10 @@ sys.path.insert(0, ROOT)
 from paper_2606_20519_gb300 import workloads as W  # noqa: E402
 
 METRIC = "PSD projections/s (fwd, fwd+VJP) at n=625/4096 vs plain FP64 GPU path at stated error"
-FP64_PEAK_GFLOPS = 1192.0  # measured FP64 FMA throughput of this GB300
+# FP64 ALU peak from unit counts and clock: 152 SMs x 2 FP64 FMA per clock per SM
+# x 2 flops x 2.07 GHz (the nominal 1.25 TFLOP/s of the part)
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+FP64_PEAK_NOTE = "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"
 
 
 def parse():
@@ -174,7 +177,7 @@ def phase_kernels(phase: str, n: int, band: int) -> str:
 
 
 def algorithmic_flops(phase: str, n: int, k: int, b: int) -> float:
-    """FP64 flops of one cone for a phase (the counts the design doc lists)."""
+    """Algorithmic FP64 flops of one cone for a phase (k = eigenpairs kept, b = band width)."""
     if phase == "dense_to_band":
         return 4.0 / 3.0 * n ** 3
     if phase == "band_to_tridiag":
@@ -403,7 +406,8 @@ def run_ours(args):
     # per call: a phase may be traced as several segments within one call
     avg_ms = dom_ms / max(1, args.steps * len(wl.calls))
     achieved = flops_launch / (avg_ms * 1e-3) / 1e9
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s FP64",
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "peak_source": FP64_PEAK_NOTE,
+                "unit": "GFLOP/s FP64",
                 "frac": achieved / FP64_PEAK_GFLOPS, "traffic": _traffic(args.config, dom_name),
                 "phase": dom_name, "kernel": phase_kernels(dom_name, n0, tuning["band"] if tuning else args.band),
                 "ms_per_launch": avg_ms, "flops_per_launch": flops_launch,
@@ -504,12 +508,17 @@ def comparator(wl, xs, dev, stream, max_calls: int = 20):
 
 
 def _traffic(config, phase):
-    """DRAM bytes per launch of the phase from a committed ncu summary, if any."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per call of the phase's kernel from the committed ncu summary
+    (a table row "| config | phase | bytes | ..." in profiles/traffic.md), if any."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
     try:
-        return json.load(open(path)).get(config, {}).get(phase)
-    except Exception:
+        for line in open(path):
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) >= 3 and cells[0] == config and cells[1] == phase:
+                return float(cells[2])
+    except (OSError, ValueError):
         return None
+    return None
 
 
 def main():
