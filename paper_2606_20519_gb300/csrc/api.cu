@@ -134,6 +134,11 @@ struct scs_psd_handle_s {
   bool trace = false;
   bool last_replayed = false;
   cudaStream_t capture_stream = nullptr;  // records graphs; never executes work
+  // second stream for work that overlaps the divide and conquer (the T factors
+  // of the one-stage reflectors); joined back with events before it is needed
+  bool use_aux = false;
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> trace_ev;
   int* status_word = nullptr;  // device
   cudaStream_t last_stream = nullptr;
@@ -167,7 +172,7 @@ struct ConeLayout {
 enum Field {
   F_A, F_BAND, F_REFL, F_D, F_E, F_V1, F_T1, F_Y, F_X, F_U3, F_MB, F_NB, F_QA, F_QB, F_LAMA, F_LAMB, F_QIN, F_UCM, F_Z,
   F_LAMK, F_DSRT, F_ZK, F_DVAL, F_TAU, F_ZHAT, F_ROT, F_RHO, F_UNRM, F_IPERM, F_IFP, F_IROT, F_IORG, F_IMAP, F_ICNT,
-  F_KINFO, F_NFIELDS
+  F_KINFO, F_TAU1, F_NFIELDS
 };
 
 int num_blocks1(int64_t n) { return n >= 3 ? (int)((n - 2 + kSy1Block - 1) / kSy1Block) : 0; }
@@ -186,7 +191,7 @@ ConeLayout cone_layout(int64_t n, int b, int path) {
       d * std::max<int64_t>((int64_t)P * b * b, (int64_t)Q * kSy1Block * kSy1Block),
       d * n * bw, d * n * bw + d * 2048, d * n * 3 * b, d * b * b, d * b * b, d * n * n, d * n * n, d * n, d * n,
       d * n * n, d * n * n, d * n * n, d * n, d * n, d * n, d * n, d * n, d * n, d * 2 * n, d * n, d * n,
-      i4 * n, i4 * n, i4 * 2 * n, i4 * n, i4 * n, i4 * 4 * n, i4 * 8};
+      i4 * n, i4 * n, i4 * 2 * n, i4 * n, i4 * n, i4 * 4 * n, i4 * 8, d * n};
   size_t o = 0;
   for (int f = 0; f < F_NFIELDS; ++f) {
     o = align_up(o);
@@ -388,6 +393,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
     d.lamB = FLD(double, F_LAMB); d.Qin = FLD(double, F_QIN); d.Ucm = FLD(double, F_UCM); d.Z = FLD(double, F_Z);
     d.lamk = FLD(double, F_LAMK); d.dsrt = FLD(double, F_DSRT); d.zk = FLD(double, F_ZK); d.dval = FLD(double, F_DVAL);
     d.tau = FLD(double, F_TAU); d.zhat = FLD(double, F_ZHAT); d.rot = FLD(double, F_ROT); d.rho = FLD(double, F_RHO);
+    d.tau1 = FLD(double, F_TAU1);
     d.unrm = FLD(double, F_UNRM); d.ifp = FLD(int, F_IFP);
     d.iperm = FLD(int, F_IPERM); d.irot = FLD(int, F_IROT); d.iorg = FLD(int, F_IORG); d.imap = FLD(int, F_IMAP);
     d.icnt = FLD(int, F_ICNT); d.kinfo = FLD(int, F_KINFO);
@@ -841,6 +847,7 @@ struct PhaseMark {
 int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStream_t s, int64_t& n_launch) {
   int rc;
   const bool want_y = (mode & MODE_Y) != 0, want_vjp = (mode & MODE_VJP) != 0;
+  bool joined = true;  // false while work on the second stream is outstanding
   const IoSlot* io = P.io_d;
   PhaseMark pm{h, s};
   CUDA_TRY(cudaMemsetAsync(P.status_d, 0, sizeof(int) * (P.ncones + 1), s));
@@ -873,9 +880,22 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
             return SCS_PSD_ECUDA;
           LAUNCH_CHECK();
         }
-        pm.begin(5);
-        launch_larft1(P.cones_d, P.ints_d + P.larft_cone_off, P.ints_d + P.larft_idx_off, P.nlarft, s);
+        // the T factors need only the reflectors: on the second stream they
+        // overlap the divide and conquer (kept on s while tracing phases)
+        const bool side = h->use_aux && !h->trace && h->aux_stream && P.nlarft > 0;
+        if (side) {
+          CUDA_TRY(cudaEventRecord(h->ev_fork, s));
+          CUDA_TRY(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
+        } else {
+          pm.begin(5);
+        }
+        launch_larft1(P.cones_d, P.ints_d + P.larft_cone_off, P.ints_d + P.larft_idx_off, P.nlarft,
+                      side ? h->aux_stream : s);
         LAUNCH_CHECK();
+        if (side) {
+          CUDA_TRY(cudaEventRecord(h->ev_join, h->aux_stream));
+          joined = false;
+        }
       }
       pm.begin(2);
       launch_band_extract(P.cones_d, nc, P.maxn, s);
@@ -918,6 +938,10 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
       launch_backtr2(P.cones_d, nc, (int)P.maxn, (int)P.maxn, P.allv ? (int)P.maxn : (int)(P.maxn + 1) / 2, P.b, s);
       LAUNCH_CHECK();
       pm.begin(5);
+      if (!joined) {
+        CUDA_TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
+        joined = true;
+      }
       if (P.bt1k_nctas) {
         launch_bt1(P.cones_d, P.ints_d + P.bt1k_cone_off, P.ints_d + P.bt1k_rank_off, P.ints_d + P.bt1k_count_off,
                    P.bt1k_nctas, P.bt1k_maxn, s);
@@ -990,6 +1014,7 @@ void record_graph(scs_psd_handle h, Plan& P, int mode, long long wait_limit) {
     P.glaunches[mode] = n_launch;
   } else {
     P.gfailed[mode] = true;
+    h->use_aux = false;  // a failed recording may leave the second stream unusable: stay on one stream
   }
   if (graph) cudaGraphDestroy(graph);
   cudaGetLastError();
@@ -1309,6 +1334,12 @@ int scs_psd_create(scs_psd_handle* h, int device) {
     return SCS_PSD_ENOMEM;
   }
   cudaMemset(H->status_word, 0, sizeof(int));
+  // the second stream and its fork/join events (without them everything runs on the caller's stream)
+  if (cudaStreamCreateWithFlags(&H->aux_stream, cudaStreamNonBlocking) == cudaSuccess &&
+      cudaEventCreateWithFlags(&H->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+      cudaEventCreateWithFlags(&H->ev_join, cudaEventDisableTiming) == cudaSuccess)
+    H->use_aux = true;
+  cudaGetLastError();
   *h = H;
   return SCS_PSD_OK;
 }
@@ -1319,6 +1350,9 @@ int scs_psd_destroy(scs_psd_handle h) {
   cudaDeviceSynchronize();
   h->plans.clear();
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   cudaFree(h->status_word);
   delete h;
   return SCS_PSD_OK;

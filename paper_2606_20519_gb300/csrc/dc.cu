@@ -352,6 +352,24 @@ __device__ __forceinline__ double warp_prod_d(double v) {
   return v;
 }
 
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// FP64 -> FP32, round to nearest even, by integer operations (a conversion
+// instruction would occupy the FP64 pipe); |v| < 2^-126 gives 0.
+__device__ __forceinline__ float f64_to_f32_rn(double v) {
+  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+  const int e = (int)((hi >> 20) & 0x7FF) - 896;
+  if (e <= 0) return 0.0f;
+  if (e >= 255) return __uint_as_float((hi & 0x80000000u) | 0x7f800000u);
+  uint32_t bits = ((uint32_t)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const uint32_t rest = lo & 0x1FFFFFFFu, half = 0x10000000u;
+  if (rest > half || (rest == half && (bits & 1u))) ++bits;
+  return __uint_as_float((hi & 0x80000000u) | bits);
+}
+
 // Root i of f(x) = 1 + rho sum_j z_j^2 / (d_j - x), d strictly increasing,
 // ||z|| = 1, solved by one warp (the sums are split over the lanes; every
 // lane ends with the same values).  Returns the origin pole and the offset
@@ -377,6 +395,71 @@ __device__ bool secular_root_warp(const double* __restrict__ dk, const double* _
   double tau = 0.5 * (lo + hi);
   const int li = i, ri = i + 1;
   bool conv = false;
+  // ---- FP32 phase: the same bracketed rational iteration with the sums in
+  // FP32 (64x the FP64 rate on this part), while the sign of f is certain
+  // beyond its FP32 error bound; the FP64 loop below then polishes from the
+  // narrowed bracket.  Only the differences d_j - d_org are formed in FP64.
+  {
+    const float rho32 = f64_to_f32_rn(rho);
+    const float p32 = f64_to_f32_rn(dk[li] - dorg);
+    const float q32 = ri < K ? f64_to_f32_rn(dk[ri] - dorg) : 0.0f;
+    for (int it = 0; it < 40; ++it) {
+      const float t32 = f64_to_f32_rn(tau);
+      float psi = 0.0f, phi = 0.0f, dpsi = 0.0f, dphi = 0.0f, aerr = 0.0f;
+      for (int j = lane; j < K; j += 32) {
+        const float del = f64_to_f32_rn(dk[j] - dorg) - t32;
+        const float zz = f64_to_f32_rn(zk[j]);
+        const float t = zz / del;
+        const float term = zz * t;
+        if (j < ri) { psi += term; dpsi = fmaf(t, t, dpsi); }
+        else { phi += term; dphi = fmaf(t, t, dphi); }
+        aerr += fabsf(term);
+      }
+      psi = rho32 * warp_sum_f(psi);
+      phi = rho32 * warp_sum_f(phi);
+      dpsi = rho32 * warp_sum_f(dpsi);
+      dphi = rho32 * warp_sum_f(dphi);
+      aerr = warp_sum_f(aerr);
+      const float g = 1.0f + psi + phi;
+      // rounding of the K terms and of their sums: (2K + 16) 2^-24 (1 + rho sum |term|)
+      const float bound = (2.0f * (float)K + 16.0f) * 5.9604645e-8f * (1.0f + rho32 * aerr);
+      if (!(fabsf(g) > bound) || !isfinite(dpsi + dphi)) break;
+      if (g > 0.0f) hi = tau; else lo = tau;
+      if (hi - lo <= 4.0 * kEps * fmax(fabs(lo), fabs(hi))) break;
+      const float dl = p32 - t32;
+      const float sl = dpsi * dl * dl;
+      const float a = psi - sl / dl;
+      float x = 0.0f;
+      bool okx = false;
+      if (ri < K) {
+        const float dr = q32 - t32;
+        const float sr = dphi * dr * dr;
+        const float bq = phi - sr / dr;
+        const float C = 1.0f + a + bq;
+        const float B2 = -(C * (p32 + q32) + sl + sr);
+        const float C2 = C * p32 * q32 + sl * q32 + sr * p32;
+        if (C != 0.0f) {
+          const float disc = B2 * B2 - 4.0f * C * C2;
+          if (disc >= 0.0f) {
+            const float qq = -0.5f * (B2 + copysignf(sqrtf(disc), B2));
+            const double x1 = (double)(qq / C);
+            if (x1 > lo && x1 < hi) { x = qq / C; okx = true; }
+            else if (qq != 0.0f) {
+              const double x2 = (double)(C2 / qq);
+              if (x2 > lo && x2 < hi) { x = C2 / qq; okx = true; }
+            }
+          }
+        }
+      } else {
+        const float C = 1.0f + a;
+        if (C > 0.0f) {
+          const double x1 = (double)(p32 + sl / C);
+          if (x1 > lo && x1 < hi) { x = p32 + sl / C; okx = true; }
+        }
+      }
+      tau = okx ? (double)x : 0.5 * (lo + hi);
+    }
+  }
   for (int it = 0; it < 100; ++it) {
     double psi = 0.0, phi = 0.0, dpsi = 0.0, dphi = 0.0, aerr = 0.0;
     for (int j = lane; j < K; j += 32) {

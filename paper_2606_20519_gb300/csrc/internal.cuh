@@ -122,6 +122,7 @@ struct ConeDev {
   int* kinfo;       // [0] k kept, [1] route (0: positive part, 1: X - negative part), [2] kept secular
                     // roots, [3] keep all eigenpairs (derivative), [4] side option, [5] first kept root
   int* status;      // per-cone status bits
+  double* tau1;     // n     tau of the one-stage reflectors (read by larft1 while the divide and conquer runs)
 };
 
 // One merge node of the divide and conquer tree.

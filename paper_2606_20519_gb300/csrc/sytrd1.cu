@@ -259,7 +259,7 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
   if (rank == 0 && tid == 0) {
     c.d[0] = __ldcg(A);
     c.e[0] = beta;
-    c.rho[0] = tau;
+    c.tau1[0] = tau;
   }
   store_reflector(c, n, 0, vc, rank, G);
   {
@@ -317,7 +317,7 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
       if (rank == 0 && tid == 0) {
         c.d[j + 1] = dj1;
         c.e[j + 1] = beta1;
-        c.rho[j + 1] = tau1;
+        c.tau1[j + 1] = tau1;
       }
       store_reflector(c, n, j + 1, vx + 1, rank, G);
       double* pnext = pbuf2 + ((j + 1) & 1) * n;
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(kSyThreads) larft1_kernel(const ConeDev* __res
   }
   __syncthreads();
   for (int j = 0; j < nr; ++j) {
-    const double tj = c.rho[q * kNb + j];
+    const double tj = c.tau1[q * kNb + j];
     if (tid < j) {
       double s = 0.0;
       for (int p = tid; p < j; ++p) s = fma(T[tid][p], Gm[p][j], s);
