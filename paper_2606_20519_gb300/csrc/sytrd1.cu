@@ -124,12 +124,12 @@ __device__ void store_reflector(const ConeDev& c, int n, int j, const double* u,
 // One pass over this CTA's columns i >= r0 (i mod G = rank), rows r0 .. n-1:
 // with UPDATE, first A(r, i) -= v_r w_i + w_r v_i (vu, wu indexed from row
 // r0 - 1); then p_i = tau * sum_r A(r, i) u_r (u indexed from row r0) into
-// pbuf[i].  Returns this CTA's sum of p_i u_i (thread 0 holds it).
+// pbuf[i].
 // RES: this CTA's columns live in shared memory (cols, column i at
 // ((i - rank) / G) * n); the owner of column r0 -- the next reflector's
 // source -- also writes its updated rows to A for every CTA to read.
 template <bool UPDATE, bool RES>
-__device__ double column_pass(double* __restrict__ A, double* __restrict__ cols, int n, int r0,
+__device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, int n, int r0,
                               const double* __restrict__ u, double tau, const double* __restrict__ vu,
                               const double* __restrict__ wu, double* pbuf, double* psum, int pcap, double* red,
                               int rank, int G) {
@@ -139,7 +139,6 @@ __device__ double column_pass(double* __restrict__ A, double* __restrict__ cols,
   const int ncol = first < n ? (n - 1 - first) / G + 1 : 0;
   const int nch = (L + kChunk - 1) / kChunk;
   const int per = pcap / nch;
-  double mypv = 0.0;
   for (int k0 = 0; k0 < ncol; k0 += per) {
     const int kc = min(ncol - k0, per);
     for (int it = warp; it < kc * nch; it += kSyThreads / 32) {
@@ -187,11 +186,10 @@ __device__ double column_pass(double* __restrict__ A, double* __restrict__ cols,
       p *= tau;
       const int i = first + G * (k0 + kk);
       __stcg(pbuf + i, p);
-      mypv = fma(p, u[i - r0], mypv);
     }
     __syncthreads();
   }
-  return block_sum256(mypv, red);
+  (void)red;
 }
 
 // Step j (reflector H_j = I - tau_j v v^T from column j, v indexed from row
@@ -226,11 +224,10 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
   double* w = sy_smem + n;          // p_j, then w_j
   double* vx = sy_smem + 2 * n;     // updated column j+1 (rows j+1 ..), then v_{j+1} at vx + 1
   double* psum = sy_smem + 3 * n;   // pcap partial dot products
-  // p and the partial sums p^T v, double-buffered by step parity: a CTA
-  // writes step j+2's values only after every CTA has passed step j+1's
-  // barrier, i.e. finished reading step j's values
+  // p, double-buffered by step parity: a CTA writes step j+2's values only
+  // after every CTA has passed step j+1's barrier, i.e. finished reading
+  // step j's values
   double* pbuf2 = c.X;              // 2 x n
-  double* part2 = c.X + 2 * n;      // 2 x G
   int* bar = c.prog;
   const int tid = threadIdx.x;
   int bstep = 0;
@@ -262,22 +259,18 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
     c.tau1[0] = tau;
   }
   store_reflector(c, n, 0, vc, rank, G);
-  {
-    const double pv = column_pass<false, RES>(A, cols, n, 1, vc, tau, nullptr, nullptr, pbuf2, psum, pcap, red, rank, G);
-    if (tid == 0) __stcg(part2 + rank, pv);
-  }
+  column_pass<false, RES>(A, cols, n, 1, vc, tau, nullptr, nullptr, pbuf2, psum, pcap, red, rank, G);
   for (int j = 0; j + 2 < n; ++j) {
     const int m = n - j - 1;
     const double* pbuf = pbuf2 + (j & 1) * n;
-    const double* part = part2 + (j & 1) * G;
     if (!group_barrier(bar, (++bstep) * G, wait_limit, &sh_flag)) {
       if (tid == 0) atomicOr(c.status, ST_TIMEOUT);
       return;
     }
     // ---- w = p - K v and the updated column j+1, in every CTA
+    // K = (tau/2) p^T v from the full p (read by every CTA anyway); all loads
+    // of a round first, then the shared-memory stores (one L2 round trip)
     double pt = 0.0;
-    for (int r = tid; r < G; r += kSyThreads) pt += __ldcg(part + r);
-    // all loads of a round first, then the shared-memory stores (one L2 round trip)
     for (int base = 0; base < m; base += 4 * kSyThreads) {
       double pr[4], ar[4];
 #pragma unroll
@@ -289,7 +282,11 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int t = base + q * kSyThreads + tid;
-        if (t < m) { w[t] = pr[q]; vx[t] = ar[q]; }
+        if (t < m) {
+          w[t] = pr[q];
+          vx[t] = ar[q];
+          pt = fma(pr[q], vc[t], pt);
+        }
       }
     }
     const double K = 0.5 * tau * block_sum256(pt, red);
@@ -321,8 +318,7 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
       }
       store_reflector(c, n, j + 1, vx + 1, rank, G);
       double* pnext = pbuf2 + ((j + 1) & 1) * n;
-      const double pv = column_pass<true, RES>(A, cols, n, j + 2, vx + 1, tau1, vc, w, pnext, psum, pcap, red, rank, G);
-      if (tid == 0) __stcg(part2 + ((j + 1) & 1) * G + rank, pv);
+      column_pass<true, RES>(A, cols, n, j + 2, vx + 1, tau1, vc, w, pnext, psum, pcap, red, rank, G);
       // v_{j+1} becomes the current reflector
       for (int t = tid; t < m - 1; t += kSyThreads) vc[t] = vx[1 + t];
       tau = tau1;
