@@ -73,9 +73,10 @@ typedef struct {
   int32_t precision;        /* scs_psd_precision */
   int32_t side;             /* 0 auto (fewer eigenpairs), 1 positive part, 2 X - negative part */
   int32_t recompute;        /* VJP: 0 auto, 1 always recompute V, 2 never (store) */
-  int32_t band;             /* 0 = automatic (one-stage tridiagonalisation up to side 2048, two-stage
-                               with band width 16 above), 1 = one-stage for every cone,
-                               2..32 = two-stage with this band width for every cone */
+  int32_t band;             /* 0 = automatic (one-stage tridiagonalisation up to side 6144, two-stage
+                               with band width 16 above; or the autotuner's choice), 1 = one-stage
+                               for every cone up to side 7600 (two-stage above), 2..32 = two-stage
+                               with this band width for every cone */
   int64_t mem_budget_bytes; /* VJP: workspace budget that triggers recompute; 0 = no limit */
   int64_t wait_limit_cycles;/* bound on device spin-waits; 0 = default */
   int32_t graphs;           /* 0 = replay a recorded CUDA graph from the second call with the same

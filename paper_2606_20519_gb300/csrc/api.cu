@@ -26,7 +26,9 @@ using namespace scs;
 namespace {
 
 constexpr int kDefaultBand = 16;
-constexpr int64_t kOneStageMax = 2048;  // auto: one-stage tridiagonalisation up to this side
+// auto: one-stage tridiagonalisation up to this side (measured faster than the
+// two-stage route at every side up to 4096 on this part, FP64 and split)
+constexpr int64_t kOneStageMax = 6144;
 constexpr long long kDefaultWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 constexpr int64_t kMaxSide = 8192;
 
@@ -338,7 +340,9 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   for (int c = 0; c < P.ncones; ++c) {
     const int64_t n = sides[big[c]];
     P.maxn = std::max(P.maxn, n);
-    path[c] = (onestage == 1) ? 1 : (onestage == 0 ? 0 : (n <= kOneStageMax ? 1 : 0));
+    // one-stage needs its vectors in shared memory: at most about 7600 (else two-stage)
+    const bool fits1 = sytrd1_smem_bytes((int)n, 1, false) <= 200 * 1024;
+    path[c] = (onestage == 1) ? (fits1 ? 1 : 0) : (onestage == 0 ? 0 : (n <= kOneStageMax ? 1 : 0));
     lay[c] = cone_layout(n, b, path[c]);
     cone_base[c] = cone_bytes;
     cone_bytes += lay[c].bytes;
