@@ -250,6 +250,43 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
     }
     }
   };
+  // Raw FP64 tile kt into the staging buffer with cp.async (every element of
+  // the tile in flight at once; out-of-range elements are zero-filled).
+  auto issue_tile = [&](int kt) {
+    const int k0 = kbeg + kt * TBK;
+    const bool kfast = ta || (sa && i0 + TBM <= k0);
+#pragma unroll
+    for (int q = 0; q < (TBM * TBK) / 128; ++q) {
+      const int e = tid + q * 128;
+      int r, k;
+      if (kfast) { k = e % TBK; r = e / TBK; } else { r = e % TBM; k = e / TBM; }
+      const int i = i0 + r, kk = k0 + k;
+      if (i < M && kk < kend) {
+        const double* src = sa ? ((i >= kk) ? A + (int64_t)i + (int64_t)kk * lda : A + (int64_t)kk + (int64_t)i * lda)
+                               : (ta ? A + (int64_t)kk + (int64_t)i * lda : A + (int64_t)i + (int64_t)kk * lda);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(&sm.sta[e])), "l"(src) : "memory");
+      } else {
+        sm.sta[e] = 0.0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < (BN * TBK + 127) / 128; ++q) {
+      const int e = tid + q * 128;
+      if ((BN * TBK) % 128 == 0 || e < BN * TBK) {
+        int c, k;
+        if (tb) { c = e % BN; k = e / BN; } else { k = e % TBK; c = e / TBK; }
+        const int j = j0 + c, kk = k0 + k;
+        if (j < N && kk < kend) {
+          const double* src = tb ? B + (int64_t)j + (int64_t)kk * ldb : B + (int64_t)kk + (int64_t)j * ldb;
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(&sm.stb[e])), "l"(src) : "memory");
+        } else {
+          sm.stb[e] = 0.0;
+        }
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (nk > 0) issue_tile(0);
   for (int kt = 0; kt < nk; ++kt) {
     const int s = kt & 1;
     if (kt >= 2) {
@@ -262,38 +299,28 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
     // k fastest for op(A) = A^T and for a symmetric tile wholly above the
     // diagonal (read from the lower triangle, i.e. transposed)
     const bool kfast = ta || (sa && i0 + TBM <= k0);
-    // ---- pass 1: FP64 values into staging, chunk exponents
-    // A tile: op(A)(i0 + r, k0 + k), 128 x TBK
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    // ---- pass 1: chunk exponents of the staged values (B scaled first if asked)
 #pragma unroll 4
     for (int q = 0; q < (TBM * TBK) / 128; ++q) {
       const int e = tid + q * 128;
       int r, k;
       if (kfast) { k = e % TBK; r = e / TBK; } else { r = e % TBM; k = e / TBM; }
-      const int i = i0 + r, kk = k0 + k;
-      double v = 0.0;
-      if (i < M && kk < kend) {
-        if (sa) v = (i >= kk) ? A[(int64_t)i + (int64_t)kk * lda] : A[(int64_t)kk + (int64_t)i * lda];
-        else if (ta) v = A[(int64_t)kk + (int64_t)i * lda];
-        else v = A[(int64_t)i + (int64_t)kk * lda];
-      }
-      sm.sta[e] = v;
-      const int ex = exp_field(v);
+      const int ex = exp_field(sm.sta[e]);
       if (ex) atomicMax(&sm.ema[s][r][k / KCH], ex);
     }
-    // B tile: op(B)(k0 + k, j0 + c) stored as BN rows (c) x 32 (k), K-major
 #pragma unroll 4
     for (int q = 0; q < (BN * TBK + 127) / 128; ++q) {
       const int e = tid + q * 128;
       if ((BN * TBK) % 128 == 0 || e < BN * TBK) {
         int c, k;
         if (tb) { c = e % BN; k = e / BN; } else { k = e % TBK; c = e / TBK; }
-        const int j = j0 + c, kk = k0 + k;
-        double v = 0.0;
-        if (j < N && kk < kend) {
-          v = tb ? B[(int64_t)j + (int64_t)kk * ldb] : B[(int64_t)kk + (int64_t)j * ldb];
-          if (scl) v *= g.bscale[kk];
+        double v = sm.stb[e];
+        if (scl && v != 0.0) {
+          v *= g.bscale[k0 + k];
+          sm.stb[e] = v;
         }
-        sm.stb[e] = v;
         const int ex = exp_field(v);
         if (ex) atomicMax(&sm.emb[s][c][k / KCH], ex);
       }
@@ -351,6 +378,8 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&sm.mbar[s])));
     }
+    // the next tile's copies fly while the next iteration waits for and drains stage kt-1
+    if (kt + 1 < nk) issue_tile(kt + 1);
   }
   // drain the last one or two stages
   for (int kt = max(0, nk - 2); kt < nk; ++kt) {
