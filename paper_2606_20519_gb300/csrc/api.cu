@@ -367,7 +367,8 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   std::vector<size_t> prog_off(P.ncones);
   for (int c = 0; c < P.ncones; ++c) {
     prog_off[c] = prog_total;
-    prog_total += std::max<int64_t>(1, sides[big[c]] - 2);
+    // bulge progress counters (n - 2), or the one-stage barrier's 8 counters 32 ints apart
+    prog_total += std::max<int64_t>(256, sides[big[c]] - 2);
   }
   // ints layout: [status (ncones+1)] [prog] [rest...]
   const int status_off = 0;

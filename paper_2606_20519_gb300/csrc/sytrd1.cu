@@ -49,24 +49,31 @@ __device__ double block_sum256(double v, double* red) {
   return ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
 }
 
-// Barrier over the G CTAs of one cone; returns false when the wait ran out.
-__device__ bool group_barrier(int* counter, int target, long long limit, int* flag) {
+// Barrier over the G CTAs of one cone with its arrivals spread over 8
+// counters (CTA r adds to counter r mod 8, 128 bytes apart) so that the
+// atomics do not queue on one address; threads 0..7 each wait for one
+// counter.  Returns false (in every thread) when a wait ran out.
+constexpr int kBarLanes = 8, kBarStride = 32;
+__device__ bool group_barrier8(int* counters, int rank, int G, int step, long long limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    atomicAdd(counter, 1);
-    int ok = 1;
-    if (ld_acquire(counter) < target) {
+    atomicAdd(counters + kBarStride * (rank % kBarLanes), 1);
+  }
+  int ok = 1;
+  const int t = threadIdx.x;
+  if (t < kBarLanes && t < G) {
+    const int target = step * ((G - 1 - t) / kBarLanes + 1);  // CTAs with rank mod 8 == t, per step
+    const int* cnt = counters + kBarStride * t;
+    if (ld_acquire(cnt) < target) {
       const long long t0 = clock64();
-      while (ld_acquire(counter) < target) {
+      while (ld_acquire(cnt) < target) {
         if (clock64() - t0 > limit) { ok = 0; break; }
       }
     }
     __threadfence();
-    *flag = ok;
   }
-  __syncthreads();
-  return *flag != 0;
+  return __syncthreads_and(ok) != 0;
 }
 
 constexpr int kChunk = 256;   // rows per work item (32 lanes x 8 loads in flight)
@@ -99,15 +106,43 @@ __device__ double make_reflector_ps(double* x, int len, double ps, double* red, 
   return sh[1];
 }
 
+// The same reflector without rescaling x: tau, beta and scal = 1/(x_0 - beta)
+// are returned and x[0] is set to x_0 - beta, so u = scal * x exactly where
+// the caller needs it (the products of the next pass fold scal into their
+// factor tau * scal, the copy into the next step's v multiplies).  One
+// shared-memory pass and one barrier shorter than make_reflector_ps.
+__device__ double make_reflector_lazy(double* x, double ps, double* red, double* sh, double* beta_out,
+                                      double* scal_out) {
+  const double sigma = block_sum256(ps, red);
+  if (threadIdx.x == 0) {
+    const double alpha = x[0];
+    double beta = alpha, tau = 0.0, scal = 0.0;
+    if (sigma != 0.0) {
+      const double nrm = sqrt(fma(alpha, alpha, sigma));
+      beta = alpha >= 0.0 ? -nrm : nrm;
+      tau = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    sh[0] = beta; sh[1] = tau; sh[2] = scal;
+    x[0] = alpha - beta;  // scal * x[0] = 1 (u_0); 0 when tau = 0
+  }
+  __syncthreads();
+  *beta_out = sh[0];
+  *scal_out = sh[2];
+  return sh[1];
+}
+
 __device__ double make_reflector(double* x, int len, double* red, double* sh, double* beta_out) {
   double ps = 0.0;
   for (int t = 1 + threadIdx.x; t < len; t += kSyThreads) ps = fma(x[t], x[t], ps);
   return make_reflector_ps(x, len, ps, red, sh, beta_out);
 }
 
-// Reflector j (u indexed from row j+1) into its 32-column block of V1, with
-// the unit diagonal and the zeros above; rows spread over the group.
-__device__ void store_reflector(const ConeDev& c, int n, int j, const double* u, int rank, int G) {
+// Reflector j (u = scal * x, x indexed from row j+1) into its 32-column
+// block of V1, with the unit diagonal and the zeros above; rows spread over
+// the group.
+__device__ void store_reflector(const ConeDev& c, int n, int j, const double* u, int rank, int G,
+                                double scal = 1.0) {
   const int q = j / kNb, col = j % kNb;
   const int r0 = q * kNb + 1;               // first row of block q
   const int mq = n - r0;                    // rows of block q
@@ -116,7 +151,7 @@ __device__ void store_reflector(const ConeDev& c, int n, int j, const double* u,
     const int row = r0 + r;
     double val = 0.0;
     if (row == j + 1) val = 1.0;
-    else if (row > j + 1) val = u[row - j - 1];
+    else if (row > j + 1) val = scal * u[row - j - 1];
     Vq[(int64_t)r + (int64_t)col * mq] = val;
   }
 }
@@ -214,8 +249,7 @@ __host__ __device__ inline size_t sytrd1_bytes(int n, int G, bool res) {
 
 template <bool RES>
 __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_limit, double* sy_smem, double* red,
-                            double* sh, int* sh_flag_p) {
-  int& sh_flag = *sh_flag_p;
+                            double* sh) {
   const int n = (int)c.n;
   double* A = c.A;
   const int pcap = sytrd1_pcap(n, G);
@@ -263,7 +297,7 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
   for (int j = 0; j + 2 < n; ++j) {
     const int m = n - j - 1;
     const double* pbuf = pbuf2 + (j & 1) * n;
-    if (!group_barrier(bar, (++bstep) * G, wait_limit, &sh_flag)) {
+    if (!group_barrier8(bar, rank, G, ++bstep, wait_limit)) {
       if (tid == 0) atomicOr(c.status, ST_TIMEOUT);
       return;
     }
@@ -307,20 +341,19 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
     }
     if (j + 3 < n) {
       // ---- reflector j+1 from rows j+2 .. of the updated column
-      double beta1;
-      const double tau1 = make_reflector_ps(vx + 1, m - 1, ps, red, sh, &beta1);
-      const double dj1 = vx[0];
-      __syncthreads();
+      double beta1, scal1;
+      const double tau1 = make_reflector_lazy(vx + 1, ps, red, sh, &beta1, &scal1);
       if (rank == 0 && tid == 0) {
-        c.d[j + 1] = dj1;
+        c.d[j + 1] = vx[0];
         c.e[j + 1] = beta1;
         c.tau1[j + 1] = tau1;
       }
-      store_reflector(c, n, j + 1, vx + 1, rank, G);
+      store_reflector(c, n, j + 1, vx + 1, rank, G, scal1);
       double* pnext = pbuf2 + ((j + 1) & 1) * n;
-      column_pass<true, RES>(A, cols, n, j + 2, vx + 1, tau1, vc, w, pnext, psum, pcap, red, rank, G);
-      // v_{j+1} becomes the current reflector
-      for (int t = tid; t < m - 1; t += kSyThreads) vc[t] = vx[1 + t];
+      // p_i = tau u^T a_i with u = scal x: the factor tau * scal
+      column_pass<true, RES>(A, cols, n, j + 2, vx + 1, tau1 * scal1, vc, w, pnext, psum, pcap, red, rank, G);
+      // v_{j+1} = scal x becomes the current reflector (v_0 = 1)
+      for (int t = tid; t < m - 1; t += kSyThreads) vc[t] = t == 0 ? 1.0 : scal1 * vx[1 + t];
       tau = tau1;
       __syncthreads();
     } else {
@@ -349,15 +382,14 @@ __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __res
   extern __shared__ double sy_smem[];
   __shared__ double red[kSyThreads / 32];
   __shared__ double sh[4];
-  __shared__ int sh_flag;
   const ConeDev& c = cones[cta_cone[blockIdx.x]];
   const int rank = cta_rank[blockIdx.x], G = cta_count[blockIdx.x];
   if (*c.status != 0) return;
   // every CTA of a cone takes the same decision (same n, G, launch)
   if (sytrd1_bytes((int)c.n, G, true) <= (size_t)smem_bytes)
-    sytrd1_body<true>(c, rank, G, wait_limit, sy_smem, red, sh, &sh_flag);
+    sytrd1_body<true>(c, rank, G, wait_limit, sy_smem, red, sh);
   else
-    sytrd1_body<false>(c, rank, G, wait_limit, sy_smem, red, sh, &sh_flag);
+    sytrd1_body<false>(c, rank, G, wait_limit, sy_smem, red, sh);
 }
 
 // T factor of each 32-reflector block (one CTA per block): G = V^T V, then
