@@ -735,10 +735,19 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
     for (int c = 0; c < P.ncones; ++c) {
       const ConeDev& d = cones[c];
       const int n = (int)d.n;
-      g[0].push_back(mk(d.A, n, d.Z, n, d.QA, n, n, n, n, 1.0, 0.0, 0, st_ptr(c)));
-      g[1].push_back(mk(d.Z, n, d.QA, n, d.QB, n, n, n, n, 1.0, 0.0, GF_TRANS_A, st_ptr(c)));
-      g[2].push_back(mk(d.Z, n, d.QB, n, d.QA, n, n, n, n, 1.0, 0.0, 0, st_ptr(c)));
-      g[3].push_back(mk(d.QA, n, d.Z, n, d.QB, n, n, n, n, 1.0, 0.0, GF_TRANS_B | GF_LOWER_C, st_ptr(c)));
+      // S-first eigenvectors (k_S = kinfo[6]): H = V_S^T G, M = H V, (scale), W = X V^T, Z1 = V_S W
+      GemmDesc q0 = mk(d.Z, n, d.A, n, d.QA, n, n, n, n, 1.0, 0.0, GF_TRANS_A, st_ptr(c));
+      GemmDesc q1 = mk(d.QA, n, d.Z, n, d.QB, n, n, n, n, 1.0, 0.0, 0, st_ptr(c));
+      GemmDesc q2 = mk(d.QB, n, d.Z, n, d.QA, n, n, n, n, 1.0, 0.0, GF_TRANS_B, st_ptr(c));
+      GemmDesc q3 = mk(d.Z, n, d.QA, n, d.QB, n, n, n, n, 1.0, 0.0, 0, st_ptr(c));
+      q0.dynM = d.kinfo + 6;
+      q1.dynM = d.kinfo + 6;
+      q2.dynM = d.kinfo + 6;
+      q3.dynK = d.kinfo + 6;
+      g[0].push_back(q0);
+      g[1].push_back(q1);
+      g[2].push_back(q2);
+      g[3].push_back(q3);
     }
     for (int q = 0; q < 4; ++q) P.vjp[q] = mb.add_gemm(g[q]);
   }
@@ -866,6 +875,9 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
     if (mode & MODE_IMPORT) {
       launch_import_eig(P.cones_d, nc, P.maxn, io, s);
       LAUNCH_CHECK();
+      launch_vjp_reorder(P.cones_d, nc, P.maxn, s);
+      n_launch += 2;
+      LAUNCH_CHECK();
     } else {
       pm.begin(0);
       launch_unpack(P.cones_d, nc, P.maxn * P.maxn, io, 0, s);
@@ -954,6 +966,13 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
       }
       for (const GemmLaunch& gl : P.bt1)
         if ((rc = run_gemm(P, gl, s, n_launch))) return rc;
+      if (P.allv) {
+        // all eigenpairs: the route's side first (the derivative and the
+        // reconstruction use only those k_S columns)
+        launch_vjp_reorder(P.cones_d, nc, P.maxn, s);
+        n_launch += 2;
+        LAUNCH_CHECK();
+      }
       if (mode & MODE_EXPORT) {
         launch_export_eig(P.cones_d, nc, P.maxn, io, s);
         LAUNCH_CHECK();
@@ -975,7 +994,7 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
       LAUNCH_CHECK();
       if ((rc = run_gemm(P, P.vjp[0], s, n_launch))) return rc;
       if ((rc = run_gemm(P, P.vjp[1], s, n_launch))) return rc;
-      launch_loewner_scale(P.cones_d, nc, P.maxn, s);
+      launch_vjp_scale(P.cones_d, nc, P.maxn, s);
       LAUNCH_CHECK();
       if ((rc = run_gemm(P, P.vjp[2], s, n_launch))) return rc;
       if ((rc = run_gemm(P, P.vjp[3], s, n_launch))) return rc;

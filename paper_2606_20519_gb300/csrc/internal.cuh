@@ -120,7 +120,8 @@ struct ConeDev {
   int* imap;        // n     output column of each kept eigenvector of a merge
   int* icnt;        // 4n    per merge node: kept, deflated, rotations, kept-of-root (indexed by start)
   int* kinfo;       // [0] k kept, [1] route (0: positive part, 1: X - negative part), [2] kept secular
-                    // roots, [3] keep all eigenpairs (derivative), [4] side option, [5] first kept root
+                    // roots, [3] keep all eigenpairs (derivative), [4] side option, [5] first kept root,
+                    // [6] all-pairs mode: |S|, the pairs of the route's side, which come first
   int* status;      // per-cone status bits
   double* tau1;     // n     tau of the one-stage reflectors (read by larft1 while the divide and conquer runs)
 };
@@ -188,7 +189,9 @@ size_t panel_smem_bytes(int b, int R);
 // Z, lamk (all n eigenpairs) <-> io->V, io->lam
 void launch_export_eig(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s);
 void launch_import_eig(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s);
-void launch_loewner_scale(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s);
+// derivative: eigenpairs into S-first order (3 launches), then the k_S x n scaling
+void launch_vjp_reorder(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s);
+void launch_vjp_scale(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s);
 void launch_pack_lower(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s);
 void launch_recon(const ConeDev* cones, int ncones, int maxn, const IoSlot* io, cudaStream_t s);
 int sytrd1_max_ctas(int maxn);

@@ -35,7 +35,8 @@ __global__ void __launch_bounds__(256) recon_kernel(const ConeDev* __restrict__ 
   const int tn = t - tm * (tm + 1) / 2;
   const int i0 = tm * BM, j0 = tn * BM;
   const bool bad = *c.status != 0;
-  const int kk = bad ? 0 : c.kinfo[0];
+  // all-pairs mode: the route's side comes first, kinfo[6] of them
+  const int kk = bad ? 0 : (c.kinfo[3] ? c.kinfo[6] : c.kinfo[0]);
   const int route = c.kinfo[1];
   const double* Z = c.Z;
   const double* lam = c.lamk;

@@ -72,3 +72,17 @@ def test_split_precision_4096(lib):
     y, st = run_split(lib, b.x, [4096])
     assert st == lib.OK
     assert rel(y, W.to_svec((Q * np.maximum(lam, 0)) @ Q.T)) <= TOL_SPLIT
+
+
+def test_split_vjp_vs_oracle(lib):
+    """The derivative's contractions also run split in SPLIT_TF32 mode."""
+    import torch
+    n = 160
+    rng = W.rng_for(8800)
+    X, Q, lam = W.from_spectrum(rng, W.spectrum_vjp(rng, n, cluster=1e-3))
+    x = W.to_svec(X)
+    g = rng.standard_normal(x.size)
+    xt, gt = torch.from_numpy(x).cuda(), torch.from_numpy(g).cuda()
+    xb = lib.proj_vjp(xt, gt, [n], opts=lib.make_opts(precision=lib.SPLIT_TF32))
+    assert lib.status(0) == lib.OK
+    assert rel(xb.cpu().numpy(), oracle.jvp(x, g)) <= TOL_SPLIT
