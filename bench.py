@@ -176,8 +176,11 @@ def phase_kernels(phase: str, n: int, band: int) -> str:
     }.get(phase, phase)
 
 
-def algorithmic_flops(phase: str, n: int, k: int, b: int) -> float:
-    """Algorithmic FP64 flops of one cone for a phase (k = eigenpairs kept, b = band width)."""
+def algorithmic_flops(phase: str, n: int, k: int, b: int, kbt: int | None = None) -> float:
+    """Algorithmic FP64 flops of one cone for a phase: k = eigenpairs of the
+    route's side (min(k+, k-)), kbt = columns back-transformed (k for the
+    projection, n when the derivative needs all pairs), b = band width."""
+    kbt = k if kbt is None else kbt
     if phase == "dense_to_band":
         return 4.0 / 3.0 * n ** 3
     if phase == "band_to_tridiag":
@@ -185,11 +188,11 @@ def algorithmic_flops(phase: str, n: int, k: int, b: int) -> float:
     if phase == "tridiag_dc":
         return 4.0 / 3.0 * n ** 3
     if phase in ("backtransform_2", "backtransform_1"):
-        return 2.0 * n * n * k
+        return 2.0 * n * n * kbt
     if phase == "reconstruct":
         return 1.0 * n * n * k
     if phase == "derivative":
-        return 8.0 * n ** 3
+        return 8.0 * k * n * n
     return 0.0
 
 
@@ -408,9 +411,10 @@ def run_ours(args):
     else:
         lam_sample = np.linalg.eigvalsh(W_smat_host(wl.calls[0][0][: n0 * (n0 + 1) // 2], n0))
     kp, kn = int((lam_sample > 0).sum()), int((lam_sample < 0).sum())
-    k = n0 if wl.vjp else min(kp, kn)
+    k = min(kp, kn)
+    kbt = n0 if wl.vjp else k
     cones_per_call = len(wl.calls[0][1])
-    flops_launch = sum(algorithmic_flops(dom_name, int(s), k, b_used) for s in wl.calls[0][1])
+    flops_launch = sum(algorithmic_flops(dom_name, int(s), k, b_used, kbt) for s in wl.calls[0][1])
     # per call: a phase may be traced as several segments within one call
     avg_ms = dom_ms / max(1, args.steps * len(wl.calls))
     achieved = flops_launch / (avg_ms * 1e-3) / 1e9
