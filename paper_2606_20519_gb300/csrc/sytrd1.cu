@@ -106,32 +106,6 @@ __device__ double make_reflector_ps(double* x, int len, double ps, double* red, 
   return sh[1];
 }
 
-// The same reflector without rescaling x: tau, beta and scal = 1/(x_0 - beta)
-// are returned and x[0] is set to x_0 - beta, so u = scal * x exactly where
-// the caller needs it (the products of the next pass fold scal into their
-// factor tau * scal, the copy into the next step's v multiplies).  One
-// shared-memory pass and one barrier shorter than make_reflector_ps.
-__device__ double make_reflector_lazy(double* x, double ps, double* red, double* sh, double* beta_out,
-                                      double* scal_out) {
-  const double sigma = block_sum256(ps, red);
-  if (threadIdx.x == 0) {
-    const double alpha = x[0];
-    double beta = alpha, tau = 0.0, scal = 0.0;
-    if (sigma != 0.0) {
-      const double nrm = sqrt(fma(alpha, alpha, sigma));
-      beta = alpha >= 0.0 ? -nrm : nrm;
-      tau = (beta - alpha) / beta;
-      scal = 1.0 / (alpha - beta);
-    }
-    sh[0] = beta; sh[1] = tau; sh[2] = scal;
-    x[0] = alpha - beta;  // scal * x[0] = 1 (u_0); 0 when tau = 0
-  }
-  __syncthreads();
-  *beta_out = sh[0];
-  *scal_out = sh[2];
-  return sh[1];
-}
-
 __device__ double make_reflector(double* x, int len, double* red, double* sh, double* beta_out) {
   double ps = 0.0;
   for (int t = 1 + threadIdx.x; t < len; t += kSyThreads) ps = fma(x[t], x[t], ps);
@@ -158,22 +132,28 @@ __device__ void store_reflector(const ConeDev& c, int n, int j, const double* u,
 
 // One pass over this CTA's columns i >= r0 (i mod G = rank), rows r0 .. n-1:
 // with UPDATE, first A(r, i) -= v_r w_i + w_r v_i (vu, wu indexed from row
-// r0 - 1); then p_i = tau * sum_r A(r, i) u_r (u indexed from row r0) into
-// pbuf[i].
+// r0 - 1); then p_i = coef[0] (A(r0, i) + coef[1] sum_{r > r0} A(r, i) x_r)
+// into pbuf[i], x indexed from row r0.  The next reflector is u = coef[1] x
+// with u_0 = 1, so p_i = tau u^T A(r0:, i) without x having been rescaled;
+// coef is read only after the pass's first barrier, so the reflector's
+// scalars may still be in the making (by thread 0) while the pass starts.
+// Work items are (column, CH-row chunk) pairs spread over the warps (CH = 128
+// for small cones, whose columns are short, else 256: 8 loads per lane).
 // RES: this CTA's columns live in shared memory (cols, column i at
 // ((i - rank) / G) * n); the owner of column r0 -- the next reflector's
 // source -- also writes its updated rows to A for every CTA to read.
-template <bool UPDATE, bool RES>
+template <bool UPDATE, bool RES, int CH>
 __device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, int n, int r0,
-                              const double* __restrict__ u, double tau, const double* __restrict__ vu,
-                              const double* __restrict__ wu, double* pbuf, double* psum, int pcap, double* red,
-                              int rank, int G) {
+                            const double* __restrict__ x, const double* coef, const double* __restrict__ vu,
+                            const double* __restrict__ wu, double* pbuf, double* psum, int pcap, int rank,
+                            int G) {
+  constexpr int NR = CH / 32;
   const int L = n - r0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int first = r0 + ((rank - r0 % G) + G) % G;
   const int ncol = first < n ? (n - 1 - first) / G + 1 : 0;
-  const int nch = (L + kChunk - 1) / kChunk;
-  const int per = pcap / nch;
+  const int nch = (L + CH - 1) / CH;
+  const int per = max(1, pcap / nch);
   for (int k0 = 0; k0 < ncol; k0 += per) {
     const int kc = min(ncol - k0, per);
     for (int it = warp; it < kc * nch; it += kSyThreads / 32) {
@@ -181,10 +161,10 @@ __device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, i
       const int i = first + G * k;
       double* gcol = A + (int64_t)i * n + r0;
       double* col = RES ? cols + (int64_t)((i - rank) / G) * n + r0 : gcol;
-      const int t0 = ch * kChunk + lane;
-      double a[8];
+      const int t0 = ch * CH + lane;
+      double a[NR];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
+      for (int r = 0; r < NR; ++r) {
         const int t = t0 + 32 * r;
         a[r] = t < L ? (RES ? col[t] : __ldcg(col + t)) : 0.0;
       }
@@ -192,7 +172,7 @@ __device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, i
         const double vi = vu[i - r0 + 1], wi = wu[i - r0 + 1];
         const bool publish = RES && i == r0;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < NR; ++r) {
           const int t = t0 + 32 * r;
           if (t < L) {
             a[r] = fma(-vu[t + 1], wi, fma(-wu[t + 1], vi, a[r]));
@@ -207,24 +187,27 @@ __device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, i
       }
       double acc = 0.0;
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
+      for (int r = 0; r < NR; ++r) {
         const int t = t0 + 32 * r;
-        if (t < L) acc = fma(a[r], u[t], acc);
+        if (t < L && t > 0) acc = fma(a[r], x[t], acc);
       }
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) psum[it] = acc;
     }
     __syncthreads();
+    const double tau = coef[0], scal = coef[1];
     for (int kk = tid; kk < kc; kk += kSyThreads) {
-      double p = 0.0;
-      for (int ch = 0; ch < nch; ++ch) p += psum[kk * nch + ch];
-      p *= tau;
+      double sdot = 0.0;
+      for (int ch = 0; ch < nch; ++ch) sdot += psum[kk * nch + ch];
       const int i = first + G * (k0 + kk);
-      __stcg(pbuf + i, p);
+      const double a0 = RES ? cols[(int64_t)((i - rank) / G) * n + r0] : __ldcg(A + (int64_t)i * n + r0);
+      __stcg(pbuf + i, tau * fma(scal, sdot, a0));
     }
     __syncthreads();
   }
-  (void)red;
+  // the caller reads the coefficients (written by thread 0 before the pass)
+  // after it: a CTA without columns still passes one barrier
+  if (ncol == 0) __syncthreads();
 }
 
 // Step j (reflector H_j = I - tau_j v v^T from column j, v indexed from row
@@ -239,7 +222,7 @@ __device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, i
 // Shared memory of a CTA: v, w, the updated column (3n), the partial sums,
 // and with RES the CTA's own columns (ceil(n / G) of n rows).
 __host__ __device__ inline int sytrd1_pcap(int n, int G) {
-  const int items = ((n + G - 1) / G) * ((n + kChunk - 1) / kChunk);
+  const int items = ((n + G - 1) / G) * ((n + 127) / 128);  // up to 128-row items
   return items < kPartMax ? items : kPartMax;
 }
 __host__ __device__ inline size_t sytrd1_bytes(int n, int G, bool res) {
@@ -293,7 +276,11 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
     c.tau1[0] = tau;
   }
   store_reflector(c, n, 0, vc, rank, G);
-  column_pass<false, RES>(A, cols, n, 1, vc, tau, nullptr, nullptr, pbuf2, psum, pcap, red, rank, G);
+  // v_0 is already scaled (u = v): coefficients (tau, 1)
+  if (tid == 0) { sh[1] = tau; sh[2] = 1.0; }
+  __syncthreads();
+  if (n <= 256) column_pass<false, RES, 128>(A, cols, n, 1, vc, sh + 1, nullptr, nullptr, pbuf2, psum, pcap, rank, G);
+  else column_pass<false, RES, kChunk>(A, cols, n, 1, vc, sh + 1, nullptr, nullptr, pbuf2, psum, pcap, rank, G);
   for (int j = 0; j + 2 < n; ++j) {
     const int m = n - j - 1;
     const double* pbuf = pbuf2 + (j & 1) * n;
@@ -340,18 +327,32 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
       }
     }
     if (j + 3 < n) {
-      // ---- reflector j+1 from rows j+2 .. of the updated column
-      double beta1, scal1;
-      const double tau1 = make_reflector_lazy(vx + 1, ps, red, sh, &beta1, &scal1);
+      // ---- reflector j+1 from rows j+2 .. of the updated column x = vx + 1:
+      // its sum of squares now; thread 0 forms tau, beta and scal = 1/(x_0 - beta)
+      // while the other warps already run the pass, which needs them only at
+      // its end (p_i = tau (a_0 + scal sum_{t >= 1} a_t x_t), u = scal x, u_0 = 1)
+      const double sigma = block_sum256(ps, red);
+      if (tid == 0) {
+        const double alpha = vx[1];
+        double beta = alpha, t1 = 0.0, sc = 0.0;
+        if (sigma != 0.0) {
+          const double nrm = sqrt(fma(alpha, alpha, sigma));
+          beta = alpha >= 0.0 ? -nrm : nrm;
+          t1 = (beta - alpha) / beta;
+          sc = 1.0 / (alpha - beta);
+        }
+        sh[0] = beta; sh[1] = t1; sh[2] = sc;
+      }
+      double* pnext = pbuf2 + ((j + 1) & 1) * n;
+      if (n <= 256) column_pass<true, RES, 128>(A, cols, n, j + 2, vx + 1, sh + 1, vc, w, pnext, psum, pcap, rank, G);
+      else column_pass<true, RES, kChunk>(A, cols, n, j + 2, vx + 1, sh + 1, vc, w, pnext, psum, pcap, rank, G);
+      const double beta1 = sh[0], tau1 = sh[1], scal1 = sh[2];
       if (rank == 0 && tid == 0) {
         c.d[j + 1] = vx[0];
         c.e[j + 1] = beta1;
         c.tau1[j + 1] = tau1;
       }
       store_reflector(c, n, j + 1, vx + 1, rank, G, scal1);
-      double* pnext = pbuf2 + ((j + 1) & 1) * n;
-      // p_i = tau u^T a_i with u = scal x: the factor tau * scal
-      column_pass<true, RES>(A, cols, n, j + 2, vx + 1, tau1 * scal1, vc, w, pnext, psum, pcap, red, rank, G);
       // v_{j+1} = scal x becomes the current reflector (v_0 = 1)
       for (int t = tid; t < m - 1; t += kSyThreads) vc[t] = t == 0 ? 1.0 : scal1 * vx[1 + t];
       tau = tau1;
