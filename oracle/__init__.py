@@ -69,6 +69,10 @@ def _load():
         lib.orc_psd_proj_route.restype = ctypes.c_int
         lib.orc_psd_jvp.argtypes = [i64, dp, dp, dp]
         lib.orc_psd_jvp.restype = ctypes.c_int
+        lib.orc_hsmat.argtypes = [i64, dp, dp, dp]
+        lib.orc_hsvec.argtypes = [i64, dp, dp, dp]
+        lib.orc_herm_proj_route.argtypes = [i64, dp, dp, dp, ctypes.c_int]
+        lib.orc_herm_proj_route.restype = ctypes.c_int
         lib.orc_set_mutation.argtypes = [ctypes.c_int]
         lib.orc_get_mutation.restype = ctypes.c_int
         lib.orc_set_threads.argtypes = [ctypes.c_int]
@@ -205,4 +209,50 @@ def jvp_batched(x, g, offsets) -> np.ndarray:
     for i in range(len(offsets) - 1):
         a, b = int(offsets[i]), int(offsets[i + 1])
         y[a:b] = jvp(x[a:b], g[a:b])
+    return y
+
+
+# ---- complex Hermitian cones (svec: per column the diagonal entry, then for
+# every row below it sqrt(2) Re, sqrt(2) Im; n^2 reals)
+def hside_of(length: int) -> int:
+    n = int(round(np.sqrt(length)))
+    if n * n != length:
+        raise ValueError(f"{length} is not n^2")
+    return n
+
+
+def herm_smat(x) -> np.ndarray:
+    """Complex Hermitian matrix of a Hermitian svec."""
+    x = _f64(x)
+    n = hside_of(x.size)
+    Ar = np.empty((n, n)); Ai = np.empty((n, n))
+    _load().orc_hsmat(n, _dp(x), _dp(Ar), _dp(Ai))
+    return Ar + 1j * Ai
+
+
+def herm_svec(A) -> np.ndarray:
+    A = np.asarray(A, dtype=np.complex128)
+    n = A.shape[0]
+    Ar = np.ascontiguousarray(A.real); Ai = np.ascontiguousarray(A.imag)
+    s = np.empty(n * n)
+    _load().orc_hsvec(n, _dp(Ar), _dp(Ai), _dp(s))
+    return s
+
+
+def herm_proj(x, route: int = 0) -> np.ndarray:
+    """Pi(X) of a complex Hermitian cone on its svec (complex Jacobi, FP64)."""
+    x = _f64(x)
+    n = hside_of(x.size)
+    y = np.empty_like(x)
+    _check(_load().orc_herm_proj_route(n, _dp(x), _dp(y), None, route), "orc_herm_proj_route")
+    return y
+
+
+def herm_proj_batched(x, sides) -> np.ndarray:
+    x = _f64(x)
+    y = np.empty_like(x)
+    o = 0
+    for n in sides:
+        y[o:o + n * n] = herm_proj(x[o:o + n * n])
+        o += n * n
     return y

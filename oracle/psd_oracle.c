@@ -16,7 +16,9 @@
  *   - the directional derivative of Pi (needed because App. E back-propagates
  *     through the eigendecomposition), by the Daleckii-Krein formula
  *         DPi(X)[H] = V (L o (V^T H V)) V^T,
- *     L_ij the divided difference of max(.,0) at (lambda_i, lambda_j).
+ *     L_ij the divided difference of max(.,0) at (lambda_i, lambda_j);
+ *   - the same projection for complex Hermitian cones (the paper's own cone
+ *     type), Pi(X) = V diag(max(lambda, 0)) V^H, by a complex Jacobi method.
  *
  * The eigendecomposition is a cyclic two-sided Jacobi method (rotation of
  * Golub & Van Loan, "Matrix Computations", Alg. 8.5.1 sym.schur2), with a
@@ -376,5 +378,191 @@ int orc_psd_jvp(int64_t n, const double* x, const double* h, double* out) {
     orc_svec(n, H, out);
   }
   free(V); free(H); free(W); free(lam);
+  return st;
+}
+
+/* ------------------------------------------------------------------------
+ * Complex Hermitian cones (the paper's cones are complex Hermitian: the
+ * vec map of App. D.1 lists X_ii, sqrt(2) Re X_ij, sqrt(2) Im X_ij).  Taken
+ * order (SCS's complex PSD cone): column by column, the diagonal entry, then
+ * for every row i > j the pair sqrt(2) Re X_ij, sqrt(2) Im X_ij; n^2 reals.
+ * Matrices are held as separate real and imaginary row-major arrays.
+ */
+int64_t orc_hsvec_len(int64_t n) { return n * n; }
+
+void orc_hsmat(int64_t n, const double* s, double* Ar, double* Ai) {
+  const double r = 0.70710678118654752440;  /* 1 / sqrt(2) */
+  int64_t k = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    Ar[j * n + j] = s[k++];
+    Ai[j * n + j] = 0.0;
+    for (int64_t i = j + 1; i < n; ++i) {
+      const double re = s[k++] * r, im = s[k++] * r;
+      Ar[i * n + j] = re; Ai[i * n + j] = im;    /* X_ij */
+      Ar[j * n + i] = re; Ai[j * n + i] = -im;   /* X_ji = conj(X_ij) */
+    }
+  }
+}
+
+void orc_hsvec(int64_t n, const double* Ar, const double* Ai, double* s) {
+  const double r2 = 1.41421356237309504880;
+  int64_t k = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    s[k++] = Ar[j * n + j];
+    for (int64_t i = j + 1; i < n; ++i) {
+      s[k++] = r2 * Ar[i * n + j];
+      s[k++] = r2 * Ai[i * n + j];
+    }
+  }
+}
+
+/*
+ * Jacobi for Hermitian matrices.  For a pair (p, q) with A_pq = |b| e^{i phi},
+ * the unitary U = D J, D = diag(1, e^{-i phi}) (which makes the pair's
+ * off-diagonal entry real, |b|) and J the real rotation of sym.schur2 for
+ * [[A_pp, |b|], [|b|, A_qq]], zeroes A_pq:
+ *   columns: col_p <- c col_p - s e^{-i phi} col_q,  col_q <- s col_p + c e^{-i phi} col_q;
+ *   rows   : row_p <- c row_p - s e^{i phi} row_q,   row_q <- s row_p + c e^{i phi} row_q.
+ * Same round-robin order and thread-count independence as the real method.
+ */
+int orc_herm_jacobi_eig(int64_t n, double* Ar, double* Ai, double* lam, double* Vr, double* Vi, int max_sweeps) {
+  for (int64_t i = 0; i < n * n; ++i) { Vr[i] = 0.0; Vi[i] = 0.0; }
+  for (int64_t i = 0; i < n; ++i) Vr[i * n + i] = 1.0;
+  if (n <= 1) {
+    if (n == 1) lam[0] = Ar[0];
+    return ORC_OK;
+  }
+  const int64_t m = (n % 2 == 0) ? n : n + 1;
+  const int64_t half = m / 2;
+  int64_t* P = (int64_t*)malloc(sizeof(int64_t) * half);
+  int64_t* Q = (int64_t*)malloc(sizeof(int64_t) * half);
+  double* C = (double*)malloc(sizeof(double) * half);
+  double* S = (double*)malloc(sizeof(double) * half);
+  double* ER = (double*)malloc(sizeof(double) * half);  /* cos(phi) */
+  double* EI = (double*)malloc(sizeof(double) * half);  /* sin(phi) */
+  if (!P || !Q || !C || !S || !ER || !EI) {
+    free(P); free(Q); free(C); free(S); free(ER); free(EI);
+    return ORC_ENOMEM;
+  }
+  const double eps = 0x1p-53;
+  const int nt = nthreads();
+  int status = ORC_ENOCONV;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    int64_t rotated = 0;
+    for (int64_t r = 0; r < m - 1; ++r) {
+      int64_t np = 0;
+      for (int64_t k = 0; k < half; ++k) {
+        int64_t p, q;
+        round_pair(m, r, k, &p, &q);
+        if (q >= n) continue;
+        const double br = Ar[p * n + q], bi = Ai[p * n + q];
+        const double ab = hypot(br, bi);
+        const double app = Ar[p * n + p], aqq = Ar[q * n + q];
+        if (ab <= 1e-300 || ab <= eps * sqrt(fabs(app)) * sqrt(fabs(aqq))) continue;
+        const double tau = (aqq - app) / (2.0 * ab);
+        double t;
+        if (fabs(tau) > 1e150) t = 0.5 / tau;
+        else if (tau >= 0.0) t = 1.0 / (tau + sqrt(1.0 + tau * tau));
+        else t = -1.0 / (-tau + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + t * t);
+        P[np] = p; Q[np] = q; C[np] = c; S[np] = t * c; ER[np] = br / ab; EI[np] = bi / ab;
+        ++np;
+      }
+      if (np == 0) continue;
+      rotated += np;
+      /* rows: row_p <- c row_p - s e^{i phi} row_q, row_q <- s row_p + c e^{i phi} row_q */
+#pragma omp parallel for num_threads(nt) schedule(static)
+      for (int64_t k = 0; k < np; ++k) {
+        double* pr = Ar + P[k] * n; double* pi = Ai + P[k] * n;
+        double* qr = Ar + Q[k] * n; double* qi = Ai + Q[k] * n;
+        const double c = C[k], s = S[k], er = ER[k], ei = EI[k];
+        for (int64_t j = 0; j < n; ++j) {
+          const double xr = pr[j], xi = pi[j], yr = qr[j], yi = qi[j];
+          const double zr = er * yr - ei * yi, zi = er * yi + ei * yr;  /* e^{i phi} y */
+          pr[j] = c * xr - s * zr; pi[j] = c * xi - s * zi;
+          qr[j] = s * xr + c * zr; qi[j] = s * xi + c * zi;
+        }
+      }
+      /* columns of A and V: col_p <- c col_p - s e^{-i phi} col_q, col_q <- s col_p + c e^{-i phi} col_q */
+#pragma omp parallel for num_threads(nt) schedule(static)
+      for (int64_t i = 0; i < n; ++i) {
+        for (int64_t k = 0; k < np; ++k) {
+          const int64_t p = P[k], q = Q[k];
+          const double c = C[k], s = S[k], er = ER[k], ei = EI[k];
+          for (int w = 0; w < 2; ++w) {
+            double* mr = (w == 0 ? Ar : Vr) + i * n;
+            double* mi = (w == 0 ? Ai : Vi) + i * n;
+            const double xr = mr[p], xi = mi[p], yr = mr[q], yi = mi[q];
+            const double zr = er * yr + ei * yi, zi = er * yi - ei * yr;  /* e^{-i phi} y */
+            mr[p] = c * xr - s * zr; mi[p] = c * xi - s * zi;
+            mr[q] = s * xr + c * zr; mi[q] = s * xi + c * zi;
+          }
+        }
+      }
+      for (int64_t k = 0; k < np; ++k) {
+        Ar[P[k] * n + Q[k]] = 0.0; Ai[P[k] * n + Q[k]] = 0.0;
+        Ar[Q[k] * n + P[k]] = 0.0; Ai[Q[k] * n + P[k]] = 0.0;
+        Ai[P[k] * n + P[k]] = 0.0; Ai[Q[k] * n + Q[k]] = 0.0;
+      }
+    }
+    if (rotated == 0) { status = ORC_OK; break; }
+  }
+  for (int64_t i = 0; i < n; ++i) lam[i] = Ar[i * n + i];
+  free(P); free(Q); free(C); free(S); free(ER); free(EI);
+  return status;
+}
+
+/*
+ * Pi(X) for a complex Hermitian cone on its svec (n^2 reals):
+ * y = svec(sum_{lam > 0} lam v v^H) (route 0) or svec(X - sum_{lam < 0} lam v v^H) (route 1).
+ */
+int orc_herm_proj_route(int64_t n, const double* x, double* y, double* lam_out, int route) {
+  if (n < 0 || (n > 0 && (!x || !y))) return ORC_EINVAL;
+  if (n == 0) return ORC_OK;
+  const int64_t len = n * n;
+  if (!all_finite(len, x)) {
+    for (int64_t i = 0; i < len; ++i) y[i] = NAN;
+    return ORC_ENONFINITE;
+  }
+  double* Ar = (double*)malloc(sizeof(double) * n * n);
+  double* Ai = (double*)malloc(sizeof(double) * n * n);
+  double* Vr = (double*)malloc(sizeof(double) * n * n);
+  double* Vi = (double*)malloc(sizeof(double) * n * n);
+  double* Yr = (double*)malloc(sizeof(double) * n * n);
+  double* Yi = (double*)malloc(sizeof(double) * n * n);
+  double* lam = (double*)malloc(sizeof(double) * n);
+  if (!Ar || !Ai || !Vr || !Vi || !Yr || !Yi || !lam) {
+    free(Ar); free(Ai); free(Vr); free(Vi); free(Yr); free(Yi); free(lam);
+    return ORC_ENOMEM;
+  }
+  orc_hsmat(n, x, Ar, Ai);
+  int st = orc_herm_jacobi_eig(n, Ar, Ai, lam, Vr, Vi, 60);
+  if (st == ORC_OK) {
+    const int nt = nthreads();
+    /* Y_ij = sum_k f_k V_ik conj(V_jk), lower triangle then mirrored */
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 8)
+    for (int64_t i = 0; i < n; ++i) {
+      for (int64_t j = 0; j <= i; ++j) {
+        double sr = 0.0, si = 0.0;
+        for (int64_t k = 0; k < n; ++k) {
+          const double f = route == 0 ? (lam[k] > 0.0 ? lam[k] : 0.0) : (lam[k] < 0.0 ? lam[k] : 0.0);
+          if (f == 0.0) continue;
+          const double ar = Vr[i * n + k], ai = Vi[i * n + k], br = Vr[j * n + k], bi = Vi[j * n + k];
+          sr += f * (ar * br + ai * bi);
+          si += f * (ai * br - ar * bi);
+        }
+        Yr[i * n + j] = sr; Yi[i * n + j] = si;
+      }
+    }
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = i + 1; j < n; ++j) { Yr[i * n + j] = Yr[j * n + i]; Yi[i * n + j] = -Yi[j * n + i]; }
+    if (route == 1) {
+      orc_hsmat(n, x, Ar, Ai);
+      for (int64_t i = 0; i < n * n; ++i) { Yr[i] = Ar[i] - Yr[i]; Yi[i] = Ai[i] - Yi[i]; }
+    }
+    orc_hsvec(n, Yr, Yi, y);
+    if (lam_out) memcpy(lam_out, lam, sizeof(double) * n);
+  }
+  free(Ar); free(Ai); free(Vr); free(Vi); free(Yr); free(Yi); free(lam);
   return st;
 }

@@ -210,3 +210,47 @@ def vjp_batch(seed: int = SEED_BASE + 5, n: int = 1296, batch: int = 8, cluster:
     b = pack(svecs, [n] * batch)
     b.extra.update(Q=Qs, lam=lams, g=rng.standard_normal(b.x.size))
     return b
+
+
+# ---- complex Hermitian cones (the paper's cones are complex Hermitian)
+def haar_unitary(rng: np.random.Generator, n: int) -> np.ndarray:
+    """Haar-random unitary: QR of a complex Gaussian with the phases of R's
+    diagonal moved into Q (Mezzadri 2007)."""
+    G = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(2.0)
+    Q, R = np.linalg.qr(G)
+    d = np.diag(R)
+    return Q * (d / np.abs(d))[None, :]
+
+
+def herm_from_spectrum(rng: np.random.Generator, lam: np.ndarray):
+    """X = U diag(lam) U^H with Haar U.  Returns (X, U, lam)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    U = haar_unitary(rng, lam.size)
+    X = (U * lam[None, :]) @ U.conj().T
+    X = 0.5 * (X + X.conj().T)
+    return X, U, lam
+
+
+def herm_gaussian(rng: np.random.Generator, n: int) -> np.ndarray:
+    """(G + G^H) / 2 with G iid complex Gaussian (unit variance per entry)."""
+    G = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(2.0)
+    return 0.5 * (G + G.conj().T)
+
+
+def to_hsvec(X: np.ndarray) -> np.ndarray:
+    """Hermitian svec: per column the (real) diagonal entry, then for every
+    row below it sqrt(2) Re X_ij, sqrt(2) Im X_ij (n^2 reals)."""
+    X = np.asarray(X, dtype=np.complex128)
+    n = X.shape[0]
+    out = np.empty(n * n)
+    k = 0
+    r2 = np.sqrt(2.0)
+    for j in range(n):
+        out[k] = X[j, j].real
+        k += 1
+        col = X[j + 1:, j]
+        m = col.size
+        out[k:k + 2 * m:2] = r2 * col.real
+        out[k + 1:k + 2 * m:2] = r2 * col.imag
+        k += 2 * m
+    return out
