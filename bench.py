@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", default="admm625",
-                   choices=["admm625", "single81", "precision4096", "uneven", "vjp1296"])
+                   choices=["admm625", "single81", "precision4096", "uneven", "vjp1296", "herm625"])
     p.add_argument("--band", type=int, default=0)
     p.add_argument("--precision", default="fp64", choices=["fp64", "split"],
                    help="fp64: FP64 throughout; split: split-TF32 tensor-core contractions")
@@ -76,6 +76,7 @@ class Workload:
     def __init__(self, name: str, calls: int = 0):
         self.name = name
         self.vjp = False
+        self.herm = False
         if name == "admm625":
             seq, Q, lam = W.admm_sequence()
             self.calls = [(x, [625]) for x in seq]
@@ -96,6 +97,12 @@ class Workload:
             self.calls = [(b.x, list(b.sides))]
             self.desc = "960 uneven cones (64 restarts x {2 x sides 4..64 + one 625/1296}) in one call"
             self.exact0 = None
+        elif name == "herm625":
+            seq, U, lam = W.herm_admm_sequence()
+            self.calls = [(x, [625]) for x in seq]
+            self.herm = True
+            self.desc = "ADMM-like sequence of 50 complex Hermitian projections, n=625 (d=5), 50 dependent calls"
+            self.exact0 = (U, lam)
         elif name == "vjp1296":
             b = W.vjp_batch()
             self.calls = [(b.x, list(b.sides))]
@@ -103,6 +110,7 @@ class Workload:
             self.vjp = True
             self.desc = "forward + Daleckii-Krein VJP, 8 matrices n=1296 (d=6), +-1e-9 clusters"
             self.exact0 = (b.extra["Q"][0], b.extra["lam"][0])
+        self.svec_len = (lambda n: n * n) if self.herm else (lambda n: n * (n + 1) // 2)
         if calls:
             self.calls = self.calls[:calls]
             self.desc += f" (first {calls} call(s) only)"
@@ -208,10 +216,12 @@ def oracle_value(wl: Workload, budget_s: float = 12.0):
     sample = []
     for x, sides in wl.calls:
         offs = np.zeros(len(sides) + 1, dtype=np.int64)
-        np.cumsum([s * (s + 1) // 2 for s in sides], out=offs[1:])
+        np.cumsum([wl.svec_len(s) for s in sides], out=offs[1:])
         for i in range(len(sides)):
             xi = x[offs[i]:offs[i + 1]]
-            if wl.vjp:
+            if wl.herm:
+                oracle.herm_proj(xi)
+            elif wl.vjp:
                 oracle.proj(xi)
                 oracle.jvp(xi, wl.g[offs[i]:offs[i + 1]])
             else:
@@ -280,7 +290,7 @@ def run_ours(args):
     xs = [torch.from_numpy(x).to(dev) for x, _ in wl.calls]
     ys = [torch.empty_like(x) for x in xs]
     gs = [torch.from_numpy(wl.g).to(dev)] if wl.vjp else None
-    shapes = [lib.shapes(s) for _, s in wl.calls]
+    shapes = [(lib.hshapes(s) if wl.herm else lib.shapes(s)) for _, s in wl.calls]
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -289,6 +299,8 @@ def run_ours(args):
             offs, sides = shapes[i]
             if wl.vjp:
                 lib.proj_vjp(x_list[i], gs[0], sides, xbar=y_list[i], y=yb, opts=opts, offsets=offs)
+            elif wl.herm:
+                lib.proj_hermitian(x_list[i], sides, out=y_list[i], opts=opts, offsets=offs)
             else:
                 lib.proj_batched(x_list[i], sides, out=y_list[i], opts=opts, offsets=offs)
 
@@ -296,7 +308,7 @@ def run_ours(args):
 
     # launch shapes: the library's autotuner on the first call's input (setup, untimed)
     tuning = None
-    if not args.no_autotune and not args.band:
+    if not args.no_autotune and not args.band and not wl.herm:
         tuning = lib.autotune(xs[0], shapes[0][1], opts=opts, offsets=shapes[0][0])
         if tuning["band"] >= 2:
             b_used = tuning["band"]
@@ -313,8 +325,9 @@ def run_ours(args):
     if wl.exact0 is not None:
         Q, lam = wl.exact0
         n0 = Q.shape[0]
-        P = W.to_svec((Q * np.maximum(lam, 0)) @ Q.T)
-        y0 = (yb if wl.vjp else ys[0])[: n0 * (n0 + 1) // 2].cpu().numpy()
+        Pm = (Q * np.maximum(lam, 0)) @ Q.conj().T
+        P = W.to_hsvec(Pm) if wl.herm else W.to_svec(Pm)
+        y0 = (yb if wl.vjp else ys[0])[: wl.svec_len(n0)].cpu().numpy()
         err0 = rel(y0, P)
 
     for _ in range(args.warmup):
@@ -373,6 +386,8 @@ def run_ours(args):
             offs, sides = shapes[i]
             if wl.vjp:
                 lib.proj_vjp(dx[i], gs[0], sides, xbar=dy[i], y=yb, opts=opts, offsets=offs)
+            elif wl.herm:
+                lib.proj_hermitian(dx[i], sides, out=dy[i], opts=opts, offsets=offs)
             else:
                 lib.proj_batched(dx[i], sides, out=dy[i], opts=opts, offsets=offs)
             hy[i].copy_(dy[i], non_blocking=True)
@@ -414,7 +429,9 @@ def run_ours(args):
     k = min(kp, kn)
     kbt = n0 if wl.vjp else k
     cones_per_call = len(wl.calls[0][1])
-    flops_launch = sum(algorithmic_flops(dom_name, int(s), k, b_used, kbt) for s in wl.calls[0][1])
+    # a Hermitian cone is projected as its real embedding of side 2n (every eigenvalue twice)
+    emb = 2 if wl.herm else 1
+    flops_launch = sum(algorithmic_flops(dom_name, emb * int(s), emb * k, b_used, emb * kbt) for s in wl.calls[0][1])
     # per call: a phase may be traced as several segments within one call
     avg_ms = dom_ms / max(1, args.steps * len(wl.calls))
     achieved = flops_launch / (avg_ms * 1e-3) / 1e9
@@ -485,6 +502,8 @@ def comparator(wl, xs, dev, stream, max_calls: int = 20):
     r_idx = {}
 
     def proj_one(s, n):
+        if wl.herm:
+            return proj_one_herm(s, n)
         A = _smat_torch(s, n)
         w, V = torch.linalg.eigh(A)
         P = (V * w.clamp(min=0)) @ V.T
@@ -493,6 +512,37 @@ def comparator(wl, xs, dev, stream, max_calls: int = 20):
             r_idx[n] = (torch.from_numpy(r).to(dev), torch.from_numpy(c).to(dev))
         r, c = r_idx[n]
         return P[r, c] * torch.where(r == c, 1.0, np.sqrt(2.0)).to(torch.float64)
+
+    h_idx = {}
+
+    def proj_one_herm(s, n):
+        # Hermitian svec: per column the diagonal, then sqrt(2) Re, sqrt(2) Im of every row below
+        if n not in h_idx:
+            d_pos, rows, cols, re_pos = [], [], [], []
+            k = 0
+            for j in range(n):
+                d_pos.append(k)
+                k += 1
+                for i in range(j + 1, n):
+                    rows.append(i); cols.append(j); re_pos.append(k)
+                    k += 2
+            t = lambda a: torch.tensor(a, dtype=torch.long, device=dev)
+            h_idx[n] = (t(d_pos), t(rows), t(cols), t(re_pos))
+        d_pos, rows, cols, re_pos = h_idx[n]
+        ar = torch.arange(n, device=dev)
+        A = torch.zeros((n, n), dtype=torch.complex128, device=dev)
+        A[ar, ar] = s[d_pos].to(torch.complex128)
+        off = torch.complex(s[re_pos], s[re_pos + 1]) / np.sqrt(2.0)
+        A[rows, cols] = off
+        A[cols, rows] = off.conj()
+        w, V = torch.linalg.eigh(A)
+        P = (V * w.clamp(min=0)) @ V.conj().T
+        out = torch.empty(n * n, dtype=torch.float64, device=dev)
+        out[d_pos] = P[ar, ar].real
+        po = P[rows, cols] * np.sqrt(2.0)
+        out[re_pos] = po.real
+        out[re_pos + 1] = po.imag
+        return out
 
     calls = list(range(min(max_calls, len(xs))))
     offs_all = [wl.calls[i][1] for i in calls]
@@ -503,7 +553,7 @@ def comparator(wl, xs, dev, stream, max_calls: int = 20):
             sides = offs_all[i]
             o = 0
             for n in sides:
-                ln = n * (n + 1) // 2
+                ln = wl.svec_len(n)
                 proj_one(xs[i][o:o + ln], n)
                 o += ln
                 out += 1
@@ -518,7 +568,8 @@ def comparator(wl, xs, dev, stream, max_calls: int = 20):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    return {"impl": "torch.linalg.eigh float64 + clamp + reconstruct", "value": units / (ms * 1e-3),
+    return {"impl": ("torch.linalg.eigh complex128" if wl.herm else "torch.linalg.eigh float64") + " + clamp + reconstruct",
+            "value": units / (ms * 1e-3),
             "unit": "projections/s", "sample": f"{units} projections"}
 
 

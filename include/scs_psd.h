@@ -123,6 +123,19 @@ int scs_psd_proj_vjp(scs_psd_handle h, const double* x, const double* g, double*
                      const int64_t* offsets, const int32_t* sides, int32_t count,
                      const scs_psd_opts* opts, void* stream);
 
+/* Complex Hermitian cones, the paper's own cone type (App. D.1's vec map
+ * carries sqrt(2) Re X_ij and sqrt(2) Im X_ij): y = hsvec(Pi(hsmat(x))),
+ * Pi(X) = V diag(max(lambda, 0)) V^H.  Hermitian svec order: column by
+ * column the (real) diagonal entry, then for every row i > j the pair
+ * sqrt(2) Re X_ij, sqrt(2) Im X_ij -- n^2 reals per cone.  Cone i occupies
+ * x[offsets[i] .. offsets[i+1]) with offsets[i+1] - offsets[i] == sides[i]^2
+ * (host arrays, offsets[0] == 0); y may alias x.  Computed through the real
+ * symmetric embedding [[Re X, -Im X], [Im X, Re X]] of side 2n, whose
+ * projection is the embedding of Pi(X); sides up to 4096.  Options and
+ * errors as scs_psd_proj_batched. */
+int scs_psd_proj_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* offsets,
+                           const int32_t* sides, int32_t count, const scs_psd_opts* opts, void* stream);
+
 /* Forward pass that keeps the eigendecomposition for a later VJP (the
  * "store" side of the store-or-recompute choice for the derivative of App. E):
  * y = Pi(x) as scs_psd_proj_batched (y may be NULL), and every eigenpair of

@@ -38,7 +38,7 @@ _handles = {}
 EXPORTS = ("scs_psd_create", "scs_psd_destroy", "scs_psd_proj", "scs_psd_proj_batched", "scs_psd_proj_vjp",
            "scs_psd_proj_store", "scs_psd_vjp_stored", "scs_psd_proj_static", "scs_psd_reserve", "scs_psd_status", "scs_psd_last_launch_count",
            "scs_psd_last_replayed", "scs_psd_strerror", "scs_psd_trace", "scs_psd_trace_read",
-           "scs_psd_autotune", "scs_psd_last_tuning")
+           "scs_psd_autotune", "scs_psd_last_tuning", "scs_psd_proj_hermitian")
 NPHASES = 8
 PHASES = ("unpack", "dense_to_band", "band_to_tridiag", "tridiag_dc", "backtransform_2", "backtransform_1",
           "reconstruct", "derivative")
@@ -69,6 +69,7 @@ def load(path: str | None = None):
         lib.scs_psd_status.argtypes = [vp, ctypes.POINTER(i32)]
         lib.scs_psd_last_launch_count.argtypes = [vp]
         lib.scs_psd_last_launch_count.restype = i64
+        lib.scs_psd_proj_hermitian.argtypes = [vp, vp, vp, vp, vp, i32, op, vp]
         lib.scs_psd_autotune.argtypes = [vp, vp, vp, vp, i32, op, vp, ctypes.POINTER(i32),
                                          ctypes.POINTER(ctypes.c_double)]
         lib.scs_psd_last_tuning.argtypes = [vp, ctypes.POINTER(i32)]
@@ -248,6 +249,34 @@ def vjp_stored(V, lam, g, sides, xbar=None, opts: Opts | None = None, offsets=No
                                    _stream_ptr(g))
     _check(rc, "scs_psd_vjp_stored")
     return xbar
+
+
+def hshapes(sides):
+    """(offsets int64[count+1], sides int32[count]) of Hermitian cones (n^2 reals each)."""
+    sides = np.ascontiguousarray(np.asarray(sides, dtype=np.int32))
+    offsets = np.zeros(sides.size + 1, dtype=np.int64)
+    np.cumsum(sides.astype(np.int64) ** 2, out=offsets[1:])
+    return offsets, sides
+
+
+def proj_hermitian(x, sides, out=None, opts: Opts | None = None, offsets=None):
+    """Projection of complex Hermitian cones on their Hermitian svec (C-ABI scs_psd_proj_hermitian)."""
+    import torch
+    _check_tensor(x, "x")
+    if offsets is None:
+        offsets, sides = hshapes(sides)
+    else:
+        offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        sides = np.ascontiguousarray(np.asarray(sides, dtype=np.int32))
+    if out is None:
+        out = torch.empty_like(x)
+    _check_tensor(out, "out")
+    rc = load().scs_psd_proj_hermitian(handle(x.device.index), _ptr(x), _ptr(out),
+                                       offsets.ctypes.data_as(ctypes.c_void_p),
+                                       sides.ctypes.data_as(ctypes.c_void_p), int(sides.size),
+                                       ctypes.byref(opts) if opts is not None else None, _stream_ptr(x))
+    _check(rc, "scs_psd_proj_hermitian")
+    return out
 
 
 TUNING_FIELDS = ("band", "gemm_ctas", "bt1_cols", "sy_share")

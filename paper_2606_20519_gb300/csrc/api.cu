@@ -128,6 +128,20 @@ struct Plan {
   }
 };
 
+// A shape list of complex Hermitian cones: the real side-2n embeddings'
+// shapes and a device buffer for their svec.
+struct HermPlan {
+  std::vector<int64_t> roff;   // real offsets (count + 1)
+  std::vector<int32_t> rsides; // 2 n
+  int64_t maxn = 0;
+  int64_t* meta_d = nullptr;   // per cone: n, Hermitian offset, real offset
+  double* buf = nullptr;       // roff[count] doubles
+  ~HermPlan() {
+    if (meta_d) cudaFree(meta_d);
+    if (buf) cudaFree(buf);
+  }
+};
+
 }  // namespace
 
 struct scs_psd_handle_s {
@@ -147,6 +161,7 @@ struct scs_psd_handle_s {
   int64_t last_launches = 0;
   std::map<std::string, std::unique_ptr<Plan>> plans;
   std::map<std::string, Tuning> tuned;  // autotuner's choices by shapes and precision
+  std::map<std::string, std::unique_ptr<HermPlan>> herm;  // Hermitian shape lists
   Tuning last_tune;
   std::mutex mu;
 };
@@ -1279,6 +1294,61 @@ int autotune(scs_psd_handle h, const double* x, const int64_t* offsets, const in
   return SCS_PSD_OK;
 }
 
+// ---- complex Hermitian cones: through the real side-2n embedding ----
+int proj_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* offsets, const int32_t* sides,
+                   int32_t count, const scs_psd_opts* opts, void* stream) {
+  if (!h || count < 0) return SCS_PSD_EINVAL;
+  if (count == 0) return SCS_PSD_OK;
+  if (!offsets || !sides || offsets[0] != 0) return SCS_PSD_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (sides[i] < 0 || 2 * (int64_t)sides[i] > kMaxSide) return SCS_PSD_EINVAL;
+    if (offsets[i + 1] - offsets[i] != (int64_t)sides[i] * sides[i]) return SCS_PSD_EINVAL;
+  }
+  if (offsets[count] == 0) return SCS_PSD_OK;
+  if (!x || !y) return SCS_PSD_EINVAL;
+  HermPlan* hp = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(h->mu);
+    if (cudaSetDevice(h->device) != cudaSuccess) return SCS_PSD_ECUDA;
+    const std::string key = plan_key(sides, count, 0, 0, 0, 0);
+    auto it = h->herm.find(key);
+    if (it == h->herm.end()) {
+      auto np = std::make_unique<HermPlan>();
+      np->roff.assign(count + 1, 0);
+      np->rsides.resize(count);
+      std::vector<int64_t> meta(3 * (size_t)count);
+      for (int i = 0; i < count; ++i) {
+        const int64_t n = sides[i];
+        np->rsides[i] = (int32_t)(2 * n);
+        np->roff[i + 1] = np->roff[i] + svec_len(2 * n);
+        np->maxn = std::max(np->maxn, n);
+        meta[3 * i] = n;
+        meta[3 * i + 1] = offsets[i];
+        meta[3 * i + 2] = np->roff[i];
+      }
+      if (cudaMalloc(&np->meta_d, sizeof(int64_t) * meta.size()) != cudaSuccess ||
+          cudaMalloc(&np->buf, sizeof(double) * (size_t)std::max<int64_t>(1, np->roff[count])) != cudaSuccess)
+        return SCS_PSD_ENOMEM;
+      if (cudaMemcpy(np->meta_d, meta.data(), sizeof(int64_t) * meta.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SCS_PSD_ECUDA;
+      hp = np.get();
+      h->herm[key] = std::move(np);
+    } else {
+      hp = it->second.get();
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_herm_embed(hp->meta_d, count, hp->maxn, x, hp->buf, s);
+  if (cudaGetLastError() != cudaSuccess) return SCS_PSD_ECUDA;
+  const IoSlot io{hp->buf, hp->buf, nullptr, nullptr, nullptr, nullptr};
+  const int rc = do_call(h, io, MODE_Y, hp->roff.data(), hp->rsides.data(), count, opts, stream);
+  if (rc) return rc;
+  launch_herm_extract(hp->meta_d, count, hp->maxn, hp->buf, y, s);
+  if (cudaGetLastError() != cudaSuccess) return SCS_PSD_ECUDA;
+  h->last_launches += 2;
+  return SCS_PSD_OK;
+}
+
 // ---- static-scratch entry point: no device allocation at all ----
 // Callers that cannot allocate device memory (inside a memory pool that owns
 // the GPU, in an embedding that forbids cudaMalloc after start-up) get the
@@ -1373,6 +1443,7 @@ int scs_psd_destroy(scs_psd_handle h) {
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
   h->plans.clear();
+  h->herm.clear();
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -1422,6 +1493,11 @@ int scs_psd_reserve(scs_psd_handle h, int64_t max_n, int32_t max_count, const sc
   (void)opts;
   if (!h || max_n < 0 || max_n > kMaxSide || max_count < 0) return SCS_PSD_EINVAL;
   return SCS_PSD_OK;
+}
+
+int scs_psd_proj_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* offsets,
+                           const int32_t* sides, int32_t count, const scs_psd_opts* opts, void* stream) {
+  return proj_hermitian(h, x, y, offsets, sides, count, opts, stream);
 }
 
 int scs_psd_autotune(scs_psd_handle h, const double* x, const int64_t* offsets, const int32_t* sides, int32_t count,

@@ -207,6 +207,9 @@ void launch_bt1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, 
 int bt1_max_side();
 // y = svec(S) or x - svec(S) from the lower triangle of S = Z diag(l) Z^T held in QA (split mode)
 void launch_pack_recon(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s);
+// complex Hermitian cones <-> real symmetric embeddings of side 2n (meta: n, Hermitian offset, real offset)
+void launch_herm_embed(const int64_t* meta, int count, int64_t maxn, const double* hs, double* ms, cudaStream_t s);
+void launch_herm_extract(const int64_t* meta, int count, int64_t maxn, const double* ms, double* hs, cudaStream_t s);
 void launch_status_reduce(const int* status, int count, int* out, cudaStream_t s);
 
 }  // namespace scs

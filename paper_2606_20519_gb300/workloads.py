@@ -254,3 +254,18 @@ def to_hsvec(X: np.ndarray) -> np.ndarray:
         out[k + 1:k + 2 * m:2] = r2 * col.imag
         k += 2 * m
     return out
+
+
+def herm_admm_sequence(seed: int = SEED_BASE + 6, n: int = 625, steps: int = 50, step_scale: float = 1e-3):
+    """The ADMM-like sequence for a complex Hermitian cone (the paper's cones
+    are complex): X_0 = U diag(lam0) U^H with the clustered spectrum of the
+    real sequence and Haar U, X_{k+1} = X_k + 1e-3 (G + G^H)/2.
+    Returns (list of Hermitian svecs, U, lam0)."""
+    rng = rng_for(seed)
+    lam = spectrum_admm(rng, n)
+    X, U, lam = herm_from_spectrum(rng, lam)
+    out = [to_hsvec(X)]
+    for _ in range(steps - 1):
+        X = X + step_scale * herm_gaussian(rng, n)
+        out.append(to_hsvec(X))
+    return out, U, lam
