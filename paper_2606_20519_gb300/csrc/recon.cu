@@ -17,8 +17,9 @@ namespace scs {
 
 namespace {
 
-constexpr int BM = 64, BK = 16;
+constexpr int BK = 16;
 
+template <int BM>
 __global__ void __launch_bounds__(256) recon_kernel(const ConeDev* __restrict__ cones, const IoSlot* __restrict__ io) {
   const double* x = io->x;
   double* y = io->y;
@@ -41,11 +42,12 @@ __global__ void __launch_bounds__(256) recon_kernel(const ConeDev* __restrict__ 
   const double* Z = c.Z;
   const double* lam = c.lamk;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
+  constexpr int R = BM / 16;  // rows (and columns) per thread
+  double acc[R][R];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < R; ++r)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[r][q] = 0.0;
+    for (int q = 0; q < R; ++q) acc[r][q] = 0.0;
   for (int k0 = 0; k0 < kk; k0 += BK) {
 #pragma unroll
     for (int q = 0; q < (BM * BK) / 256; ++q) {
@@ -67,27 +69,27 @@ __global__ void __launch_bounds__(256) recon_kernel(const ConeDev* __restrict__ 
     __syncthreads();
 #pragma unroll
     for (int l = 0; l < BK; ++l) {
-      double a[4], bv[4];
+      double a[R], bv[R];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[l][tx + 16 * r];
+      for (int r = 0; r < R; ++r) a[r] = As[l][tx + 16 * r];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) bv[q] = Bs[l][ty + 16 * q];
+      for (int q = 0; q < R; ++q) bv[q] = Bs[l][ty + 16 * q];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], bv[q], acc[r][q]);
+        for (int q = 0; q < R; ++q) acc[r][q] = fma(a[r], bv[q], acc[r][q]);
     }
     __syncthreads();
   }
   const double* xs = x + c.xoff;
   double* ys = y + c.xoff;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < R; ++q) {
     const int j = j0 + ty + 16 * q;
     if (j >= n) continue;
     const int64_t colo = (int64_t)j * n - ((int64_t)j * (j - 1)) / 2;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < R; ++r) {
       const int i = i0 + tx + 16 * r;
       if (i >= n || i < j) continue;
       const int64_t idx = colo + (i - j);
@@ -140,8 +142,17 @@ void launch_pack_recon(const ConeDev* cones, int ncones, int64_t maxn, const IoS
 
 void launch_recon(const ConeDev* cones, int ncones, int maxn, const IoSlot* io, cudaStream_t s) {
   if (ncones <= 0) return;
-  const int tiles = (maxn + BM - 1) / BM;
-  recon_kernel<<<dim3(tiles * (tiles + 1) / 2, ncones), 256, 0, s>>>(cones, io);
+  // 64-row tiles, or 32-row tiles when those would leave most SMs idle
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int t64 = (maxn + 63) / 64;
+  if ((int64_t)t64 * (t64 + 1) / 2 * ncones < sms) {
+    const int t32 = (maxn + 31) / 32;
+    recon_kernel<32><<<dim3(t32 * (t32 + 1) / 2, ncones), 256, 0, s>>>(cones, io);
+  } else {
+    recon_kernel<64><<<dim3(t64 * (t64 + 1) / 2, ncones), 256, 0, s>>>(cones, io);
+  }
 }
 
 }  // namespace scs
