@@ -31,6 +31,7 @@ namespace scs {
 namespace {
 
 constexpr int kDcThreads = 256;
+constexpr int kQinCols = 4;  // columns per CTA of dc_build_qin
 constexpr double kEps = 1.1102230246251565e-16;  // 2^-53
 
 __device__ __forceinline__ long long dkey(double x) {
@@ -288,7 +289,8 @@ __global__ void __launch_bounds__(kDcThreads) dc_prepare_kernel(const ConeDev* _
 
 // Permuted eigenvector block Qin(:, fp[j]) = Q(:, perm[j]) of each merge node;
 // the source is block diagonal (child 1 rows x child 1 columns, child 2 rows x
-// child 2 columns).  blockIdx.x = node, blockIdx.y = chunk of 32 columns.
+// child 2 columns).  blockIdx.x = node, blockIdx.y = chunk of kQinCols columns
+// (few columns per CTA: the copy is bound by load latency, not bandwidth).
 __global__ void dc_build_qin_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes) {
   const MergeNode nd = nodes[blockIdx.x];
   if (nd.n2 == 0) return;
@@ -296,11 +298,11 @@ __global__ void dc_build_qin_kernel(const ConeDev* __restrict__ cones, const Mer
   if (*c.status != 0) return;
   const int64_t n = c.n;
   const int s = nd.s, n1 = nd.n1, K = nd.n1 + nd.n2;
-  const int j0 = blockIdx.y * 32;
+  const int j0 = blockIdx.y * kQinCols;
   if (j0 >= K) return;
   const double* Qi = qin_buf(c, nd.level);
   double* Qb = c.Qin;
-  const int jend = min(K, j0 + 32);
+  const int jend = min(K, j0 + kQinCols);
   for (int j = j0; j < jend; ++j) {
     const int src = c.iperm[s + j];
     const int dst = c.ifp[s + j];
@@ -726,7 +728,7 @@ __global__ void dc_vecnorm_kernel(const ConeDev* __restrict__ cones, const Merge
 
 // U(row, j) = zhat_j / (d_j - lambda_i) / ||.||; thread = root (consecutive
 // threads write consecutive rows), blockIdx.y = chunk of components j.
-constexpr int kVecChunk = 64;
+constexpr int kVecChunk = 16;
 __global__ void dc_vectors_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes,
                                   const int* __restrict__ pos_node, int64_t total) {
   const int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -824,7 +826,7 @@ void launch_dc_vecnorm(const ConeDev* cones, const MergeNode* nodes, const int* 
 
 void launch_dc_build_qin(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s) {
   if (nnodes <= 0) return;
-  dc_build_qin_kernel<<<dim3(nnodes, (maxK + 31) / 32), 256, 0, s>>>(cones, nodes);
+  dc_build_qin_kernel<<<dim3(nnodes, (maxK + kQinCols - 1) / kQinCols), 256, 0, s>>>(cones, nodes);
 }
 
 void launch_dc_apply_rot(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total,
