@@ -57,8 +57,11 @@ constexpr int kBarLanes = 8, kBarStride = 32;
 __device__ bool group_barrier8(int* counters, int rank, int G, int step, long long limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(counters + kBarStride * (rank % kBarLanes), 1);
+    // release-ordered arrival without waiting for a reply (the CTA's writes,
+    // ordered before this by the CTA barrier, become visible first)
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(counters + kBarStride * (rank % kBarLanes)),
+                 "r"(1)
+                 : "memory");
   }
   int ok = 1;
   const int t = threadIdx.x;
