@@ -24,8 +24,9 @@
  *    of the handle's GPU, and owned by the caller.
  *  - Shape arrays (offsets, sides) are HOST arrays owned by the caller; they
  *    are read during the call only (the library plans launches from them).
- *  - The library owns its workspace (device memory sized on first use or by
- *    scs_psd_reserve) and keeps it until scs_psd_destroy.
+ *  - The library owns its workspace (device memory allocated per shape list
+ *    on first use, or ahead of it by scs_psd_reserve) and keeps it until
+ *    scs_psd_destroy (or until more than 16 shape lists are in use).
  *  - Work is enqueued on `stream` and is asynchronous; host-detectable errors
  *    (bad sizes, null pointers) are returned at once and nothing is enqueued.
  *    Errors found on the device (non-finite input, non-convergence, a bounded
@@ -195,8 +196,11 @@ int scs_psd_autotune(scs_psd_handle h, const double* x, const int64_t* offsets, 
 /* The launch shapes of the last call, as scs_psd_autotune's `chosen`. */
 int scs_psd_last_tuning(scs_psd_handle h, int32_t* out);
 
-/* Optional pre-sizing of the workspace for cones up to side max_n and
- * max_count cones of that side. */
+/* Optional set-up ahead of the first call: builds and caches the plan (the
+ * workspace and launch metadata) of the projection of max_count cones of
+ * side max_n with these options, so that a later scs_psd_proj_batched (or,
+ * for max_count 1, scs_psd_proj) with exactly these shapes and options
+ * allocates nothing.  Other shape lists are planned on their first call. */
 int scs_psd_reserve(scs_psd_handle h, int64_t max_n, int32_t max_count, const scs_psd_opts* opts);
 
 /* Synchronise the handle's last stream and return the device status of the

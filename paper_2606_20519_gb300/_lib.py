@@ -306,6 +306,12 @@ def last_tuning(device: int = 0) -> dict:
     return dict(zip(TUNING_FIELDS, [int(v) for v in out]))
 
 
+def reserve(max_n: int, max_count: int = 1, opts: Opts | None = None, device: int = 0) -> None:
+    """Build the plan of max_count cones of side max_n ahead of the first call (C-ABI scs_psd_reserve)."""
+    _check(load().scs_psd_reserve(handle(device), int(max_n), int(max_count),
+                                  ctypes.byref(opts) if opts is not None else None), "scs_psd_reserve")
+
+
 def status(device: int = 0) -> int:
     """Synchronise and return the device status of the work since the last query."""
     v = ctypes.c_int32(0)

@@ -1490,9 +1490,27 @@ int scs_psd_vjp_stored(scs_psd_handle h, const double* V, const double* lam, con
 }
 
 int scs_psd_reserve(scs_psd_handle h, int64_t max_n, int32_t max_count, const scs_psd_opts* opts) {
-  (void)opts;
   if (!h || max_n < 0 || max_n > kMaxSide || max_count < 0) return SCS_PSD_EINVAL;
-  return SCS_PSD_OK;
+  if (max_n == 0 || max_count == 0) return SCS_PSD_OK;
+  int side = 0, precision = SCS_PSD_FP64;
+  Tuning tune;
+  if (opts) {
+    if (opts->precision != SCS_PSD_FP64 && opts->precision != SCS_PSD_SPLIT_TF32) return SCS_PSD_EINVAL;
+    if (opts->band < 0 || opts->band > kMaxBand || opts->side < 0 || opts->side > 2) return SCS_PSD_EINVAL;
+    precision = opts->precision;
+    side = opts->side;
+    tune.band = opts->band;
+  }
+  const std::vector<int32_t> sides((size_t)max_count, (int32_t)max_n);
+  std::lock_guard<std::mutex> lock(h->mu);
+  if (cudaSetDevice(h->device) != cudaSuccess) return SCS_PSD_ECUDA;
+  if (!(opts && opts->band)) {
+    auto t = h->tuned.find(tune_key(sides.data(), max_count, precision));
+    if (t != h->tuned.end()) tune = t->second;
+  }
+  // the projection's plan (the derivative's is built on its first call)
+  Plan* P = nullptr;
+  return get_plan(h, sides.data(), max_count, 0, side, precision, tune, &P);
 }
 
 int scs_psd_proj_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* offsets,

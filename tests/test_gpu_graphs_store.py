@@ -137,3 +137,22 @@ def test_autograd_store_and_recompute_identical(lib):
     assert np.array_equal(grads[0], grads[1])
     # a budget below the kept bytes forces recomputation
     assert not stores_eigenpairs(SIDES, lib.make_opts(mem_budget_bytes=64))
+
+
+def test_reserve_builds_the_plan_ahead(lib):
+    """After scs_psd_reserve, the first call with those shapes allocates no device memory."""
+    import torch
+    n, count = 210, 3
+    lib.reserve(n, count)
+    rng = W.rng_for(9800)
+    x = np.concatenate([W.to_svec(W.sym_gaussian(rng, n)) for _ in range(count)])
+    xt = dev(x)
+    y = torch.empty_like(xt)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    lib.proj_batched(xt, [n] * count, out=y)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 >= free0 - (1 << 20)  # no workspace allocated by the call
+    assert lib.status(0) == lib.OK
+    assert rel(y.cpu().numpy(), oracle.proj_batched(x, lib.shapes([n] * count)[0])) <= TOL

@@ -137,3 +137,23 @@ def test_autograd_wrapper(lib):
     np.testing.assert_allclose(y.detach().cpu().numpy(), oracle.proj_batched(x, offs), rtol=0, atol=1e-12)
     ref = oracle.jvp_batched(x, g, offs)
     assert rel(xt.grad.cpu().numpy(), ref) <= TOL
+
+
+@pytest.mark.parametrize("side", [1, 2])
+def test_vjp_both_routes(lib, side):
+    """The block-structured derivative takes the positive pairs (route 0) or
+    the non-positive ones (route 1) as its small side; both give DPi."""
+    import torch
+    n = 90
+    rng = W.rng_for(8900 + side)
+    # more positive than negative eigenvalues, so the automatic route would be 1;
+    # none near zero, where Pi is not differentiable
+    lam = np.concatenate([rng.uniform(0.01, 1, 60), rng.uniform(-1, -0.01, 30)])
+    X, Q, lam = W.from_spectrum(rng, lam)
+    x = W.to_svec(X)
+    g = rng.standard_normal(x.size)
+    y = torch.empty(x.size, dtype=torch.float64, device="cuda")
+    xb = lib.proj_vjp(dev(x), dev(g), [n], y=y, opts=lib.make_opts(side=side))
+    assert lib.status(0) == lib.OK
+    assert rel(xb.cpu().numpy(), oracle.jvp(x, g)) <= TOL
+    assert rel(y.cpu().numpy(), oracle.proj(x)) <= TOL
