@@ -10,19 +10,28 @@ t -> max(t, 0) of the eigenvalues.  The paper names the approach but prints
 no polynomial.  Reading taken here:
 
 * max(t, 0) = t (1 + sign t) / 2, so Pi(X) = (X + X sign(X)) / 2;
-* sign is approximated on the spectrum of X / ||X||_F (inside [-1, 1]) by the
-  scaled Newton-Schulz iteration with the closed-form scaling of Chen & Chow
-  (2014): on [l, 1] the odd cubic g(t) = (alpha t / 2)(3 - alpha^2 t^2) with
-  alpha^2 = 3 / (1 + l + l^2) takes its maximum 1 at t = 1/alpha and
-  g(l) = g(1), so it maps [l, 1] into [g(l), 1]; the next step uses
-  l <- g(l).  Starting from l_0 = lo, the composite f = g_{K-1} o ... o g_0
-  satisfies |f(t) - sign t| <= 1 - l_K for lo <= |t| <= 1 and
-  0 <= f(t) sign(t) <= 1 for all |t| <= 1;
+* sign is approximated on the spectrum of X / ||X||_F (inside [-1, 1]) by a
+  scaled Newton-Schulz iteration.  On [l, 1] the odd cubic
+  g(t) = (alpha t / 2)(3 - alpha^2 t^2), 1 <= alpha <= sqrt(3), rises to its
+  maximum 1 at t = 1/alpha and falls to g(1) beyond it, so it maps [l, 1]
+  into [min(g(l), g(1)), 1].  The minimax choice alpha^2 = 3 / (1 + l + l^2)
+  (Chen & Chow 2014; g(l) = g(1)) sends the top of the interval down to the
+  new lower bound, where the rounding of a low-precision product is
+  amplified by about 1 / l; the scaling is therefore capped so that
+  g(1) >= 1/2: alpha_k = min(sqrt(3 / (1 + l_k + l_k^2)), 2 cos(2 pi / 9)),
+  2 cos(2 pi / 9) being the root of alpha (3 - alpha^2) / 2 = 1/2 in
+  [1, sqrt(3)].  Either way g(l_k) <= g(1), so l_{k+1} = g_k(l_k).  Starting
+  from l_0 = lo, the composite f = g_{K-1} o ... o g_0 satisfies
+  |f(t) - sign t| <= 1 - l_K for lo <= |t| <= 1 and 0 <= f(t) sign(t) <= 1
+  for all |t| <= 1;
 * steps = 0 picks the smallest K with 1 - l_K <= 1e-15 (at most 200).
 
 In matrix form one step is S <- a_k S + b_k S (S S) with a_k = 3 alpha_k / 2
 and b_k = -alpha_k^3 / 2, from S_0 = X / ||X||_F (= X / ||x||_2 on svec,
-svec being an isometry, App. D.1); X = 0 gives 0.
+svec being an isometry, App. D.1); X = 0 gives 0.  S is a symmetric matrix
+function of X, and each step keeps it symmetric ((S + S^T) / 2 after the
+product): a non-symmetric rounding residue is not a function of X, and the
+iteration amplifies it.
 
 Pins: ``tests/test_oracle_poly.py`` (the scaling against a brute-force
 minimax search, the matrix form against the scalar composite applied to the
@@ -39,6 +48,7 @@ from . import smat, svec
 
 AUTO_TOL = 1e-15
 MAX_STEPS = 200
+ALPHA_CAP = 2.0 * math.cos(2.0 * math.pi / 9.0)  # alpha (3 - alpha^2) / 2 = 1/2
 
 # A planted mistake (tests only): 1 drops the 1 + l^2 term of the scaling,
 # 2 scales S_0 by ||X||_F^2, 3 flips the sign of X sign(X) in the output.
@@ -52,7 +62,7 @@ def set_mutation(m: int) -> None:
 
 
 def poly_schedule(lo: float, steps: int = 0):
-    """Scalings alpha_k and lower bounds l_0 .. l_K of the composite (Chen & Chow 2014)."""
+    """Scalings alpha_k and lower bounds l_0 .. l_K of the composite (capped Chen & Chow 2014)."""
     if not (0.0 < lo < 1.0):
         raise ValueError("lo must lie in (0, 1)")
     if steps < 0 or steps > MAX_STEPS:
@@ -64,7 +74,7 @@ def poly_schedule(lo: float, steps: int = 0):
             break
         if steps == 0 and (1.0 - l <= AUTO_TOL or len(alphas) == MAX_STEPS):
             break
-        alpha = math.sqrt(3.0 / (1.0 + l + (0.0 if _mutation == 1 else l * l)))
+        alpha = min(math.sqrt(3.0 / (1.0 + l + (0.0 if _mutation == 1 else l * l))), ALPHA_CAP)
         l = 0.5 * alpha * l * (3.0 - alpha * alpha * l * l)
         alphas.append(alpha)
         lows.append(l)
@@ -98,6 +108,7 @@ def proj_poly_dense(X: np.ndarray, lo: float, steps: int = 0) -> np.ndarray:
     S = X / (sigma * sigma if _mutation == 2 else sigma)
     for ak, bk in zip(a, b):
         S = ak * S + bk * (S @ (S @ S))
+        S = 0.5 * (S + S.T)
     return 0.5 * (X - X @ S) if _mutation == 3 else 0.5 * (X + X @ S)
 
 

@@ -28,9 +28,10 @@ def cubic(alpha, t):
 
 
 @pytest.mark.parametrize("l", [1e-6, 1e-3, 0.05, 0.3, 0.7, 0.99])
-def test_scaling_is_the_minimax_cubic(l):
+def test_scaling_is_the_capped_minimax_cubic(l):
     """alpha of each step minimises max |1 - g(t)| over [l, 1] among the odd
-    cubics (alpha t / 2)(3 - alpha^2 t^2): a grid search finds the same alpha."""
+    cubics (alpha t / 2)(3 - alpha^2 t^2) whose value at t = 1 is at least
+    1/2: a grid search over alpha finds the same alpha."""
     alphas, lows = P.poly_schedule(l, 1)
     alpha = alphas[0]
     t = np.concatenate([np.geomspace(l, 1.0, 4001), [1.0 / alpha]])
@@ -40,19 +41,26 @@ def test_scaling_is_the_minimax_cubic(l):
         return float(np.max(np.abs(1.0 - cubic(a, t))))
 
     grid = np.linspace(1.0, math.sqrt(3.0), 20001)
+    grid = grid[cubic(grid, 1.0) >= 0.5]
     best = grid[int(np.argmin([worst(a) for a in grid]))]
     assert abs(best - alpha) <= 2 * (grid[1] - grid[0]) + 1e-9
-    # equioscillation: g(l) = g(1), maximum 1 at 1/alpha, next bound = g(l)
-    assert abs(cubic(alpha, l) - cubic(alpha, 1.0)) <= 1e-15
+    # the maximum 1 sits at 1/alpha inside [l, 1], the next bound is g(l)
     assert abs(cubic(alpha, 1.0 / alpha) - 1.0) <= 1e-15
     assert lows[1] == pytest.approx(cubic(alpha, l), rel=1e-15)
+    assert cubic(alpha, l) <= cubic(alpha, 1.0) + 1e-15
+    if l >= 0.3:
+        # uncapped: equioscillation g(l) = g(1) (Chen & Chow)
+        assert abs(cubic(alpha, l) - cubic(alpha, 1.0)) <= 1e-15
+    else:
+        # capped: g(1) = 1/2 exactly
+        assert abs(cubic(alpha, 1.0) - 0.5) <= 1e-15
 
 
 def test_schedule_limits_and_steps():
     # l = 1 gives the plain Newton-Schulz step 3t/2 - t^3/2
     a, b, _ = P.poly_coeffs(1.0 - 1e-16, 1)
     assert a[0] == pytest.approx(1.5, abs=1e-15) and b[0] == pytest.approx(-0.5, abs=1e-15)
-    for lo, k in ((1e-3, 12), (1e-7, 22), (1e-9, 26)):
+    for lo, k in ((1e-3, 13), (1e-7, 24), (1e-9, 29)):
         alphas, lows = P.poly_schedule(lo)
         assert len(alphas) == k
         assert 1.0 - lows[-1] <= P.AUTO_TOL and 1.0 - lows[-2] > P.AUTO_TOL
