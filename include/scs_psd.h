@@ -137,6 +137,44 @@ int scs_psd_proj_vjp(scs_psd_handle h, const double* x, const double* g, double*
 int scs_psd_proj_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* offsets,
                            const int32_t* sides, int32_t count, const scs_psd_opts* opts, void* stream);
 
+/* Factorization-free APPROXIMATE projection (Conclusions, "Approximate
+ * semidefinite-cone projections": a composite matrix polynomial built from
+ * matrix-matrix products alone whose scalar map reproduces the thresholding
+ * of the eigenvalues).  The paper names the approach but prints no
+ * polynomial; this one is max(t, 0) = t (1 + sign t) / 2 with sign replaced
+ * by a scaled Newton-Schulz composite:
+ *     S_0 = X / ||X||_F,  S_{k+1} = a_k S_k + b_k S_k^3,  y = svec((X + S_K X) / 2),
+ * a_k = 3 alpha_k / 2, b_k = -alpha_k^3 / 2,
+ * alpha_k = min(sqrt(3 / (1 + l_k + l_k^2)), 2 cos(2 pi / 9)),
+ * l_0 = lo, l_{k+1} = (alpha_k l_k / 2)(3 - alpha_k^2 l_k^2): the minimax
+ * scaling of Chen & Chow (2014), capped where the cubic's value at 1 falls
+ * to 1/2 (the uncapped cubic maps the top of the interval onto its bottom,
+ * where the rounding of split-precision products is amplified).
+ * Per eigenvalue l of X (sigma = ||X||_F) the result carries
+ * l (1 + f(l / sigma)) / 2, f the composite, with |f(t) - sign t| <= 1 - l_K
+ * for |t| >= lo and 0 <= f(t) sign t <= 1 otherwise; so eigenvalues above
+ * lo * sigma in magnitude are thresholded to within a factor 1 - l_K, and
+ * each smaller one contributes an error of at most |l| / 2.
+ * lo in (0, 1); steps in [1, 200], or 0 for the smallest K with
+ * 1 - l_K <= 1e-15 (for example 24 steps at lo = 1e-7, 29 at 1e-9).
+ * Layout, host shape arrays, aliasing of y and x, graph replay and status
+ * as scs_psd_proj_batched.  opts->precision: SCS_PSD_FP64, or
+ * SCS_PSD_SPLIT_TF32 for the products of cones of side >= 64 on the
+ * split-TF32 tensor-core kernel (smaller cones stay FP64); opts->graphs as
+ * for the other calls; the remaining options are ignored.  ||x||_2^2 must
+ * be finite (else the cone is marked SCS_PSD_ENONFINITE and its output is
+ * NaN); x = 0 gives 0.  Per cone of side n the handle holds 4 n^2 doubles
+ * for the shape list.  Returns SCS_PSD_EINVAL for lo or steps out of range. */
+int scs_psd_proj_poly(scs_psd_handle h, const double* x, double* y, const int64_t* offsets,
+                      const int32_t* sides, int32_t count, double lo, int32_t steps,
+                      const scs_psd_opts* opts, void* stream);
+
+/* The composite's coefficients for (lo, steps) as scs_psd_proj_poly uses
+ * them: returns K (the number of steps) and, where the pointers are not
+ * NULL, writes a[0..K), b[0..K) and l_final = l_K; -SCS_PSD_EINVAL for lo or
+ * steps out of range.  Host only (no handle, no GPU). */
+int32_t scs_psd_poly_schedule(double lo, int32_t steps, double* a, double* b, double* l_final);
+
 /* Forward pass that keeps the eigendecomposition for a later VJP (the
  * "store" side of the store-or-recompute choice for the derivative of App. E):
  * y = Pi(x) as scs_psd_proj_batched (y may be NULL), and every eigenpair of

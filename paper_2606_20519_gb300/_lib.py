@@ -38,7 +38,8 @@ _handles = {}
 EXPORTS = ("scs_psd_create", "scs_psd_destroy", "scs_psd_proj", "scs_psd_proj_batched", "scs_psd_proj_vjp",
            "scs_psd_proj_store", "scs_psd_vjp_stored", "scs_psd_proj_static", "scs_psd_reserve", "scs_psd_status", "scs_psd_last_launch_count",
            "scs_psd_last_replayed", "scs_psd_strerror", "scs_psd_trace", "scs_psd_trace_read",
-           "scs_psd_autotune", "scs_psd_last_tuning", "scs_psd_proj_hermitian")
+           "scs_psd_autotune", "scs_psd_last_tuning", "scs_psd_proj_hermitian", "scs_psd_proj_poly",
+           "scs_psd_poly_schedule")
 NPHASES = 8
 PHASES = ("unpack", "dense_to_band", "band_to_tridiag", "tridiag_dc", "backtransform_2", "backtransform_1",
           "reconstruct", "derivative")
@@ -70,6 +71,9 @@ def load(path: str | None = None):
         lib.scs_psd_last_launch_count.argtypes = [vp]
         lib.scs_psd_last_launch_count.restype = i64
         lib.scs_psd_proj_hermitian.argtypes = [vp, vp, vp, vp, vp, i32, op, vp]
+        lib.scs_psd_proj_poly.argtypes = [vp, vp, vp, vp, vp, i32, ctypes.c_double, i32, op, vp]
+        lib.scs_psd_poly_schedule.argtypes = [ctypes.c_double, i32, vp, vp, ctypes.POINTER(ctypes.c_double)]
+        lib.scs_psd_poly_schedule.restype = i32
         lib.scs_psd_autotune.argtypes = [vp, vp, vp, vp, i32, op, vp, ctypes.POINTER(i32),
                                          ctypes.POINTER(ctypes.c_double)]
         lib.scs_psd_last_tuning.argtypes = [vp, ctypes.POINTER(i32)]
@@ -276,6 +280,39 @@ def proj_hermitian(x, sides, out=None, opts: Opts | None = None, offsets=None):
                                        sides.ctypes.data_as(ctypes.c_void_p), int(sides.size),
                                        ctypes.byref(opts) if opts is not None else None, _stream_ptr(x))
     _check(rc, "scs_psd_proj_hermitian")
+    return out
+
+
+def poly_schedule(lo: float, steps: int = 0):
+    """(a, b, l_final) of the composite scs_psd_proj_poly applies (C-ABI scs_psd_poly_schedule)."""
+    lib = load()
+    k = lib.scs_psd_poly_schedule(float(lo), int(steps), None, None, None)
+    if k < 0:
+        _check(-k, "scs_psd_poly_schedule")
+    a = np.zeros(k, dtype=np.float64)
+    b = np.zeros(k, dtype=np.float64)
+    lk = ctypes.c_double(0.0)
+    lib.scs_psd_poly_schedule(float(lo), int(steps), a.ctypes.data_as(ctypes.c_void_p),
+                              b.ctypes.data_as(ctypes.c_void_p), ctypes.byref(lk))
+    return a, b, lk.value
+
+
+def proj_poly(x, sides, lo: float, steps: int = 0, out=None, opts: Opts | None = None, offsets=None):
+    """Factorization-free approximate projection of packed svec cones (C-ABI scs_psd_proj_poly)."""
+    import torch
+    _check_tensor(x, "x")
+    if offsets is None:
+        offsets, sides = shapes(sides)
+    else:
+        offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        sides = np.ascontiguousarray(np.asarray(sides, dtype=np.int32))
+    if out is None:
+        out = torch.empty_like(x)
+    _check_tensor(out, "out")
+    rc = load().scs_psd_proj_poly(handle(x.device.index), _ptr(x), _ptr(out), offsets.ctypes.data_as(ctypes.c_void_p),
+                                  sides.ctypes.data_as(ctypes.c_void_p), int(sides.size), float(lo), int(steps),
+                                  ctypes.byref(opts) if opts is not None else None, _stream_ptr(x))
+    _check(rc, "scs_psd_proj_poly")
     return out
 
 

@@ -142,6 +142,36 @@ struct HermPlan {
   }
 };
 
+// Factorization-free approximate projection of a shape list: the composite's
+// coefficients, the per-cone buffers (X, two iterates, S^2 / Y) and the
+// grouped GEMMs of every step, in launch order.
+struct PolyPlan {
+  int precision = SCS_PSD_FP64;
+  int steps = 0;
+  int ncones = 0, nparts = 0;
+  int64_t maxn = 0;
+  void* work = nullptr;
+  void* meta = nullptr;
+  PolyConeDev* cones_d = nullptr;
+  int* ints_d = nullptr;  // tile prefixes, partial-sum owners, status
+  GemmDesc* descs_d = nullptr;
+  int* part_cone_d = nullptr;
+  int* status_d = nullptr;
+  double* part_d = nullptr;
+  double* inv_d = nullptr;
+  IoSlot* io_d = nullptr;
+  std::vector<GemmLaunch> gemms;
+  std::vector<int> mirror_after;  // after gemms[0 .. m) the new iterates are mirrored (even steps: into S1)
+  int64_t eager_runs = 0, launches = 0, glaunches = 0;
+  cudaGraphExec_t gexec = nullptr;
+  bool gfailed = false;
+  ~PolyPlan() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (work) cudaFree(work);
+    if (meta) cudaFree(meta);
+  }
+};
+
 }  // namespace
 
 struct scs_psd_handle_s {
@@ -162,6 +192,7 @@ struct scs_psd_handle_s {
   std::map<std::string, std::unique_ptr<Plan>> plans;
   std::map<std::string, Tuning> tuned;  // autotuner's choices by shapes and precision
   std::map<std::string, std::unique_ptr<HermPlan>> herm;  // Hermitian shape lists
+  std::map<std::string, std::unique_ptr<PolyPlan>> poly;  // polynomial projections by shapes and schedule
   Tuning last_tune;
   std::mutex mu;
 };
@@ -834,18 +865,23 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
     if (_e != cudaSuccess) return SCS_PSD_ECUDA;            \
   } while (0)
 
-int run_gemm(const Plan& P, const GemmLaunch& g, cudaStream_t s, int64_t& n_launch) {
+int run_gemm_at(const GemmDesc* descs_d, const int* ints_d, const GemmLaunch& g, cudaStream_t s,
+                int64_t& n_launch) {
   if (g.count <= 0 || g.tiles <= 0) return SCS_PSD_OK;
   if (g.tc) {
-    launch_tc_gemm(P.descs_d + g.desc_off, P.ints_d + g.prefix_off, g.count, g.tiles, g.variant, s);
-    if (g.needs_reduce) launch_gemm_reduce(P.descs_d + g.desc_off, g.count, g.max_mn, s);
+    launch_tc_gemm(descs_d + g.desc_off, ints_d + g.prefix_off, g.count, g.tiles, g.variant, s);
+    if (g.needs_reduce) launch_gemm_reduce(descs_d + g.desc_off, g.count, g.max_mn, s);
   } else {
-    launch_gemm(P.descs_d + g.desc_off, P.ints_d + g.prefix_off, g.count, g.tiles, g.variant, g.needs_reduce,
+    launch_gemm(descs_d + g.desc_off, ints_d + g.prefix_off, g.count, g.tiles, g.variant, g.needs_reduce,
                 g.max_mn, s);
   }
   if (g.needs_reduce) ++n_launch;
   LAUNCH_CHECK();
   return SCS_PSD_OK;
+}
+
+int run_gemm(const Plan& P, const GemmLaunch& g, cudaStream_t s, int64_t& n_launch) {
+  return run_gemm_at(P.descs_d, P.ints_d, g, s, n_launch);
 }
 
 // Phase timing: an event pair per phase interval when tracing is on.
@@ -1349,6 +1385,259 @@ int proj_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* 
   return SCS_PSD_OK;
 }
 
+// ---- factorization-free approximate projection (Conclusions) ----
+// Scaled Newton-Schulz schedule: on [l, 1] the odd cubic
+// g(t) = (alpha t / 2)(3 - alpha^2 t^2) peaks at 1 (t = 1/alpha) and maps
+// [l, 1] into [g(l), 1] as long as g(l) <= g(1).  alpha is the minimax
+// choice alpha^2 = 3 / (1 + l + l^2) of Chen & Chow (2014), where g(l) = g(1),
+// capped at 2 cos(2 pi / 9), where g(1) = 1/2: the uncapped cubic sends the
+// top of the interval down to the new lower bound, and the rounding of a
+// split-precision product there is amplified by about 1 / l.
+// steps = 0: the smallest K with 1 - l_K <= 1e-15.
+constexpr int kPolyMaxSteps = 200;
+constexpr double kPolyAutoTol = 1e-15;
+
+int poly_schedule(double lo, int steps, std::vector<double>* a, std::vector<double>* b, double* lk) {
+  if (!(lo > 0.0 && lo < 1.0) || steps < 0 || steps > kPolyMaxSteps) return -1;
+  double l = lo;
+  int k = 0;
+  for (;;) {
+    if (steps > 0 && k == steps) break;
+    if (steps == 0 && (1.0 - l <= kPolyAutoTol || k == kPolyMaxSteps)) break;
+    const double al = std::min(std::sqrt(3.0 / (1.0 + l + l * l)), 2.0 * std::cos(2.0 * M_PI / 9.0));
+    if (a) a->push_back(1.5 * al);
+    if (b) b->push_back(-0.5 * al * al * al);
+    l = 0.5 * al * l * (3.0 - al * al * l * l);
+    ++k;
+  }
+  if (lk) *lk = l;
+  return k;
+}
+
+// Per cone (side n >= 1) four n x n buffers: X, the even iterates (from S_0),
+// the odd iterates, and S^2 (its lower triangle), which the last product
+// overwrites with Y.  One step is T = S S (lower triangle), S' = b T S + a S
+// (lower triangle; T read as symmetric, a S added from the B operand), then
+// S' mirrored into its upper triangle, so every iterate is exactly
+// symmetric (a non-symmetric rounding residue is not a function of X, and
+// the iteration amplifies it); the end is Y = S_K X / 2 + X / 2 (lower
+// triangle).  In split-TF32 mode the cones of side >= 64 run on the
+// tensor-core kernel, smaller ones in FP64.
+int build_poly(scs_psd_handle h, PolyPlan& P, const int64_t* offsets, const int32_t* sides, int32_t count,
+               int precision, double lo, int steps) {
+  std::vector<double> ca, cb;
+  const int K = poly_schedule(lo, steps, &ca, &cb, nullptr);
+  if (K < 0) return SCS_PSD_EINVAL;
+  P.precision = precision;
+  P.steps = K;
+  std::vector<PolyConeDev> cones;
+  std::vector<int64_t> woff;
+  int64_t work = 0;
+  for (int i = 0; i < count; ++i) {
+    const int64_t n = sides[i];
+    if (n < 1) continue;
+    PolyConeDev d{};
+    d.n = n;
+    d.xoff = offsets[i];
+    d.part0 = P.nparts;
+    d.nparts = (int)((svec_len(n) + kPolyChunk - 1) / kPolyChunk);
+    P.nparts += d.nparts;
+    P.maxn = std::max(P.maxn, n);
+    woff.push_back(work);
+    work += 4 * (int64_t)align_up((size_t)(n * n), 32);
+    cones.push_back(d);
+  }
+  P.ncones = (int)cones.size();
+  if (!P.ncones) return SCS_PSD_OK;
+  if (cudaMalloc(&P.work, sizeof(double) * (size_t)work) != cudaSuccess) return SCS_PSD_ENOMEM;
+  double* wbase = (double*)P.work;
+  std::vector<double*> S1(P.ncones), T(P.ncones);
+  for (int c = 0; c < P.ncones; ++c) {
+    const int64_t stride = (int64_t)align_up((size_t)(cones[c].n * cones[c].n), 32);
+    cones[c].X = wbase + woff[c];
+    cones[c].S0 = cones[c].X + stride;
+    S1[c] = cones[c].S0 + stride;
+    cones[c].S1 = S1[c];
+    T[c] = S1[c] + stride;
+    cones[c].Y = T[c];
+  }
+  MetaBuilder mb;
+  mb.sms = h->sms;
+  mb.split = precision == SCS_PSD_SPLIT_TF32;
+  // the status word of cone c is encoded as (offset + 1) and patched after upload
+  std::vector<int> part_cone(P.nparts);
+  for (int c = 0; c < P.ncones; ++c)
+    for (int q = 0; q < cones[c].nparts; ++q) part_cone[cones[c].part0 + q] = c;
+  auto skip_of = [](int c) { return (const int*)(intptr_t)(c + 1); };
+  auto group = [&](int big, auto make) {
+    std::vector<GemmDesc> g;
+    for (int c = 0; c < P.ncones; ++c)
+      if ((cones[c].n >= 64) == (big != 0)) g.push_back(make(c));
+    if (!g.empty()) P.gemms.push_back(mb.add_gemm(g));
+  };
+  for (int k = 0; k <= K; ++k) {
+    for (int big = 1; big >= 0; --big) {
+      if (k < K) {
+        group(big, [&](int c) {
+          const int n = (int)cones[c].n;
+          double* Sin = (k % 2 == 0) ? cones[c].S0 : S1[c];
+          return mk(Sin, n, Sin, n, T[c], n, n, n, n, 1.0, 0.0, GF_LOWER_C, skip_of(c));
+        });
+      }
+    }
+    for (int big = 1; big >= 0; --big) {
+      group(big, [&](int c) {
+        const int n = (int)cones[c].n;
+        double* Sin = (k % 2 == 0) ? cones[c].S0 : S1[c];
+        if (k == K) return mk(Sin, n, cones[c].X, n, T[c], n, n, n, n, 0.5, 0.5, GF_LOWER_C | GF_BETA_B, skip_of(c));
+        double* Sout = (k % 2 == 0) ? S1[c] : cones[c].S0;
+        return mk(T[c], n, Sin, n, Sout, n, n, n, n, cb[k], ca[k], GF_SYM_A | GF_BETA_B | GF_LOWER_C, skip_of(c));
+      });
+    }
+    if (k < K) P.mirror_after.push_back((int)P.gemms.size());
+  }
+  // metadata: cones | ints (tile prefixes, partial-sum owners, status) | descriptors | partial sums | 1/sigma |
+  // split-K scratch | io slot
+  const int prefix_n = (int)mb.ints.size();
+  std::vector<int> ints = mb.ints;
+  const int part_cone_off = (int)ints.size();
+  ints.insert(ints.end(), part_cone.begin(), part_cone.end());
+  const int status_off = (int)ints.size();
+  ints.resize(ints.size() + P.ncones, 0);
+  (void)prefix_n;
+  const size_t cones_b = align_up(sizeof(PolyConeDev) * P.ncones);
+  const size_t ints_b = align_up(sizeof(int) * ints.size());
+  const size_t descs_b = align_up(sizeof(GemmDesc) * std::max<size_t>(1, mb.descs.size()));
+  const size_t part_b = align_up(sizeof(double) * P.nparts);
+  const size_t inv_b = align_up(sizeof(double) * P.ncones);
+  const size_t scratch_b = align_up(sizeof(double) * std::max<int64_t>(1, mb.scratch_doubles));
+  const size_t io_b = align_up(sizeof(IoSlot));
+  if (cudaMalloc(&P.meta, cones_b + ints_b + descs_b + part_b + inv_b + scratch_b + io_b) != cudaSuccess)
+    return SCS_PSD_ENOMEM;
+  char* m = (char*)P.meta;
+  P.cones_d = (PolyConeDev*)m;
+  P.ints_d = (int*)(m + cones_b);
+  P.descs_d = (GemmDesc*)(m + cones_b + ints_b);
+  P.part_d = (double*)(m + cones_b + ints_b + descs_b);
+  P.inv_d = (double*)(m + cones_b + ints_b + descs_b + part_b);
+  double* scratch = (double*)(m + cones_b + ints_b + descs_b + part_b + inv_b);
+  P.io_d = (IoSlot*)(m + cones_b + ints_b + descs_b + part_b + inv_b + scratch_b);
+  P.part_cone_d = P.ints_d + part_cone_off;
+  P.status_d = P.ints_d + status_off;
+  for (int c = 0; c < P.ncones; ++c) cones[c].status = P.status_d + c;
+  for (size_t q = 0; q < mb.descs.size(); ++q) {
+    GemmDesc& g = mb.descs[q];
+    g.partial = mb.part_off[q] >= 0 ? scratch + mb.part_off[q] : nullptr;
+    if (g.skip) g.skip = P.status_d + ((intptr_t)g.skip - 1);
+  }
+  if (cudaMemcpy(P.cones_d, cones.data(), sizeof(PolyConeDev) * P.ncones, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(P.ints_d, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(P.descs_d, mb.descs.data(), sizeof(GemmDesc) * mb.descs.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return SCS_PSD_ECUDA;
+  return SCS_PSD_OK;
+}
+
+int run_poly_body(scs_psd_handle h, PolyPlan& P, cudaStream_t s, int64_t& n_launch) {
+  CUDA_TRY(cudaMemsetAsync(P.status_d, 0, sizeof(int) * P.ncones, s));
+  launch_poly_prepare(P.cones_d, P.ncones, P.part_cone_d, P.nparts, P.maxn, P.io_d, P.part_d, P.inv_d, s);
+  n_launch += 2;
+  LAUNCH_CHECK();
+  int rc;
+  size_t mi = 0;
+  for (size_t q = 0; q < P.gemms.size(); ++q) {
+    if ((rc = run_gemm_at(P.descs_d, P.ints_d, P.gemms[q], s, n_launch))) return rc;
+    if (mi < P.mirror_after.size() && (size_t)P.mirror_after[mi] == q + 1) {
+      launch_poly_mirror(P.cones_d, P.ncones, P.maxn, (int)(mi % 2), s);  // step mi wrote S1 if mi is even
+      LAUNCH_CHECK();
+      ++mi;
+    }
+  }
+  launch_poly_pack(P.cones_d, P.ncones, P.maxn, P.io_d, s);
+  LAUNCH_CHECK();
+  launch_status_reduce(P.status_d, P.ncones, h->status_word, s);
+  LAUNCH_CHECK();
+  return SCS_PSD_OK;
+}
+
+int proj_poly(scs_psd_handle h, const double* x, double* y, const int64_t* offsets, const int32_t* sides,
+              int32_t count, double lo, int32_t steps, const scs_psd_opts* opts, void* stream) {
+  if (!h) return SCS_PSD_EINVAL;
+  int rc = check_shapes(offsets, sides, count);
+  if (rc) return rc;
+  if (poly_schedule(lo, steps, nullptr, nullptr, nullptr) < 0) return SCS_PSD_EINVAL;
+  if (count == 0 || offsets[count] == 0) return SCS_PSD_OK;
+  if (!x || !y) return SCS_PSD_EINVAL;
+  int precision = SCS_PSD_FP64;
+  bool graphs = true;
+  if (opts) {
+    if (opts->precision != SCS_PSD_FP64 && opts->precision != SCS_PSD_SPLIT_TF32) return SCS_PSD_EINVAL;
+    if (opts->graphs < 0 || opts->graphs > 1 || opts->reserved != 0) return SCS_PSD_EINVAL;
+    precision = opts->precision;
+    graphs = opts->graphs == 0;
+  }
+  std::lock_guard<std::mutex> lock(h->mu);
+  if (cudaSetDevice(h->device) != cudaSuccess) return SCS_PSD_ECUDA;
+  char hdr[96];
+  snprintf(hdr, sizeof(hdr), "p%d,l%.17g,k%d:", precision, lo, steps);
+  const std::string key = std::string(hdr) + plan_key(sides, count, 0, 0, 0, 0);
+  PolyPlan* P = nullptr;
+  auto it = h->poly.find(key);
+  if (it != h->poly.end()) {
+    P = it->second.get();
+  } else {
+    if (h->poly.size() >= 8) {
+      cudaDeviceSynchronize();
+      h->poly.clear();
+    }
+    auto np = std::make_unique<PolyPlan>();
+    if ((rc = build_poly(h, *np, offsets, sides, count, precision, lo, steps))) return rc;
+    P = np.get();
+    h->poly[key] = std::move(np);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  if (!P->ncones) return SCS_PSD_OK;
+  int64_t n_launch = 0;
+  launch_set_io(P->io_d, IoSlot{x, y, nullptr, nullptr, nullptr, nullptr}, s);
+  LAUNCH_CHECK();
+  h->last_replayed = false;
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  if (graphs && !P->gfailed && P->eager_runs > 0 && cudaStreamIsCapturing(s, &cst) == cudaSuccess &&
+      cst == cudaStreamCaptureStatusNone) {
+    if (!P->gexec) {
+      if (!h->capture_stream && cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+        h->capture_stream = nullptr;
+      cudaGraph_t graph = nullptr;
+      int64_t nl = 0;
+      if (h->capture_stream &&
+          cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        const int brc = run_poly_body(h, *P, h->capture_stream, nl);
+        const cudaError_t e = cudaStreamEndCapture(h->capture_stream, &graph);
+        if (brc == SCS_PSD_OK && e == cudaSuccess && graph &&
+            cudaGraphInstantiate(&P->gexec, graph, 0) == cudaSuccess)
+          P->glaunches = nl;
+        else
+          P->gexec = nullptr;
+        if (graph) cudaGraphDestroy(graph);
+      }
+      if (!P->gexec) P->gfailed = true;
+      cudaGetLastError();
+    }
+    if (P->gexec) {
+      CUDA_TRY(cudaGraphLaunch(P->gexec, s));
+      h->last_launches = n_launch + P->glaunches;
+      h->last_replayed = true;
+      return SCS_PSD_OK;
+    }
+  }
+  cudaGetLastError();
+  if ((rc = run_poly_body(h, *P, s, n_launch))) return rc;
+  ++P->eager_runs;
+  h->last_launches = n_launch;
+  return SCS_PSD_OK;
+}
+
 // ---- static-scratch entry point: no device allocation at all ----
 // Callers that cannot allocate device memory (inside a memory pool that owns
 // the GPU, in an embedding that forbids cudaMalloc after start-up) get the
@@ -1516,6 +1805,20 @@ int scs_psd_reserve(scs_psd_handle h, int64_t max_n, int32_t max_count, const sc
 int scs_psd_proj_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* offsets,
                            const int32_t* sides, int32_t count, const scs_psd_opts* opts, void* stream) {
   return proj_hermitian(h, x, y, offsets, sides, count, opts, stream);
+}
+
+int scs_psd_proj_poly(scs_psd_handle h, const double* x, double* y, const int64_t* offsets, const int32_t* sides,
+                      int32_t count, double lo, int32_t steps, const scs_psd_opts* opts, void* stream) {
+  return proj_poly(h, x, y, offsets, sides, count, lo, steps, opts, stream);
+}
+
+int32_t scs_psd_poly_schedule(double lo, int32_t steps, double* a, double* b, double* l_final) {
+  std::vector<double> ca, cb;
+  const int k = poly_schedule(lo, steps, &ca, &cb, l_final);
+  if (k < 0) return -SCS_PSD_EINVAL;
+  if (a) std::copy(ca.begin(), ca.end(), a);
+  if (b) std::copy(cb.begin(), cb.end(), b);
+  return k;
 }
 
 int scs_psd_autotune(scs_psd_handle h, const double* x, const int64_t* offsets, const int32_t* sides, int32_t count,

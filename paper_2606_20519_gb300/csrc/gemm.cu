@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restric
       if (lowc && i < j) continue;
       double* cp = (flags & GF_TRANS_C) ? C + (int64_t)jc + (int64_t)i * ldc : C + (int64_t)i + (int64_t)jc * ldc;
       double v = alpha * acc[r][c];
-      if (beta != 0.0) v = fma(beta, *cp, v);
+      if (beta != 0.0) v = fma(beta, (flags & GF_BETA_B) ? g.B[(int64_t)i + (int64_t)j * g.ldb] : *cp, v);
       *cp = v;
     }
   }
@@ -183,7 +183,7 @@ __global__ void gemm_reduce_kernel(const GemmDesc* __restrict__ descs) {
     const int jc = g.colmap ? g.colmap[j] : j;
     double* cp = (g.flags & GF_TRANS_C) ? g.C + (int64_t)jc + (int64_t)i * g.ldc : g.C + (int64_t)i + (int64_t)jc * g.ldc;
     double v = g.alpha * s;
-    if (g.beta != 0.0) v = fma(g.beta, *cp, v);
+    if (g.beta != 0.0) v = fma(g.beta, (g.flags & GF_BETA_B) ? g.B[(int64_t)i + (int64_t)j * g.ldb] : *cp, v);
     *cp = v;
   }
 }

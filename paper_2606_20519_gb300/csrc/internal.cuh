@@ -33,6 +33,7 @@ enum : int {
   GF_LOWER_C = 8,   // only the lower triangle (i >= j) of C is computed
   GF_SCALE_B = 16,  // op(B)(k, j) is multiplied by bscale[k]
   GF_TRANS_C = 32,  // result element (i, j) is stored at C[j + i * ldc]
+  GF_BETA_B = 64,   // the beta term reads B(i, j) = B[i + j * ldb] instead of C(i, j) (B not transposed, M = K)
 };
 
 struct GemmDesc {
@@ -211,5 +212,26 @@ void launch_pack_recon(const ConeDev* cones, int ncones, int64_t maxn, const IoS
 void launch_herm_embed(const int64_t* meta, int count, int64_t maxn, const double* hs, double* ms, cudaStream_t s);
 void launch_herm_extract(const int64_t* meta, int count, int64_t maxn, const double* ms, double* hs, cudaStream_t s);
 void launch_status_reduce(const int* status, int count, int* out, cudaStream_t s);
+
+// ------------------------------------------------------------------ polynomial projection
+// One cone of the factorization-free approximate projection (S_0 = X / ||X||_F,
+// S_{k+1} = a_k S_k + b_k S_k^3, Y = (X + S_K X) / 2; the products are grouped GEMMs).
+constexpr int kPolyChunk = 16384;  // svec entries per partial sum of squares
+struct PolyConeDev {
+  int64_t n;
+  int64_t xoff;     // offset of the cone in the svec buffers
+  int part0;        // first partial sum of squares of this cone
+  int nparts;       // ceil(n (n + 1) / 2 / kPolyChunk)
+  double* X;        // n*n dense X (both triangles)
+  double* S0;       // n*n S_0, then the even iterates
+  double* S1;       // n*n the odd iterates
+  double* Y;        // n*n lower triangle of Y (the GEMMs' S^2 scratch before that)
+  int* status;      // per-cone status bits
+};
+void launch_poly_prepare(const PolyConeDev* cones, int ncones, const int* part_cone, int nparts, int64_t maxn,
+                         const IoSlot* io, double* part, double* inv, cudaStream_t s);
+void launch_poly_pack(const PolyConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s);
+// Upper triangle of the new iterate from its lower triangle (which = 0: S1, 1: S0).
+void launch_poly_mirror(const PolyConeDev* cones, int ncones, int64_t maxn, int which, cudaStream_t s);
 
 }  // namespace scs

@@ -417,8 +417,10 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
         if (alpha_one) v = acc;
         else if (alpha_mone) v = __longlong_as_double(__double_as_longlong(acc) ^ (long long)0x8000000000000000ULL);
         else v = g.alpha * acc;
-        if (beta_one) v = *cp + v;
-        else if (g.beta != 0.0) v = fma(g.beta, *cp, v);
+        if (g.beta != 0.0) {
+          const double cv = (flags & GF_BETA_B) ? g.B[(int64_t)row + (int64_t)j * ldb] : *cp;
+          v = beta_one ? cv + v : fma(g.beta, cv, v);
+        }
         *cp = v;
       }
     }

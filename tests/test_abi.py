@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -14,7 +15,7 @@ HEADER = os.path.join(ROOT, "include", "scs_psd.h")
 
 def declared_functions():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|int64_t|const char\*)\s+(scs_psd_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|int32_t|int64_t|const char\*)\s+(scs_psd_\w+)\s*\(", text, re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -56,3 +57,20 @@ def test_shapes_helper():
     offs, sides = _lib.shapes([1, 3, 0, 4])
     assert list(offs) == [0, 1, 7, 7, 17]
     assert sides.dtype.name == "int32"
+
+
+def test_poly_schedule_matches_the_oracle(lib):
+    """The library's composite coefficients (host function, no GPU) against
+    the oracle's schedule for the factorization-free projection."""
+    from oracle import poly as P
+    from paper_2606_20519_gb300 import _lib as L
+    for lo, steps in ((1e-3, 0), (1e-7, 0), (1e-9, 0), (0.25, 3)):
+        a, b, lk = L.poly_schedule(lo, steps)
+        oa, ob, olk = P.poly_coeffs(lo, steps)
+        assert len(a) == len(oa)
+        np.testing.assert_allclose(a, oa, rtol=4e-16, atol=0)
+        np.testing.assert_allclose(b, ob, rtol=8e-16, atol=0)
+        assert abs(lk - olk) <= 4e-16
+    for lo, steps in ((0.0, 0), (1.0, 0), (1e-3, -1), (1e-3, 201)):
+        with pytest.raises(L.ScsPsdError):
+            L.poly_schedule(lo, steps)
