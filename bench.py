@@ -6,7 +6,10 @@ Default workload (the ADMM-like process-matrix step at d = 5): a sequence of
 1e-3 Sym(G_k) from X_0 = Q diag(lam) Q^T with a spectrum clustered at zero,
 svec in and out (195,625 doubles each); one step = the 200 projections as
 200 dependent calls of the library's C-ABI on one stream.  Other workloads:
---config single81 | precision4096 | uneven | vjp1296.
+--config single81 | precision4096 | uneven | vjp1296 | herm625.
+--method poly runs the factorization-free approximate projection (the
+composite matrix polynomial of the paper's outlook) on the same workload,
+for the speed/accuracy comparison against the eigensolver path.
 
 Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
 on the launching stream (L2 flushed before every step by writing a 256 MB
@@ -57,6 +60,10 @@ def parse():
     p.add_argument("--config", default="admm625",
                    choices=["admm625", "single81", "precision4096", "uneven", "vjp1296", "herm625"])
     p.add_argument("--band", type=int, default=0)
+    p.add_argument("--method", default="eig", choices=["eig", "poly"],
+                   help="eig: projection by eigendecomposition; poly: factorization-free composite polynomial")
+    p.add_argument("--poly-lo", type=float, default=1e-9,
+                   help="poly: relative eigenvalue resolution lo (eigenvalues above lo * ||X||_F are thresholded)")
     p.add_argument("--precision", default="fp64", choices=["fp64", "split"],
                    help="fp64: FP64 throughout; split: split-TF32 tensor-core contractions")
     p.add_argument("--no-comparator", action="store_true")
@@ -208,9 +215,11 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def oracle_value(wl: Workload, budget_s: float = 12.0):
-    """Oracle projections/s on a bounded sample of the workload (host cores)."""
+def oracle_value(wl: Workload, budget_s: float = 12.0, poly_lo: float | None = None):
+    """Oracle projections/s on a bounded sample of the workload (host cores);
+    with poly_lo, the oracle of the factorization-free composite instead."""
     import oracle
+    from oracle import poly as oracle_poly
     oracle.build()
     done, t0 = 0, time.perf_counter()
     sample = []
@@ -219,7 +228,9 @@ def oracle_value(wl: Workload, budget_s: float = 12.0):
         np.cumsum([wl.svec_len(s) for s in sides], out=offs[1:])
         for i in range(len(sides)):
             xi = x[offs[i]:offs[i + 1]]
-            if wl.herm:
+            if poly_lo is not None:
+                oracle_poly.proj_poly(xi, poly_lo)
+            elif wl.herm:
                 oracle.herm_proj(xi)
             elif wl.vjp:
                 oracle.proj(xi)
@@ -285,6 +296,9 @@ def run_ours(args):
     prec = lib.SPLIT_TF32 if args.precision == "split" else lib.FP64
     opts = lib.make_opts(band=args.band, precision=prec) if (args.band or prec != lib.FP64) else None
     b_used = args.band or 16
+    poly = args.method == "poly"
+    if poly and (args.config in ("herm625", "vjp1296")):
+        raise SystemExit("--method poly covers the real projection workloads (no Hermitian or derivative path)")
 
     wl = Workload(args.config, args.calls)
     xs = [torch.from_numpy(x).to(dev) for x, _ in wl.calls]
@@ -297,7 +311,9 @@ def run_ours(args):
     def step(x_list, y_list):
         for i in range(len(x_list)):
             offs, sides = shapes[i]
-            if wl.vjp:
+            if poly:
+                lib.proj_poly(x_list[i], sides, args.poly_lo, out=y_list[i], opts=opts, offsets=offs)
+            elif wl.vjp:
                 lib.proj_vjp(x_list[i], gs[0], sides, xbar=y_list[i], y=yb, opts=opts, offsets=offs)
             elif wl.herm:
                 lib.proj_hermitian(x_list[i], sides, out=y_list[i], opts=opts, offsets=offs)
@@ -308,7 +324,7 @@ def run_ours(args):
 
     # launch shapes: the library's autotuner on the first call's input (setup, untimed)
     tuning = None
-    if not args.no_autotune and not args.band and not wl.herm:
+    if not args.no_autotune and not args.band and not wl.herm and not poly:
         tuning = lib.autotune(xs[0], shapes[0][1], opts=opts, offsets=shapes[0][0])
         if tuning["band"] >= 2:
             b_used = tuning["band"]
@@ -384,7 +400,9 @@ def run_ours(args):
         for i in range(len(hx)):
             dx[i].copy_(hx[i], non_blocking=True)
             offs, sides = shapes[i]
-            if wl.vjp:
+            if poly:
+                lib.proj_poly(dx[i], sides, args.poly_lo, out=dy[i], opts=opts, offsets=offs)
+            elif wl.vjp:
                 lib.proj_vjp(dx[i], gs[0], sides, xbar=dy[i], y=yb, opts=opts, offsets=offs)
             elif wl.herm:
                 lib.proj_hermitian(dx[i], sides, out=dy[i], opts=opts, offsets=offs)
@@ -417,37 +435,18 @@ def run_ours(args):
     if rank != 0:
         return 0
 
-    # ---- roofline of the dominant phase (CUDA events on the launching stream)
-    dom = max(phases.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_count) = dom
-    n0 = wl.calls[0][1][0]
-    if wl.exact0 is not None:
-        lam_sample = wl.exact0[1]          # spectrum of the construction
+    if poly:
+        roofline, poly_info = poly_roofline(lib, args, wl, ms_per_step, prec)
     else:
-        lam_sample = np.linalg.eigvalsh(W_smat_host(wl.calls[0][0][: n0 * (n0 + 1) // 2], n0))
-    kp, kn = int((lam_sample > 0).sum()), int((lam_sample < 0).sum())
-    k = min(kp, kn)
-    kbt = n0 if wl.vjp else k
-    cones_per_call = len(wl.calls[0][1])
-    # a Hermitian cone is projected as its real embedding of side 2n (every eigenvalue twice)
-    emb = 2 if wl.herm else 1
-    flops_launch = sum(algorithmic_flops(dom_name, emb * int(s), emb * k, b_used, emb * kbt) for s in wl.calls[0][1])
-    # per call: a phase may be traced as several segments within one call
-    avg_ms = dom_ms / max(1, args.steps * len(wl.calls))
-    achieved = flops_launch / (avg_ms * 1e-3) / 1e9
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "peak_source": FP64_PEAK_NOTE,
-                "unit": "GFLOP/s FP64",
-                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": _traffic(args.config, dom_name),
-                "phase": dom_name, "kernel": phase_kernels(dom_name, n0, tuning["band"] if tuning else args.band),
-                "ms_per_launch": avg_ms, "flops_per_launch": flops_launch,
-                "share": dom_ms / max(1e-9, sum(v[0] for v in phases.values()))}
+        roofline = eig_roofline(args, wl, phases, tuning, b_used)
 
     line = {
         "metric": METRIC, "value": value, "unit": "projections/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64 io, tf32x6 split products",
         "data": "synthetic (seeded PCG64), shaped like the paper's SCS iterates; no dataset",
-        "config": {"workload": wl.desc, "config": args.config, "cones_per_step": wl.units, "band": b_used,
+        "config": {"workload": wl.desc, "config": args.config, "method": poly_info if poly else "eigendecomposition",
+                   "cones_per_step": wl.units, "band": None if poly else b_used,
                    "precision": args.precision, "tuning": tuning,
                    "parallelism": f"replicas x{world}", "l2": "flushed before every timed step (256 MB write)"},
         "e2e": {"value": e2e_value, "unit": "projections/s", "h2d_bytes_per_step": wl.bytes_in,
@@ -465,11 +464,71 @@ def run_ours(args):
     if not args.no_comparator:
         line["comparator"] = comparator(wl, xs, dev, stream)
     if not args.no_cpu_baseline:
-        v, done, dt, cores, sample = oracle_value(wl, budget_s=12.0)
+        v, done, dt, cores, sample = oracle_value(wl, budget_s=12.0, poly_lo=args.poly_lo if poly else None)
         line["cpu_baseline"] = {"value": v, "unit": "projections/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{done} projections (sides {sorted(set(sample))}) in {dt:.1f} s"}
     print(json.dumps(line))
     return 0
+
+
+def eig_roofline(args, wl, phases, tuning, b_used):
+    """Roofline of the dominant traced phase of the eigendecomposition path
+    (per-phase CUDA events on the launching stream)."""
+    dom = max(phases.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_count) = dom
+    n0 = wl.calls[0][1][0]
+    if wl.exact0 is not None:
+        lam_sample = wl.exact0[1]          # spectrum of the construction
+    else:
+        lam_sample = np.linalg.eigvalsh(W_smat_host(wl.calls[0][0][: n0 * (n0 + 1) // 2], n0))
+    kp, kn = int((lam_sample > 0).sum()), int((lam_sample < 0).sum())
+    k = min(kp, kn)
+    kbt = n0 if wl.vjp else k
+    cones_per_call = len(wl.calls[0][1])
+    # a Hermitian cone is projected as its real embedding of side 2n (every eigenvalue twice)
+    emb = 2 if wl.herm else 1
+    flops_launch = sum(algorithmic_flops(dom_name, emb * int(s), emb * k, b_used, emb * kbt) for s in wl.calls[0][1])
+    # per call: a phase may be traced as several segments within one call
+    avg_ms = dom_ms / max(1, args.steps * len(wl.calls))
+    achieved = flops_launch / (avg_ms * 1e-3) / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "peak_source": FP64_PEAK_NOTE,
+                "unit": "GFLOP/s FP64",
+                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": _traffic(args.config, dom_name),
+                "phase": dom_name, "kernel": phase_kernels(dom_name, n0, tuning["band"] if tuning else args.band),
+                "ms_per_launch": avg_ms, "flops_per_launch": flops_launch,
+                "share": dom_ms / max(1e-9, sum(v[0] for v in phases.values()))}
+
+
+def poly_roofline(lib, args, wl, ms_per_step, prec):
+    """Roofline of the factorization-free path from the whole step: its work
+    is the composite's products, K (2 n^3) + n^3 flops per cone (every product
+    forms a lower triangle).  Split-TF32 products issue six TF32 products per
+    FP64 product; their peak is the measured bf16 peak x the nominal
+    TF32/BF16 ratio 1.1/2.25."""
+    a, b, lk = lib.poly_schedule(args.poly_lo)
+    K = len(a)
+    flops = sum(K * 2.0 * n ** 3 + 1.0 * n ** 3 for _, sides in wl.calls for n in sides)
+    achieved = flops / (ms_per_step * 1e-3)
+    info = {"name": "factorization-free composite polynomial (scaled Newton-Schulz sign)", "lo": args.poly_lo,
+            "steps": K, "one_minus_l_final": 1.0 - lk}
+    if prec == lib.FP64:
+        return {"bound": "alu", "achieved": achieved / 1e9, "peak": FP64_PEAK_GFLOPS, "peak_source": FP64_PEAK_NOTE,
+                "unit": "GFLOP/s FP64", "frac": achieved / 1e9 / FP64_PEAK_GFLOPS, "traffic": None,
+                "phase": "polynomial products", "kernel": "gemm_f64_kernel (grouped)",
+                "flops_per_step": flops}, info
+    peak = _tf32_peak()
+    ach = 6.0 * achieved / 1e12
+    return {"bound": "tensor", "achieved": ach, "peak": peak[0], "peak_source": peak[1], "unit": "TFLOP/s TF32",
+            "frac": ach / peak[0], "traffic": None, "phase": "polynomial products",
+            "kernel": "tc_gemm_kernel (split-TF32, grouped)", "flops_per_step_fp64_equivalent": flops}, info
+
+
+def _tf32_peak():
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return mp["bf16_tflops"] * 1.1 / 2.25, "measured bf16 burst x nominal TF32/BF16 ratio 1.1/2.25"
+    except Exception:
+        return 1900.0 * 1.1 / 2.25, "fallback bf16 1.9 PFLOP/s x nominal TF32/BF16 ratio 1.1/2.25"
 
 
 def W_smat_host(s, n):
