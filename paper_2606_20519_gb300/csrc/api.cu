@@ -36,6 +36,8 @@ struct GemmLaunch {
   int desc_off = 0, count = 0, prefix_off = 0, tiles = 0;
   int variant = GEMM_SQUARE, needs_reduce = 0;
   int tc = 0;  // 1: split-TF32 tensor-core kernel
+  int tc2 = 0;  // 1: long-contraction split-TF32 kernel (operands sliced once per launch)
+  int sjob_off = 0, njobs = 0, sprefix_off = 0, sctas = 0;  // its slice jobs
   int64_t max_mn = 0;
 };
 
@@ -160,6 +162,7 @@ struct PolyPlan {
   double* part_d = nullptr;
   double* inv_d = nullptr;
   IoSlot* io_d = nullptr;
+  SliceJob* sjobs_d = nullptr;
   std::vector<GemmLaunch> gemms;
   std::vector<int> mirror_after;  // after gemms[0 .. m) the new iterates are mirrored (even steps: into S1)
   int64_t eager_runs = 0, launches = 0, glaunches = 0;
@@ -265,6 +268,64 @@ struct MetaBuilder {
   int gemm_ctas = 2;   // split-K target, CTAs per SM
   int64_t scratch_doubles = 0;
   bool split = false;  // use the split-TF32 tensor-core kernel where the shape suits it
+  bool tc2 = false;    // with split: the long-contraction kernel (operands sliced once per launch)
+  std::vector<SliceJob> sjobs;
+  std::vector<int64_t> sjob_out;      // per slice job: offset of its output in the slice scratch (floats)
+  std::vector<int64_t> desc_as, desc_bs;  // per descriptor: slice-scratch offsets of op(A), op(B) (-1: none)
+  int64_t slice_floats = 0;
+
+  // The long-contraction kernel: tiles 128 x 128, one CTA per SM, split K in
+  // 64-wide groups; one slice job per operand of every problem.
+  GemmLaunch add_gemm_tc2(std::vector<GemmDesc> probs) {
+    GemmLaunch g;
+    g.tc2 = 1;
+    g.desc_off = (int)descs.size();
+    g.count = (int)probs.size();
+    g.prefix_off = (int)ints.size();
+    int64_t base = 0;
+    for (const GemmDesc& p : probs) {
+      int64_t tiles = (int64_t)((p.M + 127) / 128) * ((p.N + 127) / 128);
+      if (p.flags & GF_LOWER_C) tiles = (tiles + (p.M + 127) / 128) / 2 + 1;
+      base += tiles;
+    }
+    int S = 1;
+    const int64_t want = sms;
+    if (base > 0 && base < want) S = (int)std::min<int64_t>(64, (want + base - 1) / base);
+    int t = 0;
+    int64_t off = 0, soff = 0;
+    std::vector<int> sprefix;
+    int sct = 0;
+    g.sjob_off = (int)sjobs.size();
+    for (GemmDesc& p : probs) {
+      const int Sp = std::max(1, std::min(S, (p.K + 63) / 64));
+      p.splitk = Sp;
+      ints.push_back(t);
+      t += ((p.M + 127) / 128) * ((p.N + 127) / 128) * Sp;
+      part_off.push_back(Sp > 1 ? off : -1);
+      if (Sp > 1) { off += (int64_t)Sp * p.M * p.N; g.needs_reduce = 1; }
+      g.max_mn = std::max<int64_t>(g.max_mn, (int64_t)p.M * p.N);
+      const int fl = p.flags;
+      SliceJob ja{p.A, nullptr, nullptr, p.lda, p.M, p.K, (fl & GF_SYM_A) ? 2 : ((fl & GF_TRANS_A) ? 1 : 0)};
+      SliceJob jb{p.B, (fl & GF_SCALE_B) ? p.bscale : nullptr, nullptr, p.ldb, p.N, p.K, (fl & GF_TRANS_B) ? 0 : 1};
+      desc_as.push_back(soff);
+      sjobs.push_back(ja); sjob_out.push_back(soff); sprefix.push_back(sct);
+      soff += tc2_slice_floats(p.M, p.K); sct += tc2_slice_ctas(p.M, p.K);
+      desc_bs.push_back(soff);
+      sjobs.push_back(jb); sjob_out.push_back(soff); sprefix.push_back(sct);
+      soff += tc2_slice_floats(p.N, p.K); sct += tc2_slice_ctas(p.N, p.K);
+      descs.push_back(p);
+    }
+    ints.push_back(t);
+    g.tiles = t;
+    g.njobs = (int)sjobs.size() - g.sjob_off;
+    g.sprefix_off = (int)ints.size();
+    ints.insert(ints.end(), sprefix.begin(), sprefix.end());
+    ints.push_back(sct);
+    g.sctas = sct;
+    scratch_doubles = std::max(scratch_doubles, off);
+    slice_floats = std::max(slice_floats, soff);
+    return g;
+  }
 
   // Picks the engine and tile shape for the launch and a split-K factor per
   // problem so that the launch has about two CTAs per SM.
@@ -310,6 +371,8 @@ struct MetaBuilder {
       if (Sp > 1) { off += (int64_t)Sp * p.M * p.N; g.needs_reduce = 1; }
       g.max_mn = std::max<int64_t>(g.max_mn, (int64_t)p.M * p.N);
       descs.push_back(p);
+      desc_as.push_back(-1);
+      desc_bs.push_back(-1);
     }
     ints.push_back(t);
     scratch_doubles = std::max(scratch_doubles, off);
@@ -866,9 +929,15 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   } while (0)
 
 int run_gemm_at(const GemmDesc* descs_d, const int* ints_d, const GemmLaunch& g, cudaStream_t s,
-                int64_t& n_launch) {
+                int64_t& n_launch, const SliceJob* sjobs_d = nullptr) {
   if (g.count <= 0 || g.tiles <= 0) return SCS_PSD_OK;
-  if (g.tc) {
+  if (g.tc2) {
+    if (!sjobs_d) return SCS_PSD_EINVAL;
+    launch_tc2_slice(sjobs_d + g.sjob_off, ints_d + g.sprefix_off, g.njobs, g.sctas, s);
+    ++n_launch;
+    launch_tc2_gemm(descs_d + g.desc_off, ints_d + g.prefix_off, g.count, g.tiles, s);
+    if (g.needs_reduce) launch_gemm_reduce(descs_d + g.desc_off, g.count, g.max_mn, s);
+  } else if (g.tc) {
     launch_tc_gemm(descs_d + g.desc_off, ints_d + g.prefix_off, g.count, g.tiles, g.variant, s);
     if (g.needs_reduce) launch_gemm_reduce(descs_d + g.desc_off, g.count, g.max_mn, s);
   } else {
@@ -1473,7 +1542,7 @@ int build_poly(scs_psd_handle h, PolyPlan& P, const int64_t* offsets, const int3
     std::vector<GemmDesc> g;
     for (int c = 0; c < P.ncones; ++c)
       if ((cones[c].n >= 64) == (big != 0)) g.push_back(make(c));
-    if (!g.empty()) P.gemms.push_back(mb.add_gemm(g));
+    if (!g.empty()) P.gemms.push_back((big && mb.split) ? mb.add_gemm_tc2(g) : mb.add_gemm(g));
   };
   for (int k = 0; k <= K; ++k) {
     for (int big = 1; big >= 0; --big) {
@@ -1512,7 +1581,10 @@ int build_poly(scs_psd_handle h, PolyPlan& P, const int64_t* offsets, const int3
   const size_t inv_b = align_up(sizeof(double) * P.ncones);
   const size_t scratch_b = align_up(sizeof(double) * std::max<int64_t>(1, mb.scratch_doubles));
   const size_t io_b = align_up(sizeof(IoSlot));
-  if (cudaMalloc(&P.meta, cones_b + ints_b + descs_b + part_b + inv_b + scratch_b + io_b) != cudaSuccess)
+  const size_t sjobs_b = align_up(sizeof(SliceJob) * std::max<size_t>(1, mb.sjobs.size()));
+  const size_t slice_b = align_up(sizeof(float) * (size_t)std::max<int64_t>(1, mb.slice_floats));
+  if (cudaMalloc(&P.meta, cones_b + ints_b + descs_b + part_b + inv_b + scratch_b + io_b + sjobs_b + slice_b) !=
+      cudaSuccess)
     return SCS_PSD_ENOMEM;
   char* m = (char*)P.meta;
   P.cones_d = (PolyConeDev*)m;
@@ -1522,6 +1594,9 @@ int build_poly(scs_psd_handle h, PolyPlan& P, const int64_t* offsets, const int3
   P.inv_d = (double*)(m + cones_b + ints_b + descs_b + part_b);
   double* scratch = (double*)(m + cones_b + ints_b + descs_b + part_b + inv_b);
   P.io_d = (IoSlot*)(m + cones_b + ints_b + descs_b + part_b + inv_b + scratch_b);
+  P.sjobs_d = (SliceJob*)(m + cones_b + ints_b + descs_b + part_b + inv_b + scratch_b + io_b);
+  float* slices = (float*)(m + cones_b + ints_b + descs_b + part_b + inv_b + scratch_b + io_b + sjobs_b);
+  for (size_t q = 0; q < mb.sjobs.size(); ++q) mb.sjobs[q].out = slices + mb.sjob_out[q];
   P.part_cone_d = P.ints_d + part_cone_off;
   P.status_d = P.ints_d + status_off;
   for (int c = 0; c < P.ncones; ++c) cones[c].status = P.status_d + c;
@@ -1529,11 +1604,16 @@ int build_poly(scs_psd_handle h, PolyPlan& P, const int64_t* offsets, const int3
     GemmDesc& g = mb.descs[q];
     g.partial = mb.part_off[q] >= 0 ? scratch + mb.part_off[q] : nullptr;
     if (g.skip) g.skip = P.status_d + ((intptr_t)g.skip - 1);
+    g.As = mb.desc_as[q] >= 0 ? slices + mb.desc_as[q] : nullptr;
+    g.Bs = mb.desc_bs[q] >= 0 ? slices + mb.desc_bs[q] : nullptr;
   }
   if (cudaMemcpy(P.cones_d, cones.data(), sizeof(PolyConeDev) * P.ncones, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(P.ints_d, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(P.descs_d, mb.descs.data(), sizeof(GemmDesc) * mb.descs.size(), cudaMemcpyHostToDevice) !=
-          cudaSuccess)
+          cudaSuccess ||
+      (!mb.sjobs.empty() &&
+       cudaMemcpy(P.sjobs_d, mb.sjobs.data(), sizeof(SliceJob) * mb.sjobs.size(), cudaMemcpyHostToDevice) !=
+           cudaSuccess))
     return SCS_PSD_ECUDA;
   return SCS_PSD_OK;
 }
@@ -1546,7 +1626,7 @@ int run_poly_body(scs_psd_handle h, PolyPlan& P, cudaStream_t s, int64_t& n_laun
   int rc;
   size_t mi = 0;
   for (size_t q = 0; q < P.gemms.size(); ++q) {
-    if ((rc = run_gemm_at(P.descs_d, P.ints_d, P.gemms[q], s, n_launch))) return rc;
+    if ((rc = run_gemm_at(P.descs_d, P.ints_d, P.gemms[q], s, n_launch, P.sjobs_d))) return rc;
     if (mi < P.mirror_after.size() && (size_t)P.mirror_after[mi] == q + 1) {
       launch_poly_mirror(P.cones_d, P.ncones, P.maxn, (int)(mi % 2), s);  // step mi wrote S1 if mi is even
       LAUNCH_CHECK();

@@ -52,7 +52,26 @@ struct GemmDesc {
   int flags;
   int splitk;            // number of K slices (1: no split)
   double* partial;       // splitk > 1: scratch of splitk * M * N doubles
+  const float* As;       // long-contraction tensor-core kernel: op(A) sliced by launch_tc2_slice
+  const float* Bs;       //   and op(B) (as its N x K transpose)
 };
+
+// One operand of a long-contraction split-TF32 product, sliced once: the
+// element (row, k) of a rows x K matrix is p[row + k ld] (mode 0),
+// p[k + row ld] (mode 1) or the lower triangle of a symmetric p (mode 2),
+// times scale[k] if scale is set; out receives ceil(rows/128) x ceil(K/16)
+// blocks of 3 x 2048 floats.
+struct SliceJob {
+  const double* p;
+  const double* scale;
+  float* out;
+  int64_t ld;
+  int rows, K, mode;
+};
+void launch_tc2_slice(const SliceJob* jobs, const int* prefix, int njobs, int total, cudaStream_t s);
+void launch_tc2_gemm(const GemmDesc* descs, const int* tile_prefix, int count, int total_tiles, cudaStream_t s);
+int64_t tc2_slice_floats(int rows, int K);
+int tc2_slice_ctas(int rows, int K);
 
 constexpr int kGemmBK = 16;
 enum : int { GEMM_SQUARE = 0, GEMM_TALL = 1, GEMM_SHORT = 2, GEMM_SMALL = 3 };  // 64x64, 128x16, 16x128, 16x16

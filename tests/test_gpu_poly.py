@@ -148,3 +148,18 @@ def test_edge_cases(lib):
             lib.proj_poly(xt, [3], lo, steps)
     with pytest.raises(lib.ScsPsdError):
         lib.proj_poly(xt, [3], 1e-3, 0, offsets=[0, 5], )
+
+
+@pytest.mark.parametrize("n", [64, 130, 300, 700])
+def test_split_products_single_step(lib, n):
+    """One composite step isolates the split-TF32 products from the
+    iteration's amplification: S_0 = X/||X||_F, S_1 = a S_0 + b S_0^3,
+    Y = (X + S_1 X)/2 against the oracle's FP64 evaluation.  A product
+    carries 2^-31 of max|a| max|b| per term (the grid of a row's 256-wide K
+    group); for Gaussian entries max/rms is about 4, so a product is good to
+    about 16 x 2^-31 = 7.5e-9 relative, and three chained products to 5e-8."""
+    rng = W.rng_for(9600 + n)
+    x = W.to_svec(W.sym_gaussian(rng, n))
+    y, st = run(lib, x, [n], 0.3, steps=1, precision=lib.SPLIT_TF32)
+    assert st == lib.OK
+    assert rel(y, P.proj_poly(x, 0.3, 1)) <= 5e-8
