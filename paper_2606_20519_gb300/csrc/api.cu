@@ -41,6 +41,11 @@ struct GemmLaunch {
   int64_t max_mn = 0;
 };
 
+// One launch of the long-contraction kernel's slicing step over a list of operands.
+struct SliceLaunch {
+  int sjob_off = 0, njobs = 0, sprefix_off = 0, sctas = 0;
+};
+
 struct PanelStep {
   int panel = 0, njobs = 0, cluster = 1, R = 0;
   int ids_off = 0;  // offset into the int metadata
@@ -164,7 +169,12 @@ struct PolyPlan {
   IoSlot* io_d = nullptr;
   SliceJob* sjobs_d = nullptr;
   std::vector<GemmLaunch> gemms;
-  std::vector<int> mirror_after;  // after gemms[0 .. m) the new iterates are mirrored (even steps: into S1)
+  std::vector<SliceLaunch> slices;
+  struct Op {
+    int kind;  // 0: gemms[idx], 1: slices[idx], 2: mirror of the new iterate (idx: 0 = S1, 1 = S0)
+    int idx;
+  };
+  std::vector<Op> ops;
   int64_t eager_runs = 0, launches = 0, glaunches = 0;
   cudaGraphExec_t gexec = nullptr;
   bool gfailed = false;
@@ -276,7 +286,26 @@ struct MetaBuilder {
 
   // The long-contraction kernel: tiles 128 x 128, one CTA per SM, split K in
   // 64-wide groups; one slice job per operand of every problem.
-  GemmLaunch add_gemm_tc2(std::vector<GemmDesc> probs) {
+  // One launch of the slicing kernel over these operands (their outputs set by the caller).
+  SliceLaunch add_slices(const std::vector<SliceJob>& jobs) {
+    SliceLaunch L;
+    L.sjob_off = (int)sjobs.size();
+    L.njobs = (int)jobs.size();
+    L.sprefix_off = (int)ints.size();
+    int sct = 0;
+    for (const SliceJob& j : jobs) {
+      ints.push_back(sct);
+      sjobs.push_back(j);
+      sjob_out.push_back(-1);
+      sct += tc2_slice_ctas(j.rows, j.K);
+    }
+    ints.push_back(sct);
+    L.sctas = sct;
+    return L;
+  }
+
+  // make_jobs = false: the descriptors' As / Bs already point at sliced operands.
+  GemmLaunch add_gemm_tc2(std::vector<GemmDesc> probs, bool make_jobs = true) {
     GemmLaunch g;
     g.tc2 = 1;
     g.desc_off = (int)descs.size();
@@ -304,6 +333,12 @@ struct MetaBuilder {
       part_off.push_back(Sp > 1 ? off : -1);
       if (Sp > 1) { off += (int64_t)Sp * p.M * p.N; g.needs_reduce = 1; }
       g.max_mn = std::max<int64_t>(g.max_mn, (int64_t)p.M * p.N);
+      if (!make_jobs) {
+        desc_as.push_back(-1);
+        desc_bs.push_back(-1);
+        descs.push_back(p);
+        continue;
+      }
       const int fl = p.flags;
       SliceJob ja{p.A, nullptr, nullptr, p.lda, p.M, p.K, (fl & GF_SYM_A) ? 2 : ((fl & GF_TRANS_A) ? 1 : 0)};
       SliceJob jb{p.B, (fl & GF_SCALE_B) ? p.bscale : nullptr, nullptr, p.ldb, p.N, p.K, (fl & GF_TRANS_B) ? 0 : 1};
@@ -933,8 +968,10 @@ int run_gemm_at(const GemmDesc* descs_d, const int* ints_d, const GemmLaunch& g,
   if (g.count <= 0 || g.tiles <= 0) return SCS_PSD_OK;
   if (g.tc2) {
     if (!sjobs_d) return SCS_PSD_EINVAL;
-    launch_tc2_slice(sjobs_d + g.sjob_off, ints_d + g.sprefix_off, g.njobs, g.sctas, s);
-    ++n_launch;
+    if (g.njobs > 0) {
+      launch_tc2_slice(sjobs_d + g.sjob_off, ints_d + g.sprefix_off, g.njobs, g.sctas, s);
+      ++n_launch;
+    }
     launch_tc2_gemm(descs_d + g.desc_off, ints_d + g.prefix_off, g.count, g.tiles, s);
     if (g.needs_reduce) launch_gemm_reduce(descs_d + g.desc_off, g.count, g.max_mn, s);
   } else if (g.tc) {
@@ -1486,12 +1523,17 @@ int poly_schedule(double lo, int steps, std::vector<double>* a, std::vector<doub
 // Per cone (side n >= 1) four n x n buffers: X, the even iterates (from S_0),
 // the odd iterates, and S^2 (its lower triangle), which the last product
 // overwrites with Y.  One step is T = S S (lower triangle), S' = b T S + a S
-// (lower triangle; T read as symmetric, a S added from the B operand), then
-// S' mirrored into its upper triangle, so every iterate is exactly
-// symmetric (a non-symmetric rounding residue is not a function of X, and
-// the iteration amplifies it); the end is Y = S_K X / 2 + X / 2 (lower
-// triangle).  In split-TF32 mode the cones of side >= 64 run on the
-// tensor-core kernel, smaller ones in FP64.
+// (lower triangle; T read as symmetric, a S added from the B operand); the
+// end is Y = S_K X / 2 + X / 2 (lower triangle).  Every iterate is used as a
+// symmetric matrix (a non-symmetric rounding residue is not a function of X,
+// and the iteration amplifies it):
+//  * FP64 products read full operands, so each new iterate is mirrored into
+//    its upper triangle;
+//  * in split-TF32 mode the cones of side >= 64 run on the long-contraction
+//    tensor-core kernel, whose operands are sliced from lower triangles: S
+//    once per step (it is both operands of S S, by symmetry, and the B
+//    operand of T S), T once, X once per call; nothing is mirrored.
+//  Smaller cones stay on FP64 products.
 int build_poly(scs_psd_handle h, PolyPlan& P, const int64_t* offsets, const int32_t* sides, int32_t count,
                int precision, double lo, int steps) {
   std::vector<double> ca, cb;
@@ -1499,6 +1541,7 @@ int build_poly(scs_psd_handle h, PolyPlan& P, const int64_t* offsets, const int3
   if (K < 0) return SCS_PSD_EINVAL;
   P.precision = precision;
   P.steps = K;
+  const bool split = precision == SCS_PSD_SPLIT_TF32;
   std::vector<PolyConeDev> cones;
   std::vector<int64_t> woff;
   int64_t work = 0;
@@ -1510,10 +1553,12 @@ int build_poly(scs_psd_handle h, PolyPlan& P, const int64_t* offsets, const int3
     d.xoff = offsets[i];
     d.part0 = P.nparts;
     d.nparts = (int)((svec_len(n) + kPolyChunk - 1) / kPolyChunk);
+    d.mirror = (split && n >= 64) ? 0 : 1;
     P.nparts += d.nparts;
     P.maxn = std::max(P.maxn, n);
     woff.push_back(work);
     work += 4 * (int64_t)align_up((size_t)(n * n), 32);
+    if (!d.mirror) work += 3 * (int64_t)align_up((size_t)((tc2_slice_floats((int)n, (int)n) + 1) / 2), 32);
     cones.push_back(d);
   }
   P.ncones = (int)cones.size();
@@ -1521,6 +1566,8 @@ int build_poly(scs_psd_handle h, PolyPlan& P, const int64_t* offsets, const int3
   if (cudaMalloc(&P.work, sizeof(double) * (size_t)work) != cudaSuccess) return SCS_PSD_ENOMEM;
   double* wbase = (double*)P.work;
   std::vector<double*> S1(P.ncones), T(P.ncones);
+  std::vector<float*> slS(P.ncones, nullptr), slT(P.ncones, nullptr), slX(P.ncones, nullptr);
+  bool any_small = false, any_big = false;
   for (int c = 0; c < P.ncones; ++c) {
     const int64_t stride = (int64_t)align_up((size_t)(cones[c].n * cones[c].n), 32);
     cones[c].X = wbase + woff[c];
@@ -1529,41 +1576,84 @@ int build_poly(scs_psd_handle h, PolyPlan& P, const int64_t* offsets, const int3
     cones[c].S1 = S1[c];
     T[c] = S1[c] + stride;
     cones[c].Y = T[c];
+    if (!cones[c].mirror) {
+      const int64_t sst = (int64_t)align_up((size_t)((tc2_slice_floats((int)cones[c].n, (int)cones[c].n) + 1) / 2), 32);
+      double* sb = T[c] + stride;
+      slS[c] = (float*)sb;
+      slT[c] = (float*)(sb + sst);
+      slX[c] = (float*)(sb + 2 * sst);
+      any_big = true;
+    } else {
+      any_small = true;
+    }
   }
   MetaBuilder mb;
   mb.sms = h->sms;
-  mb.split = precision == SCS_PSD_SPLIT_TF32;
+  mb.split = split;
   // the status word of cone c is encoded as (offset + 1) and patched after upload
   std::vector<int> part_cone(P.nparts);
   for (int c = 0; c < P.ncones; ++c)
     for (int q = 0; q < cones[c].nparts; ++q) part_cone[cones[c].part0 + q] = c;
   auto skip_of = [](int c) { return (const int*)(intptr_t)(c + 1); };
-  auto group = [&](int big, auto make) {
+  using Op = PolyPlan::Op;
+  // one grouped launch over the cones of one kind (big: tensor-core kernel on sliced operands)
+  auto gemm_group = [&](bool big, auto make) {
     std::vector<GemmDesc> g;
     for (int c = 0; c < P.ncones; ++c)
-      if ((cones[c].n >= 64) == (big != 0)) g.push_back(make(c));
-    if (!g.empty()) P.gemms.push_back((big && mb.split) ? mb.add_gemm_tc2(g) : mb.add_gemm(g));
+      if ((cones[c].mirror == 0) == big) g.push_back(make(c));
+    if (g.empty()) return;
+    P.ops.push_back(Op{0, (int)P.gemms.size()});
+    P.gemms.push_back(big ? mb.add_gemm_tc2(g, false) : mb.add_gemm(g));
   };
-  for (int k = 0; k <= K; ++k) {
-    for (int big = 1; big >= 0; --big) {
-      if (k < K) {
-        group(big, [&](int c) {
-          const int n = (int)cones[c].n;
-          double* Sin = (k % 2 == 0) ? cones[c].S0 : S1[c];
-          return mk(Sin, n, Sin, n, T[c], n, n, n, n, 1.0, 0.0, GF_LOWER_C, skip_of(c));
-        });
-      }
+  auto slice_group = [&](auto src, auto dst) {
+    std::vector<SliceJob> jobs;
+    for (int c = 0; c < P.ncones; ++c) {
+      if (cones[c].mirror) continue;
+      const int n = (int)cones[c].n;
+      jobs.push_back(SliceJob{src(c), nullptr, dst(c), n, n, n, 2});
     }
-    for (int big = 1; big >= 0; --big) {
-      group(big, [&](int c) {
+    if (jobs.empty()) return;
+    P.ops.push_back(Op{1, (int)P.slices.size()});
+    P.slices.push_back(mb.add_slices(jobs));
+  };
+  auto tc2_desc = [&](int c, const float* As, const float* Bs, const double* B, double* C, double alpha, double beta,
+                      int flags) {
+    const int n = (int)cones[c].n;
+    GemmDesc g = mk(nullptr, n, B, n, C, n, n, n, n, alpha, beta, flags, skip_of(c));
+    g.As = As;
+    g.Bs = Bs;
+    return g;
+  };
+  if (any_big) slice_group([&](int c) { return (const double*)cones[c].X; }, [&](int c) { return slX[c]; });
+  for (int k = 0; k <= K; ++k) {
+    auto Sin = [&](int c) { return (k % 2 == 0) ? cones[c].S0 : S1[c]; };
+    auto Sout = [&](int c) { return (k % 2 == 0) ? S1[c] : cones[c].S0; };
+    if (any_big) slice_group([&](int c) { return (const double*)Sin(c); }, [&](int c) { return slS[c]; });
+    if (k < K) {
+      gemm_group(true, [&](int c) { return tc2_desc(c, slS[c], slS[c], nullptr, T[c], 1.0, 0.0, GF_LOWER_C); });
+      gemm_group(false, [&](int c) {
         const int n = (int)cones[c].n;
-        double* Sin = (k % 2 == 0) ? cones[c].S0 : S1[c];
-        if (k == K) return mk(Sin, n, cones[c].X, n, T[c], n, n, n, n, 0.5, 0.5, GF_LOWER_C | GF_BETA_B, skip_of(c));
-        double* Sout = (k % 2 == 0) ? S1[c] : cones[c].S0;
-        return mk(T[c], n, Sin, n, Sout, n, n, n, n, cb[k], ca[k], GF_SYM_A | GF_BETA_B | GF_LOWER_C, skip_of(c));
+        return mk(Sin(c), n, Sin(c), n, T[c], n, n, n, n, 1.0, 0.0, GF_LOWER_C, skip_of(c));
+      });
+      if (any_big) slice_group([&](int c) { return (const double*)T[c]; }, [&](int c) { return slT[c]; });
+      gemm_group(true, [&](int c) {
+        return tc2_desc(c, slT[c], slS[c], Sin(c), Sout(c), cb[k], ca[k], GF_LOWER_C | GF_BETA_B);
+      });
+      gemm_group(false, [&](int c) {
+        const int n = (int)cones[c].n;
+        return mk(T[c], n, Sin(c), n, Sout(c), n, n, n, n, cb[k], ca[k], GF_SYM_A | GF_BETA_B | GF_LOWER_C,
+                  skip_of(c));
+      });
+      if (any_small) P.ops.push_back(Op{2, k % 2 == 0 ? 0 : 1});
+    } else {
+      gemm_group(true, [&](int c) {
+        return tc2_desc(c, slS[c], slX[c], cones[c].X, T[c], 0.5, 0.5, GF_LOWER_C | GF_BETA_B);
+      });
+      gemm_group(false, [&](int c) {
+        const int n = (int)cones[c].n;
+        return mk(Sin(c), n, cones[c].X, n, T[c], n, n, n, n, 0.5, 0.5, GF_LOWER_C | GF_BETA_B, skip_of(c));
       });
     }
-    if (k < K) P.mirror_after.push_back((int)P.gemms.size());
   }
   // metadata: cones | ints (tile prefixes, partial-sum owners, status) | descriptors | partial sums | 1/sigma |
   // split-K scratch | io slot
@@ -1596,7 +1686,8 @@ int build_poly(scs_psd_handle h, PolyPlan& P, const int64_t* offsets, const int3
   P.io_d = (IoSlot*)(m + cones_b + ints_b + descs_b + part_b + inv_b + scratch_b);
   P.sjobs_d = (SliceJob*)(m + cones_b + ints_b + descs_b + part_b + inv_b + scratch_b + io_b);
   float* slices = (float*)(m + cones_b + ints_b + descs_b + part_b + inv_b + scratch_b + io_b + sjobs_b);
-  for (size_t q = 0; q < mb.sjobs.size(); ++q) mb.sjobs[q].out = slices + mb.sjob_out[q];
+  for (size_t q = 0; q < mb.sjobs.size(); ++q)
+    if (mb.sjob_out[q] >= 0) mb.sjobs[q].out = slices + mb.sjob_out[q];
   P.part_cone_d = P.ints_d + part_cone_off;
   P.status_d = P.ints_d + status_off;
   for (int c = 0; c < P.ncones; ++c) cones[c].status = P.status_d + c;
@@ -1604,8 +1695,8 @@ int build_poly(scs_psd_handle h, PolyPlan& P, const int64_t* offsets, const int3
     GemmDesc& g = mb.descs[q];
     g.partial = mb.part_off[q] >= 0 ? scratch + mb.part_off[q] : nullptr;
     if (g.skip) g.skip = P.status_d + ((intptr_t)g.skip - 1);
-    g.As = mb.desc_as[q] >= 0 ? slices + mb.desc_as[q] : nullptr;
-    g.Bs = mb.desc_bs[q] >= 0 ? slices + mb.desc_bs[q] : nullptr;
+    if (mb.desc_as[q] >= 0) g.As = slices + mb.desc_as[q];
+    if (mb.desc_bs[q] >= 0) g.Bs = slices + mb.desc_bs[q];
   }
   if (cudaMemcpy(P.cones_d, cones.data(), sizeof(PolyConeDev) * P.ncones, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(P.ints_d, ints.data(), sizeof(int) * ints.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1624,13 +1715,16 @@ int run_poly_body(scs_psd_handle h, PolyPlan& P, cudaStream_t s, int64_t& n_laun
   n_launch += 2;
   LAUNCH_CHECK();
   int rc;
-  size_t mi = 0;
-  for (size_t q = 0; q < P.gemms.size(); ++q) {
-    if ((rc = run_gemm_at(P.descs_d, P.ints_d, P.gemms[q], s, n_launch, P.sjobs_d))) return rc;
-    if (mi < P.mirror_after.size() && (size_t)P.mirror_after[mi] == q + 1) {
-      launch_poly_mirror(P.cones_d, P.ncones, P.maxn, (int)(mi % 2), s);  // step mi wrote S1 if mi is even
+  for (const PolyPlan::Op& op : P.ops) {
+    if (op.kind == 0) {
+      if ((rc = run_gemm_at(P.descs_d, P.ints_d, P.gemms[op.idx], s, n_launch, P.sjobs_d))) return rc;
+    } else if (op.kind == 1) {
+      const SliceLaunch& L = P.slices[op.idx];
+      launch_tc2_slice(P.sjobs_d + L.sjob_off, P.ints_d + L.sprefix_off, L.njobs, L.sctas, s);
       LAUNCH_CHECK();
-      ++mi;
+    } else {
+      launch_poly_mirror(P.cones_d, P.ncones, P.maxn, op.idx, s);
+      LAUNCH_CHECK();
     }
   }
   launch_poly_pack(P.cones_d, P.ncones, P.maxn, P.io_d, s);

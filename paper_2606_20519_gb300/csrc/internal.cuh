@@ -244,6 +244,7 @@ struct PolyConeDev {
   double* X;        // n*n dense X (both triangles)
   double* S0;       // n*n S_0, then the even iterates
   double* S1;       // n*n the odd iterates
+  int mirror;       // 1: the iterates are mirrored into their upper triangles (FP64 products)
   double* Y;        // n*n lower triangle of Y (the GEMMs' S^2 scratch before that)
   int* status;      // per-cone status bits
 };

@@ -121,7 +121,7 @@ __global__ void poly_mirror_kernel(const PolyConeDev* __restrict__ cones, int wh
   const int64_t n = c.n;
   const int bi = blockIdx.x, bj = blockIdx.y;
   if (bj > bi || (int64_t)bi * 32 >= n) return;
-  if (*c.status) return;
+  if (!c.mirror || *c.status) return;
   double* __restrict__ S = which ? c.S0 : c.S1;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int64_t ib = (int64_t)bi * 32, jb = (int64_t)bj * 32;
