@@ -119,49 +119,70 @@ __device__ __forceinline__ double job_load(const SliceJob& J, int i, int k) {
   return v;
 }
 
-// One CTA per (job, 128-row tile, 64-wide K group): exponents of the rows,
-// then the three slices of every 16-wide K tile, staged in shared memory and
-// copied out as three consecutive 8 KB blocks.
+// One CTA per (job, 64-row half of a 128-row tile, 64-wide K group): the
+// 64 x 64 piece is read once into shared memory (all loads independent),
+// then the rows' exponents are taken, and the three slices of each 16-wide K
+// tile are staged in shared memory and copied out; the 64 rows of a half
+// fill a contiguous half of every 8 KB block.
+constexpr int SR = 64;       // rows per slicing CTA
+constexpr int SLD = G2 + 1;  // row stride of the staged piece (doubles)
+constexpr int HBLK = BLK / 2;
+constexpr size_t kSliceSmem = sizeof(double) * SR * SLD + sizeof(float) * 3 * HBLK + sizeof(int) * SR;
+
 __global__ void __launch_bounds__(256) tc2_slice_kernel(const SliceJob* __restrict__ jobs,
                                                         const int* __restrict__ prefix, int njobs) {
-  __shared__ int em[M2];
-  __shared__ __align__(16) float blk[3][BLK];
+  extern __shared__ __align__(16) uint8_t sraw[];
+  float* blk = reinterpret_cast<float*>(sraw);                                    // [3][HBLK]
+  double* tile = reinterpret_cast<double*>(sraw + sizeof(float) * 3 * HBLK);       // [SR][SLD]
+  int* em = reinterpret_cast<int*>(sraw + sizeof(float) * 3 * HBLK + sizeof(double) * SR * SLD);
   const int b = blockIdx.x;
   const int jid = find_item(prefix, njobs, b);
   const SliceJob& J = jobs[jid];
   const int local = b - prefix[jid];
   const int ngrp = (J.K + G2 - 1) / G2;
-  const int tr = local / ngrp, g = local % ngrp;
-  const int r0 = tr * M2, k0 = g * G2, k1 = min(J.K, k0 + G2);
+  const int th = local / ngrp, g = local % ngrp;  // th: 64-row half index
+  const int tb = th >> 1, half = th & 1;
+  const int r0 = th * SR, k0 = g * G2, k1 = min(J.K, k0 + G2);
   const int KT = (J.K + K2 - 1) / K2;
   const int tid = threadIdx.x;
-  if (tid < M2) em[tid] = 0;
-  __syncthreads();
   // row-fast reads when consecutive rows are contiguous, K-fast otherwise
-  const bool kfast = (J.mode == 1) || (J.mode == 2 && r0 + M2 <= k0);
-  for (int e = tid; e < M2 * G2; e += 256) {
+  const bool kfast = (J.mode == 1) || (J.mode == 2 && r0 + SR <= k0);
+#pragma unroll 8
+  for (int q = 0; q < (SR * G2) / 256; ++q) {
+    const int e = tid + q * 256;
     int r, k;
-    if (kfast) { k = e % G2; r = e / G2; } else { r = e % M2; k = e / M2; }
+    if (kfast) { k = e % G2; r = e / G2; } else { r = e % SR; k = e / SR; }
     const int i = r0 + r, kk = k0 + k;
-    if (i < J.rows && kk < k1) {
-      const int ex = expf64(job_load(J, i, kk));
-      if (ex) atomicMax(&em[r], ex);
-    }
+    tile[r * SLD + k] = (i < J.rows && kk < k1) ? job_load(J, i, kk) : 0.0;
   }
   __syncthreads();
-  const int kt_end = min(KT, (k0 + G2) / K2);
-  for (int kt = k0 / K2; kt < kt_end; ++kt) {
-    for (int e = tid; e < BLK; e += 256) {
-      int r, k;
-      if (kfast) { k = e % K2; r = e / K2; } else { r = e % M2; k = e / M2; }
-      const int i = r0 + r, kk = kt * K2 + k;
-      const double v = (i < J.rows && kk < J.K) ? job_load(J, i, kk) : 0.0;
-      slice3(blk[0], blk[1], blk[2], boff(r, k), v, em[r]);
+  // exponents: four threads per row, 16 columns each
+  {
+    const int r = tid >> 2, h = tid & 3;
+    int m = 0;
+#pragma unroll
+    for (int k = h * 16; k < h * 16 + 16; ++k) m = max(m, expf64(tile[r * SLD + k]));
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    if (h == 0) em[r] = m;
+  }
+  __syncthreads();
+  const int kt0 = k0 / K2, kt_end = min(KT, (k0 + G2) / K2);
+  const uint32_t hoff = (uint32_t)half * (BLK_BYTES / 2);
+  for (int kt = kt0; kt < kt_end; ++kt) {
+#pragma unroll 4
+    for (int q = 0; q < HBLK / 256; ++q) {
+      const int e = tid + q * 256;
+      const int r = e % SR, k = e / SR;  // shared memory: any order
+      slice3(blk, blk + HBLK, blk + 2 * HBLK, boff(half * SR + r, k) - hoff, tile[r * SLD + (kt - kt0) * K2 + k],
+             em[r]);
     }
     __syncthreads();
-    float4* dst = reinterpret_cast<float4*>(J.out + (int64_t)(tr * KT + kt) * 3 * BLK);
-    const float4* src = reinterpret_cast<const float4*>(&blk[0][0]);
-    for (int q = tid; q < 3 * BLK / 4; q += 256) dst[q] = src[q];
+    float* base = J.out + (int64_t)(tb * KT + kt) * 3 * BLK + half * HBLK;
+    for (int q = tid; q < 3 * HBLK / 4; q += 256) {
+      const int sl = q / (HBLK / 4), w = q % (HBLK / 4);
+      reinterpret_cast<float4*>(base + sl * BLK)[w] = reinterpret_cast<const float4*>(blk + sl * HBLK)[w];
+    }
     __syncthreads();
   }
 }
@@ -394,7 +415,12 @@ __global__ void __launch_bounds__(288, 1) tc2_gemm_kernel(const GemmDesc* __rest
 
 void launch_tc2_slice(const SliceJob* jobs, const int* prefix, int njobs, int total, cudaStream_t s) {
   if (njobs <= 0 || total <= 0) return;
-  tc2_slice_kernel<<<total, 256, 0, s>>>(jobs, prefix, njobs);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc2_slice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSliceSmem);
+    attr = true;
+  }
+  tc2_slice_kernel<<<total, 256, kSliceSmem, s>>>(jobs, prefix, njobs);
 }
 
 void launch_tc2_gemm(const GemmDesc* descs, const int* tile_prefix, int count, int total_tiles, cudaStream_t s) {
@@ -413,6 +439,6 @@ int64_t tc2_slice_floats(int rows, int K) {
   return tiles * KT * 3 * BLK;
 }
 
-int tc2_slice_ctas(int rows, int K) { return ((rows + M2 - 1) / M2) * ((K + G2 - 1) / G2); }
+int tc2_slice_ctas(int rows, int K) { return 2 * ((rows + M2 - 1) / M2) * ((K + G2 - 1) / G2); }
 
 }  // namespace scs
