@@ -326,7 +326,7 @@ struct MetaBuilder {
     int sct = 0;
     g.sjob_off = (int)sjobs.size();
     for (GemmDesc& p : probs) {
-      const int Sp = std::max(1, std::min(S, (p.K + 63) / 64));
+      const int Sp = std::max(1, std::min(S, (p.K + 127) / 128));  // at least two 64-wide groups per piece
       p.splitk = Sp;
       ints.push_back(t);
       t += ((p.M + 127) / 128) * ((p.N + 127) / 128) * Sp;
