@@ -169,6 +169,17 @@ int scs_psd_proj_poly(scs_psd_handle h, const double* x, double* y, const int64_
                       const int32_t* sides, int32_t count, double lo, int32_t steps,
                       const scs_psd_opts* opts, void* stream);
 
+/* The same composite for complex Hermitian cones (the construction acts on
+ * the spectrum only, so it carries over): S_0 = X / ||X||_F with the complex
+ * Frobenius norm, S_{k+1} = a_k S_k + b_k S_k^3, y = hsvec((X + S_K X) / 2),
+ * on the Hermitian svec layout of scs_psd_proj_hermitian, computed through
+ * the real embedding [[Re X, -Im X], [Im X, Re X]] (its norm halved, so
+ * lo is relative to ||X||_F).  Arguments and errors as scs_psd_proj_poly;
+ * sides up to 4096. */
+int scs_psd_proj_poly_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* offsets,
+                                const int32_t* sides, int32_t count, double lo, int32_t steps,
+                                const scs_psd_opts* opts, void* stream);
+
 /* The composite's coefficients for (lo, steps) as scs_psd_proj_poly uses
  * them: returns K (the number of steps) and, where the pointers are not
  * NULL, writes a[0..K), b[0..K) and l_final = l_K; -SCS_PSD_EINVAL for lo or

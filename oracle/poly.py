@@ -44,7 +44,7 @@ import math
 
 import numpy as np
 
-from . import smat, svec
+from . import herm_smat, herm_svec, smat, svec
 
 AUTO_TOL = 1e-15
 MAX_STEPS = 200
@@ -128,6 +128,37 @@ def proj_poly_batched(x, offsets, lo: float, steps: int = 0) -> np.ndarray:
     for i in range(len(offsets) - 1):
         a, b = int(offsets[i]), int(offsets[i + 1])
         out[a:b] = proj_poly(x[a:b], lo, steps)
+    return out
+
+
+def herm_proj_poly(x, lo: float, steps: int = 0) -> np.ndarray:
+    """The approximate projection of a complex Hermitian cone on its Hermitian
+    svec: the same composite on X / ||X||_F (complex Frobenius norm), every
+    iterate kept Hermitian, Y = (X + X S) / 2 (Conclusions: the construction
+    acts on the spectrum only, so it carries over to Hermitian matrices)."""
+    x = np.asarray(x, dtype=np.float64)
+    if x.size == 0:
+        return x.copy()
+    X = herm_smat(x)
+    sigma = math.sqrt(float(np.sum(np.abs(X) ** 2)))
+    if sigma == 0.0:
+        return np.zeros_like(x)
+    a, b, _ = poly_coeffs(lo, steps)
+    S = X / sigma
+    for ak, bk in zip(a, b):
+        S = ak * S + bk * (S @ (S @ S))
+        S = 0.5 * (S + S.conj().T)
+    Y = 0.5 * (X + X @ S)
+    return herm_svec(0.5 * (Y + Y.conj().T))
+
+
+def herm_proj_poly_batched(x, sides, lo: float, steps: int = 0) -> np.ndarray:
+    x = np.asarray(x, dtype=np.float64)
+    out = np.empty_like(x)
+    o = 0
+    for n in sides:
+        out[o:o + n * n] = herm_proj_poly(x[o:o + n * n], lo, steps)
+        o += n * n
     return out
 
 

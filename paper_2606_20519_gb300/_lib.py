@@ -39,7 +39,7 @@ EXPORTS = ("scs_psd_create", "scs_psd_destroy", "scs_psd_proj", "scs_psd_proj_ba
            "scs_psd_proj_store", "scs_psd_vjp_stored", "scs_psd_proj_static", "scs_psd_reserve", "scs_psd_status", "scs_psd_last_launch_count",
            "scs_psd_last_replayed", "scs_psd_strerror", "scs_psd_trace", "scs_psd_trace_read",
            "scs_psd_autotune", "scs_psd_last_tuning", "scs_psd_proj_hermitian", "scs_psd_proj_poly",
-           "scs_psd_poly_schedule")
+           "scs_psd_poly_schedule", "scs_psd_proj_poly_hermitian")
 NPHASES = 8
 PHASES = ("unpack", "dense_to_band", "band_to_tridiag", "tridiag_dc", "backtransform_2", "backtransform_1",
           "reconstruct", "derivative")
@@ -74,6 +74,7 @@ def load(path: str | None = None):
         lib.scs_psd_proj_poly.argtypes = [vp, vp, vp, vp, vp, i32, ctypes.c_double, i32, op, vp]
         lib.scs_psd_poly_schedule.argtypes = [ctypes.c_double, i32, vp, vp, ctypes.POINTER(ctypes.c_double)]
         lib.scs_psd_poly_schedule.restype = i32
+        lib.scs_psd_proj_poly_hermitian.argtypes = [vp, vp, vp, vp, vp, i32, ctypes.c_double, i32, op, vp]
         lib.scs_psd_autotune.argtypes = [vp, vp, vp, vp, i32, op, vp, ctypes.POINTER(i32),
                                          ctypes.POINTER(ctypes.c_double)]
         lib.scs_psd_last_tuning.argtypes = [vp, ctypes.POINTER(i32)]
@@ -313,6 +314,27 @@ def proj_poly(x, sides, lo: float, steps: int = 0, out=None, opts: Opts | None =
                                   sides.ctypes.data_as(ctypes.c_void_p), int(sides.size), float(lo), int(steps),
                                   ctypes.byref(opts) if opts is not None else None, _stream_ptr(x))
     _check(rc, "scs_psd_proj_poly")
+    return out
+
+
+def proj_poly_hermitian(x, sides, lo: float, steps: int = 0, out=None, opts: Opts | None = None, offsets=None):
+    """Factorization-free approximate projection of complex Hermitian cones (C-ABI scs_psd_proj_poly_hermitian)."""
+    import torch
+    _check_tensor(x, "x")
+    if offsets is None:
+        offsets, sides = hshapes(sides)
+    else:
+        offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        sides = np.ascontiguousarray(np.asarray(sides, dtype=np.int32))
+    if out is None:
+        out = torch.empty_like(x)
+    _check_tensor(out, "out")
+    rc = load().scs_psd_proj_poly_hermitian(handle(x.device.index), _ptr(x), _ptr(out),
+                                            offsets.ctypes.data_as(ctypes.c_void_p),
+                                            sides.ctypes.data_as(ctypes.c_void_p), int(sides.size), float(lo),
+                                            int(steps), ctypes.byref(opts) if opts is not None else None,
+                                            _stream_ptr(x))
+    _check(rc, "scs_psd_proj_poly_hermitian")
     return out
 
 

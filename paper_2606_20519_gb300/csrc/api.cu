@@ -155,6 +155,7 @@ struct HermPlan {
 struct PolyPlan {
   int precision = SCS_PSD_FP64;
   int steps = 0;
+  double nsq = 1.0;  // ||X||_F^2 = nsq * ||svec||^2 (1/2 for the real embedding of a Hermitian cone)
   int ncones = 0, nparts = 0;
   int64_t maxn = 0;
   void* work = nullptr;
@@ -1437,8 +1438,14 @@ int autotune(scs_psd_handle h, const double* x, const int64_t* offsets, const in
 }
 
 // ---- complex Hermitian cones: through the real side-2n embedding ----
+int proj_poly(scs_psd_handle h, const double* x, double* y, const int64_t* offsets, const int32_t* sides,
+              int32_t count, double lo, int32_t steps, const scs_psd_opts* opts, void* stream, double nsq);
+
+// poly_lo > 0: the factorization-free composite instead of the eigendecomposition,
+// with the norm of the Hermitian matrix (half the squared norm of the embedding).
 int proj_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* offsets, const int32_t* sides,
-                   int32_t count, const scs_psd_opts* opts, void* stream) {
+                   int32_t count, const scs_psd_opts* opts, void* stream, double poly_lo = 0.0,
+                   int32_t poly_steps = 0) {
   if (!h || count < 0) return SCS_PSD_EINVAL;
   if (count == 0) return SCS_PSD_OK;
   if (!offsets || !sides || offsets[0] != 0) return SCS_PSD_EINVAL;
@@ -1483,7 +1490,9 @@ int proj_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* 
   launch_herm_embed(hp->meta_d, count, hp->maxn, x, hp->buf, s);
   if (cudaGetLastError() != cudaSuccess) return SCS_PSD_ECUDA;
   const IoSlot io{hp->buf, hp->buf, nullptr, nullptr, nullptr, nullptr};
-  const int rc = do_call(h, io, MODE_Y, hp->roff.data(), hp->rsides.data(), count, opts, stream);
+  const int rc = poly_lo > 0.0 ? proj_poly(h, hp->buf, hp->buf, hp->roff.data(), hp->rsides.data(), count, poly_lo,
+                                           poly_steps, opts, stream, 0.5)
+                               : do_call(h, io, MODE_Y, hp->roff.data(), hp->rsides.data(), count, opts, stream);
   if (rc) return rc;
   launch_herm_extract(hp->meta_d, count, hp->maxn, hp->buf, y, s);
   if (cudaGetLastError() != cudaSuccess) return SCS_PSD_ECUDA;
@@ -1535,12 +1544,13 @@ int poly_schedule(double lo, int steps, std::vector<double>* a, std::vector<doub
 //    operand of T S), T once, X once per call; nothing is mirrored.
 //  Smaller cones stay on FP64 products.
 int build_poly(scs_psd_handle h, PolyPlan& P, const int64_t* offsets, const int32_t* sides, int32_t count,
-               int precision, double lo, int steps) {
+               int precision, double lo, int steps, double nsq) {
   std::vector<double> ca, cb;
   const int K = poly_schedule(lo, steps, &ca, &cb, nullptr);
   if (K < 0) return SCS_PSD_EINVAL;
   P.precision = precision;
   P.steps = K;
+  P.nsq = nsq;
   const bool split = precision == SCS_PSD_SPLIT_TF32;
   std::vector<PolyConeDev> cones;
   std::vector<int64_t> woff;
@@ -1711,7 +1721,7 @@ int build_poly(scs_psd_handle h, PolyPlan& P, const int64_t* offsets, const int3
 
 int run_poly_body(scs_psd_handle h, PolyPlan& P, cudaStream_t s, int64_t& n_launch) {
   CUDA_TRY(cudaMemsetAsync(P.status_d, 0, sizeof(int) * P.ncones, s));
-  launch_poly_prepare(P.cones_d, P.ncones, P.part_cone_d, P.nparts, P.maxn, P.io_d, P.part_d, P.inv_d, s);
+  launch_poly_prepare(P.cones_d, P.ncones, P.part_cone_d, P.nparts, P.maxn, P.io_d, P.part_d, P.inv_d, P.nsq, s);
   n_launch += 2;
   LAUNCH_CHECK();
   int rc;
@@ -1735,7 +1745,7 @@ int run_poly_body(scs_psd_handle h, PolyPlan& P, cudaStream_t s, int64_t& n_laun
 }
 
 int proj_poly(scs_psd_handle h, const double* x, double* y, const int64_t* offsets, const int32_t* sides,
-              int32_t count, double lo, int32_t steps, const scs_psd_opts* opts, void* stream) {
+              int32_t count, double lo, int32_t steps, const scs_psd_opts* opts, void* stream, double nsq = 1.0) {
   if (!h) return SCS_PSD_EINVAL;
   int rc = check_shapes(offsets, sides, count);
   if (rc) return rc;
@@ -1753,7 +1763,7 @@ int proj_poly(scs_psd_handle h, const double* x, double* y, const int64_t* offse
   std::lock_guard<std::mutex> lock(h->mu);
   if (cudaSetDevice(h->device) != cudaSuccess) return SCS_PSD_ECUDA;
   char hdr[96];
-  snprintf(hdr, sizeof(hdr), "p%d,l%.17g,k%d:", precision, lo, steps);
+  snprintf(hdr, sizeof(hdr), "p%d,l%.17g,k%d,q%.17g:", precision, lo, steps, nsq);
   const std::string key = std::string(hdr) + plan_key(sides, count, 0, 0, 0, 0);
   PolyPlan* P = nullptr;
   auto it = h->poly.find(key);
@@ -1765,7 +1775,7 @@ int proj_poly(scs_psd_handle h, const double* x, double* y, const int64_t* offse
       h->poly.clear();
     }
     auto np = std::make_unique<PolyPlan>();
-    if ((rc = build_poly(h, *np, offsets, sides, count, precision, lo, steps))) return rc;
+    if ((rc = build_poly(h, *np, offsets, sides, count, precision, lo, steps, nsq))) return rc;
     P = np.get();
     h->poly[key] = std::move(np);
   }
@@ -1984,6 +1994,13 @@ int scs_psd_proj_hermitian(scs_psd_handle h, const double* x, double* y, const i
 int scs_psd_proj_poly(scs_psd_handle h, const double* x, double* y, const int64_t* offsets, const int32_t* sides,
                       int32_t count, double lo, int32_t steps, const scs_psd_opts* opts, void* stream) {
   return proj_poly(h, x, y, offsets, sides, count, lo, steps, opts, stream);
+}
+
+int scs_psd_proj_poly_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* offsets,
+                                const int32_t* sides, int32_t count, double lo, int32_t steps,
+                                const scs_psd_opts* opts, void* stream) {
+  if (poly_schedule(lo, steps, nullptr, nullptr, nullptr) < 0) return SCS_PSD_EINVAL;
+  return proj_hermitian(h, x, y, offsets, sides, count, opts, stream, lo, steps);
 }
 
 int32_t scs_psd_poly_schedule(double lo, int32_t steps, double* a, double* b, double* l_final) {

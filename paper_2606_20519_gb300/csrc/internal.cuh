@@ -249,7 +249,7 @@ struct PolyConeDev {
   int* status;      // per-cone status bits
 };
 void launch_poly_prepare(const PolyConeDev* cones, int ncones, const int* part_cone, int nparts, int64_t maxn,
-                         const IoSlot* io, double* part, double* inv, cudaStream_t s);
+                         const IoSlot* io, double* part, double* inv, double nsq, cudaStream_t s);
 void launch_poly_pack(const PolyConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s);
 // Upper triangle of the new iterate from its lower triangle (which = 0: S1, 1: S0).
 void launch_poly_mirror(const PolyConeDev* cones, int ncones, int64_t maxn, int which, cudaStream_t s);

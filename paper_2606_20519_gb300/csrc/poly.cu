@@ -50,10 +50,11 @@ __global__ void poly_norm_kernel(const PolyConeDev* __restrict__ cones, const in
   if (threadIdx.x == 0) part[b] = s;
 }
 
-// One warp per cone: ||X||_F^2 from the partial sums (fixed order), then
+// One warp per cone: ||X||_F^2 = nsq ||svec||^2 from the partial sums (fixed
+// order; nsq = 1/2 for the real embedding of a Hermitian cone), then
 // 1 / ||X||_F (0 for X = 0); a non-finite sum marks the cone.
 __global__ void poly_sigma_kernel(const PolyConeDev* __restrict__ cones, const double* __restrict__ part,
-                                  double* __restrict__ inv) {
+                                  double* __restrict__ inv, double nsq) {
   const PolyConeDev& c = cones[blockIdx.x];
   double s = 0.0;
   for (int q = threadIdx.x; q < c.nparts; q += 32) s += part[c.part0 + q];
@@ -61,7 +62,7 @@ __global__ void poly_sigma_kernel(const PolyConeDev* __restrict__ cones, const d
   if (threadIdx.x == 0) {
     double r = 0.0;
     if (!isfinite(s)) atomicOr(c.status, ST_NONFINITE);
-    else if (s > 0.0) r = 1.0 / sqrt(s);
+    else if (s > 0.0) r = 1.0 / sqrt(s * nsq);
     inv[blockIdx.x] = r;
   }
 }
@@ -157,10 +158,10 @@ __global__ void poly_pack_kernel(const PolyConeDev* __restrict__ cones, const Io
 }  // namespace
 
 void launch_poly_prepare(const PolyConeDev* cones, int ncones, const int* part_cone, int nparts, int64_t maxn,
-                         const IoSlot* io, double* part, double* inv, cudaStream_t s) {
+                         const IoSlot* io, double* part, double* inv, double nsq, cudaStream_t s) {
   if (ncones <= 0 || nparts <= 0) return;
   poly_norm_kernel<<<nparts, 256, 0, s>>>(cones, part_cone, io, part);
-  poly_sigma_kernel<<<ncones, 32, 0, s>>>(cones, part, inv);
+  poly_sigma_kernel<<<ncones, 32, 0, s>>>(cones, part, inv, nsq);
   const int tiles = (int)((maxn + 31) / 32);
   poly_unpack_kernel<<<dim3(tiles, tiles, ncones), dim3(32, 8), 0, s>>>(cones, io, inv);
 }

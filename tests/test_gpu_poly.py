@@ -163,3 +163,24 @@ def test_split_products_single_step(lib, n):
     y, st = run(lib, x, [n], 0.3, steps=1, precision=lib.SPLIT_TF32)
     assert st == lib.OK
     assert rel(y, P.proj_poly(x, 0.3, 1)) <= 5e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+def test_hermitian_cones(lib, precision):
+    """Complex Hermitian cones through the real embedding (norm halved), against
+    the oracle's complex evaluation of the composite."""
+    import torch
+    rng = W.rng_for(9700)
+    sides = [3, 40, 90]
+    xs = []
+    for n in sides:
+        lam = np.concatenate([rng.uniform(-1, 1, n - 1), [2e-7]])
+        X, _, _ = W.herm_from_spectrum(rng, lam)
+        xs.append(W.to_hsvec(X))
+    x = np.concatenate(xs)
+    xt = torch.from_numpy(x).cuda()
+    prec = lib.FP64 if precision == "fp64" else lib.SPLIT_TF32
+    y = lib.proj_poly_hermitian(xt, sides, 1e-7, opts=lib.make_opts(precision=prec)).cpu().numpy()
+    assert lib.status(0) == lib.OK
+    want = P.herm_proj_poly_batched(x, sides, 1e-7)
+    assert rel(y, want) <= (TOL_FP64 if precision == "fp64" else TOL_SPLIT)

@@ -187,3 +187,27 @@ def test_planted_mistakes_fail_a_pin(mutation):
     finally:
         P.set_mutation(0)
     assert not all(held)
+
+
+@pytest.mark.parametrize("n,lo", [(6, 1e-3), (20, 1e-9)])
+def test_hermitian_composite_against_lapack_eigh(n, lo):
+    """Complex Hermitian cones: the matrix form equals the scalar composite
+    applied to the eigenvalues of LAPACK's complex eigh (an independent
+    evaluation), and real input reduces to the real composite."""
+    rng = W.rng_for(7700 + n)
+    lam = np.concatenate([rng.uniform(-1, 1, n - 2), [4e-8, -1e-6]])
+    X, U, _ = W.herm_from_spectrum(rng, lam)
+    x = W.to_hsvec(X)
+    got = P.herm_proj_poly(x, lo)
+    w, V = np.linalg.eigh(X)
+    sigma = np.linalg.norm(w)
+    f = P.poly_scalar(w / sigma, lo)
+    want = W.to_hsvec((V * (0.5 * w * (1.0 + f))[None, :]) @ V.conj().T)
+    assert rel(got, want) <= 1e-12
+    # error bound against the exact projection (complex Jacobi oracle)
+    assert np.linalg.norm(got - oracle.herm_proj(x)) <= P.poly_error_bound(lam, lo) + 1e-12 * np.linalg.norm(got)
+    # a real symmetric matrix gives the real composite (embedded in the Hermitian layout)
+    R = W.sym_gaussian(rng, n)
+    yr = oracle.smat(P.proj_poly(W.to_svec(R), lo))
+    np.testing.assert_allclose(oracle.herm_smat(P.herm_proj_poly(W.to_hsvec(R.astype(complex)), lo)), yr,
+                               rtol=0, atol=1e-13 * np.abs(yr).max())
