@@ -180,6 +180,36 @@ int scs_psd_proj_poly_hermitian(scs_psd_handle h, const double* x, double* y, co
                                 const int32_t* sides, int32_t count, double lo, int32_t steps,
                                 const scs_psd_opts* opts, void* stream);
 
+/* Smallest eigenvalue of every cone: lam_min[i] = lambda_min(smat(x_i)), a
+ * DEVICE array of count doubles; layout and host shape arrays as
+ * scs_psd_proj_batched, every side >= 1 (else SCS_PSD_EINVAL).  The cones
+ * are reduced to tridiagonal form as for the projection, then lambda_min is
+ * found by multisection on Sturm counts (32 points per round, absolute
+ * resolution eps ||T||).  Non-finite cones give NaN and SCS_PSD_ENONFINITE.
+ * It serves the positivity post-processing of the paper's instrument and
+ * process steps (App. C, App. D). */
+int scs_psd_lambda_min(scs_psd_handle h, const double* x, double* lam_min, const int64_t* offsets,
+                       const int32_t* sides, int32_t count, const scs_psd_opts* opts, void* stream);
+
+/* Positivity post-processing by mixing with a multiple of the identity
+ * (App. C: the outcome blocks C_a of one instrument input mixed with white
+ * noise, nu = 1/(n_a d_Ao); App. D: a process matrix mixed with the trivial
+ * process, nu = gamma).  Cones groups[g] .. groups[g+1]-1 form group g (host
+ * array of ngroups + 1 entries, groups[0] = 0, groups[ngroups] = count,
+ * non-decreasing); nu is a host array of ngroups values.  Per group, with
+ * lambda_a = lambda_min of its blocks:
+ *     p = 1 if min_a lambda_a >= 0, else p = min over lambda_a < eps of
+ *     (nu - eps) / (nu - lambda_a),
+ * and every block becomes y_a = svec(p C_a + (1 - p) nu 1), so that the
+ * smallest eigenvalue of every mixed block is at least eps (up to rounding),
+ * with equality for the worst block.  y may alias x; p_out (DEVICE, ngroups
+ * doubles) receives the weights if not NULL.  Shapes as
+ * scs_psd_proj_batched, every side >= 1; non-finite blocks make their
+ * group's p and output NaN (status SCS_PSD_ENONFINITE). */
+int scs_psd_mix_identity(scs_psd_handle h, const double* x, double* y, const int64_t* offsets,
+                         const int32_t* sides, int32_t count, const int32_t* groups, int32_t ngroups,
+                         const double* nu, double eps, double* p_out, const scs_psd_opts* opts, void* stream);
+
 /* The composite's coefficients for (lo, steps) as scs_psd_proj_poly uses
  * them: returns K (the number of steps) and, where the pointers are not
  * NULL, writes a[0..K), b[0..K) and l_final = l_K; -SCS_PSD_EINVAL for lo or

@@ -39,7 +39,7 @@ EXPORTS = ("scs_psd_create", "scs_psd_destroy", "scs_psd_proj", "scs_psd_proj_ba
            "scs_psd_proj_store", "scs_psd_vjp_stored", "scs_psd_proj_static", "scs_psd_reserve", "scs_psd_status", "scs_psd_last_launch_count",
            "scs_psd_last_replayed", "scs_psd_strerror", "scs_psd_trace", "scs_psd_trace_read",
            "scs_psd_autotune", "scs_psd_last_tuning", "scs_psd_proj_hermitian", "scs_psd_proj_poly",
-           "scs_psd_poly_schedule", "scs_psd_proj_poly_hermitian")
+           "scs_psd_poly_schedule", "scs_psd_proj_poly_hermitian", "scs_psd_lambda_min", "scs_psd_mix_identity")
 NPHASES = 8
 PHASES = ("unpack", "dense_to_band", "band_to_tridiag", "tridiag_dc", "backtransform_2", "backtransform_1",
           "reconstruct", "derivative")
@@ -75,6 +75,8 @@ def load(path: str | None = None):
         lib.scs_psd_poly_schedule.argtypes = [ctypes.c_double, i32, vp, vp, ctypes.POINTER(ctypes.c_double)]
         lib.scs_psd_poly_schedule.restype = i32
         lib.scs_psd_proj_poly_hermitian.argtypes = [vp, vp, vp, vp, vp, i32, ctypes.c_double, i32, op, vp]
+        lib.scs_psd_lambda_min.argtypes = [vp, vp, vp, vp, vp, i32, op, vp]
+        lib.scs_psd_mix_identity.argtypes = [vp, vp, vp, vp, vp, i32, vp, i32, vp, ctypes.c_double, vp, op, vp]
         lib.scs_psd_autotune.argtypes = [vp, vp, vp, vp, i32, op, vp, ctypes.POINTER(i32),
                                          ctypes.POINTER(ctypes.c_double)]
         lib.scs_psd_last_tuning.argtypes = [vp, ctypes.POINTER(i32)]
@@ -336,6 +338,52 @@ def proj_poly_hermitian(x, sides, lo: float, steps: int = 0, out=None, opts: Opt
                                             _stream_ptr(x))
     _check(rc, "scs_psd_proj_poly_hermitian")
     return out
+
+
+def lambda_min(x, sides, out=None, opts: Opts | None = None, offsets=None):
+    """Smallest eigenvalue of every cone (C-ABI scs_psd_lambda_min): a float64 CUDA tensor of count values."""
+    import torch
+    _check_tensor(x, "x")
+    if offsets is None:
+        offsets, sides = shapes(sides)
+    else:
+        offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        sides = np.ascontiguousarray(np.asarray(sides, dtype=np.int32))
+    if out is None:
+        out = torch.empty(int(sides.size), dtype=torch.float64, device=x.device)
+    _check_tensor(out, "out")
+    rc = load().scs_psd_lambda_min(handle(x.device.index), _ptr(x), _ptr(out), offsets.ctypes.data_as(ctypes.c_void_p),
+                                   sides.ctypes.data_as(ctypes.c_void_p), int(sides.size),
+                                   ctypes.byref(opts) if opts is not None else None, _stream_ptr(x))
+    _check(rc, "scs_psd_lambda_min")
+    return out
+
+
+def mix_identity(x, sides, groups, nu, eps: float, out=None, p_out=None, opts: Opts | None = None, offsets=None):
+    """Positivity post-processing by mixing with nu * identity per group (C-ABI scs_psd_mix_identity).
+    Returns (y, p)."""
+    import torch
+    _check_tensor(x, "x")
+    if offsets is None:
+        offsets, sides = shapes(sides)
+    else:
+        offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        sides = np.ascontiguousarray(np.asarray(sides, dtype=np.int32))
+    groups = np.ascontiguousarray(np.asarray(groups, dtype=np.int32))
+    nu = np.ascontiguousarray(np.asarray(nu, dtype=np.float64))
+    if out is None:
+        out = torch.empty_like(x)
+    _check_tensor(out, "out")
+    ng = int(groups.size) - 1
+    if p_out is None:
+        p_out = torch.empty(max(ng, 1), dtype=torch.float64, device=x.device)
+    rc = load().scs_psd_mix_identity(handle(x.device.index), _ptr(x), _ptr(out),
+                                     offsets.ctypes.data_as(ctypes.c_void_p), sides.ctypes.data_as(ctypes.c_void_p),
+                                     int(sides.size), groups.ctypes.data_as(ctypes.c_void_p), ng,
+                                     nu.ctypes.data_as(ctypes.c_void_p), float(eps), _ptr(p_out),
+                                     ctypes.byref(opts) if opts is not None else None, _stream_ptr(x))
+    _check(rc, "scs_psd_mix_identity")
+    return out, p_out[:ng]
 
 
 TUNING_FIELDS = ("band", "gemm_ctas", "bt1_cols", "sy_share")

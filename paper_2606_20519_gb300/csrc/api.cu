@@ -103,7 +103,7 @@ struct Plan {
   int* ints_d = nullptr;
   GemmDesc* descs_d = nullptr;
   MergeNode* nodes_d = nullptr;
-  int64_t* triv_offs_d = nullptr;  // 3 * ntriv: svec, V and lam offsets of the side-1 cones
+  int64_t* triv_offs_d = nullptr;  // 4 * ntriv: svec, V and lam offsets and call positions of the side-1 cones
   int64_t vtotal = 0, ltotal = 0;   // doubles of a stored eigendecomposition (sum n^2, sum n)
   int* status_d = nullptr;  // ncones + 1 (last: trivial cones)
   int* prog_d = nullptr;
@@ -122,10 +122,10 @@ struct Plan {
   // Recorded launch sequences, one per output mode (MODE_* bits),
   // with the wait limit they were recorded with.
   int64_t eager_runs = 0;
-  cudaGraphExec_t gexec[16] = {};
-  long long gwait[16] = {};
-  int64_t glaunches[16] = {};
-  bool gfailed[16] = {};
+  cudaGraphExec_t gexec[32] = {};
+  long long gwait[32] = {};
+  int64_t glaunches[32] = {};
+  bool gfailed[32] = {};
   bool arena_owned = false;  // memory carved from a caller-provided region (not freed here)
   ~Plan() {
     for (cudaGraphExec_t ge : gexec)
@@ -146,6 +146,23 @@ struct HermPlan {
   ~HermPlan() {
     if (meta_d) cudaFree(meta_d);
     if (buf) cudaFree(buf);
+  }
+};
+
+// Positivity post-processing of a shape list and grouping: device copies of
+// the groups, the per-cone (offset, side, group) table, and buffers for the
+// blocks' lambda_min, the groups' nu and the mixing weights.
+struct MixPlan {
+  int count = 0, ngroups = 0;
+  int64_t maxn = 0;
+  void* mem = nullptr;
+  int* groups_d = nullptr;
+  int64_t* meta_d = nullptr;
+  double* lam_d = nullptr;
+  double* nu_d = nullptr;
+  double* p_d = nullptr;
+  ~MixPlan() {
+    if (mem) cudaFree(mem);
   }
 };
 
@@ -207,6 +224,7 @@ struct scs_psd_handle_s {
   std::map<std::string, Tuning> tuned;  // autotuner's choices by shapes and precision
   std::map<std::string, std::unique_ptr<HermPlan>> herm;  // Hermitian shape lists
   std::map<std::string, std::unique_ptr<PolyPlan>> poly;  // polynomial projections by shapes and schedule
+  std::map<std::string, std::unique_ptr<MixPlan>> mix;    // positivity post-processing by shapes and groups
   Tuning last_tune;
   std::mutex mu;
 };
@@ -458,7 +476,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
 
   // ---- cones of the main path (n >= 2) and trivial ones
   std::vector<int> big;
-  std::vector<int64_t> triv_offs, triv_voff, triv_loff;
+  std::vector<int64_t> triv_offs, triv_voff, triv_loff, triv_idx;
   std::vector<int64_t> voff(count + 1, 0), loff(count + 1, 0);
   for (int i = 0; i < count; ++i) {
     voff[i + 1] = voff[i] + (int64_t)sides[i] * sides[i];
@@ -472,12 +490,14 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
       triv_offs.push_back(P.offsets[i]);
       triv_voff.push_back(voff[i]);
       triv_loff.push_back(loff[i]);
+      triv_idx.push_back(i);
     }
   }
   P.ncones = (int)big.size();
   P.ntriv = (int)triv_offs.size();
   triv_offs.insert(triv_offs.end(), triv_voff.begin(), triv_voff.end());
   triv_offs.insert(triv_offs.end(), triv_loff.begin(), triv_loff.end());
+  triv_offs.insert(triv_offs.end(), triv_idx.begin(), triv_idx.end());
   std::vector<ConeLayout> lay(P.ncones);
   std::vector<int> path(P.ncones);
   size_t cone_bytes = 0;
@@ -530,6 +550,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
     d.xoff = P.offsets[big[c]];
     d.voff = voff[big[c]];
     d.loff = loff[big[c]];
+    d.cidx = big[c];
     d.path = path[c];
     d.b = b;
     d.npanels = path[c] ? 0 : num_panels(n, b);
@@ -902,7 +923,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   const size_t ints_b = align_up(sizeof(int) * std::max<size_t>(1, mb.ints.size()));
   const size_t descs_b = align_up(sizeof(GemmDesc) * std::max<size_t>(1, mb.descs.size()));
   const size_t nodes_b = align_up(sizeof(MergeNode) * std::max<size_t>(1, mb.nodes.size()));
-  const size_t triv_b = align_up(3 * sizeof(int64_t) * std::max(1, P.ntriv));
+  const size_t triv_b = align_up(4 * sizeof(int64_t) * std::max(1, P.ntriv));
   const size_t scratch_b = align_up(sizeof(double) * std::max<int64_t>(1, mb.scratch_doubles));
   const size_t io_b = align_up(sizeof(IoSlot));
   const size_t total = cones_b + ints_b + descs_b + nodes_b + triv_b + scratch_b + io_b;
@@ -949,7 +970,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   if (e == cudaSuccess) e = up(P.descs_d, mb.descs.data(), sizeof(GemmDesc) * mb.descs.size());
   if (e == cudaSuccess) e = up(P.nodes_d, mb.nodes.data(), sizeof(MergeNode) * mb.nodes.size());
   if (e == cudaSuccess && P.ntriv) {
-    e = up(P.triv_offs_d, triv_offs.data(), sizeof(int64_t) * 3 * P.ntriv);
+    e = up(P.triv_offs_d, triv_offs.data(), sizeof(int64_t) * 4 * P.ntriv);
   }
   for (int c = 0; c < P.ncones && e == cudaSuccess; ++c) e = up(cones[c].kinfo, &kin_all[(size_t)c * 8], 8 * sizeof(int));
   if (e != cudaSuccess) return SCS_PSD_ECUDA;
@@ -1058,16 +1079,20 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
         // the T factors need only the reflectors: on the second stream they
         // overlap the divide and conquer (kept on s while tracing phases)
         const bool side = h->use_aux && !h->trace && h->aux_stream && P.nlarft > 0;
-        if (side) {
+        if (mode & MODE_LMIN) {
+          // lambda_min stops at the tridiagonal form: no T factors
+        } else if (side) {
           CUDA_TRY(cudaEventRecord(h->ev_fork, s));
           CUDA_TRY(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
         } else {
           pm.begin(5);
         }
-        launch_larft1(P.cones_d, P.ints_d + P.larft_cone_off, P.ints_d + P.larft_idx_off, P.nlarft,
-                      side ? h->aux_stream : s);
-        LAUNCH_CHECK();
-        if (side) {
+        if (!(mode & MODE_LMIN)) {
+          launch_larft1(P.cones_d, P.ints_d + P.larft_cone_off, P.ints_d + P.larft_idx_off, P.nlarft,
+                        side ? h->aux_stream : s);
+          LAUNCH_CHECK();
+        }
+        if (side && !(mode & MODE_LMIN)) {
           CUDA_TRY(cudaEventRecord(h->ev_join, h->aux_stream));
           joined = false;
         }
@@ -1083,6 +1108,14 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
       }
       launch_tridiag_extract(P.cones_d, nc, P.maxn, s);
       LAUNCH_CHECK();
+      if (mode & MODE_LMIN) {
+        launch_lmin(P.cones_d, nc, io, s);
+        LAUNCH_CHECK();
+        pm.end();
+        launch_status_reduce(P.status_d, P.ncones + 1, h->status_word, s);
+        LAUNCH_CHECK();
+        return SCS_PSD_OK;
+      }
       pm.begin(3);
       launch_dc_leaves(P.cones_d, nc, P.maxn, s);
       LAUNCH_CHECK();
@@ -1295,6 +1328,7 @@ int do_call(scs_psd_handle h, const IoSlot& io, int mode, const int64_t* offsets
   if ((mode & MODE_Y) && !io.y) return SCS_PSD_EINVAL;
   if ((mode & MODE_VJP) && (!io.g || !io.xbar)) return SCS_PSD_EINVAL;
   if ((mode & (MODE_EXPORT | MODE_IMPORT)) && (!io.V || !io.lam)) return SCS_PSD_EINVAL;
+  if ((mode & MODE_LMIN) && !io.lam) return SCS_PSD_EINVAL;
   // every mode but the plain projection needs all n eigenpairs of each cone
   const int allv = (mode & (MODE_VJP | MODE_EXPORT | MODE_IMPORT)) ? 1 : 0;
   int side = 0, precision = SCS_PSD_FP64;
@@ -1822,6 +1856,80 @@ int proj_poly(scs_psd_handle h, const double* x, double* y, const int64_t* offse
   return SCS_PSD_OK;
 }
 
+// ---- positivity post-processing (App. C instrument step, App. D process step) ----
+int lambda_min(scs_psd_handle h, const double* x, double* lam, const int64_t* offsets, const int32_t* sides,
+               int32_t count, const scs_psd_opts* opts, void* stream) {
+  if (!h || !lam) return SCS_PSD_EINVAL;
+  for (int i = 0; i < count && sides; ++i)
+    if (sides[i] < 1) return SCS_PSD_EINVAL;  // a block without eigenvalues
+  const IoSlot io{x, nullptr, nullptr, nullptr, nullptr, lam};
+  return do_call(h, io, MODE_LMIN, offsets, sides, count, opts, stream);
+}
+
+int mix_identity(scs_psd_handle h, const double* x, double* y, const int64_t* offsets, const int32_t* sides,
+                 int32_t count, const int32_t* groups, int32_t ngroups, const double* nu, double eps, double* p_out,
+                 const scs_psd_opts* opts, void* stream) {
+  if (!h || !x || !y || !groups || !nu || ngroups < 0 || count < 0) return SCS_PSD_EINVAL;
+  int rc = check_shapes(offsets, sides, count);
+  if (rc) return rc;
+  if (groups[0] != 0 || groups[ngroups] != count) return SCS_PSD_EINVAL;
+  for (int g = 0; g < ngroups; ++g)
+    if (groups[g + 1] < groups[g]) return SCS_PSD_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (sides[i] < 1) return SCS_PSD_EINVAL;
+  if (count == 0) return SCS_PSD_OK;
+  MixPlan* mp = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(h->mu);
+    if (cudaSetDevice(h->device) != cudaSuccess) return SCS_PSD_ECUDA;
+    std::string key = plan_key(sides, count, 0, 0, 0, 0);
+    key.append(reinterpret_cast<const char*>(groups), sizeof(int32_t) * (size_t)(ngroups + 1));
+    auto it = h->mix.find(key);
+    if (it != h->mix.end()) {
+      mp = it->second.get();
+    } else {
+      if (h->mix.size() >= 8) {
+        cudaDeviceSynchronize();
+        h->mix.clear();
+      }
+      auto np = std::make_unique<MixPlan>();
+      np->count = count;
+      np->ngroups = ngroups;
+      std::vector<int64_t> meta(3 * (size_t)count);
+      for (int g = 0; g < ngroups; ++g)
+        for (int i = groups[g]; i < groups[g + 1]; ++i) {
+          meta[3 * (size_t)i] = offsets[i];
+          meta[3 * (size_t)i + 1] = sides[i];
+          meta[3 * (size_t)i + 2] = g;
+          np->maxn = std::max<int64_t>(np->maxn, sides[i]);
+        }
+      const size_t gb = align_up(sizeof(int) * (ngroups + 1)), mb2 = align_up(sizeof(int64_t) * meta.size());
+      const size_t lb = align_up(sizeof(double) * count), vb = align_up(sizeof(double) * std::max(1, ngroups));
+      if (cudaMalloc(&np->mem, gb + mb2 + lb + 2 * vb) != cudaSuccess) return SCS_PSD_ENOMEM;
+      char* m = (char*)np->mem;
+      np->groups_d = (int*)m;
+      np->meta_d = (int64_t*)(m + gb);
+      np->lam_d = (double*)(m + gb + mb2);
+      np->nu_d = (double*)(m + gb + mb2 + lb);
+      np->p_d = (double*)(m + gb + mb2 + lb + vb);
+      if (cudaMemcpy(np->groups_d, groups, sizeof(int) * (ngroups + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(np->meta_d, meta.data(), sizeof(int64_t) * meta.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SCS_PSD_ECUDA;
+      mp = np.get();
+      h->mix[key] = std::move(np);
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ngroups > 0) CUDA_TRY(cudaMemcpyAsync(mp->nu_d, nu, sizeof(double) * ngroups, cudaMemcpyHostToDevice, s));
+  if ((rc = lambda_min(h, x, mp->lam_d, offsets, sides, count, opts, stream))) return rc;
+  double* p = p_out ? p_out : mp->p_d;
+  launch_mix_weight(mp->groups_d, mp->nu_d, mp->lam_d, eps, ngroups, p, s);
+  launch_mix_apply(mp->meta_d, count, mp->maxn, x, y, p, mp->nu_d, s);
+  if (cudaGetLastError() != cudaSuccess) return SCS_PSD_ECUDA;
+  h->last_launches += 2;
+  return SCS_PSD_OK;
+}
+
 // ---- static-scratch entry point: no device allocation at all ----
 // Callers that cannot allocate device memory (inside a memory pool that owns
 // the GPU, in an embedding that forbids cudaMalloc after start-up) get the
@@ -1994,6 +2102,17 @@ int scs_psd_proj_hermitian(scs_psd_handle h, const double* x, double* y, const i
 int scs_psd_proj_poly(scs_psd_handle h, const double* x, double* y, const int64_t* offsets, const int32_t* sides,
                       int32_t count, double lo, int32_t steps, const scs_psd_opts* opts, void* stream) {
   return proj_poly(h, x, y, offsets, sides, count, lo, steps, opts, stream);
+}
+
+int scs_psd_lambda_min(scs_psd_handle h, const double* x, double* lam_min, const int64_t* offsets,
+                       const int32_t* sides, int32_t count, const scs_psd_opts* opts, void* stream) {
+  return lambda_min(h, x, lam_min, offsets, sides, count, opts, stream);
+}
+
+int scs_psd_mix_identity(scs_psd_handle h, const double* x, double* y, const int64_t* offsets, const int32_t* sides,
+                         int32_t count, const int32_t* groups, int32_t ngroups, const double* nu, double eps,
+                         double* p_out, const scs_psd_opts* opts, void* stream) {
+  return mix_identity(h, x, y, offsets, sides, count, groups, ngroups, nu, eps, p_out, opts, stream);
 }
 
 int scs_psd_proj_poly_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* offsets,

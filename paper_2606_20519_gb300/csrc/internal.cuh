@@ -144,6 +144,7 @@ struct ConeDev {
                     // [6] all-pairs mode: |S|, the pairs of the route's side, which come first
   int* status;      // per-cone status bits
   double* tau1;     // n     tau of the one-stage reflectors (read by larft1 while the divide and conquer runs)
+  int cidx;         // position of the cone in the call's shape list
 };
 
 // One merge node of the divide and conquer tree.
@@ -174,6 +175,7 @@ enum : int {
   MODE_VJP = 2,     // xbar = DPi(X)[smat(g)]
   MODE_EXPORT = 4,  // write the eigendecomposition to io->V, io->lam
   MODE_IMPORT = 8,  // take the eigendecomposition from io->V, io->lam instead of computing it
+  MODE_LMIN = 16,   // io->lam[i] = smallest eigenvalue of cone i (stops at the tridiagonal form)
 };
 
 // ------------------------------------------------------------------ kernels
@@ -181,6 +183,7 @@ void launch_set_io(IoSlot* slot, const IoSlot& v, cudaStream_t s);
 // which = 0: unpack io->x, 1: unpack io->g
 void launch_unpack(const ConeDev* cones, int ncones, int64_t maxn2, const IoSlot* io, int which, cudaStream_t s);
 // Cones of side 1: y, xbar, (V, lam) by `mode`; offs holds count svec, V and lam offsets each
+// offs: 4 * count (svec, V, lam offsets and the cone's position in the call)
 void launch_trivial(const int64_t* offs, int count, const IoSlot* io, int mode, int* status, cudaStream_t s);
 void launch_panel(const ConeDev* cones, const int* cone_ids, int njobs, int panel, int b,
                   int cluster, int rows_per_cta, cudaStream_t s);
@@ -231,6 +234,11 @@ void launch_pack_recon(const ConeDev* cones, int ncones, int64_t maxn, const IoS
 void launch_herm_embed(const int64_t* meta, int count, int64_t maxn, const double* hs, double* ms, cudaStream_t s);
 void launch_herm_extract(const int64_t* meta, int count, int64_t maxn, const double* ms, double* hs, cudaStream_t s);
 void launch_status_reduce(const int* status, int count, int* out, cudaStream_t s);
+void launch_lmin(const ConeDev* cones, int ncones, const IoSlot* io, cudaStream_t s);
+void launch_mix_weight(const int* groups, const double* nu, const double* lam, double eps, int ngroups, double* p,
+                       cudaStream_t s);
+void launch_mix_apply(const int64_t* meta, int count, int64_t maxn, const double* x, double* y, const double* p,
+                      const double* nu, cudaStream_t s);
 
 // ------------------------------------------------------------------ polynomial projection
 // One cone of the factorization-free approximate projection (S_0 = X / ||X||_F,

@@ -34,7 +34,8 @@ __global__ void unpack_kernel(const ConeDev* __restrict__ cones, const IoSlot* _
 
 // Cones of side 1: X = (x) has V = (1), l = x, so Pi(x) = max(x, 0) and
 // DPi(x)[g] = g for x > 0, 0 otherwise (the derivative taken as 0 at 0).
-// offs: [0, count) svec offsets, [count, 2 count) V offsets, [2 count, 3 count) lam offsets.
+// offs: [0, count) svec offsets, [count, 2 count) V offsets, [2 count, 3 count) lam offsets,
+// [3 count, 4 count) the cone's position in the call (MODE_LMIN: lambda_min = x).
 __global__ void trivial_kernel(const int64_t* __restrict__ offs, int count, const IoSlot* __restrict__ io, int mode,
                                int* status) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -49,6 +50,7 @@ __global__ void trivial_kernel(const int64_t* __restrict__ offs, int count, cons
     io->V[ov] = bad ? nan("") : 1.0;
     io->lam[ol] = bad ? nan("") : v;
   }
+  if (mode & MODE_LMIN) io->lam[offs[3 * count + t]] = bad ? nan("") : v;
 }
 
 // Lower band (bandwidth b) of A into band storage with 2b diagonals; the
