@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", default="admm625",
-                   choices=["admm625", "single81", "precision4096", "uneven", "vjp1296", "herm625"])
+                   choices=["admm625", "single81", "precision4096", "uneven", "vjp1296", "herm625", "mixing"])
     p.add_argument("--band", type=int, default=0)
     p.add_argument("--method", default="eig", choices=["eig", "poly"],
                    help="eig: projection by eigendecomposition; poly: factorization-free composite polynomial")
@@ -84,6 +84,7 @@ class Workload:
         self.name = name
         self.vjp = False
         self.herm = False
+        self.mixing = False
         if name == "admm625":
             seq, Q, lam = W.admm_sequence()
             self.calls = [(x, [625]) for x in seq]
@@ -103,6 +104,29 @@ class Workload:
             b = W.uneven_batch()
             self.calls = [(b.x, list(b.sides))]
             self.desc = "960 uneven cones (64 restarts x {2 x sides 4..64 + one 625/1296}) in one call"
+            self.exact0 = None
+        elif name == "mixing":
+            # App. C / D positivity post-processing on the uneven batch: the two
+            # outcome blocks of each instrument side d^2 form a group with
+            # nu = 1/(2 d) (n_a = 2, d_Ao = d); each process block is a group of
+            # its own with nu = gamma = 1/n; eps = 1e-16 as in the paper
+            b = W.uneven_batch()
+            self.calls = [(b.x, list(b.sides))]
+            groups, nu, i = [0], [], 0
+            sides = [int(v) for v in b.sides]
+            while i < len(sides):
+                if i + 1 < len(sides) and sides[i + 1] == sides[i] and sides[i] <= 64:
+                    groups.append(i + 2)
+                    nu.append(1.0 / (2.0 * round(sides[i] ** 0.5)))
+                    i += 2
+                else:
+                    groups.append(i + 1)
+                    nu.append(1.0 / sides[i])
+                    i += 1
+            self.groups, self.nu, self.eps = groups, nu, 1e-16
+            self.mixing = True
+            self.desc = ("positivity post-processing (lambda_min + mixing with nu * identity) of 960 uneven cones "
+                         "(64 restarts x {2 outcome blocks of sides 4..64 + one 625/1296 process block}), one call")
             self.exact0 = None
         elif name == "herm625":
             seq, U, lam = W.herm_admm_sequence()
@@ -226,6 +250,15 @@ def oracle_value(wl: Workload, budget_s: float = 12.0, poly_lo: float | None = N
     for x, sides in wl.calls:
         offs = np.zeros(len(sides) + 1, dtype=np.int64)
         np.cumsum([wl.svec_len(s) for s in sides], out=offs[1:])
+        if wl.mixing:
+            from oracle import mixing as oracle_mixing
+            for i in range(len(sides)):
+                oracle_mixing.lambda_min(x[offs[i]:offs[i + 1]])
+                done += 1
+                sample.append(sides[i])
+                if time.perf_counter() - t0 > budget_s:
+                    break
+            break
         for i in range(len(sides)):
             xi = x[offs[i]:offs[i + 1]]
             if poly_lo is not None:
@@ -265,15 +298,16 @@ def run_reference(args):
     units = sum(d for d, _ in times)
     secs = sum(t for _, t in times)
     value = units / secs
+    unit = "cones/s (lambda_min + mixing)" if wl.mixing else "projections/s"
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "projections/s", "n_gpus": args.gpus,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded PCG64), shaped like the paper's SCS iterates",
         "config": {"workload": wl.desc, "sample": "bounded: about 4 s of oracle work per step"},
-        "cpu_baseline": {"value": value, "unit": "projections/s", "cores": info[0], "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": unit, "cores": info[0], "kind": "oracle",
                          "sample": f"{info[1]} projections per step of the same workload"},
-        "e2e": {"value": value, "unit": "projections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
@@ -313,6 +347,8 @@ def run_ours(args):
             offs, sides = shapes[i]
             if poly:
                 lib.proj_poly(x_list[i], sides, args.poly_lo, out=y_list[i], opts=opts, offsets=offs)
+            elif wl.mixing:
+                lib.mix_identity(x_list[i], sides, wl.groups, wl.nu, wl.eps, out=y_list[i], opts=opts, offsets=offs)
             elif wl.vjp:
                 lib.proj_vjp(x_list[i], gs[0], sides, xbar=y_list[i], y=yb, opts=opts, offsets=offs)
             elif wl.herm:
@@ -324,7 +360,7 @@ def run_ours(args):
 
     # launch shapes: the library's autotuner on the first call's input (setup, untimed)
     tuning = None
-    if not args.no_autotune and not args.band and not wl.herm and not poly:
+    if not args.no_autotune and not args.band and not wl.herm and not poly and not wl.mixing:
         tuning = lib.autotune(xs[0], shapes[0][1], opts=opts, offsets=shapes[0][0])
         if tuning["band"] >= 2:
             b_used = tuning["band"]
@@ -402,6 +438,8 @@ def run_ours(args):
             offs, sides = shapes[i]
             if poly:
                 lib.proj_poly(dx[i], sides, args.poly_lo, out=dy[i], opts=opts, offsets=offs)
+            elif wl.mixing:
+                lib.mix_identity(dx[i], sides, wl.groups, wl.nu, wl.eps, out=dy[i], opts=opts, offsets=offs)
             elif wl.vjp:
                 lib.proj_vjp(dx[i], gs[0], sides, xbar=dy[i], y=yb, opts=opts, offsets=offs)
             elif wl.herm:
@@ -435,13 +473,14 @@ def run_ours(args):
     if rank != 0:
         return 0
 
+    unit = "cones/s (lambda_min + mixing)" if wl.mixing else "projections/s"
     if poly:
         roofline, poly_info = poly_roofline(lib, args, wl, ms_per_step, prec)
     else:
         roofline = eig_roofline(args, wl, phases, tuning, b_used)
 
     line = {
-        "metric": METRIC, "value": value, "unit": "projections/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else
         ("f64 io, tf32x8 split products" if poly else "f64 io, tf32x6 split products"),
@@ -450,7 +489,7 @@ def run_ours(args):
                    "cones_per_step": wl.units, "band": None if poly else b_used,
                    "precision": args.precision, "tuning": tuning,
                    "parallelism": f"replicas x{world}", "l2": "flushed before every timed step (256 MB write)"},
-        "e2e": {"value": e2e_value, "unit": "projections/s", "h2d_bytes_per_step": wl.bytes_in,
+        "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": wl.bytes_in,
                 "d2h_bytes_per_step": wl.bytes_out},
         "gpu_launches": int(launches_per_step * args.steps),
         "timing": {"value": "K untraced steps (graph replay)",
@@ -466,7 +505,7 @@ def run_ours(args):
         line["comparator"] = comparator(wl, xs, dev, stream)
     if not args.no_cpu_baseline:
         v, done, dt, cores, sample = oracle_value(wl, budget_s=12.0, poly_lo=args.poly_lo if poly else None)
-        line["cpu_baseline"] = {"value": v, "unit": "projections/s", "cores": cores, "kind": "oracle",
+        line["cpu_baseline"] = {"value": v, "unit": unit, "cores": cores, "kind": "oracle",
                                 "sample": f"{done} projections (sides {sorted(set(sample))}) in {dt:.1f} s"}
     print(json.dumps(line))
     return 0
@@ -557,7 +596,8 @@ def _smat_torch(s, n):
 
 def comparator(wl, xs, dev, stream, max_calls: int = 20):
     """The plain FP64 GPU path: torch.linalg.eigh (vendor solver) + clamp +
-    reconstruct, on the same inputs (at most max_calls calls)."""
+    reconstruct, on the same inputs (at most max_calls calls); for the mixing
+    workload torch.linalg.eigvalsh + the same weight rule."""
     import torch
     r_idx = {}
 
@@ -607,7 +647,31 @@ def comparator(wl, xs, dev, stream, max_calls: int = 20):
     calls = list(range(min(max_calls, len(xs))))
     offs_all = [wl.calls[i][1] for i in calls]
 
+    def run_mixing():
+        # torch.linalg.eigvalsh per block, the weight rule per group, the mixed svec
+        out = 0
+        for i in calls:
+            sides = offs_all[i]
+            offs = np.concatenate([[0], np.cumsum([wl.svec_len(n) for n in sides])])
+            lam = [torch.linalg.eigvalsh(_smat_torch(xs[i][offs[a]:offs[a + 1]], n))[0]
+                   for a, n in enumerate(sides)]
+            for g in range(len(wl.groups) - 1):
+                a0, a1 = wl.groups[g], wl.groups[g + 1]
+                lg = torch.stack(lam[a0:a1])
+                nu = wl.nu[g]
+                cand = torch.where(lg < wl.eps, (nu - wl.eps) / (nu - lg), torch.ones_like(lg))
+                p = torch.where(lg.min() >= 0, torch.ones((), dtype=lg.dtype, device=lg.device), cand.min())
+                for a in range(a0, a1):
+                    n = sides[a]
+                    r, c = np.triu_indices(n)
+                    dia = torch.from_numpy((r == c).astype(np.float64)).to(xs[i].device)
+                    _ = p * xs[i][offs[a]:offs[a + 1]] + (1 - p) * nu * dia
+                    out += 1
+        return out
+
     def run():
+        if wl.mixing:
+            return run_mixing()
         out = 0
         for i in calls:
             sides = offs_all[i]
@@ -628,6 +692,9 @@ def comparator(wl, xs, dev, stream, max_calls: int = 20):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    if wl.mixing:
+        return {"impl": "torch.linalg.eigvalsh float64 per block + the same weight rule + mixed svec",
+                "value": units / (ms * 1e-3), "unit": "cones/s", "sample": f"{units} cones"}
     return {"impl": ("torch.linalg.eigh complex128" if wl.herm else "torch.linalg.eigh float64") + " + clamp + reconstruct",
             "value": units / (ms * 1e-3),
             "unit": "projections/s", "sample": f"{units} projections"}
