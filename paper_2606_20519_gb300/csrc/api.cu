@@ -102,6 +102,7 @@ struct Plan {
   ConeDev* cones_d = nullptr;
   int* ints_d = nullptr;
   GemmDesc* descs_d = nullptr;
+  SliceJob* sjobs_d = nullptr;  // slice jobs of the long-contraction products (split mode)
   MergeNode* nodes_d = nullptr;
   int64_t* triv_offs_d = nullptr;  // 4 * ntriv: svec, V and lam offsets and call positions of the side-1 cones
   int64_t vtotal = 0, ltotal = 0;   // doubles of a stored eigendecomposition (sum n^2, sum n)
@@ -359,8 +360,10 @@ struct MetaBuilder {
         continue;
       }
       const int fl = p.flags;
-      SliceJob ja{p.A, nullptr, nullptr, p.lda, p.M, p.K, (fl & GF_SYM_A) ? 2 : ((fl & GF_TRANS_A) ? 1 : 0)};
-      SliceJob jb{p.B, (fl & GF_SCALE_B) ? p.bscale : nullptr, nullptr, p.ldb, p.N, p.K, (fl & GF_TRANS_B) ? 0 : 1};
+      SliceJob ja{p.A, nullptr, nullptr, p.lda, p.M, p.K, (fl & GF_SYM_A) ? 2 : ((fl & GF_TRANS_A) ? 1 : 0),
+                  p.dynM, p.dynK};
+      SliceJob jb{p.B, (fl & GF_SCALE_B) ? p.bscale : nullptr, nullptr, p.ldb, p.N, p.K, (fl & GF_TRANS_B) ? 0 : 1,
+                  p.dynN, p.dynK};
       desc_as.push_back(soff);
       sjobs.push_back(ja); sjob_out.push_back(soff); sprefix.push_back(sct);
       soff += tc2_slice_floats(p.M, p.K); sct += tc2_slice_ctas(p.M, p.K);
@@ -384,6 +387,15 @@ struct MetaBuilder {
   // Picks the engine and tile shape for the launch and a split-K factor per
   // problem so that the launch has about two CTAs per SM.
   GemmLaunch add_gemm(std::vector<GemmDesc> probs) {
+    if (split && tc2 && !probs.empty()) {
+      // long contractions go to the kernel whose operands are sliced once per product
+      int maxM = 0, minK = 1 << 30;
+      for (const GemmDesc& p : probs) {
+        maxM = std::max(maxM, p.M);
+        minK = std::min(minK, p.K);
+      }
+      if (maxM >= 128 && minK >= 256) return add_gemm_tc2(probs);
+    }
     GemmLaunch g;
     g.desc_off = (int)descs.size();
     g.count = (int)probs.size();
@@ -527,6 +539,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   mb.sms = h->sms > 0 ? h->sms : 148;
   mb.gemm_ctas = std::max(1, tune.gemm_ctas);
   mb.split = (precision == SCS_PSD_SPLIT_TF32);
+  mb.tc2 = mb.split;
   std::vector<ConeDev> cones(P.ncones);
   size_t prog_total = 0;
   std::vector<size_t> prog_off(P.ncones);
@@ -926,7 +939,9 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   const size_t triv_b = align_up(4 * sizeof(int64_t) * std::max(1, P.ntriv));
   const size_t scratch_b = align_up(sizeof(double) * std::max<int64_t>(1, mb.scratch_doubles));
   const size_t io_b = align_up(sizeof(IoSlot));
-  const size_t total = cones_b + ints_b + descs_b + nodes_b + triv_b + scratch_b + io_b;
+  const size_t sjobs_b = mb.sjobs.empty() ? 0 : align_up(sizeof(SliceJob) * mb.sjobs.size());
+  const size_t slice_b = mb.slice_floats > 0 ? align_up(sizeof(float) * (size_t)mb.slice_floats) : 0;
+  const size_t total = cones_b + ints_b + descs_b + nodes_b + triv_b + scratch_b + io_b + sjobs_b + slice_b;
   if (arena) {
     P.arena_owned = true;
     if (!(P.meta_mem = arena->take(total))) return SCS_PSD_EINVAL;
@@ -941,8 +956,16 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   P.triv_offs_d = (int64_t*)(mbase + cones_b + ints_b + descs_b + nodes_b);
   double* scratch = (double*)(mbase + cones_b + ints_b + descs_b + nodes_b + triv_b);
   P.io_d = (IoSlot*)(mbase + cones_b + ints_b + descs_b + nodes_b + triv_b + scratch_b);
-  for (size_t q = 0; q < mb.descs.size(); ++q)
+  P.sjobs_d = sjobs_b ? (SliceJob*)(mbase + cones_b + ints_b + descs_b + nodes_b + triv_b + scratch_b + io_b) : nullptr;
+  float* slices = slice_b ? (float*)(mbase + cones_b + ints_b + descs_b + nodes_b + triv_b + scratch_b + io_b + sjobs_b)
+                          : nullptr;
+  for (size_t q = 0; q < mb.sjobs.size(); ++q)
+    if (mb.sjob_out[q] >= 0) mb.sjobs[q].out = slices + mb.sjob_out[q];
+  for (size_t q = 0; q < mb.descs.size(); ++q) {
     mb.descs[q].partial = mb.part_off[q] >= 0 ? scratch + mb.part_off[q] : nullptr;
+    if (mb.desc_as[q] >= 0) mb.descs[q].As = slices + mb.desc_as[q];
+    if (mb.desc_bs[q] >= 0) mb.descs[q].Bs = slices + mb.desc_bs[q];
+  }
   P.status_d = P.ints_d + status_off;
   P.prog_d = P.ints_d + prog_base;
   P.prog_count = prog_total;
@@ -969,6 +992,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   if (e == cudaSuccess) e = up(P.ints_d, mb.ints.data(), sizeof(int) * mb.ints.size());
   if (e == cudaSuccess) e = up(P.descs_d, mb.descs.data(), sizeof(GemmDesc) * mb.descs.size());
   if (e == cudaSuccess) e = up(P.nodes_d, mb.nodes.data(), sizeof(MergeNode) * mb.nodes.size());
+  if (e == cudaSuccess && sjobs_b) e = up(P.sjobs_d, mb.sjobs.data(), sizeof(SliceJob) * mb.sjobs.size());
   if (e == cudaSuccess && P.ntriv) {
     e = up(P.triv_offs_d, triv_offs.data(), sizeof(int64_t) * 4 * P.ntriv);
   }
@@ -1009,7 +1033,7 @@ int run_gemm_at(const GemmDesc* descs_d, const int* ints_d, const GemmLaunch& g,
 }
 
 int run_gemm(const Plan& P, const GemmLaunch& g, cudaStream_t s, int64_t& n_launch) {
-  return run_gemm_at(P.descs_d, P.ints_d, g, s, n_launch);
+  return run_gemm_at(P.descs_d, P.ints_d, g, s, n_launch, P.sjobs_d);
 }
 
 // Phase timing: an event pair per phase interval when tracing is on.

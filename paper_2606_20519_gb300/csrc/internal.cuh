@@ -67,6 +67,8 @@ struct SliceJob {
   float* out;
   int64_t ld;
   int rows, K, mode;
+  const int* dynRows;  // if set: rows at or past *dynRows are zero
+  const int* dynK;     // if set: columns k at or past *dynK are zero
 };
 void launch_tc2_slice(const SliceJob* jobs, const int* prefix, int njobs, int total, cudaStream_t s);
 void launch_tc2_gemm(const GemmDesc* descs, const int* tile_prefix, int count, int total_tiles, cudaStream_t s);

@@ -142,7 +142,9 @@ __global__ void __launch_bounds__(256) tc2_slice_kernel(const SliceJob* __restri
   const int ngrp = (J.K + G2 - 1) / G2;
   const int th = local / ngrp, g = local % ngrp;  // th: 64-row half index
   const int tb = th >> 1, half = th & 1;
-  const int r0 = th * SR, k0 = g * G2, k1 = min(J.K, k0 + G2);
+  const int rows = J.dynRows ? min(J.rows, *J.dynRows) : J.rows;
+  const int Keff = J.dynK ? min(J.K, *J.dynK) : J.K;
+  const int r0 = th * SR, k0 = g * G2, k1 = min(Keff, k0 + G2);
   const int KT = (J.K + K2 - 1) / K2;
   const int tid = threadIdx.x;
   // row-fast reads when consecutive rows are contiguous, K-fast otherwise
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(256) tc2_slice_kernel(const SliceJob* __restri
     int r, k;
     if (kfast) { k = e % G2; r = e / G2; } else { r = e % SR; k = e / SR; }
     const int i = r0 + r, kk = k0 + k;
-    tile[r * SLD + k] = (i < J.rows && kk < k1) ? job_load(J, i, kk) : 0.0;
+    tile[r * SLD + k] = (i < rows && kk < k1) ? job_load(J, i, kk) : 0.0;
   }
   __syncthreads();
   // exponents: four threads per row, 16 columns each
@@ -238,8 +240,11 @@ __global__ void __launch_bounds__(288, 1) tc2_gemm_kernel(const GemmDesc* __rest
   const int p = find_item(prefix, count, tile);
   const GemmDesc& g = descs[p];
   if (g.skip && *g.skip) return;
-  const int M = g.M, N = g.N, K = g.K, S = g.splitk;
-  const int tiles_m = (M + M2 - 1) / M2;
+  const int Ms = g.M, S = g.splitk;
+  const int M = g.dynM ? min(Ms, *g.dynM) : Ms;
+  const int N = g.dynN ? min(g.N, *g.dynN) : g.N;
+  const int Kst = g.K, K = g.dynK ? min(Kst, *g.dynK) : Kst;
+  const int tiles_m = (Ms + M2 - 1) / M2;
   int local = tile - prefix[p];
   const int kb = local % S;
   local /= S;
@@ -249,8 +254,8 @@ __global__ void __launch_bounds__(288, 1) tc2_gemm_kernel(const GemmDesc* __rest
   const bool lowc = flags & GF_LOWER_C;
   if (j0 >= N || i0 >= M) return;
   if (lowc && j0 > i0 + M2 - 1) return;
-  const int KT = (K + K2 - 1) / K2;
-  const int kchunk = ((K + S - 1) / S + G2 - 1) / G2 * G2;
+  const int KT = (Kst + K2 - 1) / K2;
+  const int kchunk = ((Kst + S - 1) / S + G2 - 1) / G2 * G2;
   const int kbeg = kb * kchunk, kend = min(K, kbeg + kchunk);
   const int nk = kend > kbeg ? (kend - kbeg + K2 - 1) / K2 : 0;
   const int ngrp = (nk + GS2 - 1) / GS2;
@@ -382,7 +387,7 @@ __global__ void __launch_bounds__(288, 1) tc2_gemm_kernel(const GemmDesc* __rest
   if (!fail && warp < 8) {
     const int qd = warp & 3, half = warp >> 2;
     const int row = i0 + qd * 32 + lane;
-    double* part = (S > 1) ? g.partial + (int64_t)kb * M * g.N : nullptr;
+    double* part = (S > 1) ? g.partial + (int64_t)kb * Ms * g.N : nullptr;
     if (row < M) {
 #pragma unroll
       for (int q = 0; q < 64; ++q) {
@@ -391,7 +396,7 @@ __global__ void __launch_bounds__(288, 1) tc2_gemm_kernel(const GemmDesc* __rest
         if (lowc && !part && row < j) continue;
         const double acc = f32_f64(acc_hi[q]) + f32_f64(acc_lo[q]);
         if (part) {
-          part[(int64_t)row + (int64_t)j * M] = acc;
+          part[(int64_t)row + (int64_t)j * Ms] = acc;
           continue;
         }
         const int jc = g.colmap ? g.colmap[j] : j;
