@@ -210,6 +210,24 @@ int scs_psd_mix_identity(scs_psd_handle h, const double* x, double* y, const int
                          const int32_t* sides, int32_t count, const int32_t* groups, int32_t ngroups,
                          const double* nu, double eps, double* p_out, const scs_psd_opts* opts, void* stream);
 
+/* `iters` iterations of SCS around the projection (App. D.1, final iterates),
+ * for  min c^T x  s.t.  A x + s = b,  s in K  (K the PSD cones of the shape
+ * list, svec layout), in the homogeneous self-dual embedding:
+ *     u~ = (I + Q)^{-1}(u + v),  u = Pi_C(u~ - v),  v = v - u~ + u,
+ * u = (x [k], y [m], tau), v = (r [k], s [m], kappa), Q = [[0, A^T, c],
+ * [-A, 0, b], [-c^T, -b^T, 0]], C = R^k x K x R_+.  A (DEVICE, m x k,
+ * column-major) must have orthonormal columns (A^T A = I, as the paper's
+ * parametrization has, App. D.3; not checked): the affine step is then
+ * z_x = (a_x - A^T a_y)/2, z_y = a_y + A z_x, one product with A^T and one
+ * with A.  b (m) and c (k) are DEVICE arrays (A and c may be NULL when
+ * k = 0); u and v (k + m + 1 each,
+ * DEVICE) are updated in place.  offsets/sides (host) describe the cones of
+ * the y block, offsets[count] == m.  The projection runs with opts as in
+ * scs_psd_proj_batched.  No acceleration, over-relaxation or rescaling. */
+int scs_psd_scs_iterate(scs_psd_handle h, const double* A, const double* b, const double* c, int64_t m, int64_t k,
+                        const int64_t* offsets, const int32_t* sides, int32_t count, double* u, double* v,
+                        int32_t iters, const scs_psd_opts* opts, void* stream);
+
 /* The composite's coefficients for (lo, steps) as scs_psd_proj_poly uses
  * them: returns K (the number of steps) and, where the pointers are not
  * NULL, writes a[0..K), b[0..K) and l_final = l_K; -SCS_PSD_EINVAL for lo or

@@ -39,7 +39,8 @@ EXPORTS = ("scs_psd_create", "scs_psd_destroy", "scs_psd_proj", "scs_psd_proj_ba
            "scs_psd_proj_store", "scs_psd_vjp_stored", "scs_psd_proj_static", "scs_psd_reserve", "scs_psd_status", "scs_psd_last_launch_count",
            "scs_psd_last_replayed", "scs_psd_strerror", "scs_psd_trace", "scs_psd_trace_read",
            "scs_psd_autotune", "scs_psd_last_tuning", "scs_psd_proj_hermitian", "scs_psd_proj_poly",
-           "scs_psd_poly_schedule", "scs_psd_proj_poly_hermitian", "scs_psd_lambda_min", "scs_psd_mix_identity")
+           "scs_psd_poly_schedule", "scs_psd_proj_poly_hermitian", "scs_psd_lambda_min", "scs_psd_mix_identity",
+           "scs_psd_scs_iterate")
 NPHASES = 8
 PHASES = ("unpack", "dense_to_band", "band_to_tridiag", "tridiag_dc", "backtransform_2", "backtransform_1",
           "reconstruct", "derivative")
@@ -76,6 +77,7 @@ def load(path: str | None = None):
         lib.scs_psd_poly_schedule.restype = i32
         lib.scs_psd_proj_poly_hermitian.argtypes = [vp, vp, vp, vp, vp, i32, ctypes.c_double, i32, op, vp]
         lib.scs_psd_lambda_min.argtypes = [vp, vp, vp, vp, vp, i32, op, vp]
+        lib.scs_psd_scs_iterate.argtypes = [vp, vp, vp, vp, i64, i64, vp, vp, i32, vp, vp, i32, op, vp]
         lib.scs_psd_mix_identity.argtypes = [vp, vp, vp, vp, vp, i32, vp, i32, vp, ctypes.c_double, vp, op, vp]
         lib.scs_psd_autotune.argtypes = [vp, vp, vp, vp, i32, op, vp, ctypes.POINTER(i32),
                                          ctypes.POINTER(ctypes.c_double)]
@@ -384,6 +386,26 @@ def mix_identity(x, sides, groups, nu, eps: float, out=None, p_out=None, opts: O
                                      ctypes.byref(opts) if opts is not None else None, _stream_ptr(x))
     _check(rc, "scs_psd_mix_identity")
     return out, p_out[:ng]
+
+
+def scs_iterate(A, b, c, sides, u, v, iters: int, opts: Opts | None = None, offsets=None):
+    """SCS iterations around the projection (C-ABI scs_psd_scs_iterate); A is an m x k float64 CUDA
+    tensor with orthonormal columns (column-major, i.e. A.T contiguous); u, v updated in place."""
+    for t, nm in ((b, "b"), (u, "u"), (v, "v")):
+        _check_tensor(t, nm)
+    m, k = int(A.shape[0]), int(A.shape[1])
+    Acm = A.t().contiguous() if not A.t().is_contiguous() else A.t()
+    if offsets is None:
+        offsets, sides = shapes(sides)
+    else:
+        offsets = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        sides = np.ascontiguousarray(np.asarray(sides, dtype=np.int32))
+    rc = load().scs_psd_scs_iterate(handle(u.device.index), _ptr(Acm), _ptr(b), _ptr(c) if k else None, m, k,
+                                    offsets.ctypes.data_as(ctypes.c_void_p), sides.ctypes.data_as(ctypes.c_void_p),
+                                    int(sides.size), _ptr(u), _ptr(v), int(iters),
+                                    ctypes.byref(opts) if opts is not None else None, _stream_ptr(u))
+    _check(rc, "scs_psd_scs_iterate")
+    return u, v
 
 
 TUNING_FIELDS = ("band", "gemm_ctas", "bt1_cols", "sy_share")

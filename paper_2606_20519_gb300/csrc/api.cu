@@ -167,6 +167,18 @@ struct MixPlan {
   }
 };
 
+// Workspace of the SCS iteration for one (m, k): p = M^{-1}(c, b), 1 + h.p,
+// z, A^T w, dot partials, tau~, the projection's input and u~_y.
+struct ScsPlan {
+  int64_t m = 0, k = 0;
+  void* mem = nullptr;
+  double *p = nullptr, *hp = nullptr, *z = nullptr, *tk = nullptr, *part = nullptr, *tau = nullptr;
+  double *tin = nullptr, *uty = nullptr;
+  ~ScsPlan() {
+    if (mem) cudaFree(mem);
+  }
+};
+
 // Factorization-free approximate projection of a shape list: the composite's
 // coefficients, the per-cone buffers (X, two iterates, S^2 / Y) and the
 // grouped GEMMs of every step, in launch order.
@@ -226,6 +238,7 @@ struct scs_psd_handle_s {
   std::map<std::string, std::unique_ptr<HermPlan>> herm;  // Hermitian shape lists
   std::map<std::string, std::unique_ptr<PolyPlan>> poly;  // polynomial projections by shapes and schedule
   std::map<std::string, std::unique_ptr<MixPlan>> mix;    // positivity post-processing by shapes and groups
+  std::map<std::pair<int64_t, int64_t>, std::unique_ptr<ScsPlan>> scs;  // SCS iterations by (m, k)
   Tuning last_tune;
   std::mutex mu;
 };
@@ -1954,6 +1967,59 @@ int mix_identity(scs_psd_handle h, const double* x, double* y, const int64_t* of
   return SCS_PSD_OK;
 }
 
+// ---- the SCS iteration around the projection (App. D.1) ----
+int scs_iterate(scs_psd_handle h, const double* A, const double* b, const double* c, int64_t m, int64_t k,
+                const int64_t* offsets, const int32_t* sides, int32_t count, double* u, double* v, int32_t iters,
+                const scs_psd_opts* opts, void* stream) {
+  if (!h || !b || !u || !v || m < 1 || k < 0 || iters < 0 || (k > 0 && (!A || !c))) return SCS_PSD_EINVAL;
+  int rc = check_shapes(offsets, sides, count);
+  if (rc) return rc;
+  if (count < 1 || offsets[count] != m) return SCS_PSD_EINVAL;
+  ScsPlan* sp = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(h->mu);
+    if (cudaSetDevice(h->device) != cudaSuccess) return SCS_PSD_ECUDA;
+    auto it = h->scs.find({m, k});
+    if (it != h->scs.end()) {
+      sp = it->second.get();
+    } else {
+      auto np = std::make_unique<ScsPlan>();
+      np->m = m;
+      np->k = k;
+      const int nparts = scs_dot_parts(k + m);
+      const size_t nd = (size_t)(k + m) * 2 + (size_t)std::max<int64_t>(k, 1) + (size_t)nparts + 2 + 2 * (size_t)m;
+      if (cudaMalloc(&np->mem, sizeof(double) * (nd + 64)) != cudaSuccess) return SCS_PSD_ENOMEM;
+      double* q = (double*)np->mem;
+      np->p = q; q += k + m;
+      np->z = q; q += k + m;
+      np->tk = q; q += std::max<int64_t>(k, 1);
+      np->part = q; q += nparts;
+      np->hp = q++;
+      np->tau = q++;
+      np->tin = q; q += m;
+      np->uty = q;
+      sp = np.get();
+      h->scs[{m, k}] = std::move(np);
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_scs_setup(A, b, c, m, k, sp->p, sp->hp, sp->tk, sp->part, s);
+  if (cudaGetLastError() != cudaSuccess) return SCS_PSD_ECUDA;
+  int64_t launches = 5;
+  for (int it = 0; it < iters; ++it) {
+    launch_scs_affine(A, b, c, m, k, sp->p, sp->hp, u, v, sp->z, sp->tk, sp->part, sp->tau, sp->tin, sp->uty, s);
+    if (cudaGetLastError() != cudaSuccess) return SCS_PSD_ECUDA;
+    const IoSlot io{sp->tin, u + k, nullptr, nullptr, nullptr, nullptr};
+    if ((rc = do_call(h, io, MODE_Y, offsets, sides, count, opts, stream))) return rc;
+    launches += 6 + h->last_launches;
+    launch_scs_vy(v + k, sp->uty, u + k, m, s);
+    if (cudaGetLastError() != cudaSuccess) return SCS_PSD_ECUDA;
+    ++launches;
+  }
+  h->last_launches = launches;
+  return SCS_PSD_OK;
+}
+
 // ---- static-scratch entry point: no device allocation at all ----
 // Callers that cannot allocate device memory (inside a memory pool that owns
 // the GPU, in an embedding that forbids cudaMalloc after start-up) get the
@@ -2137,6 +2203,12 @@ int scs_psd_mix_identity(scs_psd_handle h, const double* x, double* y, const int
                          int32_t count, const int32_t* groups, int32_t ngroups, const double* nu, double eps,
                          double* p_out, const scs_psd_opts* opts, void* stream) {
   return mix_identity(h, x, y, offsets, sides, count, groups, ngroups, nu, eps, p_out, opts, stream);
+}
+
+int scs_psd_scs_iterate(scs_psd_handle h, const double* A, const double* b, const double* c, int64_t m, int64_t k,
+                        const int64_t* offsets, const int32_t* sides, int32_t count, double* u, double* v,
+                        int32_t iters, const scs_psd_opts* opts, void* stream) {
+  return scs_iterate(h, A, b, c, m, k, offsets, sides, count, u, v, iters, opts, stream);
 }
 
 int scs_psd_proj_poly_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* offsets,

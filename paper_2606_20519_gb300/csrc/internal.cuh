@@ -237,6 +237,14 @@ void launch_herm_embed(const int64_t* meta, int count, int64_t maxn, const doubl
 void launch_herm_extract(const int64_t* meta, int count, int64_t maxn, const double* ms, double* hs, cudaStream_t s);
 void launch_status_reduce(const int* status, int count, int* out, cudaStream_t s);
 void launch_lmin(const ConeDev* cones, int ncones, const IoSlot* io, cudaStream_t s);
+// SCS iteration (App. D.1) around the projection, A (m x k, column-major) with orthonormal columns
+int scs_dot_parts(int64_t len);
+void launch_scs_setup(const double* A, const double* b, const double* c, int64_t m, int64_t k, double* p,
+                      double* hp, double* tk, double* part, cudaStream_t s);
+void launch_scs_affine(const double* A, const double* b, const double* c, int64_t m, int64_t k, const double* p,
+                       const double* hp, double* u, double* v, double* z, double* tk, double* part, double* tau,
+                       double* tin, double* uty, cudaStream_t s);
+void launch_scs_vy(double* vy, const double* uty, const double* uy, int64_t m, cudaStream_t s);
 void launch_mix_weight(const int* groups, const double* nu, const double* lam, double eps, int ngroups, double* p,
                        cudaStream_t s);
 void launch_mix_apply(const int64_t* meta, int count, int64_t maxn, const double* x, double* y, const double* p,
