@@ -58,7 +58,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", default="admm625",
-                   choices=["admm625", "single81", "precision4096", "uneven", "vjp1296", "herm625", "mixing"])
+                   choices=["admm625", "single81", "precision4096", "uneven", "vjp1296", "herm625", "mixing",
+                            "scs625"])
     p.add_argument("--band", type=int, default=0)
     p.add_argument("--method", default="eig", choices=["eig", "poly"],
                    help="eig: projection by eigendecomposition; poly: factorization-free composite polynomial")
@@ -85,6 +86,7 @@ class Workload:
         self.vjp = False
         self.herm = False
         self.mixing = False
+        self.scs = None
         if name == "admm625":
             seq, Q, lam = W.admm_sequence()
             self.calls = [(x, [625]) for x in seq]
@@ -128,6 +130,17 @@ class Workload:
             self.desc = ("positivity post-processing (lambda_min + mixing with nu * identity) of 960 uneven cones "
                          "(64 restarts x {2 outcome blocks of sides 4..64 + one 625/1296 process block}), one call")
             self.exact0 = None
+        elif name == "scs625":
+            # App. D.1 SCS iterations around the projection: one PSD cone of side
+            # 625 (m = 195,625), k = 1000 parameters (orthonormal A), 10 iterations
+            # per step from SCS's initial iterates
+            At, b, c, u0, v0 = W.scs_problem()
+            self.calls = [(u0, [625])]
+            self.scs = (At, b, c, u0, v0)
+            self.iters = 10
+            self.desc = ("10 SCS iterations (closed-form affine step with A^T A = I, PSD projection of the "
+                         "n = 625 cone, dual update), m = 195,625, k = 1000")
+            self.exact0 = None
         elif name == "herm625":
             seq, U, lam = W.herm_admm_sequence()
             self.calls = [(x, [625]) for x in seq]
@@ -145,7 +158,7 @@ class Workload:
         if calls:
             self.calls = self.calls[:calls]
             self.desc += f" (first {calls} call(s) only)"
-        self.units = sum(len(s) for _, s in self.calls)
+        self.units = sum(len(s) for _, s in self.calls) if self.scs is None else self.iters
         self.bytes_in = sum(x.nbytes for x, _ in self.calls) + (self.g.nbytes if self.vjp else 0)
         self.bytes_out = sum(x.nbytes for x, _ in self.calls) * (2 if self.vjp else 1)
 
@@ -250,6 +263,15 @@ def oracle_value(wl: Workload, budget_s: float = 12.0, poly_lo: float | None = N
     for x, sides in wl.calls:
         offs = np.zeros(len(sides) + 1, dtype=np.int64)
         np.cumsum([wl.svec_len(s) for s in sides], out=offs[1:])
+        if wl.scs is not None:
+            from oracle import scs as oracle_scs
+            At, b, c, u0, v0 = wl.scs
+            uu, vv = u0, v0
+            while time.perf_counter() - t0 <= budget_s and done < wl.iters:
+                uu, vv = oracle_scs.iterate(At.T, b, c, [0, len(b)], uu, vv, 1)
+                done += 1
+                sample.append(625)
+            break
         if wl.mixing:
             from oracle import mixing as oracle_mixing
             for i in range(len(sides)):
@@ -298,7 +320,8 @@ def run_reference(args):
     units = sum(d for d, _ in times)
     secs = sum(t for _, t in times)
     value = units / secs
-    unit = "cones/s (lambda_min + mixing)" if wl.mixing else "projections/s"
+    unit = ("cones/s (lambda_min + mixing)" if wl.mixing else
+            "SCS iterations/s" if wl.scs is not None else "projections/s")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
@@ -345,7 +368,12 @@ def run_ours(args):
     def step(x_list, y_list):
         for i in range(len(x_list)):
             offs, sides = shapes[i]
-            if poly:
+            if wl.scs is not None:
+                scs_u.copy_(x_list[i])
+                scs_v.copy_(scs_v0)
+                lib.scs_iterate(scs_A, scs_b, scs_c, sides, scs_u, scs_v, wl.iters, opts=opts, offsets=offs)
+                y_list[i].copy_(scs_u)
+            elif poly:
                 lib.proj_poly(x_list[i], sides, args.poly_lo, out=y_list[i], opts=opts, offsets=offs)
             elif wl.mixing:
                 lib.mix_identity(x_list[i], sides, wl.groups, wl.nu, wl.eps, out=y_list[i], opts=opts, offsets=offs)
@@ -357,10 +385,16 @@ def run_ours(args):
                 lib.proj_batched(x_list[i], sides, out=y_list[i], opts=opts, offsets=offs)
 
     yb = torch.empty_like(xs[0]) if wl.vjp else None
+    if wl.scs is not None:
+        At, b_h, c_h, u0, v0 = wl.scs
+        scs_A = torch.from_numpy(At).to(dev).t()   # m x k, column-major
+        scs_b, scs_c = torch.from_numpy(b_h).to(dev), torch.from_numpy(c_h).to(dev)
+        scs_v0 = torch.from_numpy(v0).to(dev)
+        scs_u, scs_v = torch.empty_like(scs_v0), torch.empty_like(scs_v0)
 
     # launch shapes: the library's autotuner on the first call's input (setup, untimed)
     tuning = None
-    if not args.no_autotune and not args.band and not wl.herm and not poly and not wl.mixing:
+    if not args.no_autotune and not args.band and not wl.herm and not poly and not wl.mixing and wl.scs is None:
         tuning = lib.autotune(xs[0], shapes[0][1], opts=opts, offsets=shapes[0][0])
         if tuning["band"] >= 2:
             b_used = tuning["band"]
@@ -436,7 +470,12 @@ def run_ours(args):
         for i in range(len(hx)):
             dx[i].copy_(hx[i], non_blocking=True)
             offs, sides = shapes[i]
-            if poly:
+            if wl.scs is not None:
+                scs_u.copy_(dx[i])
+                scs_v.copy_(scs_v0)
+                lib.scs_iterate(scs_A, scs_b, scs_c, sides, scs_u, scs_v, wl.iters, opts=opts, offsets=offs)
+                dy[i].copy_(scs_u)
+            elif poly:
                 lib.proj_poly(dx[i], sides, args.poly_lo, out=dy[i], opts=opts, offsets=offs)
             elif wl.mixing:
                 lib.mix_identity(dx[i], sides, wl.groups, wl.nu, wl.eps, out=dy[i], opts=opts, offsets=offs)
@@ -473,7 +512,8 @@ def run_ours(args):
     if rank != 0:
         return 0
 
-    unit = "cones/s (lambda_min + mixing)" if wl.mixing else "projections/s"
+    unit = ("cones/s (lambda_min + mixing)" if wl.mixing else
+            "SCS iterations/s" if wl.scs is not None else "projections/s")
     if poly:
         roofline, poly_info = poly_roofline(lib, args, wl, ms_per_step, prec)
     else:
@@ -506,7 +546,8 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         v, done, dt, cores, sample = oracle_value(wl, budget_s=12.0, poly_lo=args.poly_lo if poly else None)
         line["cpu_baseline"] = {"value": v, "unit": unit, "cores": cores, "kind": "oracle",
-                                "sample": f"{done} projections (sides {sorted(set(sample))}) in {dt:.1f} s"}
+                                "sample": f"{done} {'iterations' if wl.scs is not None else 'projections'} "
+                                          f"(sides {sorted(set(sample))}) in {dt:.1f} s"}
     print(json.dumps(line))
     return 0
 
@@ -529,7 +570,8 @@ def eig_roofline(args, wl, phases, tuning, b_used):
     emb = 2 if wl.herm else 1
     flops_launch = sum(algorithmic_flops(dom_name, emb * int(s), emb * k, b_used, emb * kbt) for s in wl.calls[0][1])
     # per call: a phase may be traced as several segments within one call
-    avg_ms = dom_ms / max(1, args.steps * len(wl.calls))
+    per_call = wl.iters if wl.scs is not None else 1  # projections per call (SCS: one per iteration)
+    avg_ms = dom_ms / max(1, args.steps * len(wl.calls) * per_call)
     achieved = flops_launch / (avg_ms * 1e-3) / 1e9
     return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "peak_source": FP64_PEAK_NOTE,
                 "unit": "GFLOP/s FP64",
@@ -669,7 +711,37 @@ def comparator(wl, xs, dev, stream, max_calls: int = 20):
                     out += 1
         return out
 
+    def run_scs():
+        # the same iterations with torch ops: matmuls for the affine step, eigh for the projection
+        At, b_h, c_h, u0, v0 = wl.scs
+        A = torch.from_numpy(At).to(dev).t()
+        bt, ct = torch.from_numpy(b_h).to(dev), torch.from_numpy(c_h).to(dev)
+        k, m = At.shape
+        u, v = torch.from_numpy(u0).to(dev), torch.from_numpy(v0).to(dev)
+        px = 0.5 * (ct - A.t() @ bt)
+        py = bt + A @ px
+        hp = ct @ px + bt @ py
+        r, cc = np.triu_indices(625)
+        scale = torch.from_numpy(np.where(r == cc, 1.0, np.sqrt(2.0))).to(dev)
+        for _ in range(wl.iters):
+            w = u + v
+            zx = 0.5 * (w[:k] - A.t() @ w[k:k + m])
+            zy = w[k:k + m] + A @ zx
+            tau = (w[-1] + ct @ zx + bt @ zy) / (1 + hp)
+            ut = torch.cat([zx - tau * px, zy - tau * py, tau.reshape(1)])
+            t = ut - v
+            Y = _smat_torch(t[k:k + m], 625)
+            ev, V = torch.linalg.eigh(Y)
+            P = (V * ev.clamp(min=0)) @ V.T
+            un = torch.cat([t[:k], P[torch.from_numpy(cc).to(dev), torch.from_numpy(r).to(dev)] * scale,
+                            t[-1:].clamp(min=0)])
+            v = v - ut + un
+            u = un
+        return wl.iters
+
     def run():
+        if wl.scs is not None:
+            return run_scs()
         if wl.mixing:
             return run_mixing()
         out = 0
@@ -692,6 +764,9 @@ def comparator(wl, xs, dev, stream, max_calls: int = 20):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    if wl.scs is not None:
+        return {"impl": "the same iterations in torch: matmuls + torch.linalg.eigh float64 projection",
+                "value": units / (ms * 1e-3), "unit": "SCS iterations/s", "sample": f"{units} iterations"}
     if wl.mixing:
         return {"impl": "torch.linalg.eigvalsh float64 per block + the same weight rule + mixed svec",
                 "value": units / (ms * 1e-3), "unit": "cones/s", "sample": f"{units} cones"}

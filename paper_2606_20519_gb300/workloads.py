@@ -269,3 +269,30 @@ def herm_admm_sequence(seed: int = SEED_BASE + 6, n: int = 625, steps: int = 50,
         X = X + step_scale * herm_gaussian(rng, n)
         out.append(to_hsvec(X))
     return out, U, lam
+
+
+def orthonormal_columns(rng: np.random.Generator, m: int, k: int) -> np.ndarray:
+    """First k columns of H1 H2 (two Householder reflectors of random
+    direction): an m x k matrix with orthonormal columns in O(m k) work.
+    Returned as a C-contiguous k x m array (the m x k matrix column-major)."""
+    w1, w2 = rng.standard_normal(m), rng.standard_normal(m)
+    B = np.zeros((k, m))
+    B[np.arange(k), np.arange(k)] = 1.0                      # rows of B = columns of E = I[:, :k]
+    B -= (2.0 / (w2 @ w2)) * np.outer(w2[:k], w2)            # H2 E
+    B -= (2.0 / (w1 @ w1)) * np.outer(B @ w1, w1)            # H1 H2 E
+    return B
+
+
+def scs_problem(seed: int = SEED_BASE + 7, n: int = 625, k: int = 1000):
+    """One PSD cone of side n (d = 5) in SCS form: A (m x k, orthonormal
+    columns, as a k x m array), b ~ N(0, 1/m) (svec), c ~ N(0, 1/k), and the
+    SCS initial iterates u = v = (0, 0, 1)."""
+    rng = rng_for(seed)
+    m = n * (n + 1) // 2
+    At = orthonormal_columns(rng, m, k)
+    b = rng.standard_normal(m) / np.sqrt(m)
+    c = rng.standard_normal(k) / np.sqrt(k)
+    u = np.zeros(k + m + 1)
+    u[-1] = 1.0
+    return At, b, c, u, u.copy()
+
