@@ -1406,7 +1406,7 @@ int do_call(scs_psd_handle h, const IoSlot& io, int mode, const int64_t* offsets
 // two-stage with b = 8, 16, 32), then the GEMM split-K target (1, 2, 4 CTAs
 // per SM), then -- when the winner has one-stage cones -- the slab width of
 // the fused back-transformation (2, 4, 8 columns) and the group size of the
-// one-stage reduction (all SMs or half).  Each candidate runs once to warm up
+// one-stage reduction (all SMs, half or a quarter).  Each candidate runs once to warm up
 // and three times under CUDA events on `stream`; candidates whose device
 // status is not clean are discarded.  The winner is kept in the handle for
 // these shapes and precision and used by later calls that leave opts->band 0.
@@ -1485,9 +1485,12 @@ int autotune(scs_psd_handle h, const double* x, const int64_t* offsets, const in
       t.bt1_cols = cols;
       consider(t);
     }
-    Tuning t = best;
-    t.sy_share = 2;
-    consider(t);
+    const Tuning base2 = best;
+    for (int share : {2, 4}) {
+      Tuning t = base2;
+      t.sy_share = share;
+      consider(t);
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
