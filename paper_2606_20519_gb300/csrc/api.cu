@@ -1986,6 +1986,10 @@ int scs_iterate(scs_psd_handle h, const double* A, const double* b, const double
     if (it != h->scs.end()) {
       sp = it->second.get();
     } else {
+      if (h->scs.size() >= 8) {
+        cudaDeviceSynchronize();
+        h->scs.clear();
+      }
       auto np = std::make_unique<ScsPlan>();
       np->m = m;
       np->k = k;

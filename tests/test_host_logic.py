@@ -1,0 +1,80 @@
+"""Host-side logic that needs no GPU: the synthetic input generators of the
+newer workloads and the bench's bookkeeping (groups of the mixing workload,
+the polynomial path's flop count)."""
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+from oracle import poly as P
+from paper_2606_20519_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_orthonormal_columns_and_scs_problem():
+    rng = W.rng_for(1)
+    B = W.orthonormal_columns(rng, 300, 25)  # rows of B are the columns of A
+    np.testing.assert_allclose(B @ B.T, np.eye(25), atol=1e-14)
+    At, b, c, u, v = W.scs_problem(n=12, k=7)
+    m = 12 * 13 // 2
+    assert At.shape == (7, m) and b.shape == (m,) and c.shape == (7,)
+    assert u.shape == v.shape == (7 + m + 1,) and u[-1] == 1.0 and v[-1] == 1.0
+    np.testing.assert_allclose(At @ At.T, np.eye(7), atol=1e-14)
+    # seeded: the same call gives the same problem
+    At2, b2, _, _, _ = W.scs_problem(n=12, k=7)
+    np.testing.assert_array_equal(At, At2)
+    np.testing.assert_array_equal(b, b2)
+
+
+def test_mixing_workload_groups():
+    wl = _bench().Workload("mixing")
+    sides = wl.calls[0][1]
+    g = wl.groups
+    assert g[0] == 0 and g[-1] == len(sides) and all(g[i] < g[i + 1] for i in range(len(g) - 1))
+    assert len(wl.nu) == len(g) - 1
+    for q in range(len(g) - 1):
+        blk = sides[g[q]:g[q + 1]]
+        assert len(set(blk)) == 1  # one side per group
+        n = blk[0]
+        if len(blk) == 2:  # two outcomes of an instrument block of side d^2
+            d = round(n ** 0.5)
+            assert d * d == n and wl.nu[q] == pytest.approx(1.0 / (2 * d))
+        else:  # a process block mixed with gamma * 1
+            assert len(blk) == 1 and wl.nu[q] == pytest.approx(1.0 / n)
+    assert wl.eps == 1e-16
+
+
+def test_poly_roofline_flop_count():
+    bench = _bench()
+
+    class FakeLib:
+        FP64 = 0
+        SPLIT_TF32 = 1
+
+        @staticmethod
+        def poly_schedule(lo, steps=0):
+            a, b, lk = P.poly_coeffs(lo, steps)
+            return np.array(a), np.array(b), lk
+
+    class Args:
+        poly_lo = 1e-9
+
+    class Wl:
+        calls = [(None, [625]), (None, [4096, 4096])]
+
+    K = len(P.poly_coeffs(1e-9)[0])
+    roof, info = bench.poly_roofline(FakeLib, Args, Wl, 1.0, FakeLib.FP64)
+    want = sum(K * 2.0 * n ** 3 + float(n) ** 3 for n in (625, 4096, 4096))
+    assert roof["flops_per_step"] == pytest.approx(want, rel=1e-12)
+    assert info["steps"] == K == 29
+    roof_s, _ = bench.poly_roofline(FakeLib, Args, Wl, 1.0, FakeLib.SPLIT_TF32)
+    assert roof_s["bound"] == "tensor" and roof_s["achieved"] == pytest.approx(8.0 * want / 1e-3 / 1e12)
