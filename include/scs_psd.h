@@ -164,7 +164,9 @@ int scs_psd_proj_hermitian(scs_psd_handle h, const double* x, double* y, const i
  * for the other calls; the remaining options are ignored.  ||x||_2^2 must
  * be finite (else the cone is marked SCS_PSD_ENONFINITE and its output is
  * NaN); x = 0 gives 0.  Per cone of side n the handle holds 4 n^2 doubles
- * for the shape list.  Returns SCS_PSD_EINVAL for lo or steps out of range. */
+ * for the shape list, and in split mode three sliced copies (9 n^2 floats)
+ * for a cone of side >= 64.  Returns SCS_PSD_EINVAL for lo or steps out of
+ * range. */
 int scs_psd_proj_poly(scs_psd_handle h, const double* x, double* y, const int64_t* offsets,
                       const int32_t* sides, int32_t count, double lo, int32_t steps,
                       const scs_psd_opts* opts, void* stream);
@@ -220,10 +222,11 @@ int scs_psd_mix_identity(scs_psd_handle h, const double* x, double* y, const int
  * parametrization has, App. D.3; not checked): the affine step is then
  * z_x = (a_x - A^T a_y)/2, z_y = a_y + A z_x, one product with A^T and one
  * with A.  b (m) and c (k) are DEVICE arrays (A and c may be NULL when
- * k = 0); u and v (k + m + 1 each,
- * DEVICE) are updated in place.  offsets/sides (host) describe the cones of
- * the y block, offsets[count] == m.  The projection runs with opts as in
- * scs_psd_proj_batched.  No acceleration, over-relaxation or rescaling. */
+ * k = 0); u and v (k + m + 1 each, DEVICE) are updated in place.
+ * offsets/sides (host) describe the cones of the y block, offsets[count] ==
+ * m.  p = M^{-1}(c, b) is recomputed on every call (two more products).  The
+ * projection runs with opts as in scs_psd_proj_batched; its device status is
+ * read with scs_psd_status.  No acceleration, over-relaxation or rescaling. */
 int scs_psd_scs_iterate(scs_psd_handle h, const double* A, const double* b, const double* c, int64_t m, int64_t k,
                         const int64_t* offsets, const int32_t* sides, int32_t count, double* u, double* v,
                         int32_t iters, const scs_psd_opts* opts, void* stream);
