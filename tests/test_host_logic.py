@@ -78,3 +78,30 @@ def test_poly_roofline_flop_count():
     assert info["steps"] == K == 29
     roof_s, _ = bench.poly_roofline(FakeLib, Args, Wl, 1.0, FakeLib.SPLIT_TF32)
     assert roof_s["bound"] == "tensor" and roof_s["achieved"] == pytest.approx(8.0 * want / 1e-3 / 1e12)
+
+
+def test_reference_arm_json_contract():
+    """bench.py --impl reference times the oracle and prints one JSON line
+    with the contract's keys (no GPU needed)."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config",
+                          "single81", "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["unit"] == "projections/s"
+
+
+def test_binding_lists_every_declared_entry_point():
+    import re
+    from paper_2606_20519_gb300 import _lib
+    text = open(os.path.join(ROOT, "include", "scs_psd.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|int32_t|int64_t|const char\*)\s+(scs_psd_\w+)\s*\(", text, re.M))
+    missing = declared - set(_lib.EXPORTS)
+    assert not missing, sorted(missing)
