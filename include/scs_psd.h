@@ -64,9 +64,12 @@ typedef enum {
   SCS_PSD_SPLIT_TF32 = 1  /* dense contractions as split-TF32 tensor-core products: FP64 operands
                              sliced on a grid shared by each 16-wide K chunk into three TF32 parts
                              (10 + 11 + 11 bits), six part products, the leading ones summed exactly
-                             in FP32, compensated FP32 sums across chunks (relative error of the
-                             projection about 2e-8); Householder panels, bulge chasing, secular
-                             equations and sign decisions stay FP64 */
+                             in FP32, compensated FP32 sums across chunks; contractions with K >= 256
+                             slice each operand once, on 64-wide K groups (9 + 11 + 11 bits, eight
+                             part products).  Relative error of the projection about 2e-8 to 7e-8;
+                             operands must lie within FP32's exponent range (magnitudes between about
+                             1e-35 and 1e38).  Householder panels, bulge chasing, secular equations
+                             and sign decisions stay FP64 */
 } scs_psd_precision;
 
 /* Options; a NULL pointer means all defaults (zero-initialised struct). */
