@@ -105,3 +105,39 @@ def test_binding_lists_every_declared_entry_point():
     declared = set(re.findall(r"^\s*(?:int|int32_t|int64_t|const char\*)\s+(scs_psd_\w+)\s*\(", text, re.M))
     missing = declared - set(_lib.EXPORTS)
     assert not missing, sorted(missing)
+
+
+def test_spectrum_recipes_match_the_documented_workloads():
+    """The spectra are what the input table states (counts and ranges)."""
+    rng = W.rng_for(5)
+    s = W.spectrum_plain(rng, 81)
+    assert (s > 0).sum() == 40 and (s < 0).sum() == 40 and (s == 0).sum() == 1
+    assert s[s > 0].min() >= 0.1 and s[s > 0].max() <= 2.0 and s[s < 0].max() <= -0.1
+    s = W.spectrum_admm(rng, 625)
+    assert s.size == 625
+    tiny, pos, neg = s[:300], s[300:500], s[500:]
+    assert np.abs(tiny).max() < 1e-5 and pos.min() >= 0.01 and pos.max() <= 1.0 and neg.max() <= -0.01
+    assert neg.size == 125
+    s = W.spectrum_precision(rng, 4096)
+    assert s.size == 4096 and np.abs(s[:2048]).max() <= 1.0 and np.abs(s[2048:3072]).max() < 1e-6
+    big = np.abs(s[3072:])
+    assert big.min() >= 1e-4 and big.max() <= 100.0
+    s = W.spectrum_vjp(rng, 1296)
+    assert (s == 1e-9).sum() == 65 and (s == -1e-9).sum() == 65
+    b = W.uneven_batch(restarts=2)
+    assert list(b.sides[:15]) == [4, 4, 9, 9, 16, 16, 25, 25, 36, 36, 49, 49, 64, 64, 625]
+    assert b.sides[29] == 1296 and b.count == 30
+
+
+def test_autograd_store_or_recompute_decision():
+    from paper_2606_20519_gb300 import _lib
+    from paper_2606_20519_gb300.autograd import stores_eigenpairs
+    sides = [625, 81]
+    nv, nl = _lib.eig_sizes(sides)
+    assert (nv, nl) == (625 * 625 + 81 * 81, 706)
+    need = 8 * (nv + nl)
+    assert stores_eigenpairs(sides)  # no options: keep
+    assert stores_eigenpairs(sides, _lib.make_opts(mem_budget_bytes=need))
+    assert not stores_eigenpairs(sides, _lib.make_opts(mem_budget_bytes=need - 1))
+    assert not stores_eigenpairs(sides, _lib.make_opts(recompute=1))
+    assert stores_eigenpairs(sides, _lib.make_opts(recompute=2, mem_budget_bytes=1))
