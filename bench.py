@@ -19,6 +19,12 @@ inputs in pinned host memory and the host<->device copies inside the timed
 region.  The dominant phase's roofline uses per-phase CUDA events recorded
 by the library on the same stream during the timed steps.
 
+The default run also measures the metric's other legs, keyed under "legs"
+in the same JSON line: n = 4096 x 4 forward and n = 1296 x 8 forward + VJP,
+each in FP64 and in the split precision (3 warm-up and 3 timed steps each,
+with their own comparator, roofline, error against the construction and
+clock record); --no-legs skips them.
+
 --impl reference times the FP64 CPU oracle (the plain cyclic-Jacobi
 implementation the tests pin) on the host cores, on a bounded sample of the
 same workload.  For N > 1 (torchrun) every rank runs an independent replica
@@ -71,6 +77,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-autotune", action="store_true",
                    help="skip the library's autotuner (launch shapes by default heuristics)")
+    p.add_argument("--no-legs", action="store_true",
+                   help="default run: skip the metric's other legs (n = 4096 forward, n = 1296 forward + VJP)")
     p.add_argument("--calls", type=int, default=0,
                    help="use only the first N calls of the workload per step (profiling runs)")
     return p.parse_args()
@@ -337,6 +345,13 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm
+# The metric's other legs (forward at n = 4096, forward + VJP at n = 1296, each
+# in FP64 and in the split precision), measured in the default single-GPU run
+# beside the headline n = 625 workload.
+LEGS = (("precision4096", "fp64"), ("precision4096", "split"), ("vjp1296", "fp64"), ("vjp1296", "split"))
+LEG_STEPS, LEG_WARMUP = 3, 3
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -350,14 +365,34 @@ def run_ours(args):
     from paper_2606_20519_gb300 import _lib as lib, build
     build.build()
     lib.load()
-    prec = lib.SPLIT_TF32 if args.precision == "split" else lib.FP64
+    env = (lib, dev, local, world, rank)
+    line = measure(args, env, args.config, args.precision, args.steps, args.warmup, full=True)
+    default_run = (args.config == "admm625" and args.method == "eig" and args.precision == "fp64"
+                   and not args.calls and not args.band)
+    if world == 1 and default_run and not args.no_legs:
+        line["legs"] = {f"{cfg}_{prec}": measure(args, env, cfg, prec, min(args.steps, LEG_STEPS),
+                                                 max(args.warmup, LEG_WARMUP), full=False)
+                        for cfg, prec in LEGS}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def measure(args, env, config, precision, steps, warmup, full):
+    """Time `steps` steps of one workload after `warmup` untimed ones and
+    return its JSON record (None on ranks other than 0).  full=False (a leg
+    of the default run): no autotuning, no e2e pass, no CPU baseline, the
+    comparator on one call."""
+    import torch
+    lib, dev, local, world, rank = env
+    prec = lib.SPLIT_TF32 if precision == "split" else lib.FP64
     opts = lib.make_opts(band=args.band, precision=prec) if (args.band or prec != lib.FP64) else None
     b_used = args.band or 16
-    poly = args.method == "poly"
-    if poly and (args.config in ("herm625", "vjp1296")):
+    poly = args.method == "poly" and full
+    if poly and (config in ("herm625", "vjp1296")):
         raise SystemExit("--method poly covers the real projection workloads (no Hermitian or derivative path)")
 
-    wl = Workload(args.config, args.calls)
+    wl = Workload(config, args.calls if full else 0)
     xs = [torch.from_numpy(x).to(dev) for x, _ in wl.calls]
     ys = [torch.empty_like(x) for x in xs]
     gs = [torch.from_numpy(wl.g).to(dev)] if wl.vjp else None
@@ -394,7 +429,7 @@ def run_ours(args):
 
     # launch shapes: the library's autotuner on the first call's input (setup, untimed)
     tuning = None
-    if not args.no_autotune and not args.band and not wl.herm and not poly and not wl.mixing and wl.scs is None:
+    if full and not args.no_autotune and not args.band and not wl.herm and not poly and not wl.mixing and wl.scs is None:
         tuning = lib.autotune(xs[0], shapes[0][1], opts=opts, offsets=shapes[0][0])
         if tuning["band"] >= 2:
             b_used = tuning["band"]
@@ -416,7 +451,7 @@ def run_ours(args):
         y0 = (yb if wl.vjp else ys[0])[: wl.svec_len(n0)].cpu().numpy()
         err0 = rel(y0, P)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step(xs, ys)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
@@ -424,7 +459,7 @@ def run_ours(args):
 
     def timed_steps():
         ms, launches = 0.0, 0
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.fill_(1.0)
             barrier()
             torch.cuda.synchronize()
@@ -454,10 +489,14 @@ def run_ours(args):
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
+    ms_per_step = total_ms / steps
     value = world * wl.units / (ms_per_step * 1e-3)
 
     # ---- e2e: host buffers, copies inside the timed region
+    if not full:
+        return None if rank != 0 else leg_record(args, wl, config, precision, steps, warmup, ms_per_step, value,
+                                                  phases, tuning, b_used, clk, status, err0, launches_per_step,
+                                                  traced_ms, xs, dev, stream, ys, yb)
     hx = [torch.from_numpy(x).pin_memory() for x, _ in wl.calls]
     hy = [torch.empty_like(h).pin_memory() for h in hx]
     hg = torch.from_numpy(wl.g).pin_memory() if wl.vjp else None
@@ -490,7 +529,7 @@ def run_ours(args):
     e2e_step()
     torch.cuda.synchronize()
     e2e_ms = 0.0
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.fill_(1.0)
         barrier()
         torch.cuda.synchronize()
@@ -507,36 +546,36 @@ def run_ours(args):
         t = torch.tensor([e2e_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
-    e2e_value = world * wl.units / (e2e_ms / args.steps * 1e-3)
+    e2e_value = world * wl.units / (e2e_ms / steps * 1e-3)
 
     if rank != 0:
-        return 0
+        return None
 
     unit = ("cones/s (lambda_min + mixing)" if wl.mixing else
             "SCS iterations/s" if wl.scs is not None else "projections/s")
     if poly:
         roofline, poly_info = poly_roofline(lib, args, wl, ms_per_step, prec)
     else:
-        roofline = eig_roofline(args, wl, phases, tuning, b_used)
+        roofline = eig_roofline(args, wl, phases, tuning, b_used, steps)
 
     line = {
-        "metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else
+        "metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if precision == "fp64" else
         ("f64 io, tf32x8 split products" if poly else "f64 io, tf32x6 split products"),
         "data": "synthetic (seeded PCG64), shaped like the paper's SCS iterates; no dataset",
-        "config": {"workload": wl.desc, "config": args.config, "method": poly_info if poly else "eigendecomposition",
+        "config": {"workload": wl.desc, "config": config, "method": poly_info if poly else "eigendecomposition",
                    "cones_per_step": wl.units, "band": None if poly else b_used,
-                   "precision": args.precision, "tuning": tuning,
+                   "precision": precision, "tuning": tuning,
                    "parallelism": f"replicas x{world}", "l2": "flushed before every timed step (256 MB write)"},
         "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": wl.bytes_in,
                 "d2h_bytes_per_step": wl.bytes_out},
-        "gpu_launches": int(launches_per_step * args.steps),
+        "gpu_launches": int(launches_per_step * steps),
         "timing": {"value": "K untraced steps (graph replay)",
                    "roofline": "phase CUDA events of a second, traced pass over the same K steps",
-                   "traced_ms_per_step": traced_ms / args.steps},
+                   "traced_ms_per_step": traced_ms / steps},
         "roofline": roofline,
-        "phases_ms_per_step": {k2: v[0] / args.steps for k2, v in phases.items() if v[1]},
+        "phases_ms_per_step": {k2: v[0] / steps for k2, v in phases.items() if v[1]},
         "clocks": clk,
         "status": int(status) if status == st else int(status),
         "max_rel_err_first_cone_vs_construction": err0,
@@ -548,11 +587,59 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": v, "unit": unit, "cores": cores, "kind": "oracle",
                                 "sample": f"{done} {'iterations' if wl.scs is not None else 'projections'} "
                                           f"(sides {sorted(set(sample))}) in {dt:.1f} s"}
-    print(json.dumps(line))
-    return 0
+    if wl.vjp:
+        line["max_rel_err_vjp_first_cone_vs_construction"] = vjp_construction_error(wl, ys[0])
+    return line
 
 
-def eig_roofline(args, wl, phases, tuning, b_used):
+def leg_record(args, wl, config, precision, steps, warmup, ms_per_step, value, phases, tuning, b_used, clk,
+               status, err0, launches_per_step, traced_ms, xs, dev, stream, ys, yb):
+    """The record of one leg of the default run: value, comparator, roofline,
+    error against the construction, clocks."""
+    unit = "projections/s" if not wl.vjp else "(projection + VJP)/s"
+    rec = {
+        "value": value, "unit": unit, "workload": wl.desc, "precision": precision, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms_per_step, "cones_per_step": wl.units,
+        "dtype": "f64" if precision == "fp64" else "f64 io, split-tf32 products",
+        "roofline": eig_roofline(args, wl, phases, tuning, b_used, steps),
+        "phases_ms_per_step": {k2: v[0] / steps for k2, v in phases.items() if v[1]},
+        "timing": {"value": "K untraced steps (graph replay)", "traced_ms_per_step": traced_ms / steps},
+        "gpu_launches": int(launches_per_step * steps),
+        "clocks": clk, "status": int(status),
+        "max_rel_err_first_cone_vs_construction": err0,
+        "l2": "flushed before every timed step (256 MB write)",
+    }
+    if wl.vjp:
+        rec["max_rel_err_vjp_first_cone_vs_construction"] = vjp_construction_error(wl, ys[0])
+    if not args.no_comparator:
+        rec["comparator"] = comparator(wl, xs, dev, stream, max_calls=1)
+    return rec
+
+
+def vjp_construction_error(wl, xbar_dev):
+    """Relative error of the first cone's VJP against the derivative formed
+    from the construction X = Q diag(lam) Q^T: Q (L o (Q^T G Q)) Q^T with the
+    Loewner matrix of max(., 0) (App. E's derivative through the
+    eigendecomposition; at eigenvalues +-1e-9 of opposite sign the computed
+    cross block is fixed only to about eps ||X|| / 2e-9 by any
+    backward-stable eigensolver)."""
+    Q, lam = wl.exact0
+    n = Q.shape[0]
+    ln = n * (n + 1) // 2
+    G = W_smat_host(wl.g[:ln], n)
+    lp = np.maximum(lam, 0.0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        L = (lp[:, None] - lp[None, :]) / (lam[:, None] - lam[None, :])
+    pos = lam > 0
+    L = np.where(pos[:, None] & pos[None, :], 1.0, L)
+    L = np.where(~pos[:, None] & ~pos[None, :], 0.0, L)
+    J = Q @ (L * (Q.T @ G @ Q)) @ Q.T
+    ref = W.to_svec(J)
+    got = xbar_dev[:ln].cpu().numpy()
+    return rel(got, ref)
+
+
+def eig_roofline(args, wl, phases, tuning, b_used, steps):
     """Roofline of the dominant traced phase of the eigendecomposition path
     (per-phase CUDA events on the launching stream)."""
     dom = max(phases.items(), key=lambda kv: kv[1][0])
@@ -571,11 +658,11 @@ def eig_roofline(args, wl, phases, tuning, b_used):
     flops_launch = sum(algorithmic_flops(dom_name, emb * int(s), emb * k, b_used, emb * kbt) for s in wl.calls[0][1])
     # per call: a phase may be traced as several segments within one call
     per_call = wl.iters if wl.scs is not None else 1  # projections per call (SCS: one per iteration)
-    avg_ms = dom_ms / max(1, args.steps * len(wl.calls) * per_call)
+    avg_ms = dom_ms / max(1, steps * len(wl.calls) * per_call)
     achieved = flops_launch / (avg_ms * 1e-3) / 1e9
     return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "peak_source": FP64_PEAK_NOTE,
                 "unit": "GFLOP/s FP64",
-                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": _traffic(args.config, dom_name),
+                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": _traffic(wl.name, dom_name),
                 "phase": dom_name, "kernel": phase_kernels(dom_name, n0, tuning["band"] if tuning else args.band),
                 "ms_per_launch": avg_ms, "flops_per_launch": flops_launch,
                 "share": dom_ms / max(1e-9, sum(v[0] for v in phases.values()))}

@@ -85,8 +85,33 @@ typedef struct {
   int64_t wait_limit_cycles;/* bound on device spin-waits; 0 = default */
   int32_t graphs;           /* 0 = replay a recorded CUDA graph from the second call with the same
                                shapes and options on, 1 = always launch kernel by kernel */
-  int32_t reserved;         /* must be 0 */
+  int32_t stats;            /* 1 = record per-cone statistics of the result (scs_psd_last_stats);
+                               only for calls that write y (scs_psd_proj, scs_psd_proj_batched,
+                               scs_psd_proj_vjp and scs_psd_proj_store with y, scs_psd_scs_iterate:
+                               its last projection); 0 = none */
 } scs_psd_opts;
+
+/* Per-cone statistics of a projection (opts->stats = 1), the error statement
+ * that comes with every result.  With Y the returned projection of X:
+ *   k_pos, k_neg     eigenvalues of X found > 0 and < 0 (FP64 sign decisions);
+ *   route            0: Y formed from the positive eigenpairs, 1: as X minus the
+ *                    negative part (Moreau decomposition, App. D.1);
+ *   status           the cone's device status (an SCS_PSD_* code);
+ *   complementarity  <Y, Y - X> / (||Y||_F ||X||_F) in FP64 from the svec
+ *                    buffers (the vec_R map is an isometry, App. D.1): the
+ *                    complementarity residual of the optimality conditions
+ *                    Y >= 0, Y - X >= 0, <Y, Y - X> = 0, which the exact
+ *                    projection satisfies (the PSD cone is self-dual).  With
+ *                    Y = Pi(X) + E it equals (<E, |X|> + ||E||^2) / (||Y|| ||X||),
+ *                    |X| = 2 Pi(X) - X: to first order the relative error's
+ *                    component along |X|.  0 when Y = 0 or X = 0;
+ *   norm_y, norm_x   ||Y||_F and ||X||_F.
+ * Side-0 cones report zeros; side-1 cones their sign. */
+typedef struct {
+  int32_t k_pos, k_neg, route, status;
+  double complementarity, norm_y, norm_x;
+  double reserved;
+} scs_psd_cone_stats;
 
 /* Create a handle on CUDA device `device`.  Allocates no device memory yet. */
 int scs_psd_create(scs_psd_handle* h, int device);
@@ -269,14 +294,17 @@ int scs_psd_vjp_stored(scs_psd_handle h, const double* V, const double* lam, con
  * device, y may alias x.  All workspace -- the plan's metadata, the
  * eigensolver's buffers and a status word -- lives in a file-scope
  * __device__ array of 16 MiB that every GPU loading the library holds until
- * exit.  The first call on a device (and the first call after a call of
- * another side) sets up: it takes the array's address with
- * cudaGetSymbolAddress and writes the plan into the array with
- * cudaMemcpyAsync on `stream`; make that first call before any stream
- * capture.  Every call shares the array and leaves the last call's contents
- * in it (the status word is cleared at the start of each call), so calls
- * that overlap on the GPU race: issue them on one stream, or synchronise
- * between them.  Device-side errors fill y with NaN; no handle is needed. */
+ * exit (side 256 takes about 8 MiB of it).  Set-up happens on the first call
+ * on a device, which takes the array's address with cudaGetSymbolAddress,
+ * and on every call whose side differs from the previous call's on that
+ * device, which writes that side's plan into the array with cudaMemcpyAsync
+ * on `stream`: such calls must not be issued while `stream` is being
+ * captured (they return SCS_PSD_EINVAL then, having enqueued nothing).  A
+ * plan that does not fit the array returns SCS_PSD_ENOMEM.  Every call
+ * shares the array and leaves the last call's contents in it (the status
+ * word is cleared at the start of each call), so calls that overlap on the
+ * GPU race: issue them on one stream, or synchronise between them.
+ * Device-side errors fill y with NaN; no handle is needed. */
 int scs_psd_proj_static(const double* x, double* y, int64_t n, void* stream);
 
 /* Autotuner (launch shapes are the project's own choice; the paper fixes
@@ -305,6 +333,15 @@ int scs_psd_last_tuning(scs_psd_handle h, int32_t* out);
  * for max_count 1, scs_psd_proj) with exactly these shapes and options
  * allocates nothing.  Other shape lists are planned on their first call. */
 int scs_psd_reserve(scs_psd_handle h, int64_t max_n, int32_t max_count, const scs_psd_opts* opts);
+
+/* Statistics of the last call made on this handle with opts->stats = 1:
+ * synchronises its stream and copies `count` records (the call's number of
+ * cones, in its order) into the caller's HOST array `out`.  SCS_PSD_EINVAL
+ * if no such call was made, if count differs from its cone count, or if the
+ * handle's cached plans were dropped since (more than 16 shape lists, or
+ * scs_psd_autotune).  A call with opts->stats costs one copy of the input and
+ * one read of the input and the output (3 x 8 bytes per svec entry) more. */
+int scs_psd_last_stats(scs_psd_handle h, scs_psd_cone_stats* out, int32_t count);
 
 /* Synchronise the handle's last stream and return the device status of the
  * work enqueued since the previous call (an SCS_PSD_* code, OK if none). */

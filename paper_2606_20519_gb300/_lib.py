@@ -28,7 +28,13 @@ class ScsPsdError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("side", ctypes.c_int32), ("recompute", ctypes.c_int32),
                 ("band", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64),
-                ("wait_limit_cycles", ctypes.c_int64), ("graphs", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("wait_limit_cycles", ctypes.c_int64), ("graphs", ctypes.c_int32), ("stats", ctypes.c_int32)]
+
+
+class ConeStats(ctypes.Structure):
+    _fields_ = [("k_pos", ctypes.c_int32), ("k_neg", ctypes.c_int32), ("route", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("complementarity", ctypes.c_double), ("norm_y", ctypes.c_double),
+                ("norm_x", ctypes.c_double), ("reserved", ctypes.c_double)]
 
 
 _lib = None
@@ -40,7 +46,7 @@ EXPORTS = ("scs_psd_create", "scs_psd_destroy", "scs_psd_proj", "scs_psd_proj_ba
            "scs_psd_last_replayed", "scs_psd_strerror", "scs_psd_trace", "scs_psd_trace_read",
            "scs_psd_autotune", "scs_psd_last_tuning", "scs_psd_proj_hermitian", "scs_psd_proj_poly",
            "scs_psd_poly_schedule", "scs_psd_proj_poly_hermitian", "scs_psd_lambda_min", "scs_psd_mix_identity",
-           "scs_psd_scs_iterate")
+           "scs_psd_scs_iterate", "scs_psd_last_stats")
 NPHASES = 8
 PHASES = ("unpack", "dense_to_band", "band_to_tridiag", "tridiag_dc", "backtransform_2", "backtransform_1",
           "reconstruct", "derivative")
@@ -82,6 +88,7 @@ def load(path: str | None = None):
         lib.scs_psd_autotune.argtypes = [vp, vp, vp, vp, i32, op, vp, ctypes.POINTER(i32),
                                          ctypes.POINTER(ctypes.c_double)]
         lib.scs_psd_last_tuning.argtypes = [vp, ctypes.POINTER(i32)]
+        lib.scs_psd_last_stats.argtypes = [vp, ctypes.POINTER(ConeStats), i32]
         lib.scs_psd_last_replayed.argtypes = [vp]
         lib.scs_psd_last_replayed.restype = ctypes.c_int
         lib.scs_psd_trace.argtypes = [vp, ctypes.c_int]
@@ -120,8 +127,9 @@ def handle(device: int):
 
 
 def make_opts(precision: int = FP64, side: int = 0, band: int = 0, wait_limit_cycles: int = 0,
-              recompute: int = 0, mem_budget_bytes: int = 0, graphs: bool = True) -> Opts:
-    return Opts(precision, side, recompute, band, mem_budget_bytes, wait_limit_cycles, 0 if graphs else 1, 0)
+              recompute: int = 0, mem_budget_bytes: int = 0, graphs: bool = True, stats: bool = False) -> Opts:
+    return Opts(precision, side, recompute, band, mem_budget_bytes, wait_limit_cycles, 0 if graphs else 1,
+                1 if stats else 0)
 
 
 def _ptr(t):
@@ -446,6 +454,16 @@ def status(device: int = 0) -> int:
     v = ctypes.c_int32(0)
     _check(load().scs_psd_status(handle(device), ctypes.byref(v)), "scs_psd_status")
     return int(v.value)
+
+
+STATS_FIELDS = ("k_pos", "k_neg", "route", "status", "complementarity", "norm_y", "norm_x")
+
+
+def last_stats(count: int, device: int = 0) -> list[dict]:
+    """Per-cone statistics of the last call made with make_opts(stats=True) (C-ABI scs_psd_last_stats)."""
+    out = (ConeStats * max(1, int(count)))()
+    _check(load().scs_psd_last_stats(handle(device), out, int(count)), "scs_psd_last_stats")
+    return [{f: getattr(out[i], f) for f in STATS_FIELDS} for i in range(int(count))]
 
 
 def last_launch_count(device: int = 0) -> int:

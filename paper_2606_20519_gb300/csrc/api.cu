@@ -123,16 +123,26 @@ struct Plan {
   // Recorded launch sequences, one per output mode (MODE_* bits),
   // with the wait limit they were recorded with.
   int64_t eager_runs = 0;
-  cudaGraphExec_t gexec[32] = {};
-  long long gwait[32] = {};
-  int64_t glaunches[32] = {};
-  bool gfailed[32] = {};
+  cudaGraphExec_t gexec[kModes] = {};
+  long long gwait[kModes] = {};
+  int64_t glaunches[kModes] = {};
+  bool gfailed[kModes] = {};
   bool arena_owned = false;  // memory carved from a caller-provided region (not freed here)
+  // per-cone statistics (allocated by the first call that asks for them)
+  void* stats_mem = nullptr;
+  StatsCone* stats_cones_d = nullptr;
+  int* stats_part_cone_d = nullptr;
+  double* stats_part_d = nullptr;
+  double* stats_xs_d = nullptr;
+  ConeStats* stats_out_d = nullptr;
+  int stats_nparts = 0;
+  int64_t stats_total = 0;
   ~Plan() {
     for (cudaGraphExec_t ge : gexec)
       if (ge) cudaGraphExecDestroy(ge);
     if (!arena_owned && cone_mem) cudaFree(cone_mem);
     if (!arena_owned && meta_mem) cudaFree(meta_mem);
+    if (stats_mem) cudaFree(stats_mem);
   }
 };
 
@@ -233,6 +243,8 @@ struct scs_psd_handle_s {
   int* status_word = nullptr;  // device
   cudaStream_t last_stream = nullptr;
   int64_t last_launches = 0;
+  std::string last_stats_key;  // plan of the last call that recorded statistics ("" if none)
+  int32_t last_stats_count = 0;
   std::map<std::string, std::unique_ptr<Plan>> plans;
   std::map<std::string, Tuning> tuned;  // autotuner's choices by shapes and precision
   std::map<std::string, std::unique_ptr<HermPlan>> herm;  // Hermitian shape lists
@@ -285,7 +297,7 @@ ConeLayout cone_layout(int64_t n, int b, int path) {
       d * std::max<int64_t>((int64_t)P * b * b, (int64_t)Q * kSy1Block * kSy1Block),
       d * n * bw, d * n * bw + d * 2048, d * n * 3 * b, d * b * b, d * b * b, d * n * n, d * n * n, d * n, d * n,
       d * n * n, d * n * n, d * n * n, d * n, d * n, d * n, d * n, d * n, d * n, d * 2 * n, d * n, d * n,
-      i4 * n, i4 * n, i4 * 2 * n, i4 * n, i4 * n, i4 * 4 * n, i4 * 8, d * n};
+      i4 * n, i4 * n, i4 * 2 * n, i4 * n, i4 * n, i4 * 4 * n, i4 * 16, d * n};
   size_t o = 0;
   for (int f = 0; f < F_NFIELDS; ++f) {
     o = align_up(o);
@@ -540,7 +552,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   if (cone_bytes) {
     if (arena) {
       P.arena_owned = true;
-      if (!(P.cone_mem = arena->take(cone_bytes))) return SCS_PSD_EINVAL;
+      if (!(P.cone_mem = arena->take(cone_bytes))) return SCS_PSD_ENOMEM;
     } else if (cudaMalloc(&P.cone_mem, cone_bytes) != cudaSuccess) {
       return SCS_PSD_ENOMEM;
     }
@@ -957,7 +969,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   const size_t total = cones_b + ints_b + descs_b + nodes_b + triv_b + scratch_b + io_b + sjobs_b + slice_b;
   if (arena) {
     P.arena_owned = true;
-    if (!(P.meta_mem = arena->take(total))) return SCS_PSD_EINVAL;
+    if (!(P.meta_mem = arena->take(total))) return SCS_PSD_ENOMEM;
   } else if (cudaMalloc(&P.meta_mem, total) != cudaSuccess) {
     return SCS_PSD_ENOMEM;
   }
@@ -1082,6 +1094,12 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
   PhaseMark pm{h, s};
   CUDA_TRY(cudaMemsetAsync(P.status_d, 0, sizeof(int) * (P.ncones + 1), s));
   if (P.prog_count) CUDA_TRY(cudaMemsetAsync(P.prog_d, 0, sizeof(int) * P.prog_count, s));
+  if (mode & MODE_STATS) {
+    // the input as it was (y may alias x)
+    if (!P.stats_mem) return SCS_PSD_EINVAL;
+    launch_stats_save_x(io, P.stats_xs_d, P.stats_total, s);
+    LAUNCH_CHECK();
+  }
   if (P.ntriv) {
     launch_trivial(P.triv_offs_d, P.ntriv, io, mode, P.status_d, s);
     LAUNCH_CHECK();
@@ -1231,8 +1249,56 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
     }
   }
   pm.end();
+  if (mode & MODE_STATS) {
+    launch_stats(P.stats_cones_d, (int)P.sides.size(), P.stats_part_cone_d, P.stats_nparts, P.cones_d, P.status_d,
+                 P.stats_xs_d, io, P.stats_part_d, P.stats_out_d, s);
+    n_launch += P.stats_nparts > 0 ? 1 : 0;
+    LAUNCH_CHECK();
+  }
   launch_status_reduce(P.status_d, P.ncones + 1, h->status_word, s);
   LAUNCH_CHECK();
+  return SCS_PSD_OK;
+}
+
+// Device buffers of the per-cone statistics of a plan: the call's cone table,
+// the partial sums, a copy of the input and the output records.
+int ensure_stats(Plan& P) {
+  if (P.stats_mem) return SCS_PSD_OK;
+  const int count = (int)P.sides.size();
+  std::vector<StatsCone> sc(count);
+  std::vector<int> pc;
+  int big = 0;
+  for (int i = 0; i < count; ++i) {
+    StatsCone& c = sc[i];
+    c.off = P.offsets[i];
+    c.len = P.offsets[i + 1] - P.offsets[i];
+    c.side = P.sides[i];
+    c.cone = P.sides[i] >= 2 ? big++ : -1;
+    c.part0 = (int)pc.size();
+    c.nparts = (int)((c.len + kStatsChunk - 1) / kStatsChunk);
+    for (int q = 0; q < c.nparts; ++q) pc.push_back(i);
+  }
+  P.stats_nparts = (int)pc.size();
+  P.stats_total = P.offsets[count];
+  const size_t sc_b = align_up(sizeof(StatsCone) * std::max(1, count));
+  const size_t pc_b = align_up(sizeof(int) * std::max<size_t>(1, pc.size()));
+  const size_t part_b = align_up(3 * sizeof(double) * std::max<size_t>(1, pc.size()));
+  const size_t xs_b = align_up(sizeof(double) * (size_t)std::max<int64_t>(1, P.stats_total));
+  const size_t out_b = align_up(sizeof(ConeStats) * std::max(1, count));
+  if (cudaMalloc(&P.stats_mem, sc_b + pc_b + part_b + xs_b + out_b) != cudaSuccess) {
+    P.stats_mem = nullptr;
+    return SCS_PSD_ENOMEM;
+  }
+  char* b = (char*)P.stats_mem;
+  P.stats_cones_d = (StatsCone*)b;
+  P.stats_part_cone_d = (int*)(b + sc_b);
+  P.stats_part_d = (double*)(b + sc_b + pc_b);
+  P.stats_xs_d = (double*)(b + sc_b + pc_b + part_b);
+  P.stats_out_d = (ConeStats*)(b + sc_b + pc_b + part_b + xs_b);
+  if (cudaMemcpy(P.stats_cones_d, sc.data(), sizeof(StatsCone) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
+      (!pc.empty() &&
+       cudaMemcpy(P.stats_part_cone_d, pc.data(), sizeof(int) * pc.size(), cudaMemcpyHostToDevice) != cudaSuccess))
+    return SCS_PSD_ECUDA;
   return SCS_PSD_OK;
 }
 
@@ -1372,8 +1438,13 @@ int do_call(scs_psd_handle h, const IoSlot& io, int mode, const int64_t* offsets
   long long wait = kDefaultWaitCycles;
   if (opts) {
     if (opts->precision != SCS_PSD_FP64 && opts->precision != SCS_PSD_SPLIT_TF32) return SCS_PSD_EINVAL;
-    if (opts->graphs < 0 || opts->graphs > 1 || opts->reserved != 0) return SCS_PSD_EINVAL;
+    if (opts->graphs < 0 || opts->graphs > 1 || opts->stats < 0 || opts->stats > 1) return SCS_PSD_EINVAL;
     if (opts->band < 0 || opts->band > kMaxBand) return SCS_PSD_EINVAL;
+    if (opts->stats) {
+      // statistics describe a projection's result: the call must write y
+      if (!(mode & MODE_Y)) return SCS_PSD_EINVAL;
+      mode |= MODE_STATS;
+    }
     precision = opts->precision;
     side = opts->side;
     if (opts->wait_limit_cycles > 0) wait = opts->wait_limit_cycles;
@@ -1393,11 +1464,16 @@ int do_call(scs_psd_handle h, const IoSlot& io, int mode, const int64_t* offsets
   Plan* P = nullptr;
   rc = get_plan(h, sides, count, allv, side, precision, tune, &P);
   if (rc) return rc;
+  if ((mode & MODE_STATS) && (rc = ensure_stats(*P))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   rc = run_plan(h, *P, io, mode, wait, s, !(opts && opts->graphs == 1));
   h->last_stream = s;
   h->last_launches = P->launches;
   h->last_tune = P->tune;
+  if (mode & MODE_STATS) {
+    h->last_stats_key = rc == SCS_PSD_OK ? P->key : std::string();
+    h->last_stats_count = count;
+  }
   return rc;
 }
 
@@ -1521,6 +1597,7 @@ int proj_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* 
                    int32_t count, const scs_psd_opts* opts, void* stream, double poly_lo = 0.0,
                    int32_t poly_steps = 0) {
   if (!h || count < 0) return SCS_PSD_EINVAL;
+  if (opts && opts->stats) return SCS_PSD_EINVAL;  // statistics are kept for real cones only
   if (count == 0) return SCS_PSD_OK;
   if (!offsets || !sides || offsets[0] != 0) return SCS_PSD_EINVAL;
   for (int i = 0; i < count; ++i) {
@@ -1830,7 +1907,7 @@ int proj_poly(scs_psd_handle h, const double* x, double* y, const int64_t* offse
   bool graphs = true;
   if (opts) {
     if (opts->precision != SCS_PSD_FP64 && opts->precision != SCS_PSD_SPLIT_TF32) return SCS_PSD_EINVAL;
-    if (opts->graphs < 0 || opts->graphs > 1 || opts->reserved != 0) return SCS_PSD_EINVAL;
+    if (opts->graphs < 0 || opts->graphs > 1 || opts->stats != 0) return SCS_PSD_EINVAL;
     precision = opts->precision;
     graphs = opts->graphs == 0;
   }
@@ -2055,6 +2132,14 @@ int proj_static(const double* x, double* y, int64_t n, void* stream) {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SCS_PSD_ECUDA;
   std::lock_guard<std::mutex> lock(g_static_mu);
   StaticDeviceState& st = g_static_state[dev];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!st.ready || st.plan_n != n) {
+    // set-up (the array's address, the plan copied in from host memory) is
+    // not a stream operation that a capture could record
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cst) != cudaSuccess) return SCS_PSD_ECUDA;
+    if (cst != cudaStreamCaptureStatusNone) return SCS_PSD_EINVAL;
+  }
   if (!st.ready) {
     // once per device, with that device current: the array's device address
     void* p = nullptr;
@@ -2065,7 +2150,6 @@ int proj_static(const double* x, double* y, int64_t n, void* stream) {
     st.hview.status_word = reinterpret_cast<int*>(st.base);  // first 256 bytes
     st.ready = true;
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (st.plan_n != n) {
     st.plan.reset();
     st.plan_n = -1;
@@ -2260,6 +2344,20 @@ int scs_psd_status(scs_psd_handle h, int32_t* device_status) {
   else if (v & ST_NOCONV) code = SCS_PSD_ENOCONV;
   else if (v & ST_NONFINITE) code = SCS_PSD_ENONFINITE;
   *device_status = code;
+  return SCS_PSD_OK;
+}
+
+int scs_psd_last_stats(scs_psd_handle h, scs_psd_cone_stats* out, int32_t count) {
+  if (!h || !out || count < 0) return SCS_PSD_EINVAL;
+  std::lock_guard<std::mutex> lock(h->mu);
+  if (h->last_stats_key.empty() || count != h->last_stats_count) return SCS_PSD_EINVAL;
+  auto it = h->plans.find(h->last_stats_key);
+  if (it == h->plans.end() || !it->second->stats_out_d) return SCS_PSD_EINVAL;
+  if (count == 0) return SCS_PSD_OK;
+  static_assert(sizeof(ConeStats) == sizeof(scs_psd_cone_stats), "statistics record layout");
+  if (cudaSetDevice(h->device) != cudaSuccess || cudaStreamSynchronize(h->last_stream) != cudaSuccess ||
+      cudaMemcpy(out, it->second->stats_out_d, sizeof(ConeStats) * count, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SCS_PSD_ECUDA;
   return SCS_PSD_OK;
 }
 

@@ -698,6 +698,8 @@ __global__ void __launch_bounds__(kDcThreads) dc_select_kernel(const ConeDev* __
     c.kinfo[1] = route;
     c.kinfo[2] = kr;
     c.kinfo[5] = r_lo;
+    c.kinfo[8] = sh_pos;
+    c.kinfo[9] = sh_neg;
   }
 }
 

@@ -143,7 +143,8 @@ struct ConeDev {
   int* icnt;        // 4n    per merge node: kept, deflated, rotations, kept-of-root (indexed by start)
   int* kinfo;       // [0] k kept, [1] route (0: positive part, 1: X - negative part), [2] kept secular
                     // roots, [3] keep all eigenpairs (derivative), [4] side option, [5] first kept root,
-                    // [6] all-pairs mode: |S|, the pairs of the route's side, which come first
+                    // [6] all-pairs mode: |S|, the pairs of the route's side, which come first,
+                    // [8] eigenvalues > 0, [9] eigenvalues < 0 (16 ints)
   int* status;      // per-cone status bits
   double* tau1;     // n     tau of the one-stage reflectors (read by larft1 while the divide and conquer runs)
   int cidx;         // position of the cone in the call's shape list
@@ -178,7 +179,27 @@ enum : int {
   MODE_EXPORT = 4,  // write the eigendecomposition to io->V, io->lam
   MODE_IMPORT = 8,  // take the eigendecomposition from io->V, io->lam instead of computing it
   MODE_LMIN = 16,   // io->lam[i] = smallest eigenvalue of cone i (stops at the tridiagonal form)
+  MODE_STATS = 32,  // per-cone statistics of the result (with MODE_Y)
 };
+constexpr int kModes = 64;
+
+// ------------------------------------------------------------------ statistics
+// Per-cone statistics of a call (layout of scs_psd_cone_stats in the ABI).
+struct ConeStats {
+  int k_pos, k_neg, route, status;
+  double complementarity, norm_y, norm_x, reserved;
+};
+constexpr int kStatsChunk = 32768;  // svec entries per partial sum
+// One cone of the call's shape list: its svec range, its device cone (-1 for
+// sides 0 and 1) and its partial sums [part0, part0 + nparts).
+struct StatsCone {
+  int64_t off, len;
+  int cone, side, part0, nparts;
+};
+void launch_stats_save_x(const IoSlot* io, double* xs, int64_t total, cudaStream_t s);
+void launch_stats(const StatsCone* sc, int count, const int* part_cone, int nparts, const ConeDev* cones,
+                  const int* triv_status, const double* xs, const IoSlot* io, double* part, ConeStats* out,
+                  cudaStream_t s);
 
 // ------------------------------------------------------------------ kernels
 void launch_set_io(IoSlot* slot, const IoSlot& v, cudaStream_t s);

@@ -74,3 +74,14 @@ def test_poly_schedule_matches_the_oracle(lib):
     for lo, steps in ((0.0, 0), (1.0, 0), (1e-3, -1), (1e-3, 201)):
         with pytest.raises(L.ScsPsdError):
             L.poly_schedule(lo, steps)
+
+
+def test_stats_record_layout_and_null_handle(lib):
+    """The binding's records match the header's layout (four int32 and four
+    doubles; the options struct keeps its size with the stats field), and
+    statistics are refused without a handle."""
+    from paper_2606_20519_gb300 import _lib
+    assert ctypes.sizeof(_lib.ConeStats) == 48
+    assert ctypes.sizeof(_lib.Opts) == 40
+    out = (_lib.ConeStats * 1)()
+    assert lib.scs_psd_last_stats(None, out, 1) == _lib.EINVAL
