@@ -1,23 +1,35 @@
 // One-stage Householder tridiagonalisation for cones whose trailing matrix
-// stays in L2 (the medium sizes of the paper's process-matrix step), in a
-// single persistent cooperative kernel.
+// stays in shared memory or L2 (the medium sizes of the paper's
+// process-matrix step), in a single persistent cooperative kernel.
 //
 // CTA r of a cone's group of G CTAs owns the columns i with i mod G = r for
 // the whole reduction (both triangles are kept, so a column is contiguous).
-// Per column j there is one group barrier: before it each CTA has written
-// p_i = tau_j A(j+1:, i)^T v_j for its columns; after it every CTA forms
-// w_j, updates column j+1 itself (from its stored value, v_j and w_j) and
-// forms reflector j+1 redundantly -- the same arithmetic in every CTA, so
-// no column has to be handed from its owner -- and then makes one fused
-// pass over its own columns: the rank-2 update of step j and the products
-// p_i of step j+1.  Work items are (column, 256-row chunk) pairs spread over
-// all warps, each lane keeping 8 loads in flight.  d, e, tau and the
-// reflectors (packed into 32-column blocks with their unit diagonal and
-// zeros, ready for the blocked back-transformation) are written as they are
-// formed.  Group barriers are counters in global memory with release/acquire
-// ordering and a bounded wait (ST_TIMEOUT on expiry); the launch is
-// cooperative, so every CTA is resident.  Data written by other CTAs is read
-// with ld.global.cg (L2).
+// Step j (reflector H_j = I - tau_j v v^T from column j, v indexed from row
+// j+1, m = n - j - 1 entries, v_0 = 1) needs p = tau_j A22 v, whose entries
+// the owners of the columns produce, and column j+1 as the previous step
+// left it.  Both are published into a write-once slab of step j (2m
+// doubles) that holds a sentinel NaN until the value arrives: a reader polls
+// the values themselves, so there is no group barrier per column -- a CTA
+// starts step j as soon as the last value it needs has landed in L2.  After
+// the poll every CTA, redundantly (the same arithmetic in each, so no column
+// is handed over):
+//     K = (tau_j / 2) p^T v,
+//     column j+1 updated by step j:  a_t - p_t - v_t (p_0 - 2K),
+//     reflector j+1 from it (its sum of squares here; beta, tau, 1/(x_0 - beta)
+//     by one thread while the pass below runs);
+// then one fused pass over its own columns i >= j+2 applies the rank-2 update
+//     A(r, i) -= v_r (p_i - 2K v_i) + p_r v_i        (= v w^T + w v^T, w = p - K v)
+// and forms the next step's p_i = tau_{j+1} u^T A(j+2:, i) (one read and one
+// write of A), publishing p_i and, from the owner of column j+2, that
+// column.  Work items are (column, chunk) pairs spread over all warps.
+// d, e, tau and the reflectors (packed into 32-column blocks with their unit
+// diagonal and zeros, ready for the blocked back-transformation) are written
+// as they are formed.  The slabs live in the cone's D&C buffer QA (n^2
+// doubles, unused until the divide and conquer); every CTA fills its share
+// with the sentinel and one group barrier (release/acquire counters) orders
+// the fill before the first publication.  Every wait is bounded
+// (ST_TIMEOUT on expiry); the launch is cooperative, so every CTA is
+// resident.
 //
 // larft1_kernel then forms, for every 32-reflector block, the triangular
 // factor T of H_0 ... H_31 = I - V T V^T.
@@ -31,6 +43,9 @@ namespace {
 
 constexpr int kSyThreads = 256;
 constexpr int kNb = kSy1Block;
+// A NaN whose payload arithmetic never produces (NaN results carry the
+// canonical payload, and the matrix entering the kernel is finite).
+constexpr long long kSentinel = (long long)0xFFF5A5A5A5A5A5A5ull;
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -38,27 +53,44 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-__device__ double block_sum256(double v, double* red) {
+// Published values: single-copy-atomic 8-byte stores and loads at GPU scope.
+__device__ __forceinline__ void st_pub(double* p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ double ld_pub(const double* p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ bool pending(double v) { return __double_as_longlong(v) == kSentinel; }
+
+// Slab of step j: P_j (p_{j+1} .. p_{n-1}), then C_j (column j+1, rows j+1 ..).
+__device__ __forceinline__ double* slab(double* base, int n, int j) {
+  return base + (int64_t)2 * j * (n - 1) - (int64_t)j * (j - 1);
+}
+
+// Sum over the CTA; every thread gets the same value (pairwise, in the same
+// order).  red is [2][8]: reductions alternate halves, so the write of one
+// cannot overtake the reads of the previous one.
+__device__ double block_sum256(double v, double* red, int& parity) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double* r = red + 8 * parity;
+  parity ^= 1;
+  if (lane == 0) r[w] = v;
   __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  // pairwise (3 dependent adds instead of 7), the same order in every thread
   static_assert(kSyThreads == 256, "tree below sums 8 warps");
-  return ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
+  return ((r[0] + r[1]) + (r[2] + r[3])) + ((r[4] + r[5]) + (r[6] + r[7]));
 }
 
 // Barrier over the G CTAs of one cone with its arrivals spread over 8
-// counters (CTA r adds to counter r mod 8, 128 bytes apart) so that the
-// atomics do not queue on one address; threads 0..7 each wait for one
-// counter.  Returns false (in every thread) when a wait ran out.
+// counters (CTA r adds to counter r mod 8, 128 bytes apart); threads 0..7
+// each wait for one counter.  Returns false (in every thread) when a wait
+// ran out.
 constexpr int kBarLanes = 8, kBarStride = 32;
 __device__ bool group_barrier8(int* counters, int rank, int G, int step, long long limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    // release-ordered arrival without waiting for a reply (the CTA's writes,
-    // ordered before this by the CTA barrier, become visible first)
     asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(counters + kBarStride * (rank % kBarLanes)),
                  "r"(1)
                  : "memory");
@@ -79,16 +111,16 @@ __device__ bool group_barrier8(int* counters, int rank, int G, int step, long lo
   return __syncthreads_and(ok) != 0;
 }
 
-constexpr int kChunk = 256;   // rows per work item (32 lanes x 8 loads in flight)
 constexpr int kPartMax = 2048; // work items per round (shared-memory partial sums)
 constexpr size_t kSyResidentMax = 200 * 1024;  // dynamic shared memory of a launch, at most
 
 // Householder reflector of x[0 .. len-1] in place (every thread of the CTA
 // calls it; x in shared memory): H x = beta e_1 with H = I - tau u u^T,
 // u_0 = 1 (LAPACK convention).  x becomes u; tau and beta are returned.
-// ps: this thread's part of sum_{t >= 1} x[t]^2 (the caller's loop formed it).
-__device__ double make_reflector_ps(double* x, int len, double ps, double* red, double* sh, double* beta_out) {
-  const double sigma = block_sum256(ps, red);
+__device__ double make_reflector(double* x, int len, double* red, int& parity, double* sh, double* beta_out) {
+  double ps = 0.0;
+  for (int t = 1 + threadIdx.x; t < len; t += kSyThreads) ps = fma(x[t], x[t], ps);
+  const double sigma = block_sum256(ps, red, parity);
   if (threadIdx.x == 0) {
     const double alpha = x[0];
     double beta = alpha, tau = 0.0, scal = 0.0;
@@ -107,12 +139,6 @@ __device__ double make_reflector_ps(double* x, int len, double ps, double* red, 
   if (threadIdx.x == 0) x[0] = 1.0;
   *beta_out = sh[0];
   return sh[1];
-}
-
-__device__ double make_reflector(double* x, int len, double* red, double* sh, double* beta_out) {
-  double ps = 0.0;
-  for (int t = 1 + threadIdx.x; t < len; t += kSyThreads) ps = fma(x[t], x[t], ps);
-  return make_reflector_ps(x, len, ps, red, sh, beta_out);
 }
 
 // Reflector j (u = scal * x, x indexed from row j+1) into its 32-column
@@ -134,22 +160,21 @@ __device__ void store_reflector(const ConeDev& c, int n, int j, const double* u,
 }
 
 // One pass over this CTA's columns i >= r0 (i mod G = rank), rows r0 .. n-1:
-// with UPDATE, first A(r, i) -= v_r w_i + w_r v_i (vu, wu indexed from row
-// r0 - 1); then p_i = coef[0] (A(r0, i) + coef[1] sum_{r > r0} A(r, i) x_r)
-// into pbuf[i], x indexed from row r0.  The next reflector is u = coef[1] x
-// with u_0 = 1, so p_i = tau u^T A(r0:, i) without x having been rescaled;
-// coef is read only after the pass's first barrier, so the reflector's
-// scalars may still be in the making (by thread 0) while the pass starts.
-// Work items are (column, CH-row chunk) pairs spread over the warps (CH = 128
-// for small cones, whose columns are short, else 256: 8 loads per lane).
-// RES: this CTA's columns live in shared memory (cols, column i at
-// ((i - rank) / G) * n); the owner of column r0 -- the next reflector's
-// source -- also writes its updated rows to A for every CTA to read.
+// with UPDATE, first A(r, i) -= v_r (p_i - 2K v_i) + p_r v_i (vu, pu indexed
+// from row r0 - 1); then p_i = coef[0] (A(r0, i) + coef[1] sum_{r > r0} A(r, i) x_r)
+// published to Pn[i - r0], x indexed from row r0.  The next reflector is
+// u = coef[1] x with u_0 = 1, so p_i = tau u^T A(r0:, i) without x having
+// been rescaled; coef is read only after the pass's first barrier, so the
+// reflector's scalars may still be in the making (by thread 0) while the
+// pass starts.  The owner of column r0 -- the next reflector's source --
+// publishes its rows to Cn.  Work items are (column, CH-row chunk) pairs
+// spread over the warps.  RES: this CTA's columns live in shared memory
+// (cols, column i at ((i - rank) / G) * n).
 template <bool UPDATE, bool RES, int CH>
 __device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, int n, int r0,
                             const double* __restrict__ x, const double* coef, const double* __restrict__ vu,
-                            const double* __restrict__ wu, double* pbuf, double* psum, int pcap, int rank,
-                            int G) {
+                            const double* __restrict__ pu, double K2, double* Pn, double* Cn, double* psum, int pcap,
+                            int rank, int G) {
   constexpr int NR = CH / 32;
   const int L = n - r0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -162,8 +187,7 @@ __device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, i
     for (int it = warp; it < kc * nch; it += kSyThreads / 32) {
       const int k = k0 + it / nch, ch = it % nch;
       const int i = first + G * k;
-      double* gcol = A + (int64_t)i * n + r0;
-      double* col = RES ? cols + (int64_t)((i - rank) / G) * n + r0 : gcol;
+      double* col = RES ? cols + (int64_t)((i - rank) / G) * n + r0 : A + (int64_t)i * n + r0;
       const int t0 = ch * CH + lane;
       double a[NR];
 #pragma unroll
@@ -171,29 +195,34 @@ __device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, i
         const int t = t0 + 32 * r;
         a[r] = t < L ? (RES ? col[t] : __ldcg(col + t)) : 0.0;
       }
+      const bool publish = i == r0;
       if (UPDATE) {
-        const double vi = vu[i - r0 + 1], wi = wu[i - r0 + 1];
-        const bool publish = RES && i == r0;
+        const double vi = vu[i - r0 + 1], ai = fma(-K2, vi, pu[i - r0 + 1]);
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           const int t = t0 + 32 * r;
           if (t < L) {
-            a[r] = fma(-vu[t + 1], wi, fma(-wu[t + 1], vi, a[r]));
-            if (RES) {
-              col[t] = a[r];
-              if (publish) __stcg(gcol + t, a[r]);
-            } else {
-              __stcg(col + t, a[r]);
-            }
+            a[r] = fma(-vu[t + 1], ai, fma(-pu[t + 1], vi, a[r]));
+            if (RES) col[t] = a[r];
+            else __stcg(col + t, a[r]);
           }
         }
       }
-      double acc = 0.0;
+      if (publish) {
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        const int t = t0 + 32 * r;
-        if (t < L && t > 0) acc = fma(a[r], x[t], acc);
+        for (int r = 0; r < NR; ++r) {
+          const int t = t0 + 32 * r;
+          if (t < L) st_pub(Cn + t, a[r]);
+        }
       }
+      double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+      for (int r = 0; r < NR; r += 2) {
+        const int t = t0 + 32 * r;
+        if (t < L && t > 0) acc0 = fma(a[r], x[t], acc0);
+        if (r + 1 < NR && t + 32 < L) acc1 = fma(a[r + 1], x[t + 32], acc1);
+      }
+      double acc = acc0 + acc1;
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) psum[it] = acc;
     }
@@ -204,7 +233,7 @@ __device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, i
       for (int ch = 0; ch < nch; ++ch) sdot += psum[kk * nch + ch];
       const int i = first + G * (k0 + kk);
       const double a0 = RES ? cols[(int64_t)((i - rank) / G) * n + r0] : __ldcg(A + (int64_t)i * n + r0);
-      __stcg(pbuf + i, tau * fma(scal, sdot, a0));
+      st_pub(Pn + (i - r0), tau * fma(scal, sdot, a0));
     }
     __syncthreads();
   }
@@ -213,19 +242,71 @@ __device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, i
   if (ncol == 0) __syncthreads();
 }
 
-// Step j (reflector H_j = I - tau_j v v^T from column j, v indexed from row
-// j+1, m = n - j - 1 entries) with p = tau_j A22 v already in pbuf:
-//   every CTA, after the group barrier:  w = p - (tau_j/2)(p^T v) v, and the
-//     updated column j+1 (rows j+1 ..) from its current value, v and w --
-//     so the next reflector is formed redundantly, with no hand-off;
-//   then one pass over its own columns i >= j+2 applies the rank-2 update
-//     A <- A - v w^T - w v^T to rows j+2 .. and forms the next step's
-//     p_i = tau_{j+1} A(j+2:, i)^T v'  (fused: one read and one write of A).
-// One group barrier per column.
-// Shared memory of a CTA: v, w, the updated column (3n), the partial sums,
+template <bool UPDATE, bool RES>
+__device__ void column_pass_any(double* A, double* cols, int n, int r0, const double* x, const double* coef,
+                                const double* vu, const double* pu, double K2, double* Pn, double* Cn, double* psum,
+                                int pcap, int rank, int G) {
+  // rows per work item by the column length: fewer idle lanes in ragged
+  // chunks against fewer cross-lane sums
+  const int L = n - r0;
+  if (L > 512)
+    column_pass<UPDATE, RES, 256>(A, cols, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
+  else if (L > 160)
+    column_pass<UPDATE, RES, 128>(A, cols, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
+  else
+    column_pass<UPDATE, RES, 64>(A, cols, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
+}
+
+// Waits for the m values of P and C of a step: p into ps[], a - p into bs[];
+// returns this thread's part of p^T v, and false (in every thread) when a
+// wait ran out.
+__device__ bool poll_step(const double* P, const double* C, int m, const double* v, double* ps, double* bs,
+                          long long limit, double* pt_out) {
+  double pt = 0.0;
+  int ok = 1;
+  for (int base = 0; base < m && ok; base += 4 * kSyThreads) {
+    double pr[4], ar[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int t = base + q * kSyThreads + threadIdx.x;
+      pr[q] = t < m ? ld_pub(P + t) : 0.0;
+      ar[q] = t < m ? ld_pub(C + t) : 0.0;
+    }
+    bool miss = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) miss = miss || pending(pr[q]) || pending(ar[q]);
+    if (miss) {
+      const long long t0 = clock64();
+      while (true) {
+        miss = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int t = base + q * kSyThreads + threadIdx.x;
+          if (pending(pr[q])) { pr[q] = ld_pub(P + t); miss = miss || pending(pr[q]); }
+          if (pending(ar[q])) { ar[q] = ld_pub(C + t); miss = miss || pending(ar[q]); }
+        }
+        if (!miss) break;
+        if (clock64() - t0 > limit) { ok = 0; break; }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int t = base + q * kSyThreads + threadIdx.x;
+      if (t < m) {
+        ps[t] = pr[q];
+        bs[t] = ar[q] - pr[q];
+        pt = fma(pr[q], v[t], pt);
+      }
+    }
+  }
+  *pt_out = pt;
+  return __syncthreads_and(ok) != 0;
+}
+
+// Shared memory of a CTA: v, p, the updated column (3n), the partial sums,
 // and with RES the CTA's own columns (ceil(n / G) of n rows).
 __host__ __device__ inline int sytrd1_pcap(int n, int G) {
-  const int items = ((n + G - 1) / G) * ((n + 127) / 128);  // up to 128-row items
+  const int items = ((n + G - 1) / G) * ((n + 63) / 64);  // up to 64-row items
   return items < kPartMax ? items : kPartMax;
 }
 __host__ __device__ inline size_t sytrd1_bytes(int n, int G, bool res) {
@@ -241,25 +322,21 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
   const int pcap = sytrd1_pcap(n, G);
   double* cols = sy_smem + 3 * n + pcap;  // RES: own columns
   double* vc = sy_smem;             // v_j (rows j+1 ..)
-  double* w = sy_smem + n;          // p_j, then w_j
-  double* vx = sy_smem + 2 * n;     // updated column j+1 (rows j+1 ..), then v_{j+1} at vx + 1
+  double* ps = sy_smem + n;         // p_j (rows j+1 ..)
+  double* bs = sy_smem + 2 * n;     // column j+1 (rows j+1 ..): a - p, then updated by step j
   double* psum = sy_smem + 3 * n;   // pcap partial dot products
-  // p, double-buffered by step parity: a CTA writes step j+2's values only
-  // after every CTA has passed step j+1's barrier, i.e. finished reading
-  // step j's values
-  double* pbuf2 = c.X;              // 2 x n
-  int* bar = c.prog;
+  double* pub = c.QA;               // the steps' slabs
   const int tid = threadIdx.x;
-  int bstep = 0;
+  int parity = 0;
   if (RES) {
     for (int i = rank; i < n; i += G) {
       const double* src = A + (int64_t)i * n;
       double* dst = cols + (int64_t)((i - rank) / G) * n;
       for (int r = tid; r < n; r += kSyThreads) dst[r] = __ldcg(src + r);
     }
-    __syncthreads();
   }
   if (n < 3) {
+    __syncthreads();
     if (rank == 0 && tid == 0) {
       c.d[0] = A[0];
       c.e[0] = n == 2 ? A[1] : 0.0;
@@ -267,12 +344,21 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
     }
     return;
   }
-  // ---- prologue: reflector 0 from column 0, p_0 for my columns
+  // ---- every slab holds the sentinel before anything is published
+  {
+    const int64_t total = (int64_t)n * n - n - 2;
+    for (int64_t e = (int64_t)rank * kSyThreads + tid; e < total; e += (int64_t)G * kSyThreads)
+      pub[e] = __longlong_as_double(kSentinel);
+  }
+  if (!group_barrier8(c.prog, rank, G, 1, wait_limit)) {
+    if (tid == 0) atomicOr(c.status, ST_TIMEOUT);
+    return;
+  }
+  // ---- prologue: reflector 0 from column 0; p_0 for my columns and column 1, published into slab 0
   double beta, tau;
   for (int t = tid; t < n - 1; t += kSyThreads) vc[t] = __ldcg(A + 1 + t);
   __syncthreads();
-  tau = make_reflector(vc, n - 1, red, sh, &beta);
-  __syncthreads();
+  tau = make_reflector(vc, n - 1, red, parity, sh, &beta);
   if (rank == 0 && tid == 0) {
     c.d[0] = __ldcg(A);
     c.e[0] = beta;
@@ -282,97 +368,74 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
   // v_0 is already scaled (u = v): coefficients (tau, 1)
   if (tid == 0) { sh[1] = tau; sh[2] = 1.0; }
   __syncthreads();
-  if (n <= 256) column_pass<false, RES, 128>(A, cols, n, 1, vc, sh + 1, nullptr, nullptr, pbuf2, psum, pcap, rank, G);
-  else column_pass<false, RES, kChunk>(A, cols, n, 1, vc, sh + 1, nullptr, nullptr, pbuf2, psum, pcap, rank, G);
+  {
+    double* s0 = slab(pub, n, 0);
+    column_pass_any<false, RES>(A, cols, n, 1, vc, sh + 1, nullptr, nullptr, 0.0, s0, s0 + (n - 1), psum, pcap,
+                                rank, G);
+  }
   for (int j = 0; j + 2 < n; ++j) {
     const int m = n - j - 1;
-    const double* pbuf = pbuf2 + (j & 1) * n;
-    if (!group_barrier8(bar, rank, G, ++bstep, wait_limit)) {
+    double* P = slab(pub, n, j);
+    // ---- p and column j+1 of this step, as they arrive
+    double pt;
+    if (!poll_step(P, P + m, m, vc, ps, bs, wait_limit, &pt)) {
       if (tid == 0) atomicOr(c.status, ST_TIMEOUT);
       return;
     }
-    // ---- w = p - K v and the updated column j+1, in every CTA
-    // K = (tau/2) p^T v from the full p (read by every CTA anyway); all loads
-    // of a round first, then the shared-memory stores (one L2 round trip)
-    double pt = 0.0;
-    for (int base = 0; base < m; base += 4 * kSyThreads) {
-      double pr[4], ar[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int t = base + q * kSyThreads + tid;
-        pr[q] = t < m ? __ldcg(pbuf + j + 1 + t) : 0.0;
-        ar[q] = t < m ? __ldcg(A + (int64_t)(j + 1 + t) + (int64_t)(j + 1) * n) : 0.0;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int t = base + q * kSyThreads + tid;
-        if (t < m) {
-          w[t] = pr[q];
-          vx[t] = ar[q];
-          pt = fma(pr[q], vc[t], pt);
-        }
-      }
-    }
-    const double K = 0.5 * tau * block_sum256(pt, red);
-    // one pass: w_t = p_t - K v_t, the updated column a_t - w_t v_0 - v_t w_0,
-    // and the next reflector's sum of squares (rows j+3 ..).  w[0] keeps p_0:
-    // every thread forms w_0 from it, and nothing later reads w[0].
-    double ps = 0.0;
-    {
-      const double v0 = vc[0];
-      const double w0 = fma(-K, v0, w[0]);
-      for (int t = tid; t < m; t += kSyThreads) {
-        const double wt = fma(-K, vc[t], w[t]);
-        if (t > 0) w[t] = wt;
-        const double nc = fma(-vc[t], w0, fma(-wt, v0, vx[t]));
-        vx[t] = nc;
-        if (t >= 2) ps = fma(nc, nc, ps);
-      }
+    const double K = 0.5 * tau * block_sum256(pt, red, parity);
+    // ---- column j+1 updated by step j: (a_t - p_t) - v_t (p_0 - 2K), and the
+    // next reflector's sum of squares (rows j+3 ..)
+    const double c0 = fma(-2.0, K, ps[0]);
+    double ss = 0.0;
+    for (int t = tid; t < m; t += kSyThreads) {
+      const double nc = fma(-vc[t], c0, bs[t]);
+      bs[t] = nc;
+      if (t >= 2) ss = fma(nc, nc, ss);
     }
     if (j + 3 < n) {
-      // ---- reflector j+1 from rows j+2 .. of the updated column x = vx + 1:
-      // its sum of squares now; thread 0 forms tau, beta and scal = 1/(x_0 - beta)
-      // while the other warps already run the pass, which needs them only at
-      // its end (p_i = tau (a_0 + scal sum_{t >= 1} a_t x_t), u = scal x, u_0 = 1)
-      const double sigma = block_sum256(ps, red);
+      // ---- reflector j+1 from rows j+2 .. of the updated column x = bs + 1:
+      // thread 0 forms tau, beta and scal = 1/(x_0 - beta) while the other
+      // warps already run the pass, which needs them only at its end
+      const double sigma = block_sum256(ss, red, parity);
       if (tid == 0) {
-        const double alpha = vx[1];
-        double beta = alpha, t1 = 0.0, sc = 0.0;
+        const double alpha = bs[1];
+        double b1 = alpha, t1 = 0.0, sc = 0.0;
         if (sigma != 0.0) {
           const double nrm = sqrt(fma(alpha, alpha, sigma));
-          beta = alpha >= 0.0 ? -nrm : nrm;
-          t1 = (beta - alpha) / beta;
-          sc = 1.0 / (alpha - beta);
+          b1 = alpha >= 0.0 ? -nrm : nrm;
+          t1 = (b1 - alpha) / b1;
+          sc = 1.0 / (alpha - b1);
         }
-        sh[0] = beta; sh[1] = t1; sh[2] = sc;
+        sh[0] = b1; sh[1] = t1; sh[2] = sc;
       }
-      double* pnext = pbuf2 + ((j + 1) & 1) * n;
-      if (n <= 256) column_pass<true, RES, 128>(A, cols, n, j + 2, vx + 1, sh + 1, vc, w, pnext, psum, pcap, rank, G);
-      else column_pass<true, RES, kChunk>(A, cols, n, j + 2, vx + 1, sh + 1, vc, w, pnext, psum, pcap, rank, G);
+      double* Pn = slab(pub, n, j + 1);
+      column_pass_any<true, RES>(A, cols, n, j + 2, bs + 1, sh + 1, vc, ps, 2.0 * K, Pn, Pn + (m - 1), psum, pcap,
+                                 rank, G);
       const double beta1 = sh[0], tau1 = sh[1], scal1 = sh[2];
       if (rank == 0 && tid == 0) {
-        c.d[j + 1] = vx[0];
+        c.d[j + 1] = bs[0];
         c.e[j + 1] = beta1;
         c.tau1[j + 1] = tau1;
       }
-      store_reflector(c, n, j + 1, vx + 1, rank, G, scal1);
+      store_reflector(c, n, j + 1, bs + 1, rank, G, scal1);
       // v_{j+1} = scal x becomes the current reflector (v_0 = 1)
-      for (int t = tid; t < m - 1; t += kSyThreads) vc[t] = t == 0 ? 1.0 : scal1 * vx[1 + t];
+      for (int t = tid; t < m - 1; t += kSyThreads) vc[t] = t == 0 ? 1.0 : scal1 * bs[1 + t];
       tau = tau1;
       __syncthreads();
     } else {
       __syncthreads();
       // the last 2 x 2 block (rows n-2, n-1); A(n-1, n-1) is current in its
-      // owner's copy (and in A unless RES)
+      // owner's copy (shared memory with RES, else A)
       if (rank == 0 && tid == 0) {
-        c.d[n - 2] = vx[0];
-        c.e[n - 2] = vx[1];
+        c.d[n - 2] = bs[0];
+        c.e[n - 2] = bs[1];
         c.e[n - 1] = 0.0;
       }
-      if (rank == (RES ? (n - 1) % G : 0) && tid == 0) {
+      if (rank == (n - 1) % G && tid == 0) {
         const double a = RES ? cols[(int64_t)((n - 1 - rank) / G) * n + (n - 1)]
                              : __ldcg(A + (int64_t)(n - 1) + (int64_t)(n - 1) * n);
-        c.d[n - 1] = a - fma(vc[1], w[1], w[1] * vc[1]);
+        const double w1 = fma(-K, vc[1], ps[1]);
+        c.d[n - 1] = a - 2.0 * vc[1] * w1;
       }
     }
   }
@@ -384,7 +447,7 @@ __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __res
                                                             const int* __restrict__ cta_count,
                                                             long long wait_limit, int smem_bytes) {
   extern __shared__ double sy_smem[];
-  __shared__ double red[kSyThreads / 32];
+  __shared__ double red[2 * (kSyThreads / 32)];
   __shared__ double sh[4];
   const ConeDev& c = cones[cta_cone[blockIdx.x]];
   const int rank = cta_rank[blockIdx.x], G = cta_count[blockIdx.x];
