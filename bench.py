@@ -65,7 +65,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", default="admm625",
                    choices=["admm625", "single81", "precision4096", "uneven", "vjp1296", "herm625", "mixing",
-                            "scs625"])
+                            "scs625", "scs625kron"])
     p.add_argument("--band", type=int, default=0)
     p.add_argument("--method", default="eig", choices=["eig", "poly"],
                    help="eig: projection by eigendecomposition; poly: factorization-free composite polynomial")
@@ -144,10 +144,21 @@ class Workload:
             # per step from SCS's initial iterates
             At, b, c, u0, v0 = W.scs_problem()
             self.calls = [(u0, [625])]
-            self.scs = (At, b, c, u0, v0)
+            self.scs = ("dense", At, b, c, u0, v0)
             self.iters = 10
             self.desc = ("10 SCS iterations (closed-form affine step with A^T A = I, PSD projection of the "
                          "n = 625 cone, dual update), m = 195,625, k = 1000")
+            self.exact0 = None
+        elif name == "scs625kron":
+            # the same iterations at the process-matrix step's real size: A applied
+            # as contractions over four local bases of side 5 (App. D.2), the
+            # 14,805 coefficients of the real process subspace (App. B)
+            bases, index, b, c, u0, v0 = W.scs_kron_problem()
+            self.calls = [(u0, [625])]
+            self.scs = ("kron", bases, index, b, c, u0, v0)
+            self.iters = 10
+            self.desc = ("10 SCS iterations, process-matrix step at d = 5 (n = 625, m = 195,625): A applied as "
+                         "contractions over four real Gell-Mann-type local bases, k = 14,805 (real process subspace)")
             self.exact0 = None
         elif name == "herm625":
             seq, U, lam = W.herm_admm_sequence()
@@ -273,10 +284,15 @@ def oracle_value(wl: Workload, budget_s: float = 12.0, poly_lo: float | None = N
         np.cumsum([wl.svec_len(s) for s in sides], out=offs[1:])
         if wl.scs is not None:
             from oracle import scs as oracle_scs
-            At, b, c, u0, v0 = wl.scs
-            uu, vv = u0, v0
+            kind, *prob = wl.scs
+            uu, vv = prob[-2], prob[-1]
             while time.perf_counter() - t0 <= budget_s and done < wl.iters:
-                uu, vv = oracle_scs.iterate(At.T, b, c, [0, len(b)], uu, vv, 1)
+                if kind == "dense":
+                    At, b, c = prob[:3]
+                    uu, vv = oracle_scs.iterate(At.T, b, c, [0, len(b)], uu, vv, 1)
+                else:
+                    bases, index, b, c = prob[:4]
+                    uu, vv = oracle_scs.iterate_kron(bases, index, b, c, [0, len(b)], uu, vv, 1)
                 done += 1
                 sample.append(625)
             break
@@ -406,7 +422,7 @@ def measure(args, env, config, precision, steps, warmup, full):
             if wl.scs is not None:
                 scs_u.copy_(x_list[i])
                 scs_v.copy_(scs_v0)
-                lib.scs_iterate(scs_A, scs_b, scs_c, sides, scs_u, scs_v, wl.iters, opts=opts, offsets=offs)
+                scs_run(sides, offs)
                 y_list[i].copy_(scs_u)
             elif poly:
                 lib.proj_poly(x_list[i], sides, args.poly_lo, out=y_list[i], opts=opts, offsets=offs)
@@ -421,11 +437,22 @@ def measure(args, env, config, precision, steps, warmup, full):
 
     yb = torch.empty_like(xs[0]) if wl.vjp else None
     if wl.scs is not None:
-        At, b_h, c_h, u0, v0 = wl.scs
-        scs_A = torch.from_numpy(At).to(dev).t()   # m x k, column-major
+        kind, *prob = wl.scs
+        b_h, c_h, u0, v0 = prob[-4:]
+        if kind == "dense":
+            scs_A = torch.from_numpy(prob[0]).to(dev).t()   # m x k, column-major
+        else:
+            kron_bases = [torch.from_numpy(B).to(dev) for B in prob[0]]
+            kron_index = torch.from_numpy(prob[1]).to(dev)
         scs_b, scs_c = torch.from_numpy(b_h).to(dev), torch.from_numpy(c_h).to(dev)
         scs_v0 = torch.from_numpy(v0).to(dev)
         scs_u, scs_v = torch.empty_like(scs_v0), torch.empty_like(scs_v0)
+
+        def scs_run(sides, offs):
+            if kind == "dense":
+                lib.scs_iterate(scs_A, scs_b, scs_c, sides, scs_u, scs_v, wl.iters, opts=opts, offsets=offs)
+            else:
+                lib.scs_iterate_kron(kron_bases, kron_index, scs_b, scs_c, scs_u, scs_v, wl.iters, opts=opts)
 
     # launch shapes: the library's autotuner on the first call's input (setup, untimed)
     tuning = None
@@ -512,7 +539,7 @@ def measure(args, env, config, precision, steps, warmup, full):
             if wl.scs is not None:
                 scs_u.copy_(dx[i])
                 scs_v.copy_(scs_v0)
-                lib.scs_iterate(scs_A, scs_b, scs_c, sides, scs_u, scs_v, wl.iters, opts=opts, offsets=offs)
+                scs_run(sides, offs)
                 dy[i].copy_(scs_u)
             elif poly:
                 lib.proj_poly(dx[i], sides, args.poly_lo, out=dy[i], opts=opts, offsets=offs)
@@ -799,21 +826,44 @@ def comparator(wl, xs, dev, stream, max_calls: int = 20):
         return out
 
     def run_scs():
-        # the same iterations with torch ops: matmuls for the affine step, eigh for the projection
-        At, b_h, c_h, u0, v0 = wl.scs
-        A = torch.from_numpy(At).to(dev).t()
+        # the same iterations with torch ops: matmuls (dense A) or einsum
+        # contractions (structured A) for the affine step, eigh for the projection
+        kind, *prob = wl.scs
+        b_h, c_h, u0, v0 = prob[-4:]
         bt, ct = torch.from_numpy(b_h).to(dev), torch.from_numpy(c_h).to(dev)
-        k, m = At.shape
-        u, v = torch.from_numpy(u0).to(dev), torch.from_numpy(v0).to(dev)
-        px = 0.5 * (ct - A.t() @ bt)
-        py = bt + A @ px
-        hp = ct @ px + bt @ py
+        m = b_h.size
+        k = c_h.size
         r, cc = np.triu_indices(625)
+        rr, ccd = torch.from_numpy(r).to(dev), torch.from_numpy(cc).to(dev)
         scale = torch.from_numpy(np.where(r == cc, 1.0, np.sqrt(2.0))).to(dev)
+        if kind == "dense":
+            A = torch.from_numpy(prob[0]).to(dev).t()
+            op_n = lambda x: A @ x  # noqa: E731
+            op_t = lambda y: A.t() @ y  # noqa: E731
+        else:
+            Bs = [torch.from_numpy(B).to(dev) for B in prob[0]]
+            idx = torch.from_numpy(prob[1]).to(dev)
+            shape = [B.shape[0] for B in Bs]
+            N = 625
+
+            def op_n(x):
+                T = torch.zeros(int(np.prod(shape)), dtype=torch.float64, device=dev)
+                T[idx] = x
+                Wm = torch.einsum("abcd,aim,bjn,cko,dlp->ijklmnop", T.reshape(shape), *Bs).reshape(N, N)
+                return Wm[ccd, rr] * scale
+
+            def op_t(y):
+                Y = _smat_torch(y, N).reshape(5, 5, 5, 5, 5, 5, 5, 5)
+                T = torch.einsum("ijklmnop,aim,bjn,cko,dlp->abcd", Y, *Bs)
+                return T.reshape(-1)[idx]
+        u, v = torch.from_numpy(u0).to(dev), torch.from_numpy(v0).to(dev)
+        px = 0.5 * (ct - op_t(bt))
+        py = bt + op_n(px)
+        hp = ct @ px + bt @ py
         for _ in range(wl.iters):
             w = u + v
-            zx = 0.5 * (w[:k] - A.t() @ w[k:k + m])
-            zy = w[k:k + m] + A @ zx
+            zx = 0.5 * (w[:k] - op_t(w[k:k + m]))
+            zy = w[k:k + m] + op_n(zx)
             tau = (w[-1] + ct @ zx + bt @ zy) / (1 + hp)
             ut = torch.cat([zx - tau * px, zy - tau * py, tau.reshape(1)])
             t = ut - v
@@ -852,7 +902,8 @@ def comparator(wl, xs, dev, stream, max_calls: int = 20):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     if wl.scs is not None:
-        return {"impl": "the same iterations in torch: matmuls + torch.linalg.eigh float64 projection",
+        return {"impl": "the same iterations in torch: " + ("matmuls" if wl.scs[0] == "dense" else "einsum contractions")
+                + " + torch.linalg.eigh float64 projection",
                 "value": units / (ms * 1e-3), "unit": "SCS iterations/s", "sample": f"{units} iterations"}
     if wl.mixing:
         return {"impl": "torch.linalg.eigvalsh float64 per block + the same weight rule + mixed svec",

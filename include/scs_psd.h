@@ -259,6 +259,41 @@ int scs_psd_scs_iterate(scs_psd_handle h, const double* A, const double* b, cons
                         const int64_t* offsets, const int32_t* sides, int32_t count, double* u, double* v,
                         int32_t iters, const scs_psd_opts* opts, void* stream);
 
+/* Structured affine operator for scs_psd_scs_iterate_kron, as the paper
+ * applies A and A^T (App. D.2: tensor contractions over the local bases of
+ * the subsystems, the Kronecker products never formed).  Column j of A is
+ * svec(F_mu), mu = (mu_1 .. mu_S) the multi-index of index[j] in C order
+ * over (nbasis[0] .. nbasis[S-1]) (mu_S varies fastest), and
+ *     F_mu = B_1[mu_1] (x) B_2[mu_2] (x) ... (x) B_S[mu_S],
+ * a matrix of side N = dims[0] * ... * dims[S-1] (row index (i_1 .. i_S) in
+ * C order: the convention of numpy.kron).  B_s[b] is the d x d matrix
+ * (d = dims[s]) at basis[s] + b d^2, COLUMN-major.  Every F_mu listed must be
+ * symmetric, and the columns orthonormal (A^T A = I): orthonormal local bases
+ * and distinct indices give that; neither is checked.  App. B's process
+ * matrices, for example, take four subsystems (A_I, A_O, B_I, B_O) of side
+ * d, a generalized Gell-Mann basis per subsystem, and the coefficients the
+ * process constraints allow (2 d^6 - 3 d^4 + 2 d^2 of them). */
+#define SCS_PSD_KRON_MAX_MODES 6
+typedef struct {
+  int32_t nmodes;                               /* S, 1 .. 6 */
+  int32_t dims[SCS_PSD_KRON_MAX_MODES];         /* d_s, 1 .. 8; N = prod d_s <= 8192 */
+  int32_t nbasis[SCS_PSD_KRON_MAX_MODES];       /* k_s, 1 .. d_s^2 */
+  const double* basis[SCS_PSD_KRON_MAX_MODES];  /* DEVICE: k_s d_s^2 doubles each */
+  int64_t nparams;                              /* k, 0 .. prod k_s */
+  const int64_t* index;                         /* DEVICE: k flat indices in [0, prod k_s) */
+} scs_psd_kron_op;
+
+/* scs_psd_scs_iterate for one PSD cone of side N (m = N(N+1)/2) with the
+ * structured operator `op` instead of a dense A: each product with A or A^T
+ * costs S contractions of the coefficient tensor (at most N^2 doubles) with
+ * the local bases, where a dense A would stream m k doubles.  b (m), c (k),
+ * u and v (k + m + 1) as there; the handle keeps two work tensors of N^2
+ * doubles for (m, k).  SCS_PSD_EINVAL for sizes out of range; an index
+ * outside [0, prod k_s) is skipped on the device and makes scs_psd_status
+ * report SCS_PSD_EINVAL. */
+int scs_psd_scs_iterate_kron(scs_psd_handle h, const scs_psd_kron_op* op, const double* b, const double* c,
+                             double* u, double* v, int32_t iters, const scs_psd_opts* opts, void* stream);
+
 /* The composite's coefficients for (lo, steps) as scs_psd_proj_poly uses
  * them: returns K (the number of steps) and, where the pointers are not
  * NULL, writes a[0..K), b[0..K) and l_final = l_K; -SCS_PSD_EINVAL for lo or

@@ -31,6 +31,11 @@ class Opts(ctypes.Structure):
                 ("wait_limit_cycles", ctypes.c_int64), ("graphs", ctypes.c_int32), ("stats", ctypes.c_int32)]
 
 
+class KronOp(ctypes.Structure):
+    _fields_ = [("nmodes", ctypes.c_int32), ("dims", ctypes.c_int32 * 6), ("nbasis", ctypes.c_int32 * 6),
+                ("basis", ctypes.c_void_p * 6), ("nparams", ctypes.c_int64), ("index", ctypes.c_void_p)]
+
+
 class ConeStats(ctypes.Structure):
     _fields_ = [("k_pos", ctypes.c_int32), ("k_neg", ctypes.c_int32), ("route", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("complementarity", ctypes.c_double), ("norm_y", ctypes.c_double),
@@ -46,7 +51,7 @@ EXPORTS = ("scs_psd_create", "scs_psd_destroy", "scs_psd_proj", "scs_psd_proj_ba
            "scs_psd_last_replayed", "scs_psd_strerror", "scs_psd_trace", "scs_psd_trace_read",
            "scs_psd_autotune", "scs_psd_last_tuning", "scs_psd_proj_hermitian", "scs_psd_proj_poly",
            "scs_psd_poly_schedule", "scs_psd_proj_poly_hermitian", "scs_psd_lambda_min", "scs_psd_mix_identity",
-           "scs_psd_scs_iterate", "scs_psd_last_stats")
+           "scs_psd_scs_iterate", "scs_psd_last_stats", "scs_psd_scs_iterate_kron")
 NPHASES = 8
 PHASES = ("unpack", "dense_to_band", "band_to_tridiag", "tridiag_dc", "backtransform_2", "backtransform_1",
           "reconstruct", "derivative")
@@ -89,6 +94,7 @@ def load(path: str | None = None):
                                          ctypes.POINTER(ctypes.c_double)]
         lib.scs_psd_last_tuning.argtypes = [vp, ctypes.POINTER(i32)]
         lib.scs_psd_last_stats.argtypes = [vp, ctypes.POINTER(ConeStats), i32]
+        lib.scs_psd_scs_iterate_kron.argtypes = [vp, ctypes.POINTER(KronOp), vp, vp, vp, vp, i32, op, vp]
         lib.scs_psd_last_replayed.argtypes = [vp]
         lib.scs_psd_last_replayed.restype = ctypes.c_int
         lib.scs_psd_trace.argtypes = [vp, ctypes.c_int]
@@ -413,6 +419,47 @@ def scs_iterate(A, b, c, sides, u, v, iters: int, opts: Opts | None = None, offs
                                     int(sides.size), _ptr(u), _ptr(v), int(iters),
                                     ctypes.byref(opts) if opts is not None else None, _stream_ptr(u))
     _check(rc, "scs_psd_scs_iterate")
+    return u, v
+
+
+def kron_operator(bases, index):
+    """The C-ABI description of a structured operator: bases is a list of
+    float64 CUDA tensors of shape (k_s, d_s, d_s) holding B_s[b][i, j] (made
+    column-major per matrix here), index an int64 CUDA tensor of flat indices.
+    Returns (KronOp, tensors to keep alive while the operator is in use)."""
+    import torch
+    if len(bases) < 1 or len(bases) > 6:
+        raise ValueError("1 to 6 modes")
+    _check_index = index
+    if not isinstance(_check_index, torch.Tensor) or not index.is_cuda or index.dtype != torch.int64:
+        raise TypeError("index must be an int64 CUDA tensor")
+    keep = [index.contiguous()]
+    op = KronOp()
+    op.nmodes = len(bases)
+    for s_, B in enumerate(bases):
+        if not isinstance(B, torch.Tensor) or not B.is_cuda or B.dtype != torch.float64 or B.dim() != 3:
+            raise TypeError("each local basis must be a float64 CUDA tensor of shape (k, d, d)")
+        Bc = B.transpose(1, 2).contiguous()
+        keep.append(Bc)
+        op.dims[s_] = int(B.shape[1])
+        op.nbasis[s_] = int(B.shape[0])
+        op.basis[s_] = Bc.data_ptr()
+    op.nparams = int(keep[0].numel())
+    op.index = keep[0].data_ptr() if op.nparams else None
+    return op, keep
+
+
+def scs_iterate_kron(bases, index, b, c, u, v, iters: int, opts: Opts | None = None):
+    """SCS iterations around the projection of one cone of side prod d_s with
+    the structured operator (C-ABI scs_psd_scs_iterate_kron); u, v updated in place."""
+    for t, nm in ((b, "b"), (c, "c"), (u, "u"), (v, "v")):
+        _check_tensor(t, nm)
+    op, keep = kron_operator(bases, index)
+    rc = load().scs_psd_scs_iterate_kron(handle(u.device.index), ctypes.byref(op), _ptr(b), _ptr(c), _ptr(u),
+                                         _ptr(v), int(iters), ctypes.byref(opts) if opts is not None else None,
+                                         _stream_ptr(u))
+    del keep
+    _check(rc, "scs_psd_scs_iterate_kron")
     return u, v
 
 

@@ -184,8 +184,14 @@ struct ScsPlan {
   void* mem = nullptr;
   double *p = nullptr, *hp = nullptr, *z = nullptr, *tk = nullptr, *part = nullptr, *tau = nullptr;
   double *tin = nullptr, *uty = nullptr;
+  // structured operator: two work tensors of N^2 doubles and a status word
+  void* kmem = nullptr;
+  int64_t kdoubles = 0;
+  double *t0 = nullptr, *t1 = nullptr;
+  int* kstatus = nullptr;
   ~ScsPlan() {
     if (mem) cudaFree(mem);
+    if (kmem) cudaFree(kmem);
   }
 };
 
@@ -2048,10 +2054,12 @@ int mix_identity(scs_psd_handle h, const double* x, double* y, const int64_t* of
 }
 
 // ---- the SCS iteration around the projection (App. D.1) ----
-int scs_iterate(scs_psd_handle h, const double* A, const double* b, const double* c, int64_t m, int64_t k,
-                const int64_t* offsets, const int32_t* sides, int32_t count, double* u, double* v, int32_t iters,
-                const scs_psd_opts* opts, void* stream) {
-  if (!h || !b || !u || !v || m < 1 || k < 0 || iters < 0 || (k > 0 && (!A || !c))) return SCS_PSD_EINVAL;
+// The iterations for either operator (op.A dense, or op.kron structured with
+// kron_n2 = N^2 doubles per work tensor).
+int scs_run(scs_psd_handle h, ScsOp op, int64_t kron_n2, const double* b, const double* c, int64_t m, int64_t k,
+            const int64_t* offsets, const int32_t* sides, int32_t count, double* u, double* v, int32_t iters,
+            const scs_psd_opts* opts, void* stream) {
+  if (!h || !b || !u || !v || m < 1 || k < 0 || iters < 0 || (k > 0 && !c)) return SCS_PSD_EINVAL;
   int rc = check_shapes(offsets, sides, count);
   if (rc) return rc;
   if (count < 1 || offsets[count] != m) return SCS_PSD_EINVAL;
@@ -2085,23 +2093,76 @@ int scs_iterate(scs_psd_handle h, const double* A, const double* b, const double
       sp = np.get();
       h->scs[{m, k}] = std::move(np);
     }
+    if (!op.A && kron_n2 > sp->kdoubles) {
+      if (sp->kmem) cudaFree(sp->kmem);
+      sp->kmem = nullptr;
+      sp->kdoubles = 0;
+      if (cudaMalloc(&sp->kmem, sizeof(double) * 2 * (size_t)kron_n2 + 256) != cudaSuccess) return SCS_PSD_ENOMEM;
+      sp->kdoubles = kron_n2;
+      sp->t0 = (double*)sp->kmem;
+      sp->t1 = sp->t0 + kron_n2;
+      sp->kstatus = (int*)(sp->t1 + kron_n2);
+    }
   }
   cudaStream_t s = (cudaStream_t)stream;
-  launch_scs_setup(A, b, c, m, k, sp->p, sp->hp, sp->tk, sp->part, s);
-  if (cudaGetLastError() != cudaSuccess) return SCS_PSD_ECUDA;
   int64_t launches = 5;
+  if (!op.A) {
+    op.t0 = sp->t0;
+    op.t1 = sp->t1;
+    op.status = h->status_word;
+    kron_prepare();
+    launches += 2 * (int64_t)kron_launches(op.kron) - 3;
+  }
+  launch_scs_setup(op, b, c, m, k, sp->p, sp->hp, sp->tk, sp->part, s);
+  if (cudaGetLastError() != cudaSuccess) return SCS_PSD_ECUDA;
+  const int64_t per_affine = op.A ? 6 : 3 + 2 * (int64_t)kron_launches(op.kron);
   for (int it = 0; it < iters; ++it) {
-    launch_scs_affine(A, b, c, m, k, sp->p, sp->hp, u, v, sp->z, sp->tk, sp->part, sp->tau, sp->tin, sp->uty, s);
+    launch_scs_affine(op, b, c, m, k, sp->p, sp->hp, u, v, sp->z, sp->tk, sp->part, sp->tau, sp->tin, sp->uty, s);
     if (cudaGetLastError() != cudaSuccess) return SCS_PSD_ECUDA;
     const IoSlot io{sp->tin, u + k, nullptr, nullptr, nullptr, nullptr};
     if ((rc = do_call(h, io, MODE_Y, offsets, sides, count, opts, stream))) return rc;
-    launches += 6 + h->last_launches;
+    launches += per_affine + h->last_launches;
     launch_scs_vy(v + k, sp->uty, u + k, m, s);
     if (cudaGetLastError() != cudaSuccess) return SCS_PSD_ECUDA;
     ++launches;
   }
   h->last_launches = launches;
   return SCS_PSD_OK;
+}
+
+int scs_iterate(scs_psd_handle h, const double* A, const double* b, const double* c, int64_t m, int64_t k,
+                const int64_t* offsets, const int32_t* sides, int32_t count, double* u, double* v, int32_t iters,
+                const scs_psd_opts* opts, void* stream) {
+  if (k > 0 && !A) return SCS_PSD_EINVAL;
+  ScsOp op;
+  op.A = A;
+  return scs_run(h, op, 0, b, c, m, k, offsets, sides, count, u, v, iters, opts, stream);
+}
+
+int scs_iterate_kron(scs_psd_handle h, const scs_psd_kron_op* K, const double* b, const double* c, double* u,
+                     double* v, int32_t iters, const scs_psd_opts* opts, void* stream) {
+  if (!h || !K || K->nmodes < 1 || K->nmodes > kKronMaxModes || K->nparams < 0) return SCS_PSD_EINVAL;
+  ScsOp op;
+  KronDev& kd = op.kron;
+  kd.S = K->nmodes;
+  int64_t N = 1, Kt = 1;
+  for (int q = 0; q < kd.S; ++q) {
+    const int d = K->dims[q], kb = K->nbasis[q];
+    if (d < 1 || d > kKronMaxDim || kb < 1 || kb > d * d || !K->basis[q]) return SCS_PSD_EINVAL;
+    kd.d[q] = d;
+    kd.kb[q] = kb;
+    kd.basis[q] = K->basis[q];
+    N *= d;
+    Kt *= kb;
+  }
+  if (N > kMaxSide || K->nparams > Kt || (K->nparams > 0 && !K->index)) return SCS_PSD_EINVAL;
+  kd.index = K->index;
+  kd.k = K->nparams;
+  kd.N = N;
+  kd.Kt = Kt;
+  const int64_t offsets[2] = {0, svec_len(N)};
+  const int32_t sides[1] = {(int32_t)N};
+  return scs_run(h, op, N * N, b, c, svec_len(N), K->nparams, offsets, sides, 1, u, v, iters, opts, stream);
 }
 
 // ---- static-scratch entry point: no device allocation at all ----
@@ -2296,6 +2357,11 @@ int scs_psd_mix_identity(scs_psd_handle h, const double* x, double* y, const int
   return mix_identity(h, x, y, offsets, sides, count, groups, ngroups, nu, eps, p_out, opts, stream);
 }
 
+int scs_psd_scs_iterate_kron(scs_psd_handle h, const scs_psd_kron_op* op, const double* b, const double* c, double* u,
+                             double* v, int32_t iters, const scs_psd_opts* opts, void* stream) {
+  return scs_iterate_kron(h, op, b, c, u, v, iters, opts, stream);
+}
+
 int scs_psd_scs_iterate(scs_psd_handle h, const double* A, const double* b, const double* c, int64_t m, int64_t k,
                         const int64_t* offsets, const int32_t* sides, int32_t count, double* u, double* v,
                         int32_t iters, const scs_psd_opts* opts, void* stream) {
@@ -2340,7 +2406,8 @@ int scs_psd_status(scs_psd_handle h, int32_t* device_status) {
   if (cudaMemcpy(&v, h->status_word, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SCS_PSD_ECUDA;
   cudaMemset(h->status_word, 0, sizeof(int));
   int code = SCS_PSD_OK;
-  if (v & ST_TIMEOUT) code = SCS_PSD_ETIMEOUT;
+  if (v & ST_BADARG) code = SCS_PSD_EINVAL;
+  else if (v & ST_TIMEOUT) code = SCS_PSD_ETIMEOUT;
   else if (v & ST_NOCONV) code = SCS_PSD_ENOCONV;
   else if (v & ST_NONFINITE) code = SCS_PSD_ENONFINITE;
   *device_status = code;

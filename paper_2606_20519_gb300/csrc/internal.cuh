@@ -258,11 +258,41 @@ void launch_herm_embed(const int64_t* meta, int count, int64_t maxn, const doubl
 void launch_herm_extract(const int64_t* meta, int count, int64_t maxn, const double* ms, double* hs, cudaStream_t s);
 void launch_status_reduce(const int* status, int count, int* out, cudaStream_t s);
 void launch_lmin(const ConeDev* cones, int ncones, const IoSlot* io, cudaStream_t s);
-// SCS iteration (App. D.1) around the projection, A (m x k, column-major) with orthonormal columns
+// Structured affine operator (App. D.2): column j of A is svec of the
+// Kronecker product of local basis matrices F_s[mu_s], mu the multi-index of
+// index[j] (C order over kb); local matrix b of mode s is column-major at
+// basis[s] + b d_s^2.
+constexpr int kKronMaxModes = 6;
+constexpr int kKronMaxDim = 8;
+struct KronDev {
+  int S;
+  int d[kKronMaxModes], kb[kKronMaxModes];
+  const double* basis[kKronMaxModes];
+  const int64_t* index;
+  int64_t k, N, Kt;  // parameters, matrix side (prod d), prod kb
+};
+void kron_prepare();
+int kron_launches(const KronDev& op);
+// out = a1 (+ a2) + A x; t0, t1: work tensors of N^2 doubles each; bad indices set ST_BADARG in *status
+void launch_kron_apply(const KronDev& op, const double* x, const double* a1, const double* a2, double* out,
+                       double* t0, double* t1, int* status, cudaStream_t s);
+// out = A^T (a1 (+ a2))
+void launch_kron_apply_t(const KronDev& op, const double* a1, const double* a2, double* out, double* t0, double* t1,
+                         int* status, cudaStream_t s);
+
+// SCS iteration (App. D.1) around the projection; A with orthonormal columns,
+// dense (m x k, column-major) or structured
+struct ScsOp {
+  const double* A = nullptr;  // dense, or null for the structured operator
+  KronDev kron{};
+  double* t0 = nullptr;
+  double* t1 = nullptr;
+  int* status = nullptr;
+};
 int scs_dot_parts(int64_t len);
-void launch_scs_setup(const double* A, const double* b, const double* c, int64_t m, int64_t k, double* p,
+void launch_scs_setup(const ScsOp& op, const double* b, const double* c, int64_t m, int64_t k, double* p,
                       double* hp, double* tk, double* part, cudaStream_t s);
-void launch_scs_affine(const double* A, const double* b, const double* c, int64_t m, int64_t k, const double* p,
+void launch_scs_affine(const ScsOp& op, const double* b, const double* c, int64_t m, int64_t k, const double* p,
                        const double* hp, double* u, double* v, double* z, double* tk, double* part, double* tau,
                        double* tin, double* uty, cudaStream_t s);
 void launch_scs_vy(double* vy, const double* uty, const double* uy, int64_t m, cudaStream_t s);

@@ -5,9 +5,10 @@
 // inverse z_x = (a_x - A^T a_y) / 2, z_y = a_y + A z_x (one product with A^T,
 // one with A), and (I + Q)^{-1} follows from z = M^{-1} w and p = M^{-1}(c, b):
 //   tau~ = (w_tau + c.z_x + b.z_y) / (1 + c.p_x + b.p_y),  (x~, y~) = z - tau~ p.
-// The products stream A from HBM once each (A column-major, m x k); the rest
-// are short vector kernels; the cone projection of the y block is the
-// library's own launch sequence.
+// A dense A (column-major, m x k) is streamed from HBM once per product; a
+// structured A is applied by the contractions of kron.cu; the rest are short
+// vector kernels; the cone projection of the y block is the library's own
+// launch sequence.
 #include "internal.cuh"
 
 namespace scs {
@@ -134,28 +135,42 @@ int scs_dot_parts(int64_t len) {
   return (int)(g < 512 ? (g < 1 ? 1 : g) : 512);
 }
 
-void launch_scs_setup(const double* A, const double* b, const double* c, int64_t m, int64_t k, double* p,
+// out = A^T (a1 + a2), k entries
+void op_t(const ScsOp& op, int64_t m, int64_t k, const double* a1, const double* a2, double* out, cudaStream_t s) {
+  if (k <= 0) return;
+  if (op.A) gemv_t_kernel<<<(unsigned)k, 256, 0, s>>>(op.A, m, k, a1, a2, out);
+  else launch_kron_apply_t(op.kron, a1, a2, out, op.t0, op.t1, op.status, s);
+}
+
+// out = a1 + a2 + A x, m entries
+void op_n(const ScsOp& op, int64_t m, int64_t k, const double* x, const double* a1, const double* a2, double* out,
+          cudaStream_t s) {
+  if (op.A || k == 0) gemv_n_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(op.A, m, k, x, a1, a2, out);
+  else launch_kron_apply(op.kron, x, a1, a2, out, op.t0, op.t1, op.status, s);
+}
+
+void launch_scs_setup(const ScsOp& op, const double* b, const double* c, int64_t m, int64_t k, double* p,
                       double* hp, double* tk, double* part, cudaStream_t s) {
   // p_x = (c - A^T b) / 2, p_y = b + A p_x, hp = c . p_x + b . p_y
   if (k > 0) {
-    gemv_t_kernel<<<(unsigned)k, 256, 0, s>>>(A, m, k, b, nullptr, tk);
+    op_t(op, m, k, b, nullptr, tk, s);
     half_diff_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(c, nullptr, tk, k, p);
   }
-  gemv_n_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(A, m, k, p, b, nullptr, p + k);
+  op_n(op, m, k, p, b, nullptr, p + k, s);
   const int np = scs_dot_parts(k + m);
   dot2_kernel<<<np, 256, 0, s>>>(c, p, k, b, p + k, m, part);
   finish_kernel<<<1, 32, 0, s>>>(part, np, nullptr, nullptr, hp, nullptr);
 }
 
-void launch_scs_affine(const double* A, const double* b, const double* c, int64_t m, int64_t k, const double* p,
+void launch_scs_affine(const ScsOp& op, const double* b, const double* c, int64_t m, int64_t k, const double* p,
                        const double* hp, double* u, double* v, double* z, double* tk, double* part, double* tau,
                        double* tin, double* uty, cudaStream_t s) {
   // w = u + v; z_x = (w_x - A^T w_y) / 2; z_y = w_y + A z_x
   if (k > 0) {
-    gemv_t_kernel<<<(unsigned)k, 256, 0, s>>>(A, m, k, u + k, v + k, tk);
+    op_t(op, m, k, u + k, v + k, tk, s);
     half_diff_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(u, v, tk, k, z);
   }
-  gemv_n_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(A, m, k, z, u + k, v + k, z + k);
+  op_n(op, m, k, z, u + k, v + k, z + k, s);
   const int np = scs_dot_parts(k + m);
   dot2_kernel<<<np, 256, 0, s>>>(c, z, k, b, z + k, m, part);
   finish_kernel<<<1, 32, 0, s>>>(part, np, u + k + m, v + k + m, const_cast<double*>(hp), tau);

@@ -296,3 +296,64 @@ def scs_problem(seed: int = SEED_BASE + 7, n: int = 625, k: int = 1000):
     u[-1] = 1.0
     return At, b, c, u, u.copy()
 
+
+
+# ---- structured operator of the process-matrix step (App. B, App. D.2)
+def real_local_basis(d: int):
+    """Orthonormal basis of the real d x d matrices in the real form of the
+    generalized Gell-Mann basis: element 0 the identity / sqrt(d), then the
+    d - 1 traceless diagonal matrices diag(1, .., 1, -l, 0, ..) / sqrt(l (l + 1)),
+    then (E_ij + E_ji) / sqrt(2) and (E_ij - E_ji) / sqrt(2) for i < j.
+    Returns (B of shape (d^2, d, d), antisym flags of length d^2).  The
+    antisymmetric elements are the imaginary Gell-Mann matrices divided by i."""
+    B, anti = [np.eye(d) / np.sqrt(d)], [False]
+    for l in range(1, d):
+        D = np.zeros((d, d))
+        D[np.arange(l), np.arange(l)] = 1.0
+        D[l, l] = -float(l)
+        B.append(D / np.sqrt(l * (l + 1.0)))
+        anti.append(False)
+    for i in range(d):
+        for j in range(i + 1, d):
+            S = np.zeros((d, d))
+            S[i, j] = S[j, i] = 1.0 / np.sqrt(2.0)
+            A = np.zeros((d, d))
+            A[i, j], A[j, i] = 1.0 / np.sqrt(2.0), -1.0 / np.sqrt(2.0)
+            B += [S, A]
+            anti += [False, True]
+    return np.stack(B), np.array(anti)
+
+
+def process_allowed(d: int, real: bool = True) -> np.ndarray:
+    """Flat indices (C order over (A_I, A_O, B_I, B_O) basis indices, 0 the
+    identity) of the coefficients a bipartite process matrix may carry
+    (App. B): w_{a0,c0} for all a, c; w_{a j,c 0} with j, c traceless; w_{a 0,c l}
+    with a, l traceless -- 2 d^6 - 3 d^4 + 2 d^2 of them.  real=True keeps the
+    ones whose Kronecker product is real symmetric: an even number of
+    antisymmetric local factors."""
+    k = d * d
+    _, anti = real_local_basis(d)
+    a, j, c, l = np.meshgrid(np.arange(k), np.arange(k), np.arange(k), np.arange(k), indexing="ij")
+    ok = ((j == 0) & (l == 0)) | ((j > 0) & (l == 0) & (c > 0)) | ((j == 0) & (l > 0) & (a > 0))
+    if real:
+        na = anti[a].astype(int) + anti[j] + anti[c] + anti[l]
+        ok &= (na % 2) == 0
+    return np.flatnonzero(ok.reshape(-1)).astype(np.int64)
+
+
+def scs_kron_problem(seed: int = SEED_BASE + 8, d: int = 5):
+    """The process-matrix SDP step of App. D at local dimension d: one PSD
+    cone of side n = d^4 (four subsystems), A x = svec(sum_mu x_mu F_mu) over
+    the real process subspace (``process_allowed``), F_mu Kronecker products
+    of ``real_local_basis(d)``; b ~ N(0, 1/m), c ~ N(0, 1/k), and SCS's
+    initial iterates u = v = (0, 0, 1).  Returns (bases, index, b, c, u, v)."""
+    rng = rng_for(seed)
+    B, _ = real_local_basis(d)
+    index = process_allowed(d)
+    n = d ** 4
+    m, k = n * (n + 1) // 2, index.size
+    b = rng.standard_normal(m) / np.sqrt(m)
+    c = rng.standard_normal(k) / np.sqrt(k)
+    u = np.zeros(k + m + 1)
+    u[-1] = 1.0
+    return [B] * 4, index, b, c, u, u.copy()
