@@ -39,6 +39,13 @@ __device__ __forceinline__ long long dkey(double x) {
   return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
 }
 
+// x > 0 and x < 0 for finite x from its bit pattern (no FP64 instruction)
+__device__ __forceinline__ bool d_pos(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool d_neg(double x) {
+  const long long b = __double_as_longlong(x);
+  return b < 0 && (b & 0x7fffffffffffffffLL) != 0;
+}
+
 __device__ __forceinline__ double* qin_buf(const ConeDev& c, int level) { return (level & 1) ? c.QB : c.QA; }
 __device__ __forceinline__ double* qout_buf(const ConeDev& c, int level) { return (level & 1) ? c.QA : c.QB; }
 __device__ __forceinline__ double* lin_buf(const ConeDev& c, int level) { return (level & 1) ? c.lamB : c.lamA; }
@@ -651,13 +658,15 @@ __global__ void __launch_bounds__(kDcThreads) dc_select_kernel(const ConeDev* __
     }
     return;
   }
-  // ---- cone's final merge: choose the side and the kept eigenpairs
-  __shared__ int sh_pos, sh_neg;
-  if (tid == 0) { sh_pos = 0; sh_neg = 0; }
+  // ---- cone's final merge: choose the side and the kept eigenpairs.  Signs
+  // are read from the bit patterns (integer operations: a comparison of
+  // doubles would occupy the FP64 pipe), and every scan is spread over the CTA.
+  __shared__ int sh_pos, sh_neg, sh_lo, sh_hi, sh_wsum[kDcThreads / 32], sh_kd;
+  if (tid == 0) { sh_pos = 0; sh_neg = 0; sh_lo = kk; sh_hi = 0; }
   __syncthreads();
   int np = 0, nn = 0;
-  for (int i = tid; i < kk; i += kDcThreads) { np += lam[i] > 0.0; nn += lam[i] < 0.0; }
-  for (int r = tid; r < ndf; r += kDcThreads) { np += dfs[r] > 0.0; nn += dfs[r] < 0.0; }
+  for (int i = tid; i < kk; i += kDcThreads) { np += d_pos(lam[i]); nn += d_neg(lam[i]); }
+  for (int r = tid; r < ndf; r += kDcThreads) { np += d_pos(dfs[r]); nn += d_neg(dfs[r]); }
   atomicAdd(&sh_pos, np);
   atomicAdd(&sh_neg, nn);
   __syncthreads();
@@ -667,34 +676,62 @@ __global__ void __launch_bounds__(kDcThreads) dc_select_kernel(const ConeDev* __
   if (side == 1) route = 0;
   else if (side == 2) route = 1;
   else route = (sh_pos <= sh_neg) ? 0 : 1;
-  // kept roots form a contiguous range [r_lo, r_hi)
-  int r_lo = 0, r_hi = kk;
+  // kept roots form a contiguous range [r_lo, r_hi) of the increasing roots
   if (!allv) {
-    if (route == 0) { r_lo = kk - 0; for (int i = 0; i < kk; ++i) if (lam[i] > 0.0) { r_lo = i; break; } }
-    else { r_hi = 0; for (int i = kk - 1; i >= 0; --i) if (lam[i] < 0.0) { r_hi = i + 1; break; } }
+    if (route == 0) {
+      for (int i = tid; i < kk; i += kDcThreads)
+        if (d_pos(lam[i])) { atomicMin(&sh_lo, i); break; }
+    } else {
+      for (int i = tid; i < kk; i += kDcThreads)
+        if (d_neg(lam[i])) atomicMax(&sh_hi, i + 1);
+    }
   }
+  __syncthreads();
+  const int r_lo = (allv || route == 1) ? 0 : sh_lo;
+  const int r_hi = (allv || route == 0) ? kk : sh_hi;
   const int kr = r_hi - r_lo;
-  // roots -> Z columns 0..kr-1; kept deflated -> Z columns kr..
+  // roots -> Z columns 0..kr-1; kept deflated -> Z columns kr.., in sorted order
   int* imap = c.imap + s;
   for (int i = tid; i < kk; i += kDcThreads) {
     const bool keep = i >= r_lo && i < r_hi;
     imap[i] = keep ? (i - r_lo) : -1;
     if (keep) c.lamk[i - r_lo] = lam[i];
   }
-  if (tid == 0) {
-    int kd = 0;
-    for (int r = 0; r < ndf; ++r) {
+  {
+    // exclusive scan of the keep flags over contiguous chunks of the sorted deflated values
+    const int per = (ndf + kDcThreads - 1) / kDcThreads;
+    const int a0 = min(ndf, tid * per), a1 = min(ndf, a0 + per);
+    int mine = 0;
+    for (int r = a0; r < a1; ++r) mine += allv || (route == 0 ? d_pos(dfs[r]) : d_neg(dfs[r]));
+    const int lane = tid & 31, wid = tid >> 5;
+    int incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) sh_wsum[wid] = incl;
+    __syncthreads();
+    if (tid == 0) {
+      int run = 0;
+      for (int q = 0; q < kDcThreads / 32; ++q) { const int v = sh_wsum[q]; sh_wsum[q] = run; run += v; }
+      sh_kd = run;
+    }
+    __syncthreads();
+    int kb = sh_wsum[wid] + incl - mine;
+    for (int r = a0; r < a1; ++r) {
       const double v = dfs[r];
-      const bool keep = allv || (route == 0 ? v > 0.0 : v < 0.0);
+      const bool keep = allv || (route == 0 ? d_pos(v) : d_neg(v));
       if (keep) {
-        imap[kk + dord[r]] = kr + kd;
-        c.lamk[kr + kd] = v;
-        ++kd;
+        imap[kk + dord[r]] = kr + kb;
+        c.lamk[kr + kb] = v;
+        ++kb;
       } else {
         imap[kk + dord[r]] = -1;
       }
     }
-    c.kinfo[0] = kr + kd;
+  }
+  if (tid == 0) {
+    c.kinfo[0] = kr + sh_kd;
     c.kinfo[1] = route;
     c.kinfo[2] = kr;
     c.kinfo[5] = r_lo;

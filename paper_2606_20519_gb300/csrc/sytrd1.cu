@@ -314,6 +314,430 @@ __host__ __device__ inline size_t sytrd1_bytes(int n, int G, bool res) {
   return ((size_t)3 * n + sytrd1_pcap(n, G) + own) * sizeof(double);
 }
 
+// ---------------------------------------------------------------- double-float path
+// The shared-memory-resident route (every CTA's columns in shared memory)
+// computes in double-float arithmetic: a value is an unevaluated sum hi + lo
+// of two FP32 numbers (Dekker 1971; error-free transformations TwoSum and
+// TwoProduct with FMA), 48 significant bits, relative rounding of an
+// operation about 2^-47 of its operands.  On this part FP32 runs at 64 times
+// the FP64 rate, and every operation of the reduction is an FP32 pipe
+// instruction, where an FP64 warp instruction holds the SMSP's FP64 pipe
+// for 64 cycles.  The matrix is scaled by a power of two into [1, 2) for its
+// largest entry first (exact; FP32's exponent range then holds every entry
+// whose magnitude matters at FP64 accuracy), d and e are scaled back, the
+// reflectors and tau are scale-free.  The reflector's scalars (a square root
+// and two divisions, one thread per step) stay in FP64.
+struct __align__(8) dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfl df_make(float h, float l) {
+  dfl r;
+  r.hi = h;
+  r.lo = l;
+  return r;
+}
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return df_make(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ dfl df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df_make(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+  const dfl s = df_two_sum(x.hi, y.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ dfl df_neg(dfl x) { return df_make(-x.hi, -x.lo); }
+// x y + z
+__device__ __forceinline__ dfl df_fma(dfl x, dfl y, dfl z) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, e));
+  const dfl s = df_two_sum(p, z.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, z.lo)));
+}
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, e));
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfl df_zero() { return df_make(0.0f, 0.0f); }
+// FP64 <-> double-float (FP64 pipe: used at the boundaries only)
+__device__ __forceinline__ dfl df_from_d(double x) {
+  const float h = __double2float_rn(x);
+  return df_make(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ double df_to_d(dfl x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ dfl df_shfl_xor(dfl v, int o) {
+  return df_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+
+__device__ __forceinline__ dfl* slab(dfl* base, int n, int j) {
+  return base + (int64_t)2 * j * (n - 1) - (int64_t)j * (j - 1);
+}
+
+// Published double-float values: one 8-byte single-copy-atomic word each,
+// hi in the low half.  The sentinel's hi half is a NaN with a payload FP32
+// arithmetic never produces (NaN results carry the canonical payload).
+constexpr unsigned long long kSentinelDf = 0xA5A5A5A5FFA5A5A5ull;
+__device__ __forceinline__ void st_pub_df(dfl* p, dfl v) {
+  const unsigned long long bits =
+      ((unsigned long long)__float_as_uint(v.lo) << 32) | (unsigned long long)__float_as_uint(v.hi);
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(bits) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_pub_bits(const dfl* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ dfl df_from_bits(unsigned long long b) {
+  return df_make(__uint_as_float((unsigned)(b & 0xffffffffull)), __uint_as_float((unsigned)(b >> 32)));
+}
+
+__device__ dfl block_sum_df(dfl v, dfl* red, int& parity) {
+  for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  dfl* r = red + 8 * parity;
+  parity ^= 1;
+  if (lane == 0) r[w] = v;
+  __syncthreads();
+  return df_add(df_add(df_add(r[0], r[1]), df_add(r[2], r[3])), df_add(df_add(r[4], r[5]), df_add(r[6], r[7])));
+}
+
+// Square root and quotient in double-float: an FP32 estimate and one
+// Newton correction computed with the exact residual (about 2^-46 relative).
+__device__ __forceinline__ dfl df_sqrt(dfl a) {
+  if (a.hi <= 0.0f) return df_zero();
+  const float y = __fsqrt_rn(a.hi);
+  const float p = __fmul_rn(y, y);
+  const float pe = __fmaf_rn(y, y, -p);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo);
+  return df_fast_two_sum(y, __fdiv_rn(r, __fmul_rn(2.0f, y)));
+}
+__device__ __forceinline__ dfl df_div(dfl x, dfl y) {
+  const float q1 = __fdiv_rn(x.hi, y.hi);
+  const dfl r = df_fma(df_make(-q1, 0.0f), y, x);
+  return df_fast_two_sum(q1, __fdiv_rn(r.hi, y.hi));
+}
+
+// The reflector's scalars from alpha and sigma = sum of the other squares
+// (double-float, one thread): beta, tau and 1 / (alpha - beta).
+__device__ __forceinline__ void reflector_scalars_df(dfl alpha, dfl sigma, dfl* beta, dfl* tau, dfl* scal) {
+  *beta = alpha;
+  *tau = df_zero();
+  *scal = df_zero();
+  if (sigma.hi != 0.0f || sigma.lo != 0.0f) {
+    const dfl nrm = df_sqrt(df_fma(alpha, alpha, sigma));
+    *beta = alpha.hi >= 0.0f ? df_neg(nrm) : nrm;
+    *tau = df_div(df_add(*beta, df_neg(alpha)), *beta);
+    *scal = df_div(df_make(1.0f, 0.0f), df_add(alpha, df_neg(*beta)));
+  }
+}
+
+// The reflector's scalars from alpha and sigma = sum of the other squares
+// (FP64, one thread): beta, tau and 1 / (alpha - beta).
+__device__ __forceinline__ void reflector_scalars(double alpha, double sigma, double* beta, double* tau,
+                                                  double* scal) {
+  *beta = alpha;
+  *tau = 0.0;
+  *scal = 0.0;
+  if (sigma != 0.0) {
+    const double nrm = sqrt(fma(alpha, alpha, sigma));
+    *beta = alpha >= 0.0 ? -nrm : nrm;
+    *tau = (*beta - alpha) / *beta;
+    *scal = 1.0 / (alpha - *beta);
+  }
+}
+
+// Reflector j (u = scal x, x indexed from row j+1) into V1, as store_reflector.
+__device__ void store_reflector_df(const ConeDev& c, int n, int j, const dfl* u, int rank, int G, dfl scal,
+                                   bool scaled) {
+  const int q = j / kNb, col = j % kNb;
+  const int r0 = q * kNb + 1;
+  const int mq = n - r0;
+  double* Vq = c.V1 + (int64_t)q * n * kNb;
+  for (int r = rank * kSyThreads + threadIdx.x; r < mq; r += G * kSyThreads) {
+    const int row = r0 + r;
+    double val = 0.0;
+    if (row == j + 1) val = 1.0;
+    else if (row > j + 1) val = df_to_d(scaled ? df_mul(scal, u[row - j - 1]) : u[row - j - 1]);
+    Vq[(int64_t)r + (int64_t)col * mq] = val;
+  }
+}
+
+// column_pass for the double-float route (columns in shared memory).
+template <bool UPDATE, int CH>
+__device__ void column_pass_df(dfl* __restrict__ cols, int n, int r0, const dfl* __restrict__ x, const dfl* coef,
+                               const dfl* __restrict__ vu, const dfl* __restrict__ pu, dfl K2, dfl* Pn, dfl* Cn,
+                               dfl* psum, int pcap, int rank, int G) {
+  constexpr int NR = CH / 32;
+  const int L = n - r0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int first = r0 + ((rank - r0 % G) + G) % G;
+  const int ncol = first < n ? (n - 1 - first) / G + 1 : 0;
+  const int nch = (L + CH - 1) / CH;
+  const int per = max(1, pcap / nch);
+  for (int k0 = 0; k0 < ncol; k0 += per) {
+    const int kc = min(ncol - k0, per);
+    for (int it = warp; it < kc * nch; it += kSyThreads / 32) {
+      const int k = k0 + it / nch, ch = it % nch;
+      const int i = first + G * k;
+      dfl* col = cols + (int64_t)((i - rank) / G) * n + r0;
+      const int t0 = ch * CH + lane;
+      dfl a[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const int t = t0 + 32 * r;
+        a[r] = t < L ? col[t] : df_zero();
+      }
+      if (UPDATE) {
+        const dfl vi = vu[i - r0 + 1];
+        const dfl nai = df_neg(df_fma(df_neg(K2), vi, pu[i - r0 + 1]));  // -(p_i - 2K v_i)
+        const dfl nvi = df_neg(vi);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const int t = t0 + 32 * r;
+          if (t < L) {
+            a[r] = df_fma(vu[t + 1], nai, df_fma(pu[t + 1], nvi, a[r]));
+            col[t] = a[r];
+          }
+        }
+      }
+      if (i == r0) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const int t = t0 + 32 * r;
+          if (t < L) st_pub_df(Cn + t, a[r]);
+        }
+      }
+      dfl acc0 = df_zero(), acc1 = df_zero();
+#pragma unroll
+      for (int r = 0; r < NR; r += 2) {
+        const int t = t0 + 32 * r;
+        if (t < L && t > 0) acc0 = df_fma(a[r], x[t], acc0);
+        if (r + 1 < NR && t + 32 < L) acc1 = df_fma(a[r + 1], x[t + 32], acc1);
+      }
+      dfl acc = df_add(acc0, acc1);
+      for (int o = 16; o > 0; o >>= 1) acc = df_add(acc, df_shfl_xor(acc, o));
+      if (lane == 0) psum[it] = acc;
+    }
+    __syncthreads();
+    const dfl tau = coef[0], scal = coef[1];
+    for (int kk = tid; kk < kc; kk += kSyThreads) {
+      dfl sdot = df_zero();
+      for (int ch = 0; ch < nch; ++ch) sdot = df_add(sdot, psum[kk * nch + ch]);
+      const int i = first + G * (k0 + kk);
+      const dfl a0 = cols[(int64_t)((i - rank) / G) * n + r0];
+      st_pub_df(Pn + (i - r0), df_mul(tau, df_fma(scal, sdot, a0)));
+    }
+    __syncthreads();
+  }
+  if (ncol == 0) __syncthreads();
+}
+
+template <bool UPDATE>
+__device__ void column_pass_df_any(dfl* cols, int n, int r0, const dfl* x, const dfl* coef, const dfl* vu,
+                                   const dfl* pu, dfl K2, dfl* Pn, dfl* Cn, dfl* psum, int pcap, int rank, int G) {
+  const int L = n - r0;
+  if (L > 512)
+    column_pass_df<UPDATE, 256>(cols, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
+  else if (L > 160)
+    column_pass_df<UPDATE, 128>(cols, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
+  else
+    column_pass_df<UPDATE, 64>(cols, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
+}
+
+__device__ bool poll_step_df(const dfl* P, const dfl* C, int m, const dfl* v, dfl* ps, dfl* bs, long long limit,
+                             dfl* pt_out) {
+  dfl pt = df_zero();
+  int ok = 1;
+  for (int base = 0; base < m && ok; base += 4 * kSyThreads) {
+    unsigned long long pr[4], ar[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int t = base + q * kSyThreads + threadIdx.x;
+      pr[q] = t < m ? ld_pub_bits(P + t) : 0ull;
+      ar[q] = t < m ? ld_pub_bits(C + t) : 0ull;
+    }
+    bool miss = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) miss = miss || pr[q] == kSentinelDf || ar[q] == kSentinelDf;
+    if (miss) {
+      const long long t0 = clock64();
+      while (true) {
+        miss = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int t = base + q * kSyThreads + threadIdx.x;
+          if (pr[q] == kSentinelDf) { pr[q] = ld_pub_bits(P + t); miss = miss || pr[q] == kSentinelDf; }
+          if (ar[q] == kSentinelDf) { ar[q] = ld_pub_bits(C + t); miss = miss || ar[q] == kSentinelDf; }
+        }
+        if (!miss) break;
+        if (clock64() - t0 > limit) { ok = 0; break; }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int t = base + q * kSyThreads + threadIdx.x;
+      if (t < m) {
+        const dfl p = df_from_bits(pr[q]);
+        ps[t] = p;
+        bs[t] = df_add(df_from_bits(ar[q]), df_neg(p));
+        pt = df_fma(p, v[t], pt);
+      }
+    }
+  }
+  *pt_out = pt;
+  return __syncthreads_and(ok) != 0;
+}
+
+// The shared-memory-resident route in double-float arithmetic (structure as
+// sytrd1_body).  sh64: FP64 scalars of thread 0; shd: their double-float copies.
+__device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait_limit, double* sy_smem,
+                               dfl* red, double* sh64, dfl* shd) {
+  const int n = (int)c.n;
+  double* A = c.A;
+  const int pcap = sytrd1_pcap(n, G);
+  dfl* base = reinterpret_cast<dfl*>(sy_smem);
+  dfl* vc = base;
+  dfl* ps = base + n;
+  dfl* bs = base + 2 * n;
+  dfl* psum = base + 3 * n;
+  dfl* cols = base + 3 * n + pcap;
+  double* colsd = sy_smem + 3 * n + pcap;  // the same storage, first loaded as FP64
+  dfl* pub = reinterpret_cast<dfl*>(c.QA);
+  const int tid = threadIdx.x;
+  int parity = 0;
+  // ---- own columns as FP64, and the largest exponent among them
+  int emax = 0;
+  for (int i = rank; i < n; i += G) {
+    const double* src = A + (int64_t)i * n;
+    double* dst = colsd + (int64_t)((i - rank) / G) * n;
+    for (int r = tid; r < n; r += kSyThreads) {
+      const double v = __ldcg(src + r);
+      dst[r] = v;
+      emax = max(emax, (int)((__double2hiint(v) >> 20) & 0x7FF));
+    }
+  }
+  if (n < 3) {
+    __syncthreads();
+    if (rank == 0 && tid == 0) {
+      c.d[0] = A[0];
+      c.e[0] = n == 2 ? A[1] : 0.0;
+      if (n == 2) { c.d[1] = A[3]; c.e[1] = 0.0; }
+    }
+    return;
+  }
+  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  if ((tid & 31) == 0 && emax > 0) atomicMax(c.prog + 1, emax);
+  {
+    const int64_t total = (int64_t)n * n - n - 2;
+    const dfl sent = df_from_bits(kSentinelDf);
+    for (int64_t e = (int64_t)rank * kSyThreads + tid; e < total; e += (int64_t)G * kSyThreads) pub[e] = sent;
+  }
+  if (!group_barrier8(c.prog, rank, G, 1, wait_limit)) {
+    if (tid == 0) atomicOr(c.status, ST_TIMEOUT);
+    return;
+  }
+  // scale 2^(1023 - eb) puts the largest entry into [1, 2); outputs scale back
+  int eb = *((volatile int*)(c.prog + 1));
+  eb = min(max(eb, 1), 2045);
+  const double s_in = __longlong_as_double((long long)(2046 - eb) << 52);
+  const double s_out = __longlong_as_double((long long)eb << 52);
+  for (int i = rank; i < n; i += G) {
+    dfl* dst = cols + (int64_t)((i - rank) / G) * n;
+    const double* srcd = colsd + (int64_t)((i - rank) / G) * n;
+    for (int r = tid; r < n; r += kSyThreads) dst[r] = df_from_d(srcd[r] * s_in);
+  }
+  // ---- prologue: reflector 0 from column 0 (every CTA), p_0 and column 1 into slab 0
+  dfl ss = df_zero();
+  for (int t = tid; t < n - 1; t += kSyThreads) {
+    const dfl v = df_from_d(__ldcg(A + 1 + t) * s_in);
+    vc[t] = v;
+    if (t >= 1) ss = df_fma(v, v, ss);
+  }
+  __syncthreads();
+  {
+    const dfl sig = block_sum_df(ss, red, parity);
+    if (tid == 0) {
+      double beta, tau, scal;
+      reflector_scalars(df_to_d(vc[0]), df_to_d(sig), &beta, &tau, &scal);
+      sh64[0] = beta; sh64[1] = tau;
+      shd[0] = df_from_d(tau); shd[1] = df_from_d(scal);
+    }
+    __syncthreads();
+    const dfl scal = shd[1];
+    for (int t = 1 + tid; t < n - 1; t += kSyThreads) vc[t] = df_mul(scal, vc[t]);
+    __syncthreads();
+    if (tid == 0) vc[0] = df_make(1.0f, 0.0f);
+    if (rank == 0 && tid == 0) {
+      c.d[0] = __ldcg(A);
+      c.e[0] = sh64[0] * s_out;
+      c.tau1[0] = sh64[1];
+    }
+    store_reflector_df(c, n, 0, vc, rank, G, df_zero(), false);
+    if (tid == 0) shd[1] = df_make(1.0f, 0.0f);  // coefficients (tau, 1): v_0 is scaled already
+    __syncthreads();
+  }
+  column_pass_df_any<false>(cols, n, 1, vc, shd, nullptr, nullptr, df_zero(), slab(pub, n, 0), slab(pub, n, 0) + (n - 1),
+                            psum, pcap, rank, G);
+  dfl tau = shd[0];
+  for (int j = 0; j + 2 < n; ++j) {
+    const int m = n - j - 1;
+    dfl* P = slab(pub, n, j);
+    dfl pt;
+    if (!poll_step_df(P, P + m, m, vc, ps, bs, wait_limit, &pt)) {
+      if (tid == 0) atomicOr(c.status, ST_TIMEOUT);
+      return;
+    }
+    const dfl s = block_sum_df(pt, red, parity);
+    const dfl K = df_mul(df_make(0.5f * tau.hi, 0.5f * tau.lo), s);
+    const dfl K2 = df_make(2.0f * K.hi, 2.0f * K.lo);
+    const dfl c0 = df_add(ps[0], df_neg(K2));
+    const dfl nc0 = df_neg(c0);
+    dfl sq = df_zero();
+    for (int t = tid; t < m; t += kSyThreads) {
+      const dfl nc = df_fma(vc[t], nc0, bs[t]);
+      bs[t] = nc;
+      if (t >= 2) sq = df_fma(nc, nc, sq);
+    }
+    if (j + 3 < n) {
+      const dfl sig = block_sum_df(sq, red, parity);
+      dfl beta1;
+      if (tid == 0) reflector_scalars_df(bs[1], sig, &beta1, shd, shd + 1);
+      dfl* Pn = slab(pub, n, j + 1);
+      column_pass_df_any<true>(cols, n, j + 2, bs + 1, shd, vc, ps, K2, Pn, Pn + (m - 1), psum, pcap, rank, G);
+      const dfl tau1 = shd[0], scal1 = shd[1];
+      if (rank == 0 && tid == 0) {
+        c.d[j + 1] = df_to_d(bs[0]) * s_out;
+        c.e[j + 1] = df_to_d(beta1) * s_out;
+        c.tau1[j + 1] = df_to_d(tau1);
+      }
+      store_reflector_df(c, n, j + 1, bs + 1, rank, G, scal1, true);
+      for (int t = tid; t < m - 1; t += kSyThreads) vc[t] = t == 0 ? df_make(1.0f, 0.0f) : df_mul(scal1, bs[1 + t]);
+      tau = tau1;
+      __syncthreads();
+    } else {
+      __syncthreads();
+      if (rank == 0 && tid == 0) {
+        c.d[n - 2] = df_to_d(bs[0]) * s_out;
+        c.e[n - 2] = df_to_d(bs[1]) * s_out;
+        c.e[n - 1] = 0.0;
+      }
+      if (rank == (n - 1) % G && tid == 0) {
+        const dfl a = cols[(int64_t)((n - 1 - rank) / G) * n + (n - 1)];
+        const dfl w1 = df_fma(df_neg(K), vc[1], ps[1]);
+        const dfl two_vw = df_mul(df_make(2.0f * vc[1].hi, 2.0f * vc[1].lo), w1);
+        c.d[n - 1] = df_to_d(df_add(a, df_neg(two_vw))) * s_out;
+      }
+    }
+  }
+}
+
 template <bool RES>
 __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_limit, double* sy_smem, double* red,
                             double* sh) {
@@ -452,9 +876,10 @@ __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __res
   const ConeDev& c = cones[cta_cone[blockIdx.x]];
   const int rank = cta_rank[blockIdx.x], G = cta_count[blockIdx.x];
   if (*c.status != 0) return;
-  // every CTA of a cone takes the same decision (same n, G, launch)
+  // every CTA of a cone takes the same decision (same n, G, launch): columns
+  // in shared memory and double-float arithmetic, or columns in L2 and FP64
   if (sytrd1_bytes((int)c.n, G, true) <= (size_t)smem_bytes)
-    sytrd1_body<true>(c, rank, G, wait_limit, sy_smem, red, sh);
+    sytrd1_body_df(c, rank, G, wait_limit, sy_smem, reinterpret_cast<dfl*>(red), sh, reinterpret_cast<dfl*>(sh + 2));
   else
     sytrd1_body<false>(c, rank, G, wait_limit, sy_smem, red, sh);
 }
