@@ -416,8 +416,10 @@ struct MetaBuilder {
   }
 
   // Picks the engine and tile shape for the launch and a split-K factor per
-  // problem so that the launch has about two CTAs per SM.
-  GemmLaunch add_gemm(std::vector<GemmDesc> probs) {
+  // problem so that the launch has about two CTAs per SM.  bounded: every
+  // operand is at most about 1 in magnitude (eigenvector blocks), so the FP64
+  // path may run the 64 x 64 tiles in double-float arithmetic.
+  GemmLaunch add_gemm(std::vector<GemmDesc> probs, bool bounded = false) {
     if (split && tc2 && !probs.empty()) {
       // long contractions go to the kernel whose operands are sliced once per product
       int maxM = 0, minK = 1 << 30;
@@ -445,6 +447,7 @@ struct MetaBuilder {
     } else {
       g.variant = (maxM <= 16 && maxN <= 16) ? GEMM_SMALL
                   : (maxN <= 16) ? GEMM_TALL : (maxM <= 16) ? GEMM_SHORT : GEMM_SQUARE;
+      if (bounded && g.variant == GEMM_SQUARE && minK >= 32) g.variant = GEMM_SQUARE_DF;
       gemm_tile_shape(g.variant, &bm, &bn);
     }
     int64_t base = 0;
@@ -838,7 +841,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
       lv.pos_off = (int)mb.ints.size();
       mb.ints.insert(mb.ints.end(), loc.begin(), loc.end());
       mb.ints.insert(mb.ints.end(), nid.begin(), nid.end());
-      lv.g = mb.add_gemm(gd);
+      lv.g = mb.add_gemm(gd, true);
       P.levels.push_back(lv);
     }
   }

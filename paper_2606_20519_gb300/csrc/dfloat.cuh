@@ -1,0 +1,80 @@
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two
+// FP32 numbers with |lo| <= ulp(hi) / 2 (Dekker 1971), about 48 significant
+// bits; the error-free transformations TwoSum (Knuth) and TwoProduct (with
+// FMA) give additions and products whose rounding error is about 2^-47 of
+// the operands' magnitude.  On GB300 FP32 runs at 64 times the FP64 rate,
+// where an FP64 warp instruction holds an SMSP's FP64 pipe for 64 cycles, so
+// FP64-class accuracy costs far less in FP32 pairs than in FP64.  Operands
+// must lie within FP32's exponent range; callers scale by powers of two.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace scs {
+
+struct __align__(8) dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfl df_make(float h, float l) {
+  dfl r;
+  r.hi = h;
+  r.lo = l;
+  return r;
+}
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return df_make(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ dfl df_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df_make(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+  const dfl s = df_two_sum(x.hi, y.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ dfl df_neg(dfl x) { return df_make(-x.hi, -x.lo); }
+// x y + z
+__device__ __forceinline__ dfl df_fma(dfl x, dfl y, dfl z) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, e));
+  const dfl s = df_two_sum(p, z.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, z.lo)));
+}
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, e));
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfl df_zero() { return df_make(0.0f, 0.0f); }
+// FP64 <-> double-float (FP64 pipe: used at the boundaries only)
+__device__ __forceinline__ dfl df_from_d(double x) {
+  const float h = __double2float_rn(x);
+  return df_make(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ double df_to_d(dfl x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ dfl df_shfl_xor(dfl v, int o) {
+  return df_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+
+// Square root and quotient in double-float: an FP32 estimate and one
+// Newton correction computed with the exact residual (about 2^-46 relative).
+__device__ __forceinline__ dfl df_sqrt(dfl a) {
+  if (a.hi <= 0.0f) return df_zero();
+  const float y = __fsqrt_rn(a.hi);
+  const float p = __fmul_rn(y, y);
+  const float pe = __fmaf_rn(y, y, -p);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo);
+  return df_fast_two_sum(y, __fdiv_rn(r, __fmul_rn(2.0f, y)));
+}
+__device__ __forceinline__ dfl df_div(dfl x, dfl y) {
+  const float q1 = __fdiv_rn(x.hi, y.hi);
+  const dfl r = df_fma(df_make(-q1, 0.0f), y, x);
+  return df_fast_two_sum(q1, __fdiv_rn(r.hi, y.hi));
+}
+
+
+}  // namespace scs

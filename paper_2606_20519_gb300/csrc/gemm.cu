@@ -16,6 +16,7 @@
 // tile prefix sum maps blockIdx.x to a problem), and sizes that are only
 // known on the device (kept eigenvectors, non-deflated poles) are read from
 // device memory so that the launch sequence is static.
+#include "dfloat.cuh"
 #include "internal.cuh"
 
 namespace scs {
@@ -33,12 +34,24 @@ __device__ __forceinline__ int find_problem(const int* prefix, int count, int ti
 
 constexpr int BK = kGemmBK;
 
-template <int BM, int BN>
-__global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restrict__ descs,
-                                                       const int* __restrict__ prefix, int count) {
+// Arithmetic of the tile loop: FP64, or double-float (dfloat.cuh) for
+// operands bounded in magnitude (eigenvector blocks), where every product
+// is FP32 pipe work and only the staging conversions use the FP64 pipe.
+__device__ __forceinline__ void g_zero(double& a) { a = 0.0; }
+__device__ __forceinline__ void g_zero(dfl& a) { a = df_zero(); }
+__device__ __forceinline__ void g_cvt(double& d, double v) { d = v; }
+__device__ __forceinline__ void g_cvt(dfl& d, double v) { d = df_from_d(v); }
+__device__ __forceinline__ double g_mad(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ dfl g_mad(dfl a, dfl b, dfl c) { return df_fma(a, b, c); }
+__device__ __forceinline__ double g_val(double a) { return a; }
+__device__ __forceinline__ double g_val(dfl a) { return df_to_d(a); }
+
+template <int BM, int BN, typename T>
+__device__ __forceinline__ void gemm_body(const GemmDesc* __restrict__ descs, const int* __restrict__ prefix,
+                                          int count) {
   constexpr int TM = BM / 16, TN = BN / 16;
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
 
   const int tile = blockIdx.x;
   const int p = find_problem(prefix, count, tile);
@@ -66,11 +79,11 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restric
 
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  double acc[TM][TN];
+  T acc[TM][TN];
 #pragma unroll
   for (int r = 0; r < TM; ++r)
 #pragma unroll
-    for (int c = 0; c < TN; ++c) acc[r][c] = 0.0;
+    for (int c = 0; c < TN; ++c) g_zero(acc[r][c]);
 
   const double* __restrict__ A = g.A;
   const double* __restrict__ B = g.B;
@@ -92,7 +105,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restric
           else if (ta) v = A[(int64_t)k + (int64_t)i * lda];
           else v = A[(int64_t)i + (int64_t)k * lda];
         }
-        As[kk][ii] = v;
+        g_cvt(As[kk][ii], v);
       }
     }
 #pragma unroll
@@ -107,13 +120,13 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restric
           v = tb ? B[(int64_t)j + (int64_t)k * ldb] : B[(int64_t)k + (int64_t)j * ldb];
           if (scl) v *= g.bscale[k];
         }
-        Bs[kk][jj] = v;
+        g_cvt(Bs[kk][jj], v);
       }
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[TM], bv[TN];
+      T a[TM], bv[TN];
 #pragma unroll
       for (int r = 0; r < TM; ++r) a[r] = As[kk][tx + 16 * r];
 #pragma unroll
@@ -121,7 +134,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restric
 #pragma unroll
       for (int r = 0; r < TM; ++r)
 #pragma unroll
-        for (int c = 0; c < TN; ++c) acc[r][c] = fma(a[r], bv[c], acc[r][c]);
+        for (int c = 0; c < TN; ++c) acc[r][c] = g_mad(a[r], bv[c], acc[r][c]);
     }
     __syncthreads();
   }
@@ -136,7 +149,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restric
 #pragma unroll
       for (int r = 0; r < TM; ++r) {
         const int i = i0 + tx + 16 * r;
-        if (i < M) part[(int64_t)i + (int64_t)j * Ms] = acc[r][c];
+        if (i < M) part[(int64_t)i + (int64_t)j * Ms] = g_val(acc[r][c]);
       }
     }
     return;
@@ -155,11 +168,23 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restric
       if (i >= M) continue;
       if (lowc && i < j) continue;
       double* cp = (flags & GF_TRANS_C) ? C + (int64_t)jc + (int64_t)i * ldc : C + (int64_t)i + (int64_t)jc * ldc;
-      double v = alpha * acc[r][c];
+      double v = alpha * g_val(acc[r][c]);
       if (beta != 0.0) v = fma(beta, (flags & GF_BETA_B) ? g.B[(int64_t)i + (int64_t)j * g.ldb] : *cp, v);
       *cp = v;
     }
   }
+}
+
+template <int BM, int BN>
+__global__ void __launch_bounds__(256) gemm_f64_kernel(const GemmDesc* __restrict__ descs,
+                                                       const int* __restrict__ prefix, int count) {
+  gemm_body<BM, BN, double>(descs, prefix, count);
+}
+
+template <int BM, int BN>
+__global__ void __launch_bounds__(256) gemm_df_kernel(const GemmDesc* __restrict__ descs,
+                                                      const int* __restrict__ prefix, int count) {
+  gemm_body<BM, BN, dfl>(descs, prefix, count);
 }
 
 // Sums the split-K slices of every problem with splitk > 1 (blockIdx.y).
@@ -195,13 +220,18 @@ void gemm_tile_shape(int variant, int* bm, int* bn) {
     case GEMM_TALL: *bm = 128; *bn = 16; break;
     case GEMM_SHORT: *bm = 16; *bn = 128; break;
     case GEMM_SMALL: *bm = 16; *bn = 16; break;
-    default: *bm = 64; *bn = 64; break;
+    default: *bm = 64; *bn = 64; break;  // GEMM_SQUARE, GEMM_SQUARE_DF
   }
 }
 
 void launch_gemm(const GemmDesc* descs, const int* tile_prefix, int count, int total_tiles, int variant,
                  int needs_reduce, int64_t max_mn, cudaStream_t s) {
   if (count <= 0 || total_tiles <= 0) return;
+  if (variant == GEMM_SQUARE_DF) {
+    gemm_df_kernel<64, 64><<<total_tiles, 256, 0, s>>>(descs, tile_prefix, count);
+    if (needs_reduce) launch_gemm_reduce(descs, count, max_mn, s);
+    return;
+  }
   switch (variant) {
     case GEMM_TALL: gemm_f64_kernel<128, 16><<<total_tiles, 256, 0, s>>>(descs, tile_prefix, count); break;
     case GEMM_SHORT: gemm_f64_kernel<16, 128><<<total_tiles, 256, 0, s>>>(descs, tile_prefix, count); break;

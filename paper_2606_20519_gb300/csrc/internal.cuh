@@ -76,7 +76,9 @@ int64_t tc2_slice_floats(int rows, int K);
 int tc2_slice_ctas(int rows, int K);
 
 constexpr int kGemmBK = 16;
-enum : int { GEMM_SQUARE = 0, GEMM_TALL = 1, GEMM_SHORT = 2, GEMM_SMALL = 3 };  // 64x64, 128x16, 16x128, 16x16
+// 64x64, 128x16, 16x128, 16x16; GEMM_SQUARE_DF: 64x64 in double-float arithmetic (operands of magnitude
+// at most about 1e30, as the eigenvector blocks of the divide and conquer)
+enum : int { GEMM_SQUARE = 0, GEMM_TALL = 1, GEMM_SHORT = 2, GEMM_SMALL = 3, GEMM_SQUARE_DF = 4 };
 
 void gemm_tile_shape(int variant, int* bm, int* bn);
 

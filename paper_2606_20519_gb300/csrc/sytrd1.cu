@@ -35,6 +35,7 @@
 // factor T of H_0 ... H_31 = I - V T V^T.
 #include <math.h>
 
+#include "dfloat.cuh"
 #include "internal.cuh"
 
 namespace scs {
@@ -316,66 +317,13 @@ __host__ __device__ inline size_t sytrd1_bytes(int n, int G, bool res) {
 
 // ---------------------------------------------------------------- double-float path
 // The shared-memory-resident route (every CTA's columns in shared memory)
-// computes in double-float arithmetic: a value is an unevaluated sum hi + lo
-// of two FP32 numbers (Dekker 1971; error-free transformations TwoSum and
-// TwoProduct with FMA), 48 significant bits, relative rounding of an
-// operation about 2^-47 of its operands.  On this part FP32 runs at 64 times
-// the FP64 rate, and every operation of the reduction is an FP32 pipe
-// instruction, where an FP64 warp instruction holds the SMSP's FP64 pipe
-// for 64 cycles.  The matrix is scaled by a power of two into [1, 2) for its
-// largest entry first (exact; FP32's exponent range then holds every entry
-// whose magnitude matters at FP64 accuracy), d and e are scaled back, the
-// reflectors and tau are scale-free.  The reflector's scalars (a square root
-// and two divisions, one thread per step) stay in FP64.
-struct __align__(8) dfl {
-  float hi, lo;
-};
-
-__device__ __forceinline__ dfl df_make(float h, float l) {
-  dfl r;
-  r.hi = h;
-  r.lo = l;
-  return r;
-}
-__device__ __forceinline__ dfl df_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  return df_make(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
-}
-__device__ __forceinline__ dfl df_fast_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return df_make(s, __fsub_rn(b, __fsub_rn(s, a)));
-}
-__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
-  const dfl s = df_two_sum(x.hi, y.hi);
-  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
-}
-__device__ __forceinline__ dfl df_neg(dfl x) { return df_make(-x.hi, -x.lo); }
-// x y + z
-__device__ __forceinline__ dfl df_fma(dfl x, dfl y, dfl z) {
-  const float p = __fmul_rn(x.hi, y.hi);
-  float e = __fmaf_rn(x.hi, y.hi, -p);
-  e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, e));
-  const dfl s = df_two_sum(p, z.hi);
-  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, z.lo)));
-}
-__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
-  const float p = __fmul_rn(x.hi, y.hi);
-  float e = __fmaf_rn(x.hi, y.hi, -p);
-  e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, e));
-  return df_fast_two_sum(p, e);
-}
-__device__ __forceinline__ dfl df_zero() { return df_make(0.0f, 0.0f); }
-// FP64 <-> double-float (FP64 pipe: used at the boundaries only)
-__device__ __forceinline__ dfl df_from_d(double x) {
-  const float h = __double2float_rn(x);
-  return df_make(h, __double2float_rn(x - (double)h));
-}
-__device__ __forceinline__ double df_to_d(dfl x) { return (double)x.hi + (double)x.lo; }
-__device__ __forceinline__ dfl df_shfl_xor(dfl v, int o) {
-  return df_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
-}
-
+// computes in double-float arithmetic (dfloat.cuh): every operation of a step
+// is an FP32 pipe instruction.  The matrix is scaled by a power of two into
+// [1, 2) for its largest entry first (exact; FP32's exponent range then holds
+// every entry whose magnitude matters at FP64 accuracy), d and e are scaled
+// back, the reflectors and tau are scale-free.  FP64 is left for the
+// conversions at the boundaries (the matrix once, d, e, tau and the stored
+// reflectors) and the first reflector's scalars.
 __device__ __forceinline__ dfl* slab(dfl* base, int n, int j) {
   return base + (int64_t)2 * j * (n - 1) - (int64_t)j * (j - 1);
 }
@@ -406,22 +354,6 @@ __device__ dfl block_sum_df(dfl v, dfl* red, int& parity) {
   if (lane == 0) r[w] = v;
   __syncthreads();
   return df_add(df_add(df_add(r[0], r[1]), df_add(r[2], r[3])), df_add(df_add(r[4], r[5]), df_add(r[6], r[7])));
-}
-
-// Square root and quotient in double-float: an FP32 estimate and one
-// Newton correction computed with the exact residual (about 2^-46 relative).
-__device__ __forceinline__ dfl df_sqrt(dfl a) {
-  if (a.hi <= 0.0f) return df_zero();
-  const float y = __fsqrt_rn(a.hi);
-  const float p = __fmul_rn(y, y);
-  const float pe = __fmaf_rn(y, y, -p);
-  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo);
-  return df_fast_two_sum(y, __fdiv_rn(r, __fmul_rn(2.0f, y)));
-}
-__device__ __forceinline__ dfl df_div(dfl x, dfl y) {
-  const float q1 = __fdiv_rn(x.hi, y.hi);
-  const dfl r = df_fma(df_make(-q1, 0.0f), y, x);
-  return df_fast_two_sum(q1, __fdiv_rn(r.hi, y.hi));
 }
 
 // The reflector's scalars from alpha and sigma = sum of the other squares
@@ -483,7 +415,8 @@ __device__ void column_pass_df(dfl* __restrict__ cols, int n, int r0, const dfl*
   const int per = max(1, pcap / nch);
   for (int k0 = 0; k0 < ncol; k0 += per) {
     const int kc = min(ncol - k0, per);
-    for (int it = warp; it < kc * nch; it += kSyThreads / 32) {
+    // warp 0, whose thread 0 forms the next reflector's scalars meanwhile, takes items last
+    for (int it = (warp + kSyThreads / 32 - 1) % (kSyThreads / 32); it < kc * nch; it += kSyThreads / 32) {
       const int k = k0 + it / nch, ch = it % nch;
       const int i = first + G * k;
       dfl* col = cols + (int64_t)((i - rank) / G) * n + r0;
@@ -534,7 +467,9 @@ __device__ void column_pass_df(dfl* __restrict__ cols, int n, int r0, const dfl*
       const dfl a0 = cols[(int64_t)((i - rank) / G) * n + r0];
       st_pub_df(Pn + (i - r0), df_mul(tau, df_fma(scal, sdot, a0)));
     }
-    __syncthreads();
+    // psum is written again only by a later round of this pass (the next
+    // pass starts after the step's other barriers)
+    if (k0 + per < ncol) __syncthreads();
   }
   if (ncol == 0) __syncthreads();
 }
@@ -552,7 +487,7 @@ __device__ void column_pass_df_any(dfl* cols, int n, int r0, const dfl* x, const
 }
 
 __device__ bool poll_step_df(const dfl* P, const dfl* C, int m, const dfl* v, dfl* ps, dfl* bs, long long limit,
-                             dfl* pt_out) {
+                             dfl* red) {
   dfl pt = df_zero();
   int ok = 1;
   for (int base = 0; base < m && ok; base += 4 * kSyThreads) {
@@ -591,7 +526,9 @@ __device__ bool poll_step_df(const dfl* P, const dfl* C, int m, const dfl* v, df
       }
     }
   }
-  *pt_out = pt;
+  // this warp's part of p^T v into red[warp] before the barrier
+  for (int o = 16; o > 0; o >>= 1) pt = df_add(pt, df_shfl_xor(pt, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = pt;
   return __syncthreads_and(ok) != 0;
 }
 
@@ -689,12 +626,14 @@ __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait
   for (int j = 0; j + 2 < n; ++j) {
     const int m = n - j - 1;
     dfl* P = slab(pub, n, j);
-    dfl pt;
-    if (!poll_step_df(P, P + m, m, vc, ps, bs, wait_limit, &pt)) {
+    dfl* rp = red + 8 * parity;
+    parity ^= 1;
+    if (!poll_step_df(P, P + m, m, vc, ps, bs, wait_limit, rp)) {
       if (tid == 0) atomicOr(c.status, ST_TIMEOUT);
       return;
     }
-    const dfl s = block_sum_df(pt, red, parity);
+    const dfl s = df_add(df_add(df_add(rp[0], rp[1]), df_add(rp[2], rp[3])),
+                         df_add(df_add(rp[4], rp[5]), df_add(rp[6], rp[7])));
     const dfl K = df_mul(df_make(0.5f * tau.hi, 0.5f * tau.lo), s);
     const dfl K2 = df_make(2.0f * K.hi, 2.0f * K.lo);
     const dfl c0 = df_add(ps[0], df_neg(K2));
