@@ -477,6 +477,23 @@ def measure(args, env, config, precision, steps, warmup, full):
         P = W.to_hsvec(Pm) if wl.herm else W.to_svec(Pm)
         y0 = (yb if wl.vjp else ys[0])[: wl.svec_len(n0)].cpu().numpy()
         err0 = rel(y0, P)
+    # the error statement the library returns with each result (opts.stats):
+    # the FP64 complementarity residual <Y, Y - X> / (||Y|| ||X||) of every cone
+    # of the first call, untimed
+    stats0 = None
+    if not poly and not wl.herm and not wl.mixing and wl.scs is None:
+        offs0, sides0 = shapes[0]
+        sopts = lib.make_opts(band=args.band, precision=prec, stats=True)
+        ytmp = torch.empty_like(xs[0])
+        if wl.vjp:
+            lib.proj_vjp(xs[0], gs[0], sides0, xbar=torch.empty_like(xs[0]), y=ytmp, opts=sopts, offsets=offs0)
+        else:
+            lib.proj_batched(xs[0], sides0, out=ytmp, opts=sopts, offsets=offs0)
+        recs = lib.last_stats(len(sides0), local)
+        comp = [abs(r["complementarity"]) for r in recs]
+        stats0 = {"cones": len(recs), "max_abs_complementarity": max(comp),
+                  "k_pos_first": recs[0]["k_pos"], "k_neg_first": recs[0]["k_neg"],
+                  "status": max(r["status"] for r in recs)}
 
     for _ in range(warmup):
         step(xs, ys)
@@ -523,7 +540,7 @@ def measure(args, env, config, precision, steps, warmup, full):
     if not full:
         return None if rank != 0 else leg_record(args, wl, config, precision, steps, warmup, ms_per_step, value,
                                                   phases, tuning, b_used, clk, status, err0, launches_per_step,
-                                                  traced_ms, xs, dev, stream, ys, yb)
+                                                  traced_ms, xs, dev, stream, ys, yb, stats0)
     hx = [torch.from_numpy(x).pin_memory() for x, _ in wl.calls]
     hy = [torch.empty_like(h).pin_memory() for h in hx]
     hg = torch.from_numpy(wl.g).pin_memory() if wl.vjp else None
@@ -606,6 +623,7 @@ def measure(args, env, config, precision, steps, warmup, full):
         "clocks": clk,
         "status": int(status) if status == st else int(status),
         "max_rel_err_first_cone_vs_construction": err0,
+        "stats_first_call": stats0,
     }
     if not args.no_comparator:
         line["comparator"] = comparator(wl, xs, dev, stream)
@@ -620,7 +638,7 @@ def measure(args, env, config, precision, steps, warmup, full):
 
 
 def leg_record(args, wl, config, precision, steps, warmup, ms_per_step, value, phases, tuning, b_used, clk,
-               status, err0, launches_per_step, traced_ms, xs, dev, stream, ys, yb):
+               status, err0, launches_per_step, traced_ms, xs, dev, stream, ys, yb, stats0):
     """The record of one leg of the default run: value, comparator, roofline,
     error against the construction, clocks."""
     unit = "projections/s" if not wl.vjp else "(projection + VJP)/s"
@@ -634,6 +652,7 @@ def leg_record(args, wl, config, precision, steps, warmup, ms_per_step, value, p
         "gpu_launches": int(launches_per_step * steps),
         "clocks": clk, "status": int(status),
         "max_rel_err_first_cone_vs_construction": err0,
+        "stats_first_call": stats0,
         "l2": "flushed before every timed step (256 MB write)",
     }
     if wl.vjp:

@@ -1192,7 +1192,7 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
         LAUNCH_CHECK();
         launch_dc_apply_rot(P.cones_d, nodes, pos, P.total_pos, s);
         LAUNCH_CHECK();
-        launch_dc_secular(P.cones_d, nodes, pos, P.total_pos, s);
+        launch_dc_secular(P.cones_d, nodes, pos, P.total_pos, lv.maxK, s);
         LAUNCH_CHECK();
         launch_dc_loewner(P.cones_d, nodes, pos, P.total_pos, s);
         LAUNCH_CHECK();

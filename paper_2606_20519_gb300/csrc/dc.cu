@@ -39,6 +39,24 @@ __device__ __forceinline__ long long dkey(double x) {
   return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
 }
 
+// 1/x by Newton's iteration for the reciprocal, r <- r + r (1 - x r), from
+// the hardware's FP64 reciprocal approximation: two steps take its relative
+// error below FP64 rounding (a quotient a * rcp_nr(b) is within about 1.5 ulp
+// of a / b) in five FP64-pipe instructions, a fraction of an IEEE division.
+// Used where the quotients only feed sums and products (the secular
+// function, the Loewner products, the vector components).  Magnitudes
+// outside [2^-1000, 2^1000] take the exact division.
+__device__ __forceinline__ double rcp_nr(double x) {
+  const int ex = (__double2hiint(x) >> 20) & 0x7FF;
+  if (ex < 23 || ex > 2023) return 1.0 / x;
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 // x > 0 and x < 0 for finite x from its bit pattern (no FP64 instruction)
 __device__ __forceinline__ bool d_pos(double x) { return __double_as_longlong(x) > 0; }
 __device__ __forceinline__ bool d_neg(double x) {
@@ -384,14 +402,14 @@ __device__ __forceinline__ float f64_to_f32_rn(double v) {
 // lane ends with the same values).  Returns the origin pole and the offset
 // tau = x - d_org; false if the iteration cap was reached.
 __device__ bool secular_root_warp(const double* __restrict__ dk, const double* __restrict__ zk, int K, double rho,
-                                  int i, int lane, int* org_out, double* tau_out) {
+                                  int i, int lane, float* dif, int* org_out, double* tau_out) {
   int org;
   double lo, hi;
   if (i < K - 1) {
     const double di = dk[i];
     const double mid = 0.5 * (dk[i + 1] - di);
     double f = 0.0;
-    for (int j = lane; j < K; j += 32) f += zk[j] * zk[j] / ((dk[j] - di) - mid);
+    for (int j = lane; j < K; j += 32) f += zk[j] * zk[j] * rcp_nr((dk[j] - di) - mid);
     f = 1.0 + rho * warp_sum_d(f);
     if (f >= 0.0) { org = i; lo = 0.0; hi = mid; }
     else { org = i + 1; lo = -mid; hi = 0.0; }
@@ -409,6 +427,10 @@ __device__ bool secular_root_warp(const double* __restrict__ dk, const double* _
   // beyond its FP32 error bound; the FP64 loop below then polishes from the
   // narrowed bracket.  Only the differences d_j - d_org are formed in FP64.
   {
+    // d_j - d_org in FP32, formed in FP64 once per root (dif: this warp's K floats)
+    if (dif)
+      for (int j = lane; j < K; j += 32) dif[j] = f64_to_f32_rn(dk[j] - dorg);
+    __syncwarp();
     const float rho32 = f64_to_f32_rn(rho);
     const float p32 = f64_to_f32_rn(dk[li] - dorg);
     const float q32 = ri < K ? f64_to_f32_rn(dk[ri] - dorg) : 0.0f;
@@ -416,7 +438,7 @@ __device__ bool secular_root_warp(const double* __restrict__ dk, const double* _
       const float t32 = f64_to_f32_rn(tau);
       float psi = 0.0f, phi = 0.0f, dpsi = 0.0f, dphi = 0.0f, aerr = 0.0f;
       for (int j = lane; j < K; j += 32) {
-        const float del = f64_to_f32_rn(dk[j] - dorg) - t32;
+        const float del = (dif ? dif[j] : f64_to_f32_rn(dk[j] - dorg)) - t32;
         const float zz = f64_to_f32_rn(zk[j]);
         const float t = zz / del;
         const float term = zz * t;
@@ -474,7 +496,7 @@ __device__ bool secular_root_warp(const double* __restrict__ dk, const double* _
     for (int j = lane; j < K; j += 32) {
       const double del = (dk[j] - dorg) - tau;
       const double zz = zk[j];
-      const double t = zz / del;
+      const double t = zz * rcp_nr(del);
       const double term = zz * t;
       if (j < ri) { psi += term; dpsi = fma(t, t, dpsi); }
       else { phi += term; dphi = fma(t, t, dphi); }
@@ -558,7 +580,7 @@ __device__ __forceinline__ WarpPos warp_pos(const MergeNode* nodes, const int* p
 }
 
 __global__ void dc_secular_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes,
-                                  const int* __restrict__ pos_node, int64_t total) {
+                                  const int* __restrict__ pos_node, int64_t total, int difmax) {
   const WarpPos w = warp_pos(nodes, pos_node, total);
   if (!w.ok) return;
   const ConeDev& c = cones[w.nd.cone];
@@ -567,9 +589,11 @@ __global__ void dc_secular_kernel(const ConeDev* __restrict__ cones, const Merge
   const int kk = c.icnt[4 * s];
   if (i >= kk) return;
   const int lane = threadIdx.x & 31;
+  extern __shared__ float sec_dif[];
+  float* dif = difmax >= kk ? sec_dif + (threadIdx.x >> 5) * difmax : nullptr;
   int org;
   double tau;
-  const bool ok = secular_root_warp(c.dsrt + s, c.zk + s, kk, c.rho[s], i, lane, &org, &tau);
+  const bool ok = secular_root_warp(c.dsrt + s, c.zk + s, kk, c.rho[s], i, lane, dif, &org, &tau);
   if (lane == 0) {
     c.iorg[s + i] = org;
     c.tau[s + i] = tau;
@@ -600,8 +624,8 @@ __global__ void dc_loewner_kernel(const ConeDev* __restrict__ cones, const Merge
   const double dj = dk[j];
   double prod = 1.0;
   for (int i = lane; i < kk; i += 32) {
-    if (i < j) prod *= lam_minus_d(dk, org, tau, i, j) / (dk[i] - dj);
-    else if (i > j) prod *= lam_minus_d(dk, org, tau, i - 1, j) / (dk[i] - dj);
+    if (i < j) prod *= lam_minus_d(dk, org, tau, i, j) * rcp_nr(dk[i] - dj);
+    else if (i > j) prod *= lam_minus_d(dk, org, tau, i - 1, j) * rcp_nr(dk[i] - dj);
   }
   prod = warp_prod_d(prod) * (lam_minus_d(dk, org, tau, kk - 1, j) / c.rho[s]);
   if (lane == 0) c.zhat[s + j] = copysign(sqrt(fabs(prod)), c.zk[s + j]);
@@ -758,7 +782,7 @@ __global__ void dc_vecnorm_kernel(const ConeDev* __restrict__ cones, const Merge
   const double tau = c.tau[s + i];
   double nrm = 0.0;
   for (int j = lane; j < kk; j += 32) {
-    const double u = zh[j] / ((dk[j] - dorg) - tau);
+    const double u = zh[j] * rcp_nr((dk[j] - dorg) - tau);
     nrm = fma(u, u, nrm);
   }
   nrm = warp_sum_d(nrm);
@@ -797,7 +821,7 @@ __global__ void dc_vectors_kernel(const ConeDev* __restrict__ cones, const Merge
   const double inv = c.unrm[s + i];
   double* U = c.Ucm + s + row + (int64_t)s * n;  // U[j * n] = component j
   const int jend = min(kk, j0 + kVecChunk);
-  for (int j = j0; j < jend; ++j) U[(int64_t)j * n] = inv * (zh[j] / ((dk[j] - dorg) - tau));
+  for (int j = j0; j < jend; ++j) U[(int64_t)j * n] = inv * (zh[j] * rcp_nr((dk[j] - dorg) - tau));
 }
 
 // deflated columns: Qin(:, kk + q) -> output column; blockIdx.x = node,
@@ -845,10 +869,20 @@ void launch_dc_prepare(const ConeDev* cones, const MergeNode* nodes, int nnodes,
   dc_prepare_kernel<<<nnodes, kDcThreads, smem, s>>>(cones, nodes);
 }
 
-void launch_dc_secular(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total,
+void launch_dc_secular(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total, int maxK,
                        cudaStream_t s) {
   if (total <= 0) return;
-  dc_secular_kernel<<<(unsigned)((total * 32 + 127) / 128), 128, 0, s>>>(cones, nodes, pos_node, total);
+  // four warps per CTA, each with maxK floats of shared memory (none when that would not fit)
+  constexpr size_t kSecSmemMax = 160 * 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(dc_secular_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSecSmemMax);
+    attr = true;
+  }
+  const size_t smem = (size_t)4 * maxK * sizeof(float);
+  const int difmax = smem <= kSecSmemMax ? maxK : 0;
+  dc_secular_kernel<<<(unsigned)((total * 32 + 127) / 128), 128, difmax ? smem : 0, s>>>(cones, nodes, pos_node,
+                                                                                         total, difmax);
 }
 
 void launch_dc_loewner(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total,

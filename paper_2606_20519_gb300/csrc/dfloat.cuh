@@ -60,20 +60,23 @@ __device__ __forceinline__ dfl df_shfl_xor(dfl v, int o) {
   return df_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
 }
 
-// Square root and quotient in double-float: an FP32 estimate and one
-// Newton correction computed with the exact residual (about 2^-46 relative).
+// Square root and quotient in double-float: a correctly rounded FP32
+// estimate and one Newton correction from the exact residual (about 2^-46
+// relative); the correction, about 2^-24 of the estimate, takes an
+// approximate FP32 quotient.
 __device__ __forceinline__ dfl df_sqrt(dfl a) {
   if (a.hi <= 0.0f) return df_zero();
   const float y = __fsqrt_rn(a.hi);
   const float p = __fmul_rn(y, y);
   const float pe = __fmaf_rn(y, y, -p);
   const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo);
-  return df_fast_two_sum(y, __fdiv_rn(r, __fmul_rn(2.0f, y)));
+  // the correction is about 2^-24 of y: an approximate quotient (2 ulp) suffices
+  return df_fast_two_sum(y, __fdividef(r, __fmul_rn(2.0f, y)));
 }
 __device__ __forceinline__ dfl df_div(dfl x, dfl y) {
   const float q1 = __fdiv_rn(x.hi, y.hi);
   const dfl r = df_fma(df_make(-q1, 0.0f), y, x);
-  return df_fast_two_sum(q1, __fdiv_rn(r.hi, y.hi));
+  return df_fast_two_sum(q1, __fdividef(r.hi, y.hi));
 }
 
 

@@ -220,7 +220,7 @@ void launch_tridiag_extract(const ConeDev* cones, int ncones, int64_t maxn, cuda
 void launch_dc_leaves(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s);
 void launch_dc_prepare(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s);
 void launch_dc_secular(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total_pos,
-                       cudaStream_t s);
+                       int maxK, cudaStream_t s);
 void launch_dc_loewner(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total_pos,
                        cudaStream_t s);
 void launch_dc_select(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s);

@@ -310,9 +310,11 @@ __host__ __device__ inline int sytrd1_pcap(int n, int G) {
   const int items = ((n + G - 1) / G) * ((n + 63) / 64);  // up to 64-row items
   return items < kPartMax ? items : kPartMax;
 }
+// Resident route (double-float): two v buffers, p, the updated column (4n)
+// and the CTA's own columns; otherwise v, p, column and the partial sums.
 __host__ __device__ inline size_t sytrd1_bytes(int n, int G, bool res) {
-  const size_t own = res ? (size_t)((n + G - 1) / G) * n : 0;
-  return ((size_t)3 * n + sytrd1_pcap(n, G) + own) * sizeof(double);
+  if (res) return ((size_t)4 * n + (size_t)((n + G - 1) / G) * n) * sizeof(double);
+  return ((size_t)3 * n + sytrd1_pcap(n, G)) * sizeof(double);
 }
 
 // ---------------------------------------------------------------- double-float path
@@ -401,90 +403,75 @@ __device__ void store_reflector_df(const ConeDev& c, int n, int j, const dfl* u,
   }
 }
 
-// column_pass for the double-float route (columns in shared memory).
-template <bool UPDATE, int CH>
-__device__ void column_pass_df(dfl* __restrict__ cols, int n, int r0, const dfl* __restrict__ x, const dfl* coef,
-                               const dfl* __restrict__ vu, const dfl* __restrict__ pu, dfl K2, dfl* Pn, dfl* Cn,
-                               dfl* psum, int pcap, int rank, int G) {
-  constexpr int NR = CH / 32;
-  const int L = n - r0;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int first = r0 + ((rank - r0 % G) + G) % G;
-  const int ncol = first < n ? (n - 1 - first) / G + 1 : 0;
-  const int nch = (L + CH - 1) / CH;
-  const int per = max(1, pcap / nch);
-  for (int k0 = 0; k0 < ncol; k0 += per) {
-    const int kc = min(ncol - k0, per);
-    // warp 0, whose thread 0 forms the next reflector's scalars meanwhile, takes items last
-    for (int it = (warp + kSyThreads / 32 - 1) % (kSyThreads / 32); it < kc * nch; it += kSyThreads / 32) {
-      const int k = k0 + it / nch, ch = it % nch;
-      const int i = first + G * k;
-      dfl* col = cols + (int64_t)((i - rank) / G) * n + r0;
-      const int t0 = ch * CH + lane;
-      dfl a[NR];
-#pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        const int t = t0 + 32 * r;
-        a[r] = t < L ? col[t] : df_zero();
-      }
-      if (UPDATE) {
-        const dfl vi = vu[i - r0 + 1];
-        const dfl nai = df_neg(df_fma(df_neg(K2), vi, pu[i - r0 + 1]));  // -(p_i - 2K v_i)
-        const dfl nvi = df_neg(vi);
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const int t = t0 + 32 * r;
-          if (t < L) {
-            a[r] = df_fma(vu[t + 1], nai, df_fma(pu[t + 1], nvi, a[r]));
-            col[t] = a[r];
-          }
-        }
-      }
-      if (i == r0) {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const int t = t0 + 32 * r;
-          if (t < L) st_pub_df(Cn + t, a[r]);
-        }
-      }
-      dfl acc0 = df_zero(), acc1 = df_zero();
-#pragma unroll
-      for (int r = 0; r < NR; r += 2) {
-        const int t = t0 + 32 * r;
-        if (t < L && t > 0) acc0 = df_fma(a[r], x[t], acc0);
-        if (r + 1 < NR && t + 32 < L) acc1 = df_fma(a[r + 1], x[t + 32], acc1);
-      }
-      dfl acc = df_add(acc0, acc1);
-      for (int o = 16; o > 0; o >>= 1) acc = df_add(acc, df_shfl_xor(acc, o));
-      if (lane == 0) psum[it] = acc;
+// Waits (bounded) until thread 0 of this CTA has announced the reflector's
+// scalars for `tag`.
+__device__ __forceinline__ void wait_coef(const int* coef_tag, int tag, int* status) {
+  if (*(volatile const int*)coef_tag != tag) {
+    long long spins = 0;
+    while (*(volatile const int*)coef_tag != tag) {
+      if (++spins > (1ll << 30)) { atomicOr(status, ST_TIMEOUT); break; }
     }
-    __syncthreads();
-    const dfl tau = coef[0], scal = coef[1];
-    for (int kk = tid; kk < kc; kk += kSyThreads) {
-      dfl sdot = df_zero();
-      for (int ch = 0; ch < nch; ++ch) sdot = df_add(sdot, psum[kk * nch + ch]);
-      const int i = first + G * (k0 + kk);
-      const dfl a0 = cols[(int64_t)((i - rank) / G) * n + r0];
-      st_pub_df(Pn + (i - r0), df_mul(tau, df_fma(scal, sdot, a0)));
-    }
-    // psum is written again only by a later round of this pass (the next
-    // pass starts after the step's other barriers)
-    if (k0 + per < ncol) __syncthreads();
   }
-  if (ncol == 0) __syncthreads();
+  __threadfence_block();
 }
 
+// The double-float pass with one warp per column: the warp applies step
+// j's rank-2 update to all of its column's rows, forms the column's whole dot
+// product with the next reflector's source x, and its lane 0 publishes
+// p_i = tau (A(r0, i) + scal sum_{r > r0} A(r, i) x_r) as soon as thread 0 has
+// set the reflector's scalars (coef, announced by *coef_tag = tag).  No CTA
+// barrier: columns go to warps 1, 2, .., 7, 0 (warp 0's thread 0 forms the
+// scalars first).  The owner of column r0 publishes its rows to Cn.
 template <bool UPDATE>
-__device__ void column_pass_df_any(dfl* cols, int n, int r0, const dfl* x, const dfl* coef, const dfl* vu,
-                                   const dfl* pu, dfl K2, dfl* Pn, dfl* Cn, dfl* psum, int pcap, int rank, int G) {
+__device__ void column_pass_dfw(dfl* __restrict__ cols, int n, int r0, const dfl* __restrict__ x, const dfl* coef,
+                                const int* coef_tag, int tag, const dfl* __restrict__ vu,
+                                const dfl* __restrict__ pu, dfl K2, dfl* Pn, dfl* Cn, int rank, int G,
+                                int* status) {
+  constexpr int U = 4;
+  constexpr int NW = kSyThreads / 32;
   const int L = n - r0;
-  if (L > 512)
-    column_pass_df<UPDATE, 256>(cols, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
-  else if (L > 160)
-    column_pass_df<UPDATE, 128>(cols, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
-  else
-    column_pass_df<UPDATE, 64>(cols, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int first = r0 + ((rank - r0 % G) + G) % G;
+  const int ncol = first < n ? (n - 1 - first) / G + 1 : 0;
+  for (int k = (warp + NW - 1) % NW; k < ncol; k += NW) {
+    const int i = first + G * k;
+    dfl* col = cols + (int64_t)((i - rank) / G) * n + r0;
+    const bool pub_col = i == r0;
+    dfl nai = df_zero(), nvi = df_zero();
+    if (UPDATE) {
+      const dfl vi = vu[i - r0 + 1];
+      nai = df_neg(df_fma(df_neg(K2), vi, pu[i - r0 + 1]));  // -(p_i - 2K v_i)
+      nvi = df_neg(vi);
+    }
+    dfl acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = df_zero();
+    for (int t0 = lane; t0 < L; t0 += 32 * U) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int t = t0 + 32 * u;
+        if (t < L) {
+          dfl a = col[t];
+          if (UPDATE) {
+            a = df_fma(vu[t + 1], nai, df_fma(pu[t + 1], nvi, a));
+            col[t] = a;
+          }
+          if (pub_col) st_pub_df(Cn + t, a);
+          if (t > 0) acc[u] = df_fma(a, x[t], acc[u]);
+        }
+      }
+    }
+    dfl sdot = df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3]));
+    for (int o = 16; o > 0; o >>= 1) sdot = df_add(sdot, df_shfl_xor(sdot, o));
+    if (lane == 0) {
+      // thread 0 of this CTA forms the scalars while the columns are updated
+      wait_coef(coef_tag, tag, status);
+      const dfl tau = coef[0], scal = coef[1];
+      st_pub_df(Pn + (i - r0), df_mul(tau, df_fma(scal, sdot, col[0])));
+    }
+  }
 }
+
 
 __device__ bool poll_step_df(const dfl* P, const dfl* C, int m, const dfl* v, dfl* ps, dfl* bs, long long limit,
                              dfl* red) {
@@ -535,17 +522,16 @@ __device__ bool poll_step_df(const dfl* P, const dfl* C, int m, const dfl* v, df
 // The shared-memory-resident route in double-float arithmetic (structure as
 // sytrd1_body).  sh64: FP64 scalars of thread 0; shd: their double-float copies.
 __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait_limit, double* sy_smem,
-                               dfl* red, double* sh64, dfl* shd) {
+                               dfl* red, double* sh64, dfl* shd, int* coef_tag) {
   const int n = (int)c.n;
   double* A = c.A;
-  const int pcap = sytrd1_pcap(n, G);
   dfl* base = reinterpret_cast<dfl*>(sy_smem);
-  dfl* vc = base;
-  dfl* ps = base + n;
-  dfl* bs = base + 2 * n;
-  dfl* psum = base + 3 * n;
-  dfl* cols = base + 3 * n + pcap;
-  double* colsd = sy_smem + 3 * n + pcap;  // the same storage, first loaded as FP64
+  dfl* vc = base;           // v of the current step (two buffers, alternating)
+  dfl* vn = base + n;
+  dfl* ps = base + 2 * n;
+  dfl* bs = base + 3 * n;
+  dfl* cols = base + 4 * n;
+  double* colsd = sy_smem + 4 * n;  // the same storage, first loaded as FP64
   dfl* pub = reinterpret_cast<dfl*>(c.QA);
   const int tid = threadIdx.x;
   int parity = 0;
@@ -617,12 +603,16 @@ __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait
       c.tau1[0] = sh64[1];
     }
     store_reflector_df(c, n, 0, vc, rank, G, df_zero(), false);
-    if (tid == 0) shd[1] = df_make(1.0f, 0.0f);  // coefficients (tau, 1): v_0 is scaled already
+    if (tid == 0) {
+      shd[1] = df_make(1.0f, 0.0f);  // coefficients (tau, 1): v_0 is scaled already
+      *coef_tag = -1;
+    }
     __syncthreads();
   }
-  column_pass_df_any<false>(cols, n, 1, vc, shd, nullptr, nullptr, df_zero(), slab(pub, n, 0), slab(pub, n, 0) + (n - 1),
-                            psum, pcap, rank, G);
+  column_pass_dfw<false>(cols, n, 1, vc, shd, coef_tag, -1, nullptr, nullptr, df_zero(), slab(pub, n, 0),
+                         slab(pub, n, 0) + (n - 1), rank, G, c.status);
   dfl tau = shd[0];
+  __syncthreads();
   for (int j = 0; j + 2 < n; ++j) {
     const int m = n - j - 1;
     dfl* P = slab(pub, n, j);
@@ -647,9 +637,16 @@ __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait
     if (j + 3 < n) {
       const dfl sig = block_sum_df(sq, red, parity);
       dfl beta1;
-      if (tid == 0) reflector_scalars_df(bs[1], sig, &beta1, shd, shd + 1);
+      if (tid == 0) {
+        reflector_scalars_df(bs[1], sig, &beta1, shd, shd + 1);
+        __threadfence_block();
+        *(volatile int*)coef_tag = j;
+      }
       dfl* Pn = slab(pub, n, j + 1);
-      column_pass_df_any<true>(cols, n, j + 2, bs + 1, shd, vc, ps, K2, Pn, Pn + (m - 1), psum, pcap, rank, G);
+      column_pass_dfw<true>(cols, n, j + 2, bs + 1, shd, coef_tag, j, vc, ps, K2, Pn, Pn + (m - 1), rank, G,
+                            c.status);
+      // every thread reads the scalars after thread 0 announced them
+      wait_coef(coef_tag, j, c.status);
       const dfl tau1 = shd[0], scal1 = shd[1];
       if (rank == 0 && tid == 0) {
         c.d[j + 1] = df_to_d(bs[0]) * s_out;
@@ -657,9 +654,14 @@ __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait
         c.tau1[j + 1] = df_to_d(tau1);
       }
       store_reflector_df(c, n, j + 1, bs + 1, rank, G, scal1, true);
-      for (int t = tid; t < m - 1; t += kSyThreads) vc[t] = t == 0 ? df_make(1.0f, 0.0f) : df_mul(scal1, bs[1 + t]);
+      // v_{j+1} into the other buffer (the current one may still be read by a
+      // warp's update), then the barrier before the next step reads it
+      for (int t = tid; t < m - 1; t += kSyThreads) vn[t] = t == 0 ? df_make(1.0f, 0.0f) : df_mul(scal1, bs[1 + t]);
       tau = tau1;
       __syncthreads();
+      dfl* tmp = vc;
+      vc = vn;
+      vn = tmp;
     } else {
       __syncthreads();
       if (rank == 0 && tid == 0) {
@@ -817,8 +819,10 @@ __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __res
   if (*c.status != 0) return;
   // every CTA of a cone takes the same decision (same n, G, launch): columns
   // in shared memory and double-float arithmetic, or columns in L2 and FP64
+  __shared__ int coef_tag;
   if (sytrd1_bytes((int)c.n, G, true) <= (size_t)smem_bytes)
-    sytrd1_body_df(c, rank, G, wait_limit, sy_smem, reinterpret_cast<dfl*>(red), sh, reinterpret_cast<dfl*>(sh + 2));
+    sytrd1_body_df(c, rank, G, wait_limit, sy_smem, reinterpret_cast<dfl*>(red), sh, reinterpret_cast<dfl*>(sh + 2),
+                   &coef_tag);
   else
     sytrd1_body<false>(c, rank, G, wait_limit, sy_smem, red, sh);
 }
