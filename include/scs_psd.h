@@ -158,10 +158,16 @@ int scs_psd_proj_vjp(scs_psd_handle h, const double* x, const double* g, double*
  * column the (real) diagonal entry, then for every row i > j the pair
  * sqrt(2) Re X_ij, sqrt(2) Im X_ij -- n^2 reals per cone.  Cone i occupies
  * x[offsets[i] .. offsets[i+1]) with offsets[i+1] - offsets[i] == sides[i]^2
- * (host arrays, offsets[0] == 0); y may alias x.  Computed through the real
- * symmetric embedding [[Re X, -Im X], [Im X, Re X]] of side 2n, whose
- * projection is the embedding of Pi(X); sides up to 4096.  Options and
- * errors as scs_psd_proj_batched. */
+ * (host arrays, offsets[0] == 0); y may alias x.  When every side is at most
+ * 1100 and opts->band is 0, the cones are reduced natively: complex
+ * Householder reflectors (real off-diagonals) to a real symmetric
+ * tridiagonal form, the real divide and conquer, the complex
+ * back-transformation of the kept eigenvectors and the reconstruction
+ * straight into the Hermitian svec (complex double-float arithmetic in the
+ * reduction, the back-transformation and the reconstruction).  Otherwise
+ * through the real symmetric embedding [[Re X, -Im X], [Im X, Re X]] of
+ * side 2n, whose projection is the embedding of Pi(X); sides up to 4096.
+ * Options (opts->stats excepted) and errors as scs_psd_proj_batched. */
 int scs_psd_proj_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* offsets,
                            const int32_t* sides, int32_t count, const scs_psd_opts* opts, void* stream);
 

@@ -128,6 +128,15 @@ struct Plan {
   int64_t glaunches[kModes] = {};
   bool gfailed[kModes] = {};
   bool arena_owned = false;  // memory carved from a caller-provided region (not freed here)
+  // complex Hermitian cones reduced natively (herm): the cones' complex
+  // workspace, the reduction's CTA groups, the T-factor blocks, the
+  // back-transformation's CTAs
+  bool herm = false;
+  void* hmem = nullptr;
+  HConeDev* hcones_d = nullptr;
+  std::vector<Sytrd1Launch> hetrd;
+  int hlarft_n = 0, hlarft_cone_off = 0, hlarft_idx_off = 0;
+  int hbt_nctas = 0, hbt_cone_off = 0, hbt_rank_off = 0, hbt_count_off = 0;
   // per-cone statistics (allocated by the first call that asks for them)
   void* stats_mem = nullptr;
   StatsCone* stats_cones_d = nullptr;
@@ -143,6 +152,7 @@ struct Plan {
     if (!arena_owned && cone_mem) cudaFree(cone_mem);
     if (!arena_owned && meta_mem) cudaFree(meta_mem);
     if (stats_mem) cudaFree(stats_mem);
+    if (hmem) cudaFree(hmem);
   }
 };
 
@@ -509,16 +519,19 @@ struct Arena {
 };
 
 int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, int b, int allv, int side,
-               int precision, int onestage, const Tuning& tune, Arena* arena = nullptr) {
+               int precision, int onestage, const Tuning& tune, Arena* arena = nullptr, bool herm = false) {
   P.tune = tune;
   P.b = b;
   P.allv = allv;
   P.side = side;
   P.precision = precision;
+  P.herm = herm;
+  if (herm) onestage = 1;  // the complex reduction hands over a tridiagonal form
   P.sides.assign(sides, sides + count);
   P.offsets.resize(count + 1);
   P.offsets[0] = 0;
-  for (int i = 0; i < count; ++i) P.offsets[i + 1] = P.offsets[i] + svec_len(sides[i]);
+  for (int i = 0; i < count; ++i)
+    P.offsets[i + 1] = P.offsets[i] + (herm ? (int64_t)sides[i] * sides[i] : svec_len(sides[i]));
 
   // ---- cones of the main path (n >= 2) and trivial ones
   std::vector<int> big;
@@ -787,6 +800,73 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
     }
   }
 
+  // ---- complex Hermitian cones: reduction groups, T-factor blocks, back-transformation CTAs
+  std::vector<HConeDev> hcones;
+  size_t hbytes = 0;
+  std::vector<size_t> hoff;
+  if (herm) {
+    const int sms = std::max(1, h->sms);
+    std::vector<int> G(P.ncones);
+    size_t maxneed = 0;
+    for (int c = 0; c < P.ncones; ++c) {
+      const int n = (int)cones[c].n;
+      int g = n >= 256 ? std::min(sms, n / 4) : 1;
+      while (g < sms && hetrd1_smem_bytes(n, g) > kHetrdSmemMax) ++g;
+      if (hetrd1_smem_bytes(n, g) > kHetrdSmemMax) return SCS_PSD_EINVAL;
+      G[c] = g;
+      maxneed = std::max(maxneed, hetrd1_smem_bytes(n, g));
+    }
+    int c = 0;
+    while (c < P.ncones) {
+      // cones of one cooperative launch: every CTA co-resident
+      Sytrd1Launch sl;
+      size_t need = 0;
+      int total = 0;
+      std::vector<int> cc, rr, gg;
+      while (c < P.ncones) {
+        const size_t nd = std::max(need, hetrd1_smem_bytes((int)cones[c].n, G[c]));
+        const int cap = std::max(1, hetrd1_max_ctas_for(nd));
+        if (total > 0 && total + G[c] > cap) break;
+        need = nd;
+        for (int r = 0; r < G[c]; ++r) { cc.push_back(c); rr.push_back(r); gg.push_back(G[c]); }
+        total += G[c];
+        ++c;
+      }
+      sl.nctas = total;
+      sl.smem = need;
+      sl.maxn = 0;
+      sl.cone_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), cc.begin(), cc.end());
+      sl.rank_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), rr.begin(), rr.end());
+      sl.count_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), gg.begin(), gg.end());
+      P.hetrd.push_back(sl);
+    }
+    (void)maxneed;
+    std::vector<int> bc, bi, tc, tr, tg;
+    for (int q = 0; q < P.ncones; ++q) {
+      const int64_t n = cones[q].n;
+      for (int k = 0; k < hcone_blocks(n); ++k) { bc.push_back(q); bi.push_back(k); }
+      // back-transformation: about four kept columns per CTA for half the columns kept
+      const int g = (int)std::max<int64_t>(1, std::min<int64_t>(2 * sms, (n / 2 + 3) / 4));
+      for (int r = 0; r < g; ++r) { tc.push_back(q); tr.push_back(r); tg.push_back(g); }
+    }
+    P.hlarft_n = (int)bc.size();
+    P.hlarft_cone_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), bc.begin(), bc.end());
+    P.hlarft_idx_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), bi.begin(), bi.end());
+    P.hbt_nctas = (int)tc.size();
+    P.hbt_cone_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), tc.begin(), tc.end());
+    P.hbt_rank_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), tr.begin(), tr.end());
+    P.hbt_count_off = (int)mb.ints.size(); mb.ints.insert(mb.ints.end(), tg.begin(), tg.end());
+    // complex workspace per cone: publication slabs, V blocks, T blocks, tau, W
+    hoff.resize(P.ncones);
+    for (int q = 0; q < P.ncones; ++q) {
+      const int64_t n = cones[q].n;
+      hoff[q] = hbytes;
+      hbytes += align_up(sizeof(double) * hcone_pub_doubles(n)) + align_up(sizeof(cdf) * hcone_v_elems(n)) +
+                align_up(sizeof(cdf) * hcone_t_elems(n)) + align_up(sizeof(cdf) * (size_t)n) +
+                align_up(sizeof(cdf) * (size_t)(n * n));
+    }
+  }
+
   // ---- divide and conquer levels
   {
     std::vector<int64_t> pos_base(P.ncones);
@@ -1010,6 +1090,35 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
   }
   for (GemmDesc& g : mb.descs)
     if (g.skip) g.skip = P.ints_d + ((intptr_t)g.skip - 1);
+  if (herm && P.ncones) {
+    if (cudaMalloc(&P.hmem, hbytes + align_up(sizeof(HConeDev) * P.ncones)) != cudaSuccess) {
+      P.hmem = nullptr;
+      return SCS_PSD_ENOMEM;
+    }
+    char* hb = (char*)P.hmem;
+    P.hcones_d = (HConeDev*)(hb + hbytes);
+    hcones.resize(P.ncones);
+    for (int q = 0; q < P.ncones; ++q) {
+      const ConeDev& d = cones[q];
+      const int64_t n = d.n;
+      HConeDev& hc = hcones[q];
+      char* o = hb + hoff[q];
+      hc.n = n;
+      hc.xoff = d.xoff;
+      hc.d = d.d;
+      hc.e = d.e;
+      hc.status = d.status;
+      hc.prog = d.prog;
+      hc.Z = d.Z;
+      hc.lamk = d.lamk;
+      hc.kinfo = d.kinfo;
+      hc.pub = (dfl*)o; o += align_up(sizeof(double) * hcone_pub_doubles(n));
+      hc.V = (cdf*)o; o += align_up(sizeof(cdf) * hcone_v_elems(n));
+      hc.T = (cdf*)o; o += align_up(sizeof(cdf) * hcone_t_elems(n));
+      hc.tau = (cdf*)o; o += align_up(sizeof(cdf) * (size_t)n);
+      hc.W = (cdf*)o;
+    }
+  }
   // kinfo: [3] all eigenpairs, [4] side option (staged in a host block next to the rest)
   std::vector<int> kin_all((size_t)P.ncones * 8, 0);
   for (int c = 0; c < P.ncones; ++c) {
@@ -1031,6 +1140,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
     e = up(P.triv_offs_d, triv_offs.data(), sizeof(int64_t) * 4 * P.ntriv);
   }
   for (int c = 0; c < P.ncones && e == cudaSuccess; ++c) e = up(cones[c].kinfo, &kin_all[(size_t)c * 8], 8 * sizeof(int));
+  if (e == cudaSuccess && herm && P.ncones) e = up(P.hcones_d, hcones.data(), sizeof(HConeDev) * P.ncones);
   if (e != cudaSuccess) return SCS_PSD_ECUDA;
   (void)h;
   return SCS_PSD_OK;
@@ -1122,63 +1232,89 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
       n_launch += 2;
       LAUNCH_CHECK();
     } else {
-      pm.begin(0);
-      launch_unpack(P.cones_d, nc, P.maxn * P.maxn, io, 0, s);
-      LAUNCH_CHECK();
-      if (!P.panels.empty()) pm.begin(1);
-      for (const PanelStep& ps : P.panels) {
-        launch_panel(P.cones_d, P.ints_d + ps.ids_off, ps.njobs, ps.panel, P.b, ps.cluster, ps.R, s);
-        LAUNCH_CHECK();
-        for (int q = 0; q < 6; ++q)
-          if ((rc = run_gemm(P, ps.g[q], s, n_launch))) return rc;
-      }
-      if (!P.sytrd1.empty()) {
+      if (P.herm) {
+        // complex Hermitian cones: reduction straight from the Hermitian svec to
+        // the real tridiagonal form, the T factors on the second stream
         pm.begin(1);
-        for (const Sytrd1Launch& sl : P.sytrd1) {
-          if (launch_sytrd1(P.cones_d, P.ints_d + sl.cone_off, P.ints_d + sl.rank_off, P.ints_d + sl.count_off,
-                            sl.nctas, sl.maxn, sl.smem, wait_limit, s))
+        for (const Sytrd1Launch& sl : P.hetrd) {
+          if (launch_hetrd1(P.hcones_d, P.ints_d + sl.cone_off, P.ints_d + sl.rank_off, P.ints_d + sl.count_off,
+                            sl.nctas, sl.smem, io, wait_limit, s))
             return SCS_PSD_ECUDA;
           LAUNCH_CHECK();
         }
-        // the T factors need only the reflectors: on the second stream they
-        // overlap the divide and conquer (kept on s while tracing phases)
-        const bool side = h->use_aux && !h->trace && h->aux_stream && P.nlarft > 0;
-        if (mode & MODE_LMIN) {
-          // lambda_min stops at the tridiagonal form: no T factors
-        } else if (side) {
+        const bool side = h->use_aux && !h->trace && h->aux_stream && P.hlarft_n > 0;
+        if (side) {
           CUDA_TRY(cudaEventRecord(h->ev_fork, s));
           CUDA_TRY(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
         } else {
           pm.begin(5);
         }
-        if (!(mode & MODE_LMIN)) {
-          launch_larft1(P.cones_d, P.ints_d + P.larft_cone_off, P.ints_d + P.larft_idx_off, P.nlarft,
-                        side ? h->aux_stream : s);
-          LAUNCH_CHECK();
-        }
-        if (side && !(mode & MODE_LMIN)) {
+        launch_hlarft(P.hcones_d, P.ints_d + P.hlarft_cone_off, P.ints_d + P.hlarft_idx_off, P.hlarft_n,
+                      side ? h->aux_stream : s);
+        LAUNCH_CHECK();
+        if (side) {
           CUDA_TRY(cudaEventRecord(h->ev_join, h->aux_stream));
           joined = false;
         }
-      }
-      pm.begin(2);
-      launch_band_extract(P.cones_d, nc, P.maxn, s);
-      LAUNCH_CHECK();
-      for (const BulgeLaunch& bl : P.bulges) {
-        if (launch_bulge(P.cones_d, bl.ncones, P.ints_d + bl.cone_off, P.ints_d + bl.rank_off,
-                         P.ints_d + bl.count_off, bl.nctas, P.b, wait_limit, s))
-          return SCS_PSD_ECUDA;
+      } else {
+        pm.begin(0);
+        launch_unpack(P.cones_d, nc, P.maxn * P.maxn, io, 0, s);
         LAUNCH_CHECK();
-      }
-      launch_tridiag_extract(P.cones_d, nc, P.maxn, s);
-      LAUNCH_CHECK();
-      if (mode & MODE_LMIN) {
-        launch_lmin(P.cones_d, nc, io, s);
+        if (!P.panels.empty()) pm.begin(1);
+        for (const PanelStep& ps : P.panels) {
+          launch_panel(P.cones_d, P.ints_d + ps.ids_off, ps.njobs, ps.panel, P.b, ps.cluster, ps.R, s);
+          LAUNCH_CHECK();
+          for (int q = 0; q < 6; ++q)
+            if ((rc = run_gemm(P, ps.g[q], s, n_launch))) return rc;
+        }
+        if (!P.sytrd1.empty()) {
+          pm.begin(1);
+          for (const Sytrd1Launch& sl : P.sytrd1) {
+            if (launch_sytrd1(P.cones_d, P.ints_d + sl.cone_off, P.ints_d + sl.rank_off, P.ints_d + sl.count_off,
+                              sl.nctas, sl.maxn, sl.smem, wait_limit, s))
+              return SCS_PSD_ECUDA;
+            LAUNCH_CHECK();
+          }
+          // the T factors need only the reflectors: on the second stream they
+          // overlap the divide and conquer (kept on s while tracing phases)
+          const bool side = h->use_aux && !h->trace && h->aux_stream && P.nlarft > 0;
+          if (mode & MODE_LMIN) {
+            // lambda_min stops at the tridiagonal form: no T factors
+          } else if (side) {
+            CUDA_TRY(cudaEventRecord(h->ev_fork, s));
+            CUDA_TRY(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
+          } else {
+            pm.begin(5);
+          }
+          if (!(mode & MODE_LMIN)) {
+            launch_larft1(P.cones_d, P.ints_d + P.larft_cone_off, P.ints_d + P.larft_idx_off, P.nlarft,
+                          side ? h->aux_stream : s);
+            LAUNCH_CHECK();
+          }
+          if (side && !(mode & MODE_LMIN)) {
+            CUDA_TRY(cudaEventRecord(h->ev_join, h->aux_stream));
+            joined = false;
+          }
+        }
+        pm.begin(2);
+        launch_band_extract(P.cones_d, nc, P.maxn, s);
         LAUNCH_CHECK();
-        pm.end();
-        launch_status_reduce(P.status_d, P.ncones + 1, h->status_word, s);
+        for (const BulgeLaunch& bl : P.bulges) {
+          if (launch_bulge(P.cones_d, bl.ncones, P.ints_d + bl.cone_off, P.ints_d + bl.rank_off,
+                           P.ints_d + bl.count_off, bl.nctas, P.b, wait_limit, s))
+            return SCS_PSD_ECUDA;
+          LAUNCH_CHECK();
+        }
+        launch_tridiag_extract(P.cones_d, nc, P.maxn, s);
         LAUNCH_CHECK();
-        return SCS_PSD_OK;
+        if (mode & MODE_LMIN) {
+          launch_lmin(P.cones_d, nc, io, s);
+          LAUNCH_CHECK();
+          pm.end();
+          launch_status_reduce(P.status_d, P.ncones + 1, h->status_word, s);
+          LAUNCH_CHECK();
+          return SCS_PSD_OK;
+        }
       }
       pm.begin(3);
       launch_dc_leaves(P.cones_d, nc, P.maxn, s);
@@ -1205,6 +1341,23 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
         if ((rc = run_gemm(P, lv.g, s, n_launch))) return rc;
         launch_dc_copy_deflated(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
         LAUNCH_CHECK();
+      }
+      if (P.herm) {
+        pm.begin(5);
+        if (!joined) {
+          CUDA_TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
+          joined = true;
+        }
+        launch_hbt(P.hcones_d, P.ints_d + P.hbt_cone_off, P.ints_d + P.hbt_rank_off, P.ints_d + P.hbt_count_off,
+                   P.hbt_nctas, (int)P.maxn, s);
+        LAUNCH_CHECK();
+        pm.begin(6);
+        launch_hrecon(P.hcones_d, nc, (int)P.maxn, io, s);
+        LAUNCH_CHECK();
+        pm.end();
+        launch_status_reduce(P.status_d, P.ncones + 1, h->status_word, s);
+        LAUNCH_CHECK();
+        return SCS_PSD_OK;
       }
       pm.begin(4);
       launch_backtr2(P.cones_d, nc, (int)P.maxn, (int)P.maxn, P.allv ? (int)P.maxn : (int)(P.maxn + 1) / 2, P.b, s);
@@ -1404,12 +1557,13 @@ std::string tune_key(const int32_t* sides, int32_t count, int precision) {
 
 // The cached plan for these shapes, options and launch shapes (built on first use).
 int get_plan(scs_psd_handle h, const int32_t* sides, int32_t count, int allv, int side, int precision,
-             const Tuning& tune, Plan** out) {
+             const Tuning& tune, Plan** out, bool herm = false) {
   int b = kDefaultBand, onestage = -1;
   if (tune.band == 1) onestage = 1;
   else if (tune.band >= 2) { onestage = 0; b = tune.band; }
   if (b < 2 || b > kMaxBand) return SCS_PSD_EINVAL;
-  const std::string key = plan_key(sides, count, b, allv, side, precision) + (char)('A' + onestage + 1) + tune.str();
+  const std::string key = plan_key(sides, count, b, allv, side, precision) + (char)('A' + onestage + 1) + tune.str() +
+                          (herm ? "H" : "");
   auto it = h->plans.find(key);
   if (it != h->plans.end()) {
     *out = it->second.get();
@@ -1421,7 +1575,7 @@ int get_plan(scs_psd_handle h, const int32_t* sides, int32_t count, int allv, in
   }
   auto np = std::make_unique<Plan>();
   np->key = key;
-  const int rc = build_plan(h, *np, sides, count, b, allv, side, precision, onestage, tune);
+  const int rc = build_plan(h, *np, sides, count, b, allv, side, precision, onestage, tune, nullptr, herm);
   if (rc) return rc;
   *out = np.get();
   h->plans[key] = std::move(np);
@@ -1431,9 +1585,9 @@ int get_plan(scs_psd_handle h, const int32_t* sides, int32_t count, int allv, in
 // One call of any entry point: `mode` (MODE_* bits) says which of io's
 // buffers are read and written; every one it names must be non-NULL.
 int do_call(scs_psd_handle h, const IoSlot& io, int mode, const int64_t* offsets, const int32_t* sides,
-            int32_t count, const scs_psd_opts* opts, void* stream) {
+            int32_t count, const scs_psd_opts* opts, void* stream, bool herm = false) {
   if (!h) return SCS_PSD_EINVAL;
-  int rc = check_shapes(offsets, sides, count);
+  int rc = herm ? SCS_PSD_OK : check_shapes(offsets, sides, count);
   if (rc) return rc;
   if (count == 0 || offsets[count] == 0) return SCS_PSD_OK;
   if (!(mode & MODE_IMPORT) && !io.x) return SCS_PSD_EINVAL;
@@ -1471,7 +1625,7 @@ int do_call(scs_psd_handle h, const IoSlot& io, int mode, const int64_t* offsets
     if (t != h->tuned.end()) tune = t->second;
   }
   Plan* P = nullptr;
-  rc = get_plan(h, sides, count, allv, side, precision, tune, &P);
+  rc = get_plan(h, sides, count, allv, side, precision, tune, &P, herm);
   if (rc) return rc;
   if ((mode & MODE_STATS) && (rc = ensure_stats(*P))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1615,6 +1769,15 @@ int proj_hermitian(scs_psd_handle h, const double* x, double* y, const int64_t* 
   }
   if (offsets[count] == 0) return SCS_PSD_OK;
   if (!x || !y) return SCS_PSD_EINVAL;
+  // native complex route: every side within the shared-memory reduction's
+  // reach, the eigendecomposition method, the automatic route
+  bool native = poly_lo <= 0.0 && !(opts && opts->band);
+  for (int i = 0; i < count && native; ++i)
+    native = sides[i] <= kHermNativeMax && hetrd1_smem_bytes(sides[i], std::max(1, h->sms)) <= kHetrdSmemMax;
+  if (native) {
+    const IoSlot io{x, y, nullptr, nullptr, nullptr, nullptr};
+    return do_call(h, io, MODE_Y, offsets, sides, count, opts, stream, true);
+  }
   HermPlan* hp = nullptr;
   {
     std::lock_guard<std::mutex> lock(h->mu);

@@ -80,4 +80,31 @@ __device__ __forceinline__ dfl df_div(dfl x, dfl y) {
 }
 
 
+// Complex double-float: re and im parts as double-float values (16 bytes).
+struct __align__(16) cdf {
+  dfl re, im;
+};
+__device__ __forceinline__ cdf c_make(dfl r, dfl i) {
+  cdf c;
+  c.re = r;
+  c.im = i;
+  return c;
+}
+__device__ __forceinline__ cdf c_zero() { return c_make(df_zero(), df_zero()); }
+__device__ __forceinline__ cdf c_one() { return c_make(df_make(1.0f, 0.0f), df_zero()); }
+__device__ __forceinline__ cdf c_conj(cdf a) { return c_make(a.re, df_neg(a.im)); }
+__device__ __forceinline__ cdf c_neg(cdf a) { return c_make(df_neg(a.re), df_neg(a.im)); }
+__device__ __forceinline__ cdf c_add(cdf a, cdf b) { return c_make(df_add(a.re, b.re), df_add(a.im, b.im)); }
+// a b + c
+__device__ __forceinline__ cdf c_fma(cdf a, cdf b, cdf c) {
+  return c_make(df_fma(a.re, b.re, df_fma(df_neg(a.im), b.im, c.re)), df_fma(a.re, b.im, df_fma(a.im, b.re, c.im)));
+}
+// conj(a) b + c
+__device__ __forceinline__ cdf c_cfma(cdf a, cdf b, cdf c) {
+  return c_make(df_fma(a.re, b.re, df_fma(a.im, b.im, c.re)), df_fma(a.re, b.im, df_fma(df_neg(a.im), b.re, c.im)));
+}
+__device__ __forceinline__ cdf c_mul(cdf a, cdf b) { return c_fma(a, b, c_zero()); }
+__device__ __forceinline__ cdf c_shfl_xor(cdf v, int o) { return c_make(df_shfl_xor(v.re, o), df_shfl_xor(v.im, o)); }
+__device__ __forceinline__ cdf c_from_d(double re, double im) { return c_make(df_from_d(re), df_from_d(im)); }
+
 }  // namespace scs

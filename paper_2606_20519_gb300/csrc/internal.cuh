@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dfloat.cuh"
+
 namespace scs {
 
 // Per-cone device status bits (OR-ed together).
@@ -302,6 +304,43 @@ void launch_mix_weight(const int* groups, const double* nu, const double* lam, d
                        cudaStream_t s);
 void launch_mix_apply(const int64_t* meta, int count, int64_t maxn, const double* x, double* y, const double* p,
                       const double* nu, cudaStream_t s);
+
+// ------------------------------------------------------------------ complex Hermitian cones (native)
+// One complex Hermitian cone of side n: the real plan's cone (same index)
+// holds its tridiagonal form (d, e), status, counters and the divide and
+// conquer's output (Z, lamk, kinfo); the complex workspace holds the
+// publication slabs of the reduction, the reflectors in blocks of 32 (V:
+// rows 32 q + 1 .. n-1 of block q, unit diagonal, zeros above), their T
+// factors, tau, and W = Q Z.
+struct HConeDev {
+  int64_t n, xoff;  // side, offset of the cone in the Hermitian svec buffers (n^2 reals each)
+  double* d;
+  double* e;
+  int* status;
+  int* prog;
+  const double* Z;
+  const double* lamk;
+  const int* kinfo;
+  dfl* pub;   // 2 n (n - 1) words
+  cdf* V;     // hcone_v_elems(n)
+  cdf* T;     // hcone_t_elems(n)
+  cdf* tau;   // n
+  cdf* W;     // n x n
+};
+constexpr int kHermNativeMax = 1100;  // largest side reduced natively (the columns must fit in shared memory)
+constexpr size_t kHetrdSmemMax = 220 * 1024;  // dynamic shared memory of one reduction CTA
+size_t hetrd1_smem_bytes(int n, int G);
+int hetrd1_max_ctas_for(size_t smem);
+size_t hcone_pub_doubles(int64_t n);
+size_t hcone_v_elems(int64_t n);
+size_t hcone_t_elems(int64_t n);
+int hcone_blocks(int64_t n);
+int launch_hetrd1(const HConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,
+                  size_t smem, const IoSlot* io, long long wait_limit, cudaStream_t s);
+void launch_hlarft(const HConeDev* cones, const int* blk_cone, const int* blk_index, int nblocks, cudaStream_t s);
+void launch_hbt(const HConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,
+                int maxn, cudaStream_t s);
+void launch_hrecon(const HConeDev* cones, int ncones, int maxn, const IoSlot* io, cudaStream_t s);
 
 // ------------------------------------------------------------------ polynomial projection
 // One cone of the factorization-free approximate projection (S_0 = X / ||X||_F,

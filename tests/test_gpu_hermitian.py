@@ -66,3 +66,19 @@ def test_construction_and_moreau_side(lib):
         y, st = run(lib, x, [n], opts=lib.make_opts(side=side))
         assert st == lib.OK
         assert rel(y, exact) <= TOL
+
+
+@pytest.mark.parametrize("n", [40, 300])
+def test_native_and_embedding_routes_agree_with_oracle(lib, n):
+    """The native complex reduction (the automatic route for sides up to
+    1100) and the real embedding of side 2n (taken when opts.band is set)
+    both against the complex oracle."""
+    rng = W.rng_for(9780 + n)
+    x = W.to_hsvec(W.herm_gaussian(rng, n))
+    ref = oracle.herm_proj(x)
+    y_native, st = run(lib, x, [n])
+    assert st == lib.OK
+    assert rel(y_native, ref) <= TOL
+    y_embed, st = run(lib, x, [n], opts=lib.make_opts(band=1))
+    assert st == lib.OK
+    assert rel(y_embed, ref) <= TOL
