@@ -4,6 +4,7 @@
 // one sweep act on disjoint row blocks, so a whole sweep is applied at once
 // (one thread per reflector and column), sweeps one after the other.  Each
 // CTA holds a slab of columns of Z in shared memory for the whole pass.
+#include "dfloat.cuh"
 #include "internal.cuh"
 
 namespace scs {
@@ -158,10 +159,11 @@ constexpr int kB1Threads = 256;
 constexpr int kB1MaxCols = 8;
 constexpr size_t kB1SmemMax = 200 * 1024;
 
+template <typename E>
 struct Stage1Block {
   int r0, mq, bb, wb;
-  const double* V;
-  const double* T;
+  const E* V;
+  const E* T;
 };
 
 __device__ __forceinline__ int stage1_nblocks(const ConeDev& c) {
@@ -170,31 +172,34 @@ __device__ __forceinline__ int stage1_nblocks(const ConeDev& c) {
   return n >= 3 ? (n - 2 + kSy1Block - 1) / kSy1Block : 0;
 }
 
-__device__ __forceinline__ Stage1Block stage1_block(const ConeDev& c, int q) {
+template <typename E>
+__device__ __forceinline__ Stage1Block<E> stage1_block(const ConeDev& c, int q) {
   const int n = (int)c.n;
-  Stage1Block k;
+  const E* V1 = reinterpret_cast<const E*>(c.V1);
+  const E* T1 = reinterpret_cast<const E*>(c.T1);
+  Stage1Block<E> k;
   if (c.path == 0) {
     k.wb = c.b;
     k.r0 = (q + 1) * c.b;
     k.mq = n - k.r0;
     k.bb = min(c.b, k.mq);
-    k.V = c.V1 + (int64_t)q * n * c.b;
-    k.T = c.T1 + (int64_t)q * c.b * c.b;
+    k.V = V1 + (int64_t)q * n * c.b;
+    k.T = T1 + (int64_t)q * c.b * c.b;
   } else {
     k.wb = kSy1Block;
     k.r0 = q * kSy1Block + 1;
     k.mq = n - k.r0;
     k.bb = min(kSy1Block, n - 2 - q * kSy1Block);
-    k.V = c.V1 + (int64_t)q * n * kSy1Block;
-    k.T = c.T1 + (int64_t)q * kSy1Block * kSy1Block;
+    k.V = V1 + (int64_t)q * n * kSy1Block;
+    k.T = T1 + (int64_t)q * kSy1Block * kSy1Block;
   }
   return k;
 }
 
 // Sum of v over the warp, recursive halving: on return lane l holds the sum
 // of element (l >> (5 - log2 NV)) of v.
-template <int NV>
-__device__ __forceinline__ double warp_reduce_scatter(double (&v)[NV]) {
+template <int NV, typename E>
+__device__ __forceinline__ E warp_reduce_scatter(E (&v)[NV]) {
   const int lane = threadIdx.x & 31;
   int cnt = NV;
 #pragma unroll
@@ -205,55 +210,59 @@ __device__ __forceinline__ double warp_reduce_scatter(double (&v)[NV]) {
 #pragma unroll
       for (int i = 0; i < NV / 2; ++i) {
         if (i < half) {
-          const double send = up ? v[i] : v[i + half];
-          const double keep = up ? v[i + half] : v[i];
-          v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+          const E send = up ? v[i] : v[i + half];
+          const E keep = up ? v[i + half] : v[i];
+          v[i] = g_add(keep, g_shfl_xor(send, off));
         }
       }
       cnt = half;
     } else {
-      v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+      v[0] = g_add(v[0], g_shfl_xor(v[0], off));
     }
   }
   return v[0];
 }
 
-template <int KC>
-__device__ void bt1_slab(const ConeDev& c, int j0, int ncols, double* zs, double* Wsm, double* Wt) {
+// One slab of KC columns through every block, in element type E (FP64, or
+// double-float when the reflectors and T factors were stored as FP32 pairs).
+template <int KC, typename E>
+__device__ void bt1_slab(const ConeDev& c, int j0, int ncols, E* zs, E* Wsm, E* Wt) {
   const int n = (int)c.n;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   double* Z = c.Z;
   // rows 1 .. n-1 of the slab (row 0 is untouched: Q1 = diag(1, Q1'))
   for (int e = tid; e < KC * n; e += kB1Threads) {
     const int col = e / n, r = e - col * n;
-    zs[e] = col < ncols ? Z[(int64_t)r + (int64_t)(j0 + col) * n] : 0.0;
+    g_cvt(zs[e], col < ncols ? Z[(int64_t)r + (int64_t)(j0 + col) * n] : 0.0);
   }
   __syncthreads();
   const int nblk = stage1_nblocks(c);
   for (int q = nblk - 1; q >= 0; --q) {
-    const Stage1Block B = stage1_block(c, q);
+    const Stage1Block<E> B = stage1_block<E>(c, q);
     // ---- W = V^T Z(r0:, slab): warp w takes reflectors 4w .. 4w+3
     {
-      double acc[4 * KC];
+      E acc[4 * KC];
 #pragma unroll
-      for (int i = 0; i < 4 * KC; ++i) acc[i] = 0.0;
+      for (int i = 0; i < 4 * KC; ++i) g_zero(acc[i]);
       const int a0 = warp * 4;
       if (a0 < B.bb) {
-        const double* zr = zs + B.r0;
+        const E* zr = zs + B.r0;
 #pragma unroll 2
         for (int r = lane; r < B.mq; r += 32) {
-          double z[KC];
+          E z[KC];
 #pragma unroll
           for (int col = 0; col < KC; ++col) z[col] = zr[col * n + r];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            const double v = (a0 + i < B.bb) ? __ldg(B.V + r + (int64_t)(a0 + i) * B.mq) : 0.0;
+            E v;
+            if (a0 + i < B.bb) v = g_ldg(B.V + r + (int64_t)(a0 + i) * B.mq);
+            else g_zero(v);
 #pragma unroll
-            for (int col = 0; col < KC; ++col) acc[i * KC + col] = fma(v, z[col], acc[i * KC + col]);
+            for (int col = 0; col < KC; ++col) acc[i * KC + col] = g_mad(v, z[col], acc[i * KC + col]);
           }
         }
       }
-      const double s = warp_reduce_scatter<4 * KC>(acc);
+      const E s = warp_reduce_scatter<4 * KC>(acc);
       constexpr int kShift = (4 * KC == 32) ? 0 : (4 * KC == 16) ? 1 : (4 * KC == 8) ? 2 : 3;
       if ((lane & ((1 << kShift) - 1)) == 0) {
         const int idx = lane >> kShift;  // i * KC + col
@@ -264,45 +273,61 @@ __device__ void bt1_slab(const ConeDev& c, int j0, int ncols, double* zs, double
     // ---- W' = T W (T upper triangular)
     if (tid < kSy1Block * KC) {
       const int a = tid / KC, col = tid % KC;
-      double s0 = 0.0, s1 = 0.0;
+      E s0, s1;
+      g_zero(s0);
+      g_zero(s1);
       if (a < B.bb) {
         int bq = a;
         for (; bq + 1 < B.bb; bq += 2) {
-          s0 = fma(__ldg(B.T + a + (int64_t)bq * B.wb), Wsm[bq * KC + col], s0);
-          s1 = fma(__ldg(B.T + a + (int64_t)(bq + 1) * B.wb), Wsm[(bq + 1) * KC + col], s1);
+          s0 = g_mad(g_ldg(B.T + a + (int64_t)bq * B.wb), Wsm[bq * KC + col], s0);
+          s1 = g_mad(g_ldg(B.T + a + (int64_t)(bq + 1) * B.wb), Wsm[(bq + 1) * KC + col], s1);
         }
-        if (bq < B.bb) s0 = fma(__ldg(B.T + a + (int64_t)bq * B.wb), Wsm[bq * KC + col], s0);
+        if (bq < B.bb) s0 = g_mad(g_ldg(B.T + a + (int64_t)bq * B.wb), Wsm[bq * KC + col], s0);
       }
-      Wt[a * KC + col] = s0 + s1;
+      Wt[a * KC + col] = g_add(s0, s1);
     }
     __syncthreads();
     // ---- Z(r0:, slab) -= V W'
     for (int r = tid; r < B.mq; r += kB1Threads) {
-      double s0[KC], s1[KC];
+      E s0[KC], s1[KC];
 #pragma unroll
-      for (int col = 0; col < KC; ++col) { s0[col] = 0.0; s1[col] = 0.0; }
+      for (int col = 0; col < KC; ++col) { g_zero(s0[col]); g_zero(s1[col]); }
 #pragma unroll 8
       for (int a = 0; a < kSy1Block; a += 2) {
         if (a < B.bb) {
-          const double v0 = __ldg(B.V + r + (int64_t)a * B.mq);
-          const double v1 = (a + 1 < B.bb) ? __ldg(B.V + r + (int64_t)(a + 1) * B.mq) : 0.0;
+          const E v0 = g_ldg(B.V + r + (int64_t)a * B.mq);
+          E v1;
+          if (a + 1 < B.bb) v1 = g_ldg(B.V + r + (int64_t)(a + 1) * B.mq);
+          else g_zero(v1);
 #pragma unroll
           for (int col = 0; col < KC; ++col) {
-            s0[col] = fma(v0, Wt[a * KC + col], s0[col]);
-            s1[col] = fma(v1, Wt[(a + 1) * KC + col], s1[col]);
+            s0[col] = g_mad(v0, Wt[a * KC + col], s0[col]);
+            s1[col] = g_mad(v1, Wt[(a + 1) * KC + col], s1[col]);
           }
         }
       }
 #pragma unroll
-      for (int col = 0; col < KC; ++col) zs[col * n + B.r0 + r] -= s0[col] + s1[col];
+      for (int col = 0; col < KC; ++col)
+        zs[col * n + B.r0 + r] = g_add(zs[col * n + B.r0 + r], g_neg(g_add(s0[col], s1[col])));
     }
     __syncthreads();
   }
   for (int e = tid; e < KC * n; e += kB1Threads) {
     const int col = e / n, r = e - col * n;
-    if (col < ncols && r >= 1) Z[(int64_t)r + (int64_t)(j0 + col) * n] = zs[e];
+    if (col < ncols && r >= 1) Z[(int64_t)r + (int64_t)(j0 + col) * n] = g_val(zs[e]);
   }
   __syncthreads();
+}
+
+template <typename E>
+__device__ void bt1_cols(const ConeDev& c, int lo, int hi, int kcmax, E* smem, E* Wsm, E* Wt) {
+  for (int j0 = lo; j0 < hi;) {
+    const int left = hi - j0;
+    if (left > 4 && kcmax >= 8) { bt1_slab<8, E>(c, j0, min(left, 8), smem, Wsm, Wt); j0 += min(left, 8); }
+    else if (left > 2 && kcmax >= 4) { bt1_slab<4, E>(c, j0, min(left, 4), smem, Wsm, Wt); j0 += min(left, 4); }
+    else if (left >= 2 && kcmax >= 2) { bt1_slab<2, E>(c, j0, 2, smem, Wsm, Wt); j0 += 2; }
+    else { bt1_slab<1, E>(c, j0, 1, smem, Wsm, Wt); j0 += 1; }
+  }
 }
 
 __global__ void __launch_bounds__(kB1Threads) bt1_kernel(const ConeDev* __restrict__ cones,
@@ -310,6 +335,7 @@ __global__ void __launch_bounds__(kB1Threads) bt1_kernel(const ConeDev* __restri
                                                          const int* __restrict__ cta_rank,
                                                          const int* __restrict__ cta_count, int kcmax) {
   extern __shared__ double b1_smem[];
+  // 8-byte elements either way (FP64, or an FP32 pair)
   __shared__ double Wsm[kSy1Block * kB1MaxCols];
   __shared__ double Wt[kSy1Block * kB1MaxCols];
   const ConeDev& c = cones[cta_cone[blockIdx.x]];
@@ -320,13 +346,13 @@ __global__ void __launch_bounds__(kB1Threads) bt1_kernel(const ConeDev* __restri
   const int base = k / G, extra = k % G;
   const int lo = rank * base + min(rank, extra);
   const int hi = lo + base + (rank < extra ? 1 : 0);
-  for (int j0 = lo; j0 < hi;) {
-    const int left = hi - j0;
-    if (left > 4 && kcmax >= 8) { bt1_slab<8>(c, j0, min(left, 8), b1_smem, Wsm, Wt); j0 += min(left, 8); }
-    else if (left > 2 && kcmax >= 4) { bt1_slab<4>(c, j0, min(left, 4), b1_smem, Wsm, Wt); j0 += min(left, 4); }
-    else if (left >= 2 && kcmax >= 2) { bt1_slab<2>(c, j0, 2, b1_smem, Wsm, Wt); j0 += 2; }
-    else { bt1_slab<1>(c, j0, 1, b1_smem, Wsm, Wt); j0 += 1; }
-  }
+  // one-stage reflectors and T factors are FP32 pairs (written so by the
+  // shared-memory reduction, or converted by larft1_kernel)
+  if (c.path == 1)
+    bt1_cols<dfl>(c, lo, hi, kcmax, reinterpret_cast<dfl*>(b1_smem), reinterpret_cast<dfl*>(Wsm),
+                  reinterpret_cast<dfl*>(Wt));
+  else
+    bt1_cols<double>(c, lo, hi, kcmax, b1_smem, Wsm, Wt);
 }
 
 }  // namespace

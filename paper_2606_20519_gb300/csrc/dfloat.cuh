@@ -56,6 +56,44 @@ __device__ __forceinline__ dfl df_from_d(double x) {
   return df_make(h, __double2float_rn(x - (double)h));
 }
 __device__ __forceinline__ double df_to_d(dfl x) { return (double)x.hi + (double)x.lo; }
+// The same split by integer operations (no FP64-pipe instruction): hi is x
+// rounded to FP32 (to nearest, ties to even) from its 53-bit significand,
+// lo the remaining 29 bits rounded to FP32.  For operands bounded in
+// magnitude: |x| below 2^-126 gives 0, and lo is dropped below 2^-74
+// (its weight is under 2^-98 there); |x| beyond FP32's range gives +-inf.
+// df_from_d_scaled(x, s) converts x 2^-s the same way (s a whole number, the
+// power of two applied to the exponent field).
+__device__ __forceinline__ dfl df_from_d_scaled(double x, int s) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  const int eraw = (int)((b >> 52) & 0x7FF);
+  if (eraw == 0) return df_zero();
+  const int e = eraw == 0x7FF ? eraw : eraw - s;
+  if (e < 1023 - 126) return df_zero();
+  if (e > 1023 + 127) return df_make(__int_as_float(sgn | 0x7F800000u | (e == 0x7FF && (b << 12) ? 0x400000u : 0u)), 0.0f);
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull;
+  unsigned mh = (unsigned)(m >> 29);     // top 24 bits, in [2^23, 2^24)
+  int rem = (int)(m & 0x1FFFFFFFull);   // the 29 bits below them
+  if (rem > 0x10000000 || (rem == 0x10000000 && (mh & 1u))) {
+    ++mh;
+    rem -= 0x20000000;
+  }
+  int fe = e - 1023 + 127;
+  if (mh == 0x1000000u) {
+    mh = 0x800000u;
+    ++fe;
+  }
+  if (fe > 254) return df_make(__int_as_float(sgn | 0x7F800000u), 0.0f);
+  const float hi = __int_as_float(sgn | ((unsigned)fe << 23) | (mh & 0x7FFFFFu));
+  float lo = 0.0f;
+  const int le = e - 1075 + 127;  // biased exponent of the weight of rem's unit
+  if (rem != 0 && le >= 1) {
+    lo = __fmul_rn(__int2float_rn(rem), __int_as_float((unsigned)le << 23));
+    if (sgn) lo = -lo;
+  }
+  return df_make(hi, lo);
+}
+__device__ __forceinline__ dfl df_from_d_int(double x) { return df_from_d_scaled(x, 0); }
 __device__ __forceinline__ dfl df_shfl_xor(dfl v, int o) {
   return df_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
 }
@@ -79,6 +117,34 @@ __device__ __forceinline__ dfl df_div(dfl x, dfl y) {
   return df_fast_two_sum(q1, __fdividef(r.hi, y.hi));
 }
 
+
+// Kernels written once for FP64 and double-float elements (the generic
+// arithmetic below): FP64 where the operands span FP64's range, double-float
+// where they are bounded in magnitude (eigenvector blocks, reflectors of a
+// scaled matrix), where every product is FP32 pipe work and only the
+// conversions at the boundary use the FP64 pipe.
+__device__ __forceinline__ void g_zero(double& a) { a = 0.0; }
+__device__ __forceinline__ void g_zero(dfl& a) { a = df_zero(); }
+__device__ __forceinline__ void g_cvt(double& d, double v) { d = v; }
+__device__ __forceinline__ void g_cvt(dfl& d, double v) { d = df_from_d_int(v); }
+__device__ __forceinline__ double g_mad(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ dfl g_mad(dfl a, dfl b, dfl c) { return df_fma(a, b, c); }
+__device__ __forceinline__ double g_val(double a) { return a; }
+__device__ __forceinline__ double g_val(dfl a) { return df_to_d(a); }
+__device__ __forceinline__ double g_add(double a, double b) { return a + b; }
+__device__ __forceinline__ dfl g_add(dfl a, dfl b) { return df_add(a, b); }
+__device__ __forceinline__ double g_neg(double a) { return -a; }
+__device__ __forceinline__ dfl g_neg(dfl a) { return df_neg(a); }
+__device__ __forceinline__ bool g_is_zero(double a) { return a == 0.0; }
+__device__ __forceinline__ bool g_is_zero(dfl a) { return a.hi == 0.0f && a.lo == 0.0f; }
+__device__ __forceinline__ double g_shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ dfl g_shfl_xor(dfl v, int o) { return df_shfl_xor(v, o); }
+// read-only (non-coherent) loads
+__device__ __forceinline__ double g_ldg(const double* p) { return __ldg(p); }
+__device__ __forceinline__ dfl g_ldg(const dfl* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return df_make(v.x, v.y);
+}
 
 // Complex double-float: re and im parts as double-float values (16 bytes).
 struct __align__(16) cdf {

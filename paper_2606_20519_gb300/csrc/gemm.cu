@@ -34,18 +34,6 @@ __device__ __forceinline__ int find_problem(const int* prefix, int count, int ti
 
 constexpr int BK = kGemmBK;
 
-// Arithmetic of the tile loop: FP64, or double-float (dfloat.cuh) for
-// operands bounded in magnitude (eigenvector blocks), where every product
-// is FP32 pipe work and only the staging conversions use the FP64 pipe.
-__device__ __forceinline__ void g_zero(double& a) { a = 0.0; }
-__device__ __forceinline__ void g_zero(dfl& a) { a = df_zero(); }
-__device__ __forceinline__ void g_cvt(double& d, double v) { d = v; }
-__device__ __forceinline__ void g_cvt(dfl& d, double v) { d = df_from_d(v); }
-__device__ __forceinline__ double g_mad(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ dfl g_mad(dfl a, dfl b, dfl c) { return df_fma(a, b, c); }
-__device__ __forceinline__ double g_val(double a) { return a; }
-__device__ __forceinline__ double g_val(dfl a) { return df_to_d(a); }
-
 template <int BM, int BN, typename T>
 __device__ __forceinline__ void gemm_body(const GemmDesc* __restrict__ descs, const int* __restrict__ prefix,
                                           int count) {

@@ -116,8 +116,9 @@ struct ConeDev {
   int* prog;        // nsweeps progress counters of the bulge chasing
   double* d;        // n diagonal of the tridiagonal matrix
   double* e;        // n off-diagonal (e[i] couples i and i+1)
-  double* V1;       // stage-1 reflectors: npanels blocks of n*b (rows m_p)
-  double* T1;       // npanels blocks of b*b
+  double* V1;       // stage-1 reflectors: npanels blocks of n*b (rows m_p); one-stage cones: FP32 pairs
+                    // once larft1 has run (8 bytes per element either way)
+  double* T1;       // npanels blocks of b*b (one-stage cones: FP32 pairs)
   double* Y;        // n*b   A22 V
   double* X;        // n*b   Y T
   double* U3;       // n*3b  [V | W | V] for the rank-2b update
@@ -148,6 +149,7 @@ struct ConeDev {
   int* kinfo;       // [0] k kept, [1] route (0: positive part, 1: X - negative part), [2] kept secular
                     // roots, [3] keep all eigenpairs (derivative), [4] side option, [5] first kept root,
                     // [6] all-pairs mode: |S|, the pairs of the route's side, which come first,
+                    // [7] the one-stage reduction wrote V1 as FP32 pairs (else FP64, converted by larft1),
                     // [8] eigenvalues > 0, [9] eigenvalues < 0 (16 ints)
   int* status;      // per-cone status bits
   double* tau1;     // n     tau of the one-stage reflectors (read by larft1 while the divide and conquer runs)

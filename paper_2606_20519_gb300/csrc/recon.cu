@@ -11,6 +11,7 @@
 // A cone whose status is not clean is filled with NaN.
 #include <math.h>
 
+#include "dfloat.cuh"
 #include "internal.cuh"
 
 namespace scs {
@@ -19,12 +20,17 @@ namespace {
 
 constexpr int BK = 16;
 
+// The products run in double-float (FP32 pairs): Z's entries are bounded by
+// one and the eigenvalues are scaled by 2^-s, s the exponent of the largest
+// |l_k| (integer operations on the exponent field); the sum is scaled back in
+// FP64 in the epilogue.
 template <int BM>
-__global__ void __launch_bounds__(256) recon_kernel(const ConeDev* __restrict__ cones, const IoSlot* __restrict__ io) {
+__global__ void __launch_bounds__(256, 2) recon_kernel(const ConeDev* __restrict__ cones, const IoSlot* __restrict__ io) {
   const double* x = io->x;
   double* y = io->y;
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BM + 1];
+  __shared__ dfl As[BK][BM + 1];
+  __shared__ dfl Bs[BK][BM + 1];
+  __shared__ int s_exp;
   const ConeDev& c = cones[blockIdx.y];
   const int n = (int)c.n;
   const int tiles = (n + BM - 1) / BM;
@@ -42,25 +48,36 @@ __global__ void __launch_bounds__(256) recon_kernel(const ConeDev* __restrict__ 
   const double* Z = c.Z;
   const double* lam = c.lamk;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // the largest biased exponent of the kept eigenvalues
+  if (tid == 0) s_exp = 0;
+  __syncthreads();
+  {
+    int m = 0;
+    for (int k = tid; k < kk; k += 256) m = max(m, (int)((__double2hiint(lam[k]) >> 20) & 0x7FF));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0 && m > 0) atomicMax(&s_exp, m);
+  }
+  __syncthreads();
+  const int es = min(max(s_exp, 1), 2045);  // l 2^-(es - 1023) lies within [-2, 2]
   constexpr int R = BM / 16;  // rows (and columns) per thread
-  double acc[R][R];
+  dfl acc[R][R];
 #pragma unroll
   for (int r = 0; r < R; ++r)
 #pragma unroll
-    for (int q = 0; q < R; ++q) acc[r][q] = 0.0;
+    for (int q = 0; q < R; ++q) acc[r][q] = df_zero();
   for (int k0 = 0; k0 < kk; k0 += BK) {
 #pragma unroll
     for (int q = 0; q < (BM * BK) / 256; ++q) {
       const int e = tid + q * 256;
       const int ii = e % BM, l = e / BM;
       const int i = i0 + ii, j = j0 + ii, k = k0 + l;
-      double a = 0.0, bv = 0.0;
+      dfl a = df_zero(), bv = df_zero();
       if (k < kk) {
-        if (i < n) a = Z[(int64_t)i + (int64_t)k * n];
+        if (i < n) a = df_from_d_int(Z[(int64_t)i + (int64_t)k * n]);
         if (j < n) {
           // all eigenpairs are present when the derivative is needed: clip by side
           const double lk = route == 0 ? fmax(lam[k], 0.0) : fmin(lam[k], 0.0);
-          bv = Z[(int64_t)j + (int64_t)k * n] * lk;
+          bv = df_mul(df_from_d_int(Z[(int64_t)j + (int64_t)k * n]), df_from_d_scaled(lk, es - 1023));
         }
       }
       As[l][ii] = a;
@@ -69,7 +86,7 @@ __global__ void __launch_bounds__(256) recon_kernel(const ConeDev* __restrict__ 
     __syncthreads();
 #pragma unroll
     for (int l = 0; l < BK; ++l) {
-      double a[R], bv[R];
+      dfl a[R], bv[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) a[r] = As[l][tx + 16 * r];
 #pragma unroll
@@ -77,10 +94,11 @@ __global__ void __launch_bounds__(256) recon_kernel(const ConeDev* __restrict__ 
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int q = 0; q < R; ++q) acc[r][q] = fma(a[r], bv[q], acc[r][q]);
+        for (int q = 0; q < R; ++q) acc[r][q] = df_fma(a[r], bv[q], acc[r][q]);
     }
     __syncthreads();
   }
+  const double up = __longlong_as_double((long long)es << 52);  // 2^(es - 1023)
   const double* xs = x + c.xoff;
   double* ys = y + c.xoff;
 #pragma unroll
@@ -93,11 +111,12 @@ __global__ void __launch_bounds__(256) recon_kernel(const ConeDev* __restrict__ 
       const int i = i0 + tx + 16 * r;
       if (i >= n || i < j) continue;
       const int64_t idx = colo + (i - j);
-      const double sc = (i == j) ? 1.0 : M_SQRT2;
+      const double sc = (i == j) ? up : M_SQRT2 * up;
+      const double sv = df_to_d(acc[r][q]);
       double v;
       if (bad) v = nan("");
-      else if (route == 0) v = sc * acc[r][q];
-      else v = fma(-sc, acc[r][q], xs[idx]);
+      else if (route == 0) v = sc * sv;
+      else v = fma(-sc, sv, xs[idx]);
       ys[idx] = v;
     }
   }

@@ -393,12 +393,13 @@ __device__ void store_reflector_df(const ConeDev& c, int n, int j, const dfl* u,
   const int q = j / kNb, col = j % kNb;
   const int r0 = q * kNb + 1;
   const int mq = n - r0;
-  double* Vq = c.V1 + (int64_t)q * n * kNb;
+  // double-float pairs (the back-transformation of this route reads them so)
+  dfl* Vq = reinterpret_cast<dfl*>(c.V1) + (int64_t)q * n * kNb;
   for (int r = rank * kSyThreads + threadIdx.x; r < mq; r += G * kSyThreads) {
     const int row = r0 + r;
-    double val = 0.0;
-    if (row == j + 1) val = 1.0;
-    else if (row > j + 1) val = df_to_d(scaled ? df_mul(scal, u[row - j - 1]) : u[row - j - 1]);
+    dfl val = df_zero();
+    if (row == j + 1) val = df_make(1.0f, 0.0f);
+    else if (row > j + 1) val = scaled ? df_mul(scal, u[row - j - 1]) : u[row - j - 1];
     Vq[(int64_t)r + (int64_t)col * mq] = val;
   }
 }
@@ -820,7 +821,11 @@ __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __res
   // every CTA of a cone takes the same decision (same n, G, launch): columns
   // in shared memory and double-float arithmetic, or columns in L2 and FP64
   __shared__ int coef_tag;
-  if (sytrd1_bytes((int)c.n, G, true) <= (size_t)smem_bytes)
+  const bool res = sytrd1_bytes((int)c.n, G, true) <= (size_t)smem_bytes;
+  // the format of the reflector blocks V1 and their T factors: double-float
+  // pairs (shared-memory route) or FP64
+  if (rank == 0 && threadIdx.x == 0) c.kinfo[7] = res ? 1 : 0;
+  if (res)
     sytrd1_body_df(c, rank, G, wait_limit, sy_smem, reinterpret_cast<dfl*>(red), sh, reinterpret_cast<dfl*>(sh + 2),
                    &coef_tag);
   else
@@ -828,62 +833,89 @@ __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __res
 }
 
 // T factor of each 32-reflector block (one CTA per block): G = V^T V, then
-// T(a, j) = -tau_j sum_{q=a}^{j-1} T(a, q) G(q, j), T(j, j) = tau_j.
-__global__ void __launch_bounds__(kSyThreads) larft1_kernel(const ConeDev* __restrict__ cones,
-                                                            const int* __restrict__ blk_cone,
-                                                            const int* __restrict__ blk_index) {
-  __shared__ double Gm[kNb][kNb + 1];
-  __shared__ double T[kNb][kNb + 1];
-  __shared__ double part[kSyThreads / kNb][kNb];
-  const ConeDev& c = cones[blk_cone[blockIdx.x]];
-  if (*c.status != 0) return;
-  const int q = blk_index[blockIdx.x];
+// T(a, j) = -tau_j sum_{q=a}^{j-1} T(a, q) G(q, j), T(j, j) = tau_j; written
+// generically, run in double-float (the blocks are FP32 pairs on exit).
+template <typename E>
+__device__ void larft1_body(const ConeDev& c, int q, E (*Gm)[kNb + 1], E (*T)[kNb + 1], E (*part)[kNb]) {
   const int n = (int)c.n;
   const int r0 = q * kNb + 1, mq = n - r0;
   const int nr = min(kNb, n - 2 - q * kNb);  // reflectors in the block
-  const double* Vq = c.V1 + (int64_t)q * n * kNb;
+  const E* Vq = reinterpret_cast<const E*>(c.V1) + (int64_t)q * n * kNb;
   const int tid = threadIdx.x;
   // partial Grams: thread = (row group, column cc); 8 row groups of 32 lanes
   const int cc = tid % kNb, grp = tid / kNb;
-  double acc[kNb];
+  E acc[kNb];
 #pragma unroll
-  for (int a = 0; a < kNb; ++a) acc[a] = 0.0;
+  for (int a = 0; a < kNb; ++a) g_zero(acc[a]);
   if (cc < nr)
     for (int r = grp; r < mq; r += kSyThreads / kNb) {
-      const double vc = Vq[(int64_t)r + (int64_t)cc * mq];
-      if (vc == 0.0) continue;
+      const E vc = Vq[(int64_t)r + (int64_t)cc * mq];
+      if (g_is_zero(vc)) continue;
 #pragma unroll
       for (int a = 0; a < kNb; ++a)
-        if (a < cc) acc[a] = fma(Vq[(int64_t)r + (int64_t)a * mq], vc, acc[a]);
+        if (a < cc) acc[a] = g_mad(Vq[(int64_t)r + (int64_t)a * mq], vc, acc[a]);
     }
 #pragma unroll
   for (int a = 0; a < kNb; ++a) {
     part[grp][cc] = acc[a];
     __syncthreads();
     if (tid < kNb) {
-      double g = 0.0;
-      for (int p = 0; p < kSyThreads / kNb; ++p) g += part[p][tid];
+      E g;
+      g_zero(g);
+      for (int p = 0; p < kSyThreads / kNb; ++p) g = g_add(g, part[p][tid]);
       Gm[a][tid] = g;
-      for (int b2 = 0; b2 < kNb; ++b2) T[a][b2] = 0.0;
+      for (int b2 = 0; b2 < kNb; ++b2) g_zero(T[a][b2]);
     }
     __syncthreads();
   }
   __syncthreads();
   for (int j = 0; j < nr; ++j) {
-    const double tj = c.tau1[q * kNb + j];
+    E tj;
+    g_cvt(tj, c.tau1[q * kNb + j]);
     if (tid < j) {
-      double s = 0.0;
-      for (int p = tid; p < j; ++p) s = fma(T[tid][p], Gm[p][j], s);
-      T[tid][j] = -tj * s;
+      E s;
+      g_zero(s);
+      for (int p = tid; p < j; ++p) s = g_mad(T[tid][p], Gm[p][j], s);
+      E m;
+      g_zero(m);
+      T[tid][j] = g_mad(g_neg(tj), s, m);
     }
     if (tid == 0) T[j][j] = tj;
     __syncthreads();
   }
-  double* Tq = c.T1 + (int64_t)q * kNb * kNb;
+  E* Tq = reinterpret_cast<E*>(c.T1) + (int64_t)q * kNb * kNb;
   for (int e = tid; e < kNb * kNb; e += kSyThreads) {
     const int a = e % kNb, b2 = e / kNb;
     Tq[a + b2 * kNb] = T[a][b2];
   }
+}
+
+__global__ void __launch_bounds__(kSyThreads) larft1_kernel(const ConeDev* __restrict__ cones,
+                                                            const int* __restrict__ blk_cone,
+                                                            const int* __restrict__ blk_index) {
+  // 8-byte elements either way (FP64, or an FP32 pair)
+  __shared__ double Gm[kNb][kNb + 1];
+  __shared__ double T[kNb][kNb + 1];
+  __shared__ double part[kSyThreads / kNb][kNb];
+  const ConeDev& c = cones[blk_cone[blockIdx.x]];
+  if (*c.status != 0) return;
+  const int q = blk_index[blockIdx.x];
+  if (!c.kinfo[7]) {
+    // FP64 reflectors (columns in L2): this block becomes FP32 pairs in
+    // place (|v| <= 1), so the fused back-transformation runs in
+    // double-float for every one-stage cone
+    const int n = (int)c.n;
+    const int mq = n - (q * kNb + 1);
+    const int nr = min(kNb, n - 2 - q * kNb);
+    double* Vd = c.V1 + (int64_t)q * n * kNb;
+    for (int64_t e = threadIdx.x; e < (int64_t)mq * nr; e += kSyThreads) {
+      const double v = Vd[e];
+      reinterpret_cast<dfl*>(Vd)[e] = df_from_d_int(v);
+    }
+    __syncthreads();
+  }
+  larft1_body<dfl>(c, q, reinterpret_cast<dfl(*)[kNb + 1]>(Gm), reinterpret_cast<dfl(*)[kNb + 1]>(T),
+                   reinterpret_cast<dfl(*)[kNb]>(part));
 }
 
 }  // namespace
