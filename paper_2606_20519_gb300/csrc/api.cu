@@ -293,7 +293,7 @@ struct ConeLayout {
 
 enum Field {
   F_A, F_BAND, F_REFL, F_D, F_E, F_V1, F_T1, F_Y, F_X, F_U3, F_MB, F_NB, F_QA, F_QB, F_LAMA, F_LAMB, F_QIN, F_UCM, F_Z,
-  F_LAMK, F_DSRT, F_ZK, F_DVAL, F_TAU, F_ZHAT, F_ROT, F_RHO, F_UNRM, F_IPERM, F_IFP, F_IROT, F_IORG, F_IMAP, F_ICNT,
+  F_LAMK, F_DSRT, F_ZK, F_DVAL, F_TAU, F_ZHAT, F_ROT, F_RHO, F_IPERM, F_IFP, F_IROT, F_IORG, F_IMAP, F_ICNT,
   F_KINFO, F_TAU1, F_NFIELDS
 };
 
@@ -312,7 +312,7 @@ ConeLayout cone_layout(int64_t n, int b, int path) {
       d * std::max<int64_t>((int64_t)P * n * b, (int64_t)Q * n * kSy1Block),
       d * std::max<int64_t>((int64_t)P * b * b, (int64_t)Q * kSy1Block * kSy1Block),
       d * n * bw, d * n * bw + d * 2048, d * n * 3 * b, d * b * b, d * b * b, d * n * n, d * n * n, d * n, d * n,
-      d * n * n, d * n * n, d * n * n, d * n, d * n, d * n, d * n, d * n, d * n, d * 2 * n, d * n, d * n,
+      d * n * n, d * n * n, d * n * n, d * n, d * n, d * n, d * n, d * n, d * n, d * 2 * n, d * n,
       i4 * n, i4 * n, i4 * 2 * n, i4 * n, i4 * n, i4 * 4 * n, i4 * 16, d * n};
   size_t o = 0;
   for (int f = 0; f < F_NFIELDS; ++f) {
@@ -427,7 +427,8 @@ struct MetaBuilder {
 
   // Picks the engine and tile shape for the launch and a split-K factor per
   // problem so that the launch has about two CTAs per SM.  bounded: every
-  // operand is at most about 1 in magnitude (eigenvector blocks), so the FP64
+  // operand lies well inside FP32's exponent range (eigenvector blocks, and
+  // their products with a matrix scaled to its largest entry), so the FP64
   // path may run the 64 x 64 tiles in double-float arithmetic.
   GemmLaunch add_gemm(std::vector<GemmDesc> probs, bool bounded = false) {
     if (split && tc2 && !probs.empty()) {
@@ -444,10 +445,14 @@ struct MetaBuilder {
     g.count = (int)probs.size();
     g.prefix_off = (int)ints.size();
     int maxM = 0, maxN = 0, minK = 1 << 30;
+    double fma_total = 0.0;
+    int64_t tiles64 = 0;
     for (const GemmDesc& p : probs) {
       maxM = std::max(maxM, p.M);
       maxN = std::max(maxN, p.N);
       minK = std::min(minK, p.K);
+      fma_total += (double)p.M * p.N * p.K;
+      tiles64 += (int64_t)((p.M + 63) / 64) * ((p.N + 63) / 64);
     }
     int bm, bn;
     g.tc = (split && maxM >= 64 && minK >= 32 && !probs.empty()) ? 1 : 0;
@@ -457,6 +462,11 @@ struct MetaBuilder {
     } else {
       g.variant = (maxM <= 16 && maxN <= 16) ? GEMM_SMALL
                   : (maxN <= 16) ? GEMM_TALL : (maxM <= 16) ? GEMM_SHORT : GEMM_SQUARE;
+      // few small products (fewer 64 x 64 tiles than SMs, at most 16M FMA in
+      // all): 16 x 16 FP64 tiles spread them over every SM, where 64 x 64
+      // tiles left most SMs idle (the divide and conquer's merges of 32 .. 128
+      // rows at n = 625 took 37 .. 44 us each in 64 x 64 tiles)
+      if (g.variant == GEMM_SQUARE && tiles64 < sms && fma_total <= 16.0 * 1024 * 1024) g.variant = GEMM_SMALL;
       if (bounded && g.variant == GEMM_SQUARE && minK >= 32) g.variant = GEMM_SQUARE_DF;
       gemm_tile_shape(g.variant, &bm, &bn);
     }
@@ -625,7 +635,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
     d.lamk = FLD(double, F_LAMK); d.dsrt = FLD(double, F_DSRT); d.zk = FLD(double, F_ZK); d.dval = FLD(double, F_DVAL);
     d.tau = FLD(double, F_TAU); d.zhat = FLD(double, F_ZHAT); d.rot = FLD(double, F_ROT); d.rho = FLD(double, F_RHO);
     d.tau1 = FLD(double, F_TAU1);
-    d.unrm = FLD(double, F_UNRM); d.ifp = FLD(int, F_IFP);
+    d.ifp = FLD(int, F_IFP);
     d.iperm = FLD(int, F_IPERM); d.irot = FLD(int, F_IROT); d.iorg = FLD(int, F_IORG); d.imap = FLD(int, F_IMAP);
     d.icnt = FLD(int, F_ICNT); d.kinfo = FLD(int, F_KINFO);
 #undef FLD
@@ -756,9 +766,12 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
             work += std::pow((double)cones[list[i]].n, 3.0);
             ++i;
           }
-          std::vector<int> give(grp.size(), 1);
-          if (spread) {
-            int left = cap - (int)grp.size();
+          // CTAs per cone: a share of the co-resident CTAs by work, at least 4
+          // columns each
+          auto spread_give = [&](int budget) {
+            std::vector<int> give(grp.size(), 1);
+            if (!spread) return give;
+            const int left = budget - (int)grp.size();
             for (size_t q = 0; q < grp.size(); ++q) {
               const double share = std::pow((double)cones[grp[q]].n, 3.0) / work;
               int extra = (int)(share * left);
@@ -766,7 +779,9 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
               extra = std::min(extra, sm_cap - 1);
               give[q] += extra;
             }
-          }
+            return give;
+          };
+          std::vector<int> give = spread_give(cap);
           Sytrd1Launch sl;
           sl.maxn = (int)maxn1;
           // shared-memory-resident columns when every cone of the launch fits and
@@ -777,7 +792,20 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
               need = std::max(need, sytrd1_smem_bytes((int)cones[grp[q]].n, give[q], true));
             int total = 0;
             for (int g : give) total += g;
-            if (need <= 200 * 1024 && sytrd1_max_ctas_for(need) >= total) sl.smem = need;
+            if (need <= 200 * 1024 && sytrd1_max_ctas_for(need) >= total) {
+              sl.smem = need;
+            } else if (spread && tune.sy_share <= 1) {
+              // columns in L2: whole waves of r CTAs per SM (an SM with one CTA
+              // more than the others sets every step's pace), r near one CTA per
+              // 28 columns per SM (measured: 8 cones of side 1296 at 2 per SM,
+              // 57 ms; at 4 per SM, 74 ms; 4 cones of side 4096 best at 4)
+              double cols = 0.0;
+              for (int c : grp) cols += (double)cones[c].n;
+              const int sms_all = std::max(1, h->sms);
+              int r = (int)std::lround(cols / (28.0 * sms_all));
+              r = std::max(1, std::min(r, std::max(1, cap / sms_all)));
+              give = spread_give(std::max((int)grp.size(), r * sms_all));
+            }
           }
           std::vector<int> cc, rr, gg;
           for (size_t q = 0; q < grp.size(); ++q)
@@ -1042,7 +1070,8 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
       g[2].push_back(q2);
       g[3].push_back(q3);
     }
-    for (int q = 0; q < 4; ++q) P.vjp[q] = mb.add_gemm(g[q]);
+    // operands bounded: eigenvectors, and G scaled by a power of two to its largest entry
+    for (int q = 0; q < 4; ++q) P.vjp[q] = mb.add_gemm(g[q], true);
   }
 
   // ---- allocate and upload metadata
@@ -1334,8 +1363,6 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
         LAUNCH_CHECK();
         launch_dc_select(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
         LAUNCH_CHECK();
-        launch_dc_vecnorm(P.cones_d, nodes, pos, P.total_pos, s);
-        LAUNCH_CHECK();
         launch_dc_vectors(P.cones_d, nodes, pos, P.total_pos, lv.maxK, s);
         LAUNCH_CHECK();
         if ((rc = run_gemm(P, lv.g, s, n_launch))) return rc;
@@ -1398,6 +1425,8 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
     }
     if (want_vjp) {
       pm.begin(7);
+      launch_vjp_gexp(P.cones_d, nc, io, s);
+      LAUNCH_CHECK();
       launch_unpack(P.cones_d, nc, P.maxn * P.maxn, io, 1, s);
       LAUNCH_CHECK();
       if ((rc = run_gemm(P, P.vjp[0], s, n_launch))) return rc;

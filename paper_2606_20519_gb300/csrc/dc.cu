@@ -402,7 +402,7 @@ __device__ __forceinline__ float f64_to_f32_rn(double v) {
 // lane ends with the same values).  Returns the origin pole and the offset
 // tau = x - d_org; false if the iteration cap was reached.
 __device__ bool secular_root_warp(const double* __restrict__ dk, const double* __restrict__ zk, int K, double rho,
-                                  int i, int lane, float* dif, int* org_out, double* tau_out) {
+                                  int i, int lane, float* dif, double* difd, int* org_out, double* tau_out) {
   int org;
   double lo, hi;
   if (i < K - 1) {
@@ -427,9 +427,14 @@ __device__ bool secular_root_warp(const double* __restrict__ dk, const double* _
   // beyond its FP32 error bound; the FP64 loop below then polishes from the
   // narrowed bracket.  Only the differences d_j - d_org are formed in FP64.
   {
-    // d_j - d_org in FP32, formed in FP64 once per root (dif: this warp's K floats)
+    // d_j - d_org, formed in FP64 once per root (difd: this warp's K doubles)
+    // and rounded to FP32 (dif: K floats)
     if (dif)
-      for (int j = lane; j < K; j += 32) dif[j] = f64_to_f32_rn(dk[j] - dorg);
+      for (int j = lane; j < K; j += 32) {
+        const double dd = dk[j] - dorg;
+        difd[j] = dd;
+        dif[j] = f64_to_f32_rn(dd);
+      }
     __syncwarp();
     const float rho32 = f64_to_f32_rn(rho);
     const float p32 = f64_to_f32_rn(dk[li] - dorg);
@@ -491,34 +496,38 @@ __device__ bool secular_root_warp(const double* __restrict__ dk, const double* _
       tau = okx ? (double)x : 0.5 * (lo + hi);
     }
   }
+  const double p = dk[li] - dorg;
+  const double q = ri < K ? dk[ri] - dorg : 0.0;
   for (int it = 0; it < 100; ++it) {
-    double psi = 0.0, phi = 0.0, dpsi = 0.0, dphi = 0.0, aerr = 0.0;
+    double psi = 0.0, phi = 0.0, dpsi = 0.0, dphi = 0.0;
     for (int j = lane; j < K; j += 32) {
-      const double del = (dk[j] - dorg) - tau;
+      const double del = (dif ? difd[j] : dk[j] - dorg) - tau;
       const double zz = zk[j];
       const double t = zz * rcp_nr(del);
       const double term = zz * t;
       if (j < ri) { psi += term; dpsi = fma(t, t, dpsi); }
       else { phi += term; dphi = fma(t, t, dphi); }
-      aerr += fabs(term);
     }
-    psi = rho * warp_sum_d(psi);
-    phi = rho * warp_sum_d(phi);
+    psi = warp_sum_d(psi);
+    phi = warp_sum_d(phi);
+    // sum |term|: d_j - lambda is formed exactly enough to carry its sign (the
+    // pole differences in FP64, tau inside the bracket), so the terms left of
+    // the root (j < ri) are negative and the others positive
+    const double aerr = phi - psi;
+    psi *= rho;
+    phi *= rho;
     dpsi = rho * warp_sum_d(dpsi);
     dphi = rho * warp_sum_d(dphi);
-    aerr = warp_sum_d(aerr);
     const double g = 1.0 + psi + phi;
     if (fabs(g) <= 8.0 * kEps * K * (1.0 + rho * aerr)) { conv = true; break; }
     if (g > 0.0) hi = tau; else lo = tau;
     if (hi - lo <= 4.0 * kEps * fmax(fabs(lo), fabs(hi))) { conv = true; break; }
-    const double p = dk[li] - dorg;
     const double dl = p - tau;
     const double sl = dpsi * dl * dl;
     const double a = psi - sl / dl;
     double x = 0.0;
     bool okx = false;
     if (ri < K) {
-      const double q = dk[ri] - dorg;
       const double dr = q - tau;
       const double sr = dphi * dr * dr;
       const double bq = phi - sr / dr;
@@ -589,11 +598,14 @@ __global__ void dc_secular_kernel(const ConeDev* __restrict__ cones, const Merge
   const int kk = c.icnt[4 * s];
   if (i >= kk) return;
   const int lane = threadIdx.x & 31;
-  extern __shared__ float sec_dif[];
-  float* dif = difmax >= kk ? sec_dif + (threadIdx.x >> 5) * difmax : nullptr;
+  // per warp: difmax doubles, then (after the four warps' doubles) difmax floats
+  extern __shared__ double sec_difd[];
+  const int wq = threadIdx.x >> 5;
+  double* difd = difmax >= kk ? sec_difd + wq * difmax : nullptr;
+  float* dif = difmax >= kk ? reinterpret_cast<float*>(sec_difd + 4 * difmax) + wq * difmax : nullptr;
   int org;
   double tau;
-  const bool ok = secular_root_warp(c.dsrt + s, c.zk + s, kk, c.rho[s], i, lane, dif, &org, &tau);
+  const bool ok = secular_root_warp(c.dsrt + s, c.zk + s, kk, c.rho[s], i, lane, dif, difd, &org, &tau);
   if (lane == 0) {
     c.iorg[s + i] = org;
     c.tau[s + i] = tau;
@@ -765,7 +777,9 @@ __global__ void __launch_bounds__(kDcThreads) dc_select_kernel(const ConeDev* __
 }
 
 // ---------------------------------------------------------------- vectors
-__global__ void dc_vecnorm_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes,
+// U(row, j) = zhat_j / (d_j - lambda_i) / ||.||: one warp per root i forms
+// the components (lanes over j) and their norm, then rescales its own stores.
+__global__ void dc_vectors_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes,
                                   const int* __restrict__ pos_node, int64_t total) {
   const WarpPos w = warp_pos(nodes, pos_node, total);
   if (!w.ok) return;
@@ -774,54 +788,26 @@ __global__ void dc_vecnorm_kernel(const ConeDev* __restrict__ cones, const Merge
   const int s = w.nd.s, i = w.idx;
   const int kk = c.icnt[4 * s];
   if (i >= kk) return;
-  if (w.nd.root && c.imap[s + i] < 0) return;
-  const int lane = threadIdx.x & 31;
-  const double* dk = c.dsrt + s;
-  const double* zh = c.zhat + s;
-  const double dorg = dk[c.iorg[s + i]];
-  const double tau = c.tau[s + i];
-  double nrm = 0.0;
-  for (int j = lane; j < kk; j += 32) {
-    const double u = zh[j] * rcp_nr((dk[j] - dorg) - tau);
-    nrm = fma(u, u, nrm);
-  }
-  nrm = warp_sum_d(nrm);
-  if (lane == 0) c.unrm[s + i] = 1.0 / sqrt(nrm);
-}
-
-// U(row, j) = zhat_j / (d_j - lambda_i) / ||.||; thread = root (consecutive
-// threads write consecutive rows), blockIdx.y = chunk of components j.
-constexpr int kVecChunk = 16;
-__global__ void dc_vectors_kernel(const ConeDev* __restrict__ cones, const MergeNode* __restrict__ nodes,
-                                  const int* __restrict__ pos_node, int64_t total) {
-  const int64_t gp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gp >= total) return;
-  const int ni = pos_node[total + gp];
-  if (ni < 0) return;
-  const MergeNode nd = nodes[ni];
-  if (nd.n2 == 0) return;
-  const ConeDev& c = cones[nd.cone];
-  if (*c.status != 0) return;
-  const int i = pos_node[gp];
-  const int s = nd.s;
-  const int kk = c.icnt[4 * s];
-  if (i >= kk) return;
-  const int j0 = blockIdx.y * kVecChunk;
-  if (j0 >= kk) return;
   int row = i;
-  if (nd.root) {
+  if (w.nd.root) {
     row = c.imap[s + i];
     if (row < 0) return;
   }
+  const int lane = threadIdx.x & 31;
   const int64_t n = c.n;
   const double* dk = c.dsrt + s;
   const double* zh = c.zhat + s;
   const double dorg = dk[c.iorg[s + i]];
   const double tau = c.tau[s + i];
-  const double inv = c.unrm[s + i];
   double* U = c.Ucm + s + row + (int64_t)s * n;  // U[j * n] = component j
-  const int jend = min(kk, j0 + kVecChunk);
-  for (int j = j0; j < jend; ++j) U[(int64_t)j * n] = inv * (zh[j] * rcp_nr((dk[j] - dorg) - tau));
+  double nrm = 0.0;
+  for (int j = lane; j < kk; j += 32) {
+    const double u = zh[j] * rcp_nr((dk[j] - dorg) - tau);
+    U[(int64_t)j * n] = u;
+    nrm = fma(u, u, nrm);
+  }
+  const double inv = 1.0 / sqrt(warp_sum_d(nrm));
+  for (int j = lane; j < kk; j += 32) U[(int64_t)j * n] *= inv;
 }
 
 // deflated columns: Qin(:, kk + q) -> output column; blockIdx.x = node,
@@ -872,14 +858,15 @@ void launch_dc_prepare(const ConeDev* cones, const MergeNode* nodes, int nnodes,
 void launch_dc_secular(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total, int maxK,
                        cudaStream_t s) {
   if (total <= 0) return;
-  // four warps per CTA, each with maxK floats of shared memory (none when that would not fit)
+  // four warps per CTA, each with maxK doubles and maxK floats of shared
+  // memory (none when that would not fit)
   constexpr size_t kSecSmemMax = 160 * 1024;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(dc_secular_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSecSmemMax);
     attr = true;
   }
-  const size_t smem = (size_t)4 * maxK * sizeof(float);
+  const size_t smem = (size_t)4 * maxK * (sizeof(double) + sizeof(float));
   const int difmax = smem <= kSecSmemMax ? maxK : 0;
   dc_secular_kernel<<<(unsigned)((total * 32 + 127) / 128), 128, difmax ? smem : 0, s>>>(cones, nodes, pos_node,
                                                                                          total, difmax);
@@ -889,12 +876,6 @@ void launch_dc_loewner(const ConeDev* cones, const MergeNode* nodes, const int* 
                        cudaStream_t s) {
   if (total <= 0) return;
   dc_loewner_kernel<<<(unsigned)((total * 32 + 127) / 128), 128, 0, s>>>(cones, nodes, pos_node, total);
-}
-
-void launch_dc_vecnorm(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total,
-                       cudaStream_t s) {
-  if (total <= 0) return;
-  dc_vecnorm_kernel<<<(unsigned)((total * 32 + 127) / 128), 128, 0, s>>>(cones, nodes, pos_node, total);
 }
 
 void launch_dc_build_qin(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s) {
@@ -916,9 +897,9 @@ void launch_dc_select(const ConeDev* cones, const MergeNode* nodes, int nnodes, 
 
 void launch_dc_vectors(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total, int maxK,
                        cudaStream_t s) {
+  (void)maxK;
   if (total <= 0) return;
-  dc_vectors_kernel<<<dim3((unsigned)((total + 127) / 128), (maxK + kVecChunk - 1) / kVecChunk), 128, 0, s>>>(
-      cones, nodes, pos_node, total);
+  dc_vectors_kernel<<<(unsigned)((total * 32 + 127) / 128), 128, 0, s>>>(cones, nodes, pos_node, total);
 }
 
 void launch_dc_copy_deflated(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s) {

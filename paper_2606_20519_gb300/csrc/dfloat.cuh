@@ -50,6 +50,42 @@ __device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
   return df_fast_two_sum(p, e);
 }
 __device__ __forceinline__ dfl df_zero() { return df_make(0.0f, 0.0f); }
+// x + y u + z w with one renormalisation (TwoProduct of each hi part, TwoSum
+// of the three leading terms, the error terms summed in FP32).
+__device__ __forceinline__ dfl df_add2prod(dfl x, dfl y, dfl u, dfl z, dfl w) {
+  const float p1 = __fmul_rn(y.hi, u.hi);
+  float e1 = __fmaf_rn(y.hi, u.hi, -p1);
+  e1 = __fmaf_rn(y.hi, u.lo, __fmaf_rn(y.lo, u.hi, e1));
+  const float p2 = __fmul_rn(z.hi, w.hi);
+  float e2 = __fmaf_rn(z.hi, w.hi, -p2);
+  e2 = __fmaf_rn(z.hi, w.lo, __fmaf_rn(z.lo, w.hi, e2));
+  const dfl s1 = df_two_sum(x.hi, p1);
+  const dfl s2 = df_two_sum(s1.hi, p2);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(x.lo, e1), __fadd_rn(e2, s1.lo)), s2.lo);
+  return df_fast_two_sum(s2.hi, lo);
+}
+// Compensated dot product of double-float vectors (the scheme of Ogita, Rump
+// and Oishi's Dot2): the products' hi parts are summed with TwoSum into s,
+// every error term into the FP32 compensation c; df_dot_value renormalises.
+struct df_dot {
+  float s, c;
+};
+__device__ __forceinline__ df_dot df_dot_zero() {
+  df_dot d;
+  d.s = 0.0f;
+  d.c = 0.0f;
+  return d;
+}
+__device__ __forceinline__ df_dot df_dot_add(df_dot d, dfl a, dfl x) {
+  const float p = __fmul_rn(a.hi, x.hi);
+  float e = __fmaf_rn(a.hi, x.hi, -p);
+  e = __fmaf_rn(a.hi, x.lo, __fmaf_rn(a.lo, x.hi, e));
+  const dfl t = df_two_sum(d.s, p);
+  d.s = t.hi;
+  d.c = __fadd_rn(d.c, __fadd_rn(t.lo, e));
+  return d;
+}
+__device__ __forceinline__ dfl df_dot_value(df_dot d) { return df_two_sum(d.s, d.c); }
 // FP64 <-> double-float (FP64 pipe: used at the boundaries only)
 __device__ __forceinline__ dfl df_from_d(double x) {
   const float h = __double2float_rn(x);

@@ -139,7 +139,6 @@ struct ConeDev {
   double* zhat;     // n     Loewner-corrected z
   double* rot;      // 2n    Givens rotations (c, s) of the deflation
   double* rho;      // n     rank-one weight per merge node (indexed by start)
-  double* unrm;     // n     1 / norm of each secular eigenvector
   int* iperm;       // n     sorted position -> column of the child blocks
   int* ifp;         // n     sorted position -> column of the merged block (kept first)
   int* irot;        // 2n    rotation column pairs
@@ -150,7 +149,8 @@ struct ConeDev {
                     // roots, [3] keep all eigenpairs (derivative), [4] side option, [5] first kept root,
                     // [6] all-pairs mode: |S|, the pairs of the route's side, which come first,
                     // [7] the one-stage reduction wrote V1 as FP32 pairs (else FP64, converted by larft1),
-                    // [8] eigenvalues > 0, [9] eigenvalues < 0 (16 ints)
+                    // [8] eigenvalues > 0, [9] eigenvalues < 0, [10] largest biased exponent of the
+                    // derivative's input g (16 ints)
   int* status;      // per-cone status bits
   double* tau1;     // n     tau of the one-stage reflectors (read by larft1 while the divide and conquer runs)
   int cidx;         // position of the cone in the call's shape list
@@ -234,8 +234,6 @@ void launch_dc_copy_deflated(const ConeDev* cones, const MergeNode* nodes, int n
 void launch_dc_build_qin(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s);
 void launch_dc_apply_rot(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total_pos,
                          cudaStream_t s);
-void launch_dc_vecnorm(const ConeDev* cones, const MergeNode* nodes, const int* pos_node, int64_t total_pos,
-                       cudaStream_t s);
 void launch_backtr2(const ConeDev* cones, int ncones, int maxn, int maxk, int kexp, int band, cudaStream_t s);
 size_t panel_smem_bytes(int b, int R);
 // Z, lamk (all n eigenpairs) <-> io->V, io->lam
@@ -244,6 +242,17 @@ void launch_import_eig(const ConeDev* cones, int ncones, int64_t maxn, const IoS
 // derivative: eigenpairs into S-first order (3 launches), then the k_S x n scaling
 void launch_vjp_reorder(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s);
 void launch_vjp_scale(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s);
+void launch_vjp_gexp(const ConeDev* cones, int ncones, const IoSlot* io, cudaStream_t s);
+// The derivative's input scale: G enters the contractions as G / up, up = 2^(e - 1023)
+// for e the largest biased exponent of g (kinfo[10]), clamped to [1, 2045].
+__device__ __forceinline__ double vjp_gscale_up(int e) {
+  e = e < 1 ? 1 : (e > 2045 ? 2045 : e);
+  return __longlong_as_double((long long)e << 52);
+}
+__device__ __forceinline__ double vjp_gscale_down(int e) {
+  e = e < 1 ? 1 : (e > 2045 ? 2045 : e);
+  return __longlong_as_double((long long)(2046 - e) << 52);
+}
 void launch_pack_lower(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s);
 void launch_recon(const ConeDev* cones, int ncones, int maxn, const IoSlot* io, cudaStream_t s);
 int sytrd1_max_ctas(int maxn);

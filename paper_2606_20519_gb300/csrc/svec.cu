@@ -20,12 +20,14 @@ __global__ void unpack_kernel(const ConeDev* __restrict__ cones, const IoSlot* _
   const int64_t n = c.n;
   const int64_t nn = n * n;
   const double* xs = x + c.xoff;
+  // the derivative's input enters scaled by a power of two (kinfo[10])
+  const double down = which ? vjp_gscale_down(c.kinfo[10]) : 1.0;
   bool bad = false;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e % n, j = e / n;
     const int64_t lo = i >= j ? i : j, hi = i >= j ? j : i;  // (row, col) in the lower triangle
     double v = xs[svec_col_offset(n, hi) + (lo - hi)];
-    if (lo != hi) v *= M_SQRT1_2;
+    v *= (lo != hi) ? M_SQRT1_2 * down : down;
     if (!isfinite(v)) bad = true;
     c.A[e] = v;
   }

@@ -444,9 +444,9 @@ __device__ void column_pass_dfw(dfl* __restrict__ cols, int n, int r0, const dfl
       nai = df_neg(df_fma(df_neg(K2), vi, pu[i - r0 + 1]));  // -(p_i - 2K v_i)
       nvi = df_neg(vi);
     }
-    dfl acc[U];
+    df_dot acc[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) acc[u] = df_zero();
+    for (int u = 0; u < U; ++u) acc[u] = df_dot_zero();
     for (int t0 = lane; t0 < L; t0 += 32 * U) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -454,15 +454,16 @@ __device__ void column_pass_dfw(dfl* __restrict__ cols, int n, int r0, const dfl
         if (t < L) {
           dfl a = col[t];
           if (UPDATE) {
-            a = df_fma(vu[t + 1], nai, df_fma(pu[t + 1], nvi, a));
+            a = df_add2prod(a, vu[t + 1], nai, pu[t + 1], nvi);
             col[t] = a;
           }
           if (pub_col) st_pub_df(Cn + t, a);
-          if (t > 0) acc[u] = df_fma(a, x[t], acc[u]);
+          if (t > 0) acc[u] = df_dot_add(acc[u], a, x[t]);
         }
       }
     }
-    dfl sdot = df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3]));
+    dfl sdot = df_add(df_add(df_dot_value(acc[0]), df_dot_value(acc[1])),
+                      df_add(df_dot_value(acc[2]), df_dot_value(acc[3])));
     for (int o = 16; o > 0; o >>= 1) sdot = df_add(sdot, df_shfl_xor(sdot, o));
     if (lane == 0) {
       // thread 0 of this CTA forms the scalars while the columns are updated

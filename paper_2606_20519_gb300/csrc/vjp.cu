@@ -18,7 +18,10 @@
 // The eigenpairs are first reordered so that S comes first (route 0: S =
 // {l > 0}; route 1: S = {l <= 0}; the route is the projection's side).  The
 // contractions run in the grouped GEMM; this file holds the reordering, the
-// elementwise scaling and the final svec packing.
+// elementwise scaling and the final svec packing.  G enters the contractions
+// scaled by 2^-s, s the exponent of its largest entry (exact), so that every
+// operand lies within FP32's exponent range and the FP64 path may run them
+// in double-float arithmetic; the packing scales back.
 #include <math.h>
 
 #include "internal.cuh"
@@ -135,6 +138,23 @@ __global__ void vjp_scale_kernel(const ConeDev* __restrict__ cones) {
   }
 }
 
+// kinfo[10] = the largest biased exponent of the cone's g (one CTA per cone).
+__global__ void vjp_gexp_kernel(const ConeDev* __restrict__ cones, const IoSlot* __restrict__ io) {
+  const ConeDev& c = cones[blockIdx.x];
+  const int64_t len = c.n * (c.n + 1) / 2;
+  const double* g = io->g + c.xoff;
+  int m = 0;
+  for (int64_t e = threadIdx.x; e < len; e += blockDim.x) m = max(m, (__double2hiint(g[e]) >> 20) & 0x7FF);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ int wm[32];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, wm[w]);
+    c.kinfo[10] = m;
+  }
+}
+
 // Stored eigendecomposition out: V block = Z (all n columns), lam = lamk;
 // NaN for a cone whose status is bad.
 __global__ void export_eig_kernel(const ConeDev* __restrict__ cones, const IoSlot* __restrict__ io) {
@@ -178,6 +198,7 @@ __global__ void pack_lower_kernel(const ConeDev* __restrict__ cones, const IoSlo
   const int64_t len = n * (n + 1) / 2;
   const bool bad = *c.status != 0;
   double* out = xbar + c.xoff;
+  const double up = vjp_gscale_up(c.kinfo[10]);  // G was scaled by 1 / up
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (int64_t)gridDim.x * blockDim.x) {
     // invert t -> (i, j), column j starts at j*n - j(j-1)/2
     double jd = ((2.0 * n + 1.0) - sqrt((2.0 * n + 1.0) * (2.0 * n + 1.0) - 8.0 * (double)t)) * 0.5;
@@ -187,7 +208,7 @@ __global__ void pack_lower_kernel(const ConeDev* __restrict__ cones, const IoSlo
     while (j > 0 && j * n - (j * (j - 1)) / 2 > t) --j;
     while (j + 1 < n && (j + 1) * n - ((j + 1) * j) / 2 <= t) ++j;
     const int64_t i = j + (t - (j * n - (j * (j - 1)) / 2));
-    const double sc = (i == j) ? 1.0 : M_SQRT2;
+    const double sc = (i == j) ? up : M_SQRT2 * up;
     double h = c.QB[i + j * n] + c.QB[j + i * n];
     if (c.kinfo[1] == 1) h = c.A[i + j * n] - h;
     out[t] = bad ? nan("") : sc * h;
@@ -203,6 +224,11 @@ void launch_vjp_reorder(const ConeDev* cones, int ncones, int64_t maxn, cudaStre
   vjp_partition_kernel<<<ncones, 256, 0, s>>>(cones);
   vjp_permute_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones);
   vjp_copyback_kernel<<<dim3(gx, ncones), 256, 0, s>>>(cones);
+}
+
+void launch_vjp_gexp(const ConeDev* cones, int ncones, const IoSlot* io, cudaStream_t s) {
+  if (ncones <= 0) return;
+  vjp_gexp_kernel<<<ncones, 1024, 0, s>>>(cones, io);
 }
 
 void launch_vjp_scale(const ConeDev* cones, int ncones, int64_t maxn, cudaStream_t s) {
