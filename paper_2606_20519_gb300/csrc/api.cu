@@ -873,8 +873,9 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
     for (int q = 0; q < P.ncones; ++q) {
       const int64_t n = cones[q].n;
       for (int k = 0; k < hcone_blocks(n); ++k) { bc.push_back(q); bi.push_back(k); }
-      // back-transformation: about four kept columns per CTA for half the columns kept
-      const int g = (int)std::max<int64_t>(1, std::min<int64_t>(2 * sms, (n / 2 + 3) / 4));
+      // back-transformation: about two kept columns per CTA for half the columns
+      // kept (every SM busy at n = 625; each CTA streams the reflector blocks from L2)
+      const int g = (int)std::max<int64_t>(1, std::min<int64_t>(2 * sms, (n / 2 + 1) / 2));
       for (int r = 0; r < g; ++r) { tc.push_back(q); tr.push_back(r); tg.push_back(g); }
     }
     P.hlarft_n = (int)bc.size();
@@ -915,6 +916,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
         const int64_t n = cones[c].n;
         const int L = num_levels(n);
         if (l >= L) continue;
+        if (l == 0 && n >= 3) continue;  // 2 x 2 leaves (closed form) stand in for level 0
         const int64_t half = int64_t(1) << l, full = half << 1;
         for (int64_t s = 0; s < n; s += full) {
           MergeNode nd;
@@ -946,6 +948,7 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
         }
       }
       lv.nnodes = (int)mb.nodes.size() - lv.nodes_off;
+      if (lv.nnodes == 0) continue;
       lv.pos_off = (int)mb.ints.size();
       mb.ints.insert(mb.ints.end(), loc.begin(), loc.end());
       mb.ints.insert(mb.ints.end(), nid.begin(), nid.end());

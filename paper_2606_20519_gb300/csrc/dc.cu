@@ -69,15 +69,65 @@ __device__ __forceinline__ double* qout_buf(const ConeDev& c, int level) { retur
 __device__ __forceinline__ double* lin_buf(const ConeDev& c, int level) { return (level & 1) ? c.lamB : c.lamA; }
 __device__ __forceinline__ double* lout_buf(const ConeDev& c, int level) { return (level & 1) ? c.lamA : c.lamB; }
 
+// Leaves.  Sides n >= 3 tear only the off-diagonals e_m with m odd, so the
+// leaves are the 2 x 2 blocks [[d_2i - |e_2i-1|, e_2i], [e_2i, d_2i+1 -
+// |e_2i+1|]] (and a 1 x 1 block last for odd n), solved in closed form by one
+// Jacobi rotation (t the smaller root of t^2 + 2 theta t - 1 = 0,
+// theta = (c - a) / 2b: eigenvalues a - t b and c + t b, eigenvectors (cs,
+// -sn) and (sn, cs)); they stand in for level 0's merges and feed level 1.
+// Side 2 keeps the 1 x 1 leaves (its level-0 merge is the root).
 __global__ void dc_leaves_kernel(const ConeDev* __restrict__ cones) {
   const ConeDev& c = cones[blockIdx.y];
   const int64_t n = c.n;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double di = c.d[i];
-    if (i > 0) di -= fabs(c.e[i - 1]);
-    if (i + 1 < n) di -= fabs(c.e[i]);
-    c.lamA[i] = di;
-    c.QA[i + i * n] = 1.0;
+  if (n < 3) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      double di = c.d[i];
+      if (i > 0) di -= fabs(c.e[i - 1]);
+      if (i + 1 < n) di -= fabs(c.e[i]);
+      c.lamA[i] = di;
+      c.QA[i + i * n] = 1.0;
+    }
+    return;
+  }
+  double* Q = qin_buf(c, 1);
+  double* lam = lin_buf(c, 1);
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 2 * p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = 2 * p;
+    double a = c.d[i];
+    if (i > 0) a -= fabs(c.e[i - 1]);
+    if (i + 1 == n) {  // the last 1 x 1 leaf of an odd side
+      lam[i] = a;
+      Q[i + i * n] = 1.0;
+      continue;
+    }
+    double b = c.e[i];
+    double cc = c.d[i + 1];
+    if (i + 2 < n) cc -= fabs(c.e[i + 1]);
+    double l1, l2, cs, sn;
+    if (b == 0.0) {
+      l1 = a; l2 = cc; cs = 1.0; sn = 0.0;
+    } else {
+      const double theta = (cc - a) / (2.0 * b);
+      const double at = fabs(theta);
+      const double t = at > 1e150 ? copysign(0.5 / at, theta)
+                                  : copysign(1.0 / (at + sqrt(fma(theta, theta, 1.0))), theta);
+      cs = 1.0 / sqrt(fma(t, t, 1.0));
+      sn = t * cs;
+      l1 = a - t * b;
+      l2 = cc + t * b;
+    }
+    // columns (cs, -sn) for l1 and (sn, cs) for l2, in ascending order
+    double q00 = cs, q10 = -sn, q01 = sn, q11 = cs;
+    if (l1 > l2) {
+      const double tl = l1; l1 = l2; l2 = tl;
+      q00 = sn; q10 = cs; q01 = cs; q11 = -sn;
+    }
+    lam[i] = l1;
+    lam[i + 1] = l2;
+    Q[i + i * n] = q00;
+    Q[(i + 1) + i * n] = q10;
+    Q[i + (i + 1) * n] = q01;
+    Q[(i + 1) + (i + 1) * n] = q11;
   }
 }
 
@@ -427,13 +477,15 @@ __device__ bool secular_root_warp(const double* __restrict__ dk, const double* _
   // beyond its FP32 error bound; the FP64 loop below then polishes from the
   // narrowed bracket.  Only the differences d_j - d_org are formed in FP64.
   {
-    // d_j - d_org, formed in FP64 once per root (difd: this warp's K doubles)
-    // and rounded to FP32 (dif: K floats)
+    // d_j - d_org, formed in FP64 once per root (difd: this warp's 2K
+    // doubles, the differences then z_j^2) and rounded to FP32 (dif: K floats)
     if (dif)
       for (int j = lane; j < K; j += 32) {
         const double dd = dk[j] - dorg;
         difd[j] = dd;
         dif[j] = f64_to_f32_rn(dd);
+        const double zj = zk[j];
+        difd[K + j] = zj * zj;
       }
     __syncwarp();
     const float rho32 = f64_to_f32_rn(rho);
@@ -445,7 +497,7 @@ __device__ bool secular_root_warp(const double* __restrict__ dk, const double* _
       for (int j = lane; j < K; j += 32) {
         const float del = (dif ? dif[j] : f64_to_f32_rn(dk[j] - dorg)) - t32;
         const float zz = f64_to_f32_rn(zk[j]);
-        const float t = zz / del;
+        const float t = __fdividef(zz, del);  // within 2 ulp: inside the bound below
         const float term = zz * t;
         if (j < ri) { psi += term; dpsi = fmaf(t, t, dpsi); }
         else { phi += term; dphi = fmaf(t, t, dphi); }
@@ -462,15 +514,17 @@ __device__ bool secular_root_warp(const double* __restrict__ dk, const double* _
       if (!(fabsf(g) > bound) || !isfinite(dpsi + dphi)) break;
       if (g > 0.0f) hi = tau; else lo = tau;
       if (hi - lo <= 4.0 * kEps * fmax(fabs(lo), fabs(hi))) break;
+      // two-pole model psi(x) ~ a + sl / (p - x) matching psi and psi' at tau:
+      // sl = psi' dl^2, a = psi - sl / dl = psi - psi' dl
       const float dl = p32 - t32;
       const float sl = dpsi * dl * dl;
-      const float a = psi - sl / dl;
+      const float a = fmaf(-dpsi, dl, psi);
       float x = 0.0f;
       bool okx = false;
       if (ri < K) {
         const float dr = q32 - t32;
         const float sr = dphi * dr * dr;
-        const float bq = phi - sr / dr;
+        const float bq = fmaf(-dphi, dr, phi);
         const float C = 1.0f + a + bq;
         const float B2 = -(C * (p32 + q32) + sl + sr);
         const float C2 = C * p32 * q32 + sl * q32 + sr * p32;
@@ -502,11 +556,17 @@ __device__ bool secular_root_warp(const double* __restrict__ dk, const double* _
     double psi = 0.0, phi = 0.0, dpsi = 0.0, dphi = 0.0;
     for (int j = lane; j < K; j += 32) {
       const double del = (dif ? difd[j] : dk[j] - dorg) - tau;
-      const double zz = zk[j];
-      const double t = zz * rcp_nr(del);
-      const double term = zz * t;
-      if (j < ri) { psi += term; dpsi = fma(t, t, dpsi); }
-      else { phi += term; dphi = fma(t, t, dphi); }
+      const double r = rcp_nr(del);
+      double zz2;
+      if (dif) {
+        zz2 = difd[K + j];
+      } else {
+        const double zj = zk[j];
+        zz2 = zj * zj;
+      }
+      const double term = zz2 * r;  // z_j^2 / del; its derivative term z_j^2 / del^2 = term r
+      if (j < ri) { psi += term; dpsi = fma(term, r, dpsi); }
+      else { phi += term; dphi = fma(term, r, dphi); }
     }
     psi = warp_sum_d(psi);
     phi = warp_sum_d(phi);
@@ -524,13 +584,13 @@ __device__ bool secular_root_warp(const double* __restrict__ dk, const double* _
     if (hi - lo <= 4.0 * kEps * fmax(fabs(lo), fabs(hi))) { conv = true; break; }
     const double dl = p - tau;
     const double sl = dpsi * dl * dl;
-    const double a = psi - sl / dl;
+    const double a = fma(-dpsi, dl, psi);  // psi - sl / dl
     double x = 0.0;
     bool okx = false;
     if (ri < K) {
       const double dr = q - tau;
       const double sr = dphi * dr * dr;
-      const double bq = phi - sr / dr;
+      const double bq = fma(-dphi, dr, phi);  // phi - sr / dr
       const double C = 1.0 + a + bq;
       const double A2 = C;
       const double B2 = -(C * (p + q) + sl + sr);
@@ -598,11 +658,12 @@ __global__ void dc_secular_kernel(const ConeDev* __restrict__ cones, const Merge
   const int kk = c.icnt[4 * s];
   if (i >= kk) return;
   const int lane = threadIdx.x & 31;
-  // per warp: difmax doubles, then (after the four warps' doubles) difmax floats
+  // per warp: 2 difmax doubles (pole differences, z^2), then (after the four
+  // warps' doubles) difmax floats
   extern __shared__ double sec_difd[];
   const int wq = threadIdx.x >> 5;
-  double* difd = difmax >= kk ? sec_difd + wq * difmax : nullptr;
-  float* dif = difmax >= kk ? reinterpret_cast<float*>(sec_difd + 4 * difmax) + wq * difmax : nullptr;
+  double* difd = difmax >= kk ? sec_difd + 2 * wq * difmax : nullptr;
+  float* dif = difmax >= kk ? reinterpret_cast<float*>(sec_difd + 8 * difmax) + wq * difmax : nullptr;
   int org;
   double tau;
   const bool ok = secular_root_warp(c.dsrt + s, c.zk + s, kk, c.rho[s], i, lane, dif, difd, &org, &tau);
@@ -866,7 +927,7 @@ void launch_dc_secular(const ConeDev* cones, const MergeNode* nodes, const int* 
     cudaFuncSetAttribute(dc_secular_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSecSmemMax);
     attr = true;
   }
-  const size_t smem = (size_t)4 * maxK * (sizeof(double) + sizeof(float));
+  const size_t smem = (size_t)4 * maxK * (2 * sizeof(double) + sizeof(float));
   const int difmax = smem <= kSecSmemMax ? maxK : 0;
   dc_secular_kernel<<<(unsigned)((total * 32 + 127) / 128), 128, difmax ? smem : 0, s>>>(cones, nodes, pos_node,
                                                                                          total, difmax);

@@ -64,6 +64,31 @@ __device__ __forceinline__ dfl df_add2prod(dfl x, dfl y, dfl u, dfl z, dfl w) {
   const float lo = __fadd_rn(__fadd_rn(__fadd_rn(x.lo, e1), __fadd_rn(e2, s1.lo)), s2.lo);
   return df_fast_two_sum(s2.hi, lo);
 }
+// x + y1 u1 + y2 u2 + y3 u3 + y4 u4 with one renormalisation (the real or
+// imaginary part of a complex update a + v w + p q).
+__device__ __forceinline__ dfl df_add4prod(dfl x, dfl y1, dfl u1, dfl y2, dfl u2, dfl y3, dfl u3, dfl y4, dfl u4) {
+  const float p1 = __fmul_rn(y1.hi, u1.hi);
+  float e = __fmaf_rn(y1.hi, u1.hi, -p1);
+  e = __fmaf_rn(y1.hi, u1.lo, __fmaf_rn(y1.lo, u1.hi, e));
+  const float p2 = __fmul_rn(y2.hi, u2.hi);
+  e = __fadd_rn(e, __fmaf_rn(y2.hi, u2.hi, -p2));
+  e = __fmaf_rn(y2.hi, u2.lo, __fmaf_rn(y2.lo, u2.hi, e));
+  const float p3 = __fmul_rn(y3.hi, u3.hi);
+  e = __fadd_rn(e, __fmaf_rn(y3.hi, u3.hi, -p3));
+  e = __fmaf_rn(y3.hi, u3.lo, __fmaf_rn(y3.lo, u3.hi, e));
+  const float p4 = __fmul_rn(y4.hi, u4.hi);
+  e = __fadd_rn(e, __fmaf_rn(y4.hi, u4.hi, -p4));
+  e = __fmaf_rn(y4.hi, u4.lo, __fmaf_rn(y4.lo, u4.hi, e));
+  dfl s = df_two_sum(x.hi, p1);
+  float lo = __fadd_rn(x.lo, s.lo);
+  s = df_two_sum(s.hi, p2);
+  lo = __fadd_rn(lo, s.lo);
+  s = df_two_sum(s.hi, p3);
+  lo = __fadd_rn(lo, s.lo);
+  s = df_two_sum(s.hi, p4);
+  lo = __fadd_rn(__fadd_rn(lo, s.lo), e);
+  return df_fast_two_sum(s.hi, lo);
+}
 // Compensated dot product of double-float vectors (the scheme of Ogita, Rump
 // and Oishi's Dot2): the products' hi parts are summed with TwoSum into s,
 // every error term into the FP32 compensation c; df_dot_value renormalises.
@@ -206,6 +231,27 @@ __device__ __forceinline__ cdf c_cfma(cdf a, cdf b, cdf c) {
   return c_make(df_fma(a.re, b.re, df_fma(a.im, b.im, c.re)), df_fma(a.re, b.im, df_fma(df_neg(a.im), b.re, c.im)));
 }
 __device__ __forceinline__ cdf c_mul(cdf a, cdf b) { return c_fma(a, b, c_zero()); }
+// a + v w + p q with one renormalisation per part
+__device__ __forceinline__ cdf c_add2prod(cdf a, cdf v, cdf w, cdf p, cdf q) {
+  return c_make(df_add4prod(a.re, v.re, w.re, df_neg(v.im), w.im, p.re, q.re, df_neg(p.im), q.im),
+                df_add4prod(a.im, v.re, w.im, v.im, w.re, p.re, q.im, p.im, q.re));
+}
+// compensated accumulation of conj(a) x
+struct c_dot {
+  df_dot re, im;
+};
+__device__ __forceinline__ c_dot c_dot_zero() {
+  c_dot d;
+  d.re = df_dot_zero();
+  d.im = df_dot_zero();
+  return d;
+}
+__device__ __forceinline__ c_dot c_dot_add(c_dot d, cdf a, cdf x) {
+  d.re = df_dot_add(df_dot_add(d.re, a.re, x.re), a.im, x.im);
+  d.im = df_dot_add(df_dot_add(d.im, a.re, x.im), df_neg(a.im), x.re);
+  return d;
+}
+__device__ __forceinline__ cdf c_dot_value(c_dot d) { return c_make(df_dot_value(d.re), df_dot_value(d.im)); }
 __device__ __forceinline__ cdf c_shfl_xor(cdf v, int o) { return c_make(df_shfl_xor(v.re, o), df_shfl_xor(v.im, o)); }
 __device__ __forceinline__ cdf c_from_d(double re, double im) { return c_make(df_from_d(re), df_from_d(im)); }
 

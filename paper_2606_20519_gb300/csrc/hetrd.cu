@@ -169,9 +169,9 @@ __device__ void h_column_pass(cdf* __restrict__ cols, int n, int r0, const cdf* 
       nai = c_neg(c_conj(t2));
       ncvi = c_neg(c_conj(vi));
     }
-    cdf acc[U];
+    c_dot acc[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) acc[u] = c_zero();
+    for (int u = 0; u < U; ++u) acc[u] = c_dot_zero();
     for (int t0 = lane; t0 < L; t0 += 32 * U) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -179,18 +179,18 @@ __device__ void h_column_pass(cdf* __restrict__ cols, int n, int r0, const cdf* 
         if (t < L) {
           cdf a = col[t];
           if (UPDATE) {
-            a = c_fma(vu[t + 1], nai, c_fma(pu[t + 1], ncvi, a));
+            a = c_add2prod(a, vu[t + 1], nai, pu[t + 1], ncvi);
             col[t] = a;
           }
           if (pub_col) {
             hst_pub(Cn + 2 * t, a.re);
             hst_pub(Cn + 2 * t + 1, a.im);
           }
-          if (t > 0) acc[u] = c_cfma(a, x[t], acc[u]);
+          if (t > 0) acc[u] = c_dot_add(acc[u], a, x[t]);
         }
       }
     }
-    cdf sdot = c_add(acc[0], acc[1]);
+    cdf sdot = c_add(c_dot_value(acc[0]), c_dot_value(acc[1]));
     for (int o = 16; o > 0; o >>= 1) sdot = c_add(sdot, c_shfl_xor(sdot, o));
     if (lane == 0) {
       h_wait_tag(tag_p, tag, status);
