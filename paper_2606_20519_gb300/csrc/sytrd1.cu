@@ -310,11 +310,12 @@ __host__ __device__ inline int sytrd1_pcap(int n, int G) {
   const int items = ((n + G - 1) / G) * ((n + 63) / 64);  // up to 64-row items
   return items < kPartMax ? items : kPartMax;
 }
-// Resident route (double-float): two v buffers, p, the updated column (4n)
-// and the CTA's own columns; otherwise v, p, column and the partial sums.
+// Double-float routes: two v buffers, p and the updated column (4n pairs),
+// and with res the CTA's own columns (ceil(n / G) of n rows); the columns
+// otherwise stay in global memory.
 __host__ __device__ inline size_t sytrd1_bytes(int n, int G, bool res) {
   if (res) return ((size_t)4 * n + (size_t)((n + G - 1) / G) * n) * sizeof(double);
-  return ((size_t)3 * n + sytrd1_pcap(n, G)) * sizeof(double);
+  return (size_t)4 * n * sizeof(double);
 }
 
 // ---------------------------------------------------------------- double-float path
@@ -423,12 +424,13 @@ __device__ __forceinline__ void wait_coef(const int* coef_tag, int tag, int* sta
 // set the reflector's scalars (coef, announced by *coef_tag = tag).  No CTA
 // barrier: columns go to warps 1, 2, .., 7, 0 (warp 0's thread 0 forms the
 // scalars first).  The owner of column r0 publishes its rows to Cn.
-template <bool UPDATE>
+template <bool UPDATE, bool GLB>
 __device__ void column_pass_dfw(dfl* __restrict__ cols, int n, int r0, const dfl* __restrict__ x, const dfl* coef,
                                 const int* coef_tag, int tag, const dfl* __restrict__ vu,
                                 const dfl* __restrict__ pu, dfl K2, dfl* Pn, dfl* Cn, int rank, int G,
                                 int* status) {
-  constexpr int U = 4;
+  // columns in L2 (GLB): more rows in flight per lane
+  constexpr int U = GLB ? 8 : 4;
   constexpr int NW = kSyThreads / 32;
   const int L = n - r0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -436,7 +438,7 @@ __device__ void column_pass_dfw(dfl* __restrict__ cols, int n, int r0, const dfl
   const int ncol = first < n ? (n - 1 - first) / G + 1 : 0;
   for (int k = (warp + NW - 1) % NW; k < ncol; k += NW) {
     const int i = first + G * k;
-    dfl* col = cols + (int64_t)((i - rank) / G) * n + r0;
+    dfl* col = cols + (int64_t)(GLB ? i : (i - rank) / G) * n + r0;
     const bool pub_col = i == r0;
     dfl nai = df_zero(), nvi = df_zero();
     if (UPDATE) {
@@ -462,8 +464,9 @@ __device__ void column_pass_dfw(dfl* __restrict__ cols, int n, int r0, const dfl
         }
       }
     }
-    dfl sdot = df_add(df_add(df_dot_value(acc[0]), df_dot_value(acc[1])),
-                      df_add(df_dot_value(acc[2]), df_dot_value(acc[3])));
+    dfl sdot = df_dot_value(acc[0]);
+#pragma unroll
+    for (int u = 1; u < U; ++u) sdot = df_add(sdot, df_dot_value(acc[u]));
     for (int o = 16; o > 0; o >>= 1) sdot = df_add(sdot, df_shfl_xor(sdot, o));
     if (lane == 0) {
       // thread 0 of this CTA forms the scalars while the columns are updated
@@ -521,8 +524,13 @@ __device__ bool poll_step_df(const dfl* P, const dfl* C, int m, const dfl* v, df
   return __syncthreads_and(ok) != 0;
 }
 
-// The shared-memory-resident route in double-float arithmetic (structure as
-// sytrd1_body).  sh64: FP64 scalars of thread 0; shd: their double-float copies.
+// The double-float route (structure as sytrd1_body).  The CTA's own columns
+// live in shared memory (GLB false: column i at slot (i - rank) / G), or, when
+// they do not fit, in place of the FP64 matrix in global memory (GLB: column
+// i where it was, as FP32 pairs of the same 8 bytes; only the owner touches
+// it, so it stays in L2).  sh64: FP64 scalars of thread 0; shd: their
+// double-float copies.
+template <bool GLB>
 __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait_limit, double* sy_smem,
                                dfl* red, double* sh64, dfl* shd, int* coef_tag) {
   const int n = (int)c.n;
@@ -532,8 +540,9 @@ __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait
   dfl* vn = base + n;
   dfl* ps = base + 2 * n;
   dfl* bs = base + 3 * n;
-  dfl* cols = base + 4 * n;
-  double* colsd = sy_smem + 4 * n;  // the same storage, first loaded as FP64
+  dfl* cols = GLB ? reinterpret_cast<dfl*>(A) : base + 4 * n;
+  double* colsd = GLB ? A : sy_smem + 4 * n;  // the same storage, first holding FP64
+  auto slot = [&](int i) -> int64_t { return GLB ? i : (i - rank) / G; };
   dfl* pub = reinterpret_cast<dfl*>(c.QA);
   const int tid = threadIdx.x;
   int parity = 0;
@@ -541,12 +550,20 @@ __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait
   int emax = 0;
   for (int i = rank; i < n; i += G) {
     const double* src = A + (int64_t)i * n;
-    double* dst = colsd + (int64_t)((i - rank) / G) * n;
+    double* dst = colsd + slot(i) * n;
     for (int r = tid; r < n; r += kSyThreads) {
       const double v = __ldcg(src + r);
-      dst[r] = v;
+      if (!GLB) dst[r] = v;
       emax = max(emax, (int)((__double2hiint(v) >> 20) & 0x7FF));
     }
+  }
+  // GLB: column 0 and A(0, 0) are read before any owner rewrites its columns
+  // in place (vc holds column 0's rows 1 .. n-1 as FP64 until the prologue)
+  double a00 = 0.0;
+  if (GLB && n >= 3) {
+    double* v64 = reinterpret_cast<double*>(vc);
+    for (int t = tid; t < n - 1; t += kSyThreads) v64[t] = __ldcg(A + 1 + t);
+    a00 = __ldcg(A);
   }
   if (n < 3) {
     __syncthreads();
@@ -574,14 +591,15 @@ __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait
   const double s_in = __longlong_as_double((long long)(2046 - eb) << 52);
   const double s_out = __longlong_as_double((long long)eb << 52);
   for (int i = rank; i < n; i += G) {
-    dfl* dst = cols + (int64_t)((i - rank) / G) * n;
-    const double* srcd = colsd + (int64_t)((i - rank) / G) * n;
+    dfl* dst = cols + slot(i) * n;
+    const double* srcd = colsd + slot(i) * n;
     for (int r = tid; r < n; r += kSyThreads) dst[r] = df_from_d(srcd[r] * s_in);
   }
   // ---- prologue: reflector 0 from column 0 (every CTA), p_0 and column 1 into slab 0
   dfl ss = df_zero();
   for (int t = tid; t < n - 1; t += kSyThreads) {
-    const dfl v = df_from_d(__ldcg(A + 1 + t) * s_in);
+    const double a = GLB ? reinterpret_cast<const double*>(vc)[t] : __ldcg(A + 1 + t);
+    const dfl v = df_from_d(a * s_in);
     vc[t] = v;
     if (t >= 1) ss = df_fma(v, v, ss);
   }
@@ -600,7 +618,7 @@ __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait
     __syncthreads();
     if (tid == 0) vc[0] = df_make(1.0f, 0.0f);
     if (rank == 0 && tid == 0) {
-      c.d[0] = __ldcg(A);
+      c.d[0] = GLB ? a00 : __ldcg(A);
       c.e[0] = sh64[0] * s_out;
       c.tau1[0] = sh64[1];
     }
@@ -611,8 +629,8 @@ __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait
     }
     __syncthreads();
   }
-  column_pass_dfw<false>(cols, n, 1, vc, shd, coef_tag, -1, nullptr, nullptr, df_zero(), slab(pub, n, 0),
-                         slab(pub, n, 0) + (n - 1), rank, G, c.status);
+  column_pass_dfw<false, GLB>(cols, n, 1, vc, shd, coef_tag, -1, nullptr, nullptr, df_zero(), slab(pub, n, 0),
+                              slab(pub, n, 0) + (n - 1), rank, G, c.status);
   dfl tau = shd[0];
   __syncthreads();
   for (int j = 0; j + 2 < n; ++j) {
@@ -645,8 +663,8 @@ __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait
         *(volatile int*)coef_tag = j;
       }
       dfl* Pn = slab(pub, n, j + 1);
-      column_pass_dfw<true>(cols, n, j + 2, bs + 1, shd, coef_tag, j, vc, ps, K2, Pn, Pn + (m - 1), rank, G,
-                            c.status);
+      column_pass_dfw<true, GLB>(cols, n, j + 2, bs + 1, shd, coef_tag, j, vc, ps, K2, Pn, Pn + (m - 1), rank,
+                                 G, c.status);
       // every thread reads the scalars after thread 0 announced them
       wait_coef(coef_tag, j, c.status);
       const dfl tau1 = shd[0], scal1 = shd[1];
@@ -672,7 +690,7 @@ __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait
         c.e[n - 1] = 0.0;
       }
       if (rank == (n - 1) % G && tid == 0) {
-        const dfl a = cols[(int64_t)((n - 1 - rank) / G) * n + (n - 1)];
+        const dfl a = cols[slot(n - 1) * n + (n - 1)];
         const dfl w1 = df_fma(df_neg(K), vc[1], ps[1]);
         const dfl two_vw = df_mul(df_make(2.0f * vc[1].hi, 2.0f * vc[1].lo), w1);
         c.d[n - 1] = df_to_d(df_add(a, df_neg(two_vw))) * s_out;
@@ -823,11 +841,15 @@ __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __res
   // in shared memory and double-float arithmetic, or columns in L2 and FP64
   __shared__ int coef_tag;
   const bool res = sytrd1_bytes((int)c.n, G, true) <= (size_t)smem_bytes;
-  // the format of the reflector blocks V1 and their T factors: double-float
-  // pairs (shared-memory route) or FP64
-  if (rank == 0 && threadIdx.x == 0) c.kinfo[7] = res ? 1 : 0;
-  if (res)
-    sytrd1_body_df(c, rank, G, wait_limit, sy_smem, reinterpret_cast<dfl*>(red), sh, reinterpret_cast<dfl*>(sh + 2),
+  const bool glb = !res && sytrd1_bytes((int)c.n, G, false) <= (size_t)smem_bytes;
+  // the format of the reflector blocks V1: double-float pairs (both
+  // double-float routes) or FP64
+  if (rank == 0 && threadIdx.x == 0) c.kinfo[7] = (res || glb) ? 1 : 0;
+  if (glb)
+    sytrd1_body_df<true>(c, rank, G, wait_limit, sy_smem, reinterpret_cast<dfl*>(red), sh, reinterpret_cast<dfl*>(sh + 2),
+                         &coef_tag);
+  else if (res)
+    sytrd1_body_df<false>(c, rank, G, wait_limit, sy_smem, reinterpret_cast<dfl*>(red), sh, reinterpret_cast<dfl*>(sh + 2),
                    &coef_tag);
   else
     sytrd1_body<false>(c, rank, G, wait_limit, sy_smem, red, sh);
