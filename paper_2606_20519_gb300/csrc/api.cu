@@ -60,6 +60,7 @@ struct BulgeLaunch {
 struct Sytrd1Launch {
   int nctas = 0, maxn = 0;
   size_t smem = 0;
+  int glb = 0;  // columns in L2 computed in double-float (else FP64)
   int cone_off = 0, rank_off = 0, count_off = 0;
 };
 
@@ -806,6 +807,25 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
               r = std::max(1, std::min(r, std::max(1, cap / sms_all)));
               give = spread_give(std::max((int)grp.size(), r * sms_all));
             }
+            if (sl.smem == 0) {
+              // columns in L2: double-float arithmetic when the launch's matrices
+              // stay in L2 (8 cones of side 1296, 107 MB: 45 ms against 58 ms in
+              // FP64); beyond that the FP64 route, whose instruction stream keeps
+              // more of the stream from HBM in flight (4 cones of side 4096: 0.71 s
+              // against 1.43 s)
+              double bytes = 0.0;
+              int mx = 0, tot = 0;
+              for (size_t q = 0; q < grp.size(); ++q) {
+                bytes += 8.0 * (double)cones[grp[q]].n * (double)cones[grp[q]].n;
+                mx = std::max<int>(mx, (int)cones[grp[q]].n);
+                tot += give[q];
+              }
+              const size_t gb = sytrd1_glb_smem_bytes(mx);
+              if (bytes <= 112.0 * 1024 * 1024 && gb <= 200 * 1024 && sytrd1_max_ctas_for(gb) >= tot) {
+                sl.glb = 1;
+                sl.smem = gb;
+              }
+            }
           }
           std::vector<int> cc, rr, gg;
           for (size_t q = 0; q < grp.size(); ++q)
@@ -1303,7 +1323,7 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
           pm.begin(1);
           for (const Sytrd1Launch& sl : P.sytrd1) {
             if (launch_sytrd1(P.cones_d, P.ints_d + sl.cone_off, P.ints_d + sl.rank_off, P.ints_d + sl.count_off,
-                              sl.nctas, sl.maxn, sl.smem, wait_limit, s))
+                              sl.nctas, sl.maxn, sl.smem, sl.glb, wait_limit, s))
               return SCS_PSD_ECUDA;
             LAUNCH_CHECK();
           }

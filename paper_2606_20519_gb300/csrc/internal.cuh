@@ -259,8 +259,10 @@ int sytrd1_max_ctas(int maxn);
 int sytrd1_max_ctas_for(size_t smem_bytes);
 // dynamic shared memory of one CTA for side n in a group of G (resident: its columns in shared memory)
 size_t sytrd1_smem_bytes(int n, int G, bool resident);
+// the double-float route with the columns in global memory (glb launches)
+size_t sytrd1_glb_smem_bytes(int n);
 int launch_sytrd1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,
-                  int maxn, size_t smem_bytes, long long wait_limit, cudaStream_t s);
+                  int maxn, size_t smem_bytes, int glb, long long wait_limit, cudaStream_t s);
 void launch_larft1(const ConeDev* cones, const int* blk_cone, const int* blk_index, int nblocks, cudaStream_t s);
 // Z <- Q1 Z for the stage-1 blocks in one launch (CTA tables as launch_sytrd1); cones of side <= bt1_max_side()
 void launch_bt1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,

@@ -310,13 +310,15 @@ __host__ __device__ inline int sytrd1_pcap(int n, int G) {
   const int items = ((n + G - 1) / G) * ((n + 63) / 64);  // up to 64-row items
   return items < kPartMax ? items : kPartMax;
 }
-// Double-float routes: two v buffers, p and the updated column (4n pairs),
-// and with res the CTA's own columns (ceil(n / G) of n rows); the columns
-// otherwise stay in global memory.
+// Shared memory of a CTA.  Resident route (double-float): two v buffers, p,
+// the updated column (4n pairs) and the CTA's own columns; otherwise (FP64,
+// columns in L2) v, p, column and the partial sums.
 __host__ __device__ inline size_t sytrd1_bytes(int n, int G, bool res) {
   if (res) return ((size_t)4 * n + (size_t)((n + G - 1) / G) * n) * sizeof(double);
-  return (size_t)4 * n * sizeof(double);
+  return ((size_t)3 * n + sytrd1_pcap(n, G)) * sizeof(double);
 }
+// Double-float route with the columns in global memory: the 4n pairs only.
+__host__ __device__ inline size_t sytrd1_glb_bytes(int n) { return (size_t)4 * n * sizeof(double); }
 
 // ---------------------------------------------------------------- double-float path
 // The shared-memory-resident route (every CTA's columns in shared memory)
@@ -830,7 +832,7 @@ __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __res
                                                             const int* __restrict__ cta_cone,
                                                             const int* __restrict__ cta_rank,
                                                             const int* __restrict__ cta_count,
-                                                            long long wait_limit, int smem_bytes) {
+                                                            long long wait_limit, int smem_bytes, int glb_ok) {
   extern __shared__ double sy_smem[];
   __shared__ double red[2 * (kSyThreads / 32)];
   __shared__ double sh[4];
@@ -841,7 +843,7 @@ __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __res
   // in shared memory and double-float arithmetic, or columns in L2 and FP64
   __shared__ int coef_tag;
   const bool res = sytrd1_bytes((int)c.n, G, true) <= (size_t)smem_bytes;
-  const bool glb = !res && sytrd1_bytes((int)c.n, G, false) <= (size_t)smem_bytes;
+  const bool glb = !res && glb_ok && sytrd1_glb_bytes((int)c.n) <= (size_t)smem_bytes;
   // the format of the reflector blocks V1: double-float pairs (both
   // double-float routes) or FP64
   if (rank == 0 && threadIdx.x == 0) c.kinfo[7] = (res || glb) ? 1 : 0;
@@ -956,10 +958,13 @@ int sytrd1_max_ctas_for(size_t smem) {
 
 int sytrd1_max_ctas(int maxn) { return sytrd1_max_ctas_for(sytrd1_bytes(maxn, 1, false)); }
 
+size_t sytrd1_glb_smem_bytes(int n) { return sytrd1_glb_bytes(n); }
+
 int launch_sytrd1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,
-                  int maxn, size_t smem, long long wait_limit, cudaStream_t s) {
+                  int maxn, size_t smem, int glb, long long wait_limit, cudaStream_t s) {
   if (nctas <= 0) return 0;
   if (smem < sytrd1_bytes(maxn, 1, false)) smem = sytrd1_bytes(maxn, 1, false);
+  if (glb && smem < sytrd1_glb_bytes(maxn)) smem = sytrd1_glb_bytes(maxn);
   // co-resident CTAs (they wait on one another); the attribute also survives graph recording
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nctas);
@@ -971,7 +976,8 @@ int launch_sytrd1(const ConeDev* cones, const int* cta_cone, const int* cta_rank
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return (int)cudaLaunchKernelEx(&cfg, sytrd1_kernel, cones, cta_cone, cta_rank, cta_count, wait_limit, (int)smem);
+  return (int)cudaLaunchKernelEx(&cfg, sytrd1_kernel, cones, cta_cone, cta_rank, cta_count, wait_limit, (int)smem,
+                                glb);
 }
 
 void launch_larft1(const ConeDev* cones, const int* blk_cone, const int* blk_index, int nblocks, cudaStream_t s) {
