@@ -234,7 +234,7 @@ class ClockSampler:
 # ---------------------------------------------------------------- helpers
 def phase_kernels(phase: str, n: int, band: int) -> str:
     """The kernel(s) a traced phase consists of, for the path a side-n cone takes."""
-    one_stage = band == 1 or (band == 0 and n <= 2048)
+    one_stage = band == 1 or (band == 0 and n <= 6144)  # the library's automatic route
     return {
         "unpack": "unpack_kernel",
         "dense_to_band": "sytrd1_kernel" if one_stage else "panel_kernel + grouped GEMMs",
@@ -699,9 +699,14 @@ def eig_roofline(args, wl, phases, tuning, b_used, steps):
     k = min(kp, kn)
     kbt = n0 if wl.vjp else k
     cones_per_call = len(wl.calls[0][1])
-    # a Hermitian cone is projected as its real embedding of side 2n (every eigenvalue twice)
-    emb = 2 if wl.herm else 1
-    flops_launch = sum(algorithmic_flops(dom_name, emb * int(s), emb * k, b_used, emb * kbt) for s in wl.calls[0][1])
+    # Hermitian cones: the native complex route (sides up to 1100, automatic route) does
+    # four real flops' work per complex operation in every phase but the real divide and
+    # conquer; the real embedding of side 2n (every eigenvalue twice) otherwise
+    native = wl.herm and args.band == 0 and max(int(s) for s in wl.calls[0][1]) <= 1100
+    emb = 2 if (wl.herm and not native) else 1
+    cplx = 4.0 if (native and dom_name != "tridiag_dc") else 1.0
+    flops_launch = sum(cplx * algorithmic_flops(dom_name, emb * int(s), emb * k, b_used, emb * kbt)
+                       for s in wl.calls[0][1])
     # per call: a phase may be traced as several segments within one call
     per_call = wl.iters if wl.scs is not None else 1  # projections per call (SCS: one per iteration)
     avg_ms = dom_ms / max(1, steps * len(wl.calls) * per_call)

@@ -33,6 +33,7 @@
 //
 // larft1_kernel then forms, for every 32-reflector block, the triangular
 // factor T of H_0 ... H_31 = I - V T V^T.
+#include <limits.h>
 #include <math.h>
 
 #include "dfloat.cuh"
@@ -426,11 +427,14 @@ __device__ __forceinline__ void wait_coef(const int* coef_tag, int tag, int* sta
 // set the reflector's scalars (coef, announced by *coef_tag = tag).  No CTA
 // barrier: columns go to warps 1, 2, .., 7, 0 (warp 0's thread 0 forms the
 // scalars first).  The owner of column r0 publishes its rows to Cn.
+// With at most NW / 2 columns, two warps share each column (interleaved
+// chunks of rows): the second hands its part of the dot product to the
+// first through half_part[k], announced by half_tag[k] = tag.
 template <bool UPDATE, bool GLB>
 __device__ void column_pass_dfw(dfl* __restrict__ cols, int n, int r0, const dfl* __restrict__ x, const dfl* coef,
                                 const int* coef_tag, int tag, const dfl* __restrict__ vu,
                                 const dfl* __restrict__ pu, dfl K2, dfl* Pn, dfl* Cn, int rank, int G,
-                                int* status) {
+                                int* status, int* half_tag, dfl* half_part) {
   // columns in L2 (GLB): more rows in flight per lane
   constexpr int U = GLB ? 8 : 4;
   constexpr int NW = kSyThreads / 32;
@@ -438,7 +442,11 @@ __device__ void column_pass_dfw(dfl* __restrict__ cols, int n, int r0, const dfl
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int first = r0 + ((rank - r0 % G) + G) % G;
   const int ncol = first < n ? (n - 1 - first) / G + 1 : 0;
-  for (int k = (warp + NW - 1) % NW; k < ncol; k += NW) {
+  const int vw = (warp + NW - 1) % NW;  // warp 0 (whose thread 0 forms the scalars) last
+  const bool split = 2 * ncol <= NW;
+  const int half = split ? (vw & 1) : 0;
+  const int tstride = (split ? 2 : 1) * 32 * U;
+  for (int k = split ? vw / 2 : vw; k < ncol; k += split ? NW / 2 : NW) {
     const int i = first + G * k;
     dfl* col = cols + (int64_t)(GLB ? i : (i - rank) / G) * n + r0;
     const bool pub_col = i == r0;
@@ -451,7 +459,7 @@ __device__ void column_pass_dfw(dfl* __restrict__ cols, int n, int r0, const dfl
     df_dot acc[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) acc[u] = df_dot_zero();
-    for (int t0 = lane; t0 < L; t0 += 32 * U) {
+    for (int t0 = lane + half * 32 * U; t0 < L; t0 += tstride) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int t = t0 + 32 * u;
@@ -470,7 +478,19 @@ __device__ void column_pass_dfw(dfl* __restrict__ cols, int n, int r0, const dfl
 #pragma unroll
     for (int u = 1; u < U; ++u) sdot = df_add(sdot, df_dot_value(acc[u]));
     for (int o = 16; o > 0; o >>= 1) sdot = df_add(sdot, df_shfl_xor(sdot, o));
+    if (split && half == 1) {
+      if (lane == 0) {
+        half_part[k] = sdot;
+        __threadfence_block();
+        *(volatile int*)(half_tag + k) = tag;
+      }
+      continue;  // the first warp of the pair publishes
+    }
     if (lane == 0) {
+      if (split) {
+        wait_coef(half_tag + k, tag, status);
+        sdot = df_add(sdot, half_part[k]);
+      }
       // thread 0 of this CTA forms the scalars while the columns are updated
       wait_coef(coef_tag, tag, status);
       const dfl tau = coef[0], scal = coef[1];
@@ -534,7 +554,7 @@ __device__ bool poll_step_df(const dfl* P, const dfl* C, int m, const dfl* v, df
 // double-float copies.
 template <bool GLB>
 __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait_limit, double* sy_smem,
-                               dfl* red, double* sh64, dfl* shd, int* coef_tag) {
+                               dfl* red, double* sh64, dfl* shd, int* coef_tag, int* half_tag, dfl* half_part) {
   const int n = (int)c.n;
   double* A = c.A;
   dfl* base = reinterpret_cast<dfl*>(sy_smem);
@@ -632,7 +652,7 @@ __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait
     __syncthreads();
   }
   column_pass_dfw<false, GLB>(cols, n, 1, vc, shd, coef_tag, -1, nullptr, nullptr, df_zero(), slab(pub, n, 0),
-                              slab(pub, n, 0) + (n - 1), rank, G, c.status);
+                              slab(pub, n, 0) + (n - 1), rank, G, c.status, half_tag, half_part);
   dfl tau = shd[0];
   __syncthreads();
   for (int j = 0; j + 2 < n; ++j) {
@@ -666,7 +686,7 @@ __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait
       }
       dfl* Pn = slab(pub, n, j + 1);
       column_pass_dfw<true, GLB>(cols, n, j + 2, bs + 1, shd, coef_tag, j, vc, ps, K2, Pn, Pn + (m - 1), rank,
-                                 G, c.status);
+                                 G, c.status, half_tag, half_part);
       // every thread reads the scalars after thread 0 announced them
       wait_coef(coef_tag, j, c.status);
       const dfl tau1 = shd[0], scal1 = shd[1];
@@ -842,17 +862,21 @@ __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __res
   // every CTA of a cone takes the same decision (same n, G, launch): columns
   // in shared memory and double-float arithmetic, or columns in L2 and FP64
   __shared__ int coef_tag;
+  __shared__ int half_tag[kSyThreads / 64];
+  __shared__ dfl half_part[kSyThreads / 64];
+  // no pass has announced a part yet (the first CTA barrier of the body orders this)
+  if (threadIdx.x < kSyThreads / 64) half_tag[threadIdx.x] = INT_MIN;
   const bool res = sytrd1_bytes((int)c.n, G, true) <= (size_t)smem_bytes;
   const bool glb = !res && glb_ok && sytrd1_glb_bytes((int)c.n) <= (size_t)smem_bytes;
   // the format of the reflector blocks V1: double-float pairs (both
   // double-float routes) or FP64
   if (rank == 0 && threadIdx.x == 0) c.kinfo[7] = (res || glb) ? 1 : 0;
   if (glb)
-    sytrd1_body_df<true>(c, rank, G, wait_limit, sy_smem, reinterpret_cast<dfl*>(red), sh, reinterpret_cast<dfl*>(sh + 2),
-                         &coef_tag);
+    sytrd1_body_df<true>(c, rank, G, wait_limit, sy_smem, reinterpret_cast<dfl*>(red), sh,
+                         reinterpret_cast<dfl*>(sh + 2), &coef_tag, half_tag, half_part);
   else if (res)
-    sytrd1_body_df<false>(c, rank, G, wait_limit, sy_smem, reinterpret_cast<dfl*>(red), sh, reinterpret_cast<dfl*>(sh + 2),
-                   &coef_tag);
+    sytrd1_body_df<false>(c, rank, G, wait_limit, sy_smem, reinterpret_cast<dfl*>(red), sh,
+                          reinterpret_cast<dfl*>(sh + 2), &coef_tag, half_tag, half_part);
   else
     sytrd1_body<false>(c, rank, G, wait_limit, sy_smem, red, sh);
 }

@@ -15,7 +15,9 @@ FP64 oracle, for the paths the measured configurations run:
   process blocks by the optimality conditions of the projection;
 * the two-stage route (dense -> band -> tridiagonal, band 16) at n = 1100,
   where the panel factorisation runs on a multi-CTA cluster and the band
-  reduction on several sweeps at once.
+  reduction on several sweeps at once;
+* the one-stage reduction in double-float with the columns in global memory
+  (sides 1700 and 1300), against the constructions.
 
 The oracle (cyclic Jacobi) takes seconds to tens of seconds per cone at
 these sizes on the host cores; each reference is computed once per module."""
@@ -149,3 +151,23 @@ def test_two_stage_multi_panel_1100(lib):
     assert rel(y, oracle.proj(x)) <= TOL
     assert rel(y, W.to_svec((Q * np.maximum(lam, 0)) @ Q.T)) <= TOL
     assert lib.last_tuning(0)["band"] == 16
+
+
+@pytest.mark.parametrize("sides", [[1700], [1700, 1300]])
+def test_double_float_columns_in_l2(lib, sides):
+    """Sides whose columns no longer fit in shared memory (one cone of 1700,
+    and two cones sharing the SMs) run the one-stage reduction in
+    double-float arithmetic with the columns kept in global memory; against
+    the exact projection of the constructions, at 1e-10."""
+    rng = W.rng_for(2200 + len(sides))
+    xs, refs = [], []
+    for n in sides:
+        X, Q, lam = W.from_spectrum(rng, W.spectrum_admm(rng, n))
+        xs.append(W.to_svec(X))
+        refs.append(W.to_svec((Q * np.maximum(lam, 0)) @ Q.T))
+    y = lib.proj_batched(dev(np.concatenate(xs)), sides).cpu().numpy()
+    assert lib.status(0) == lib.OK
+    o = 0
+    for x, ref in zip(xs, refs):
+        assert rel(y[o:o + x.size], ref) <= TOL
+        o += x.size
