@@ -27,6 +27,7 @@
 // the next column becomes (a_t - p_t) - v_t (conj(p_0) - 2K); and with the
 // next reflector u = scal x (u_0 = 1), p_i = tau (conj(a_0) + scal sum_{t>=1}
 // conj(a_t) x_t) since A(i, r) = conj(A(r, i)).
+#include <limits.h>
 #include <math.h>
 
 #include "dfloat.cuh"
@@ -146,17 +147,25 @@ __device__ __forceinline__ void h_wait_tag(const int* tag_p, int tag, int* statu
 // conj dot product with x, p_i = tau (conj(a_0) + scal dot) published to Pn
 // (re, im) once the scalars are announced; the owner of column r0 publishes
 // its rows to Cn.
+// With at most NW / 2 columns, two warps share each column (interleaved
+// chunks of rows); the second hands its part of the dot product to the first
+// through half_part[k], announced by half_tag[k] = tag.
 template <bool UPDATE>
 __device__ void h_column_pass(cdf* __restrict__ cols, int n, int r0, const cdf* __restrict__ x, const cdf* coef,
                               const int* tag_p, int tag, const cdf* __restrict__ vu, const cdf* __restrict__ pu,
-                              dfl K2, dfl* Pn, dfl* Cn, int rank, int G, int* status) {
+                              dfl K2, dfl* Pn, dfl* Cn, int rank, int G, int* status, int* half_tag,
+                              cdf* half_part) {
   constexpr int U = 2;
   constexpr int NW = kHThreads / 32;
   const int L = n - r0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int first = r0 + ((rank - r0 % G) + G) % G;
   const int ncol = first < n ? (n - 1 - first) / G + 1 : 0;
-  for (int k = (warp + NW - 1) % NW; k < ncol; k += NW) {
+  const int vw = (warp + NW - 1) % NW;  // warp 0 (whose thread 0 forms the scalars) last
+  const bool split = 2 * ncol <= NW;
+  const int half = split ? (vw & 1) : 0;
+  const int tstride = (split ? 2 : 1) * 32 * U;
+  for (int k = split ? vw / 2 : vw; k < ncol; k += split ? NW / 2 : NW) {
     const int i = first + G * k;
     cdf* col = cols + (int64_t)((i - rank) / G) * n + r0;
     const bool pub_col = i == r0;
@@ -172,7 +181,7 @@ __device__ void h_column_pass(cdf* __restrict__ cols, int n, int r0, const cdf* 
     c_dot acc[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) acc[u] = c_dot_zero();
-    for (int t0 = lane; t0 < L; t0 += 32 * U) {
+    for (int t0 = lane + half * 32 * U; t0 < L; t0 += tstride) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int t = t0 + 32 * u;
@@ -192,7 +201,19 @@ __device__ void h_column_pass(cdf* __restrict__ cols, int n, int r0, const cdf* 
     }
     cdf sdot = c_add(c_dot_value(acc[0]), c_dot_value(acc[1]));
     for (int o = 16; o > 0; o >>= 1) sdot = c_add(sdot, c_shfl_xor(sdot, o));
+    if (split && half == 1) {
+      if (lane == 0) {
+        half_part[k] = sdot;
+        __threadfence_block();
+        *(volatile int*)(half_tag + k) = tag;
+      }
+      continue;  // the first warp of the pair publishes
+    }
     if (lane == 0) {
+      if (split) {
+        h_wait_tag(half_tag + k, tag, status);
+        sdot = c_add(sdot, half_part[k]);
+      }
       h_wait_tag(tag_p, tag, status);
       const cdf tau = coef[0], scal = coef[1];
       const cdf pv = c_mul(tau, c_fma(scal, sdot, c_conj(col[0])));
@@ -264,7 +285,8 @@ __device__ bool h_poll(const dfl* P, const dfl* C, int m, const cdf* v, cdf* ps,
 }
 
 __device__ void hetrd1_body(const HConeDev& c, const double* __restrict__ xs, int rank, int G, long long wait_limit,
-                            double* smem, dfl* red, cdf* redc, cdf* shc, dfl* shb, int* tag_p) {
+                            double* smem, dfl* red, cdf* redc, cdf* shc, dfl* shb, int* tag_p, int* half_tag,
+                            cdf* half_part) {
   const int n = (int)c.n;
   cdf* base = reinterpret_cast<cdf*>(smem);
   cdf* vc = base;
@@ -354,7 +376,7 @@ __device__ void hetrd1_body(const HConeDev& c, const double* __restrict__ xs, in
     __syncthreads();
   }
   h_column_pass<false>(cols, n, 1, vc, shc, tag_p, -1, nullptr, nullptr, df_zero(), pub + hslab(n, 0),
-                       pub + hslab(n, 0) + 2 * (n - 1), rank, G, c.status);
+                       pub + hslab(n, 0) + 2 * (n - 1), rank, G, c.status, half_tag, half_part);
   cdf tau = shc[0];
   __syncthreads();
   for (int j = 0; j + 1 < n; ++j) {
@@ -389,7 +411,7 @@ __device__ void hetrd1_body(const HConeDev& c, const double* __restrict__ xs, in
       }
       dfl* Pn = pub + hslab(n, j + 1);
       h_column_pass<true>(cols, n, j + 2, bs + 1, shc, tag_p, j, vc, ps, K2, Pn, Pn + 2 * (m - 1), rank, G,
-                          c.status);
+                          c.status, half_tag, half_part);
       h_wait_tag(tag_p, j, c.status);
       const cdf tau1 = shc[0], scal1 = shc[1];
       if (rank == 0 && tid == 0) {
@@ -425,9 +447,14 @@ __global__ void __launch_bounds__(kHThreads) hetrd1_kernel(const HConeDev* __res
   __shared__ cdf shc[2];
   __shared__ dfl shb[1];
   __shared__ int tag;
+  __shared__ int half_tag[kHThreads / 64];
+  __shared__ cdf half_part[kHThreads / 64];
   const HConeDev& c = cones[cta_cone[blockIdx.x]];
   if (*c.status != 0) return;
-  hetrd1_body(c, io->x, cta_rank[blockIdx.x], cta_count[blockIdx.x], wait_limit, h_smem, red, redc, shc, shb, &tag);
+  // no pass has announced a part yet (the body's first CTA barrier orders this)
+  if (threadIdx.x < kHThreads / 64) half_tag[threadIdx.x] = INT_MIN;
+  hetrd1_body(c, io->x, cta_rank[blockIdx.x], cta_count[blockIdx.x], wait_limit, h_smem, red, redc, shc, shb, &tag,
+              half_tag, half_part);
 }
 
 // ---------------------------------------------------------------- T factors

@@ -1,6 +1,9 @@
 // One-stage Householder tridiagonalisation for cones whose trailing matrix
 // stays in shared memory or L2 (the medium sizes of the paper's
-// process-matrix step), in a single persistent cooperative kernel.
+// process-matrix step), in a single persistent cooperative kernel.  Three
+// routes share the structure below: double-float with the columns in shared
+// memory, double-float with the columns in place in global memory (launches
+// whose matrices fit in L2), and FP64 with the columns in L2 (larger ones).
 //
 // CTA r of a cone's group of G CTAs owns the columns i with i mod G = r for
 // the whole reduction (both triangles are kept, so a column is contiguous).
@@ -21,7 +24,8 @@
 //     A(r, i) -= v_r (p_i - 2K v_i) + p_r v_i        (= v w^T + w v^T, w = p - K v)
 // and forms the next step's p_i = tau_{j+1} u^T A(j+2:, i) (one read and one
 // write of A), publishing p_i and, from the owner of column j+2, that
-// column.  Work items are (column, chunk) pairs spread over all warps.
+// column (one or two warps per column in the double-float routes, (column,
+// chunk) work items over all warps in the FP64 route).
 // d, e, tau and the reflectors (packed into 32-column blocks with their unit
 // diagonal and zeros, ready for the blocked back-transformation) are written
 // as they are formed.  The slabs live in the cone's D&C buffer QA (n^2
@@ -170,10 +174,9 @@ __device__ void store_reflector(const ConeDev& c, int n, int j, const double* u,
 // reflector's scalars may still be in the making (by thread 0) while the
 // pass starts.  The owner of column r0 -- the next reflector's source --
 // publishes its rows to Cn.  Work items are (column, CH-row chunk) pairs
-// spread over the warps.  RES: this CTA's columns live in shared memory
-// (cols, column i at ((i - rank) / G) * n).
-template <bool UPDATE, bool RES, int CH>
-__device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, int n, int r0,
+// spread over the warps; the columns are read from and written to L2.
+template <bool UPDATE, int CH>
+__device__ void column_pass(double* __restrict__ A, int n, int r0,
                             const double* __restrict__ x, const double* coef, const double* __restrict__ vu,
                             const double* __restrict__ pu, double K2, double* Pn, double* Cn, double* psum, int pcap,
                             int rank, int G) {
@@ -189,13 +192,13 @@ __device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, i
     for (int it = warp; it < kc * nch; it += kSyThreads / 32) {
       const int k = k0 + it / nch, ch = it % nch;
       const int i = first + G * k;
-      double* col = RES ? cols + (int64_t)((i - rank) / G) * n + r0 : A + (int64_t)i * n + r0;
+      double* col = A + (int64_t)i * n + r0;
       const int t0 = ch * CH + lane;
       double a[NR];
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
         const int t = t0 + 32 * r;
-        a[r] = t < L ? (RES ? col[t] : __ldcg(col + t)) : 0.0;
+        a[r] = t < L ? __ldcg(col + t) : 0.0;
       }
       const bool publish = i == r0;
       if (UPDATE) {
@@ -205,8 +208,7 @@ __device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, i
           const int t = t0 + 32 * r;
           if (t < L) {
             a[r] = fma(-vu[t + 1], ai, fma(-pu[t + 1], vi, a[r]));
-            if (RES) col[t] = a[r];
-            else __stcg(col + t, a[r]);
+            __stcg(col + t, a[r]);
           }
         }
       }
@@ -234,7 +236,7 @@ __device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, i
       double sdot = 0.0;
       for (int ch = 0; ch < nch; ++ch) sdot += psum[kk * nch + ch];
       const int i = first + G * (k0 + kk);
-      const double a0 = RES ? cols[(int64_t)((i - rank) / G) * n + r0] : __ldcg(A + (int64_t)i * n + r0);
+      const double a0 = __ldcg(A + (int64_t)i * n + r0);
       st_pub(Pn + (i - r0), tau * fma(scal, sdot, a0));
     }
     __syncthreads();
@@ -244,19 +246,19 @@ __device__ void column_pass(double* __restrict__ A, double* __restrict__ cols, i
   if (ncol == 0) __syncthreads();
 }
 
-template <bool UPDATE, bool RES>
-__device__ void column_pass_any(double* A, double* cols, int n, int r0, const double* x, const double* coef,
-                                const double* vu, const double* pu, double K2, double* Pn, double* Cn, double* psum,
-                                int pcap, int rank, int G) {
+template <bool UPDATE>
+__device__ void column_pass_any(double* A, int n, int r0, const double* x, const double* coef, const double* vu,
+                                const double* pu, double K2, double* Pn, double* Cn, double* psum, int pcap, int rank,
+                                int G) {
   // rows per work item by the column length: fewer idle lanes in ragged
   // chunks against fewer cross-lane sums
   const int L = n - r0;
   if (L > 512)
-    column_pass<UPDATE, RES, 256>(A, cols, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
+    column_pass<UPDATE, 256>(A, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
   else if (L > 160)
-    column_pass<UPDATE, RES, 128>(A, cols, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
+    column_pass<UPDATE, 128>(A, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
   else
-    column_pass<UPDATE, RES, 64>(A, cols, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
+    column_pass<UPDATE, 64>(A, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
 }
 
 // Waits for the m values of P and C of a step: p into ps[], a - p into bs[];
@@ -305,8 +307,7 @@ __device__ bool poll_step(const double* P, const double* C, int m, const double*
   return __syncthreads_and(ok) != 0;
 }
 
-// Shared memory of a CTA: v, p, the updated column (3n), the partial sums,
-// and with RES the CTA's own columns (ceil(n / G) of n rows).
+// Partial sums of the FP64 route's pass: (column, 64-row chunk) items per round.
 __host__ __device__ inline int sytrd1_pcap(int n, int G) {
   const int items = ((n + G - 1) / G) * ((n + 63) / 64);  // up to 64-row items
   return items < kPartMax ? items : kPartMax;
@@ -721,13 +722,13 @@ __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait
   }
 }
 
-template <bool RES>
+// The FP64 route with the columns in L2 (cones beyond the double-float
+// routes' reach: matrices larger than L2).
 __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_limit, double* sy_smem, double* red,
                             double* sh) {
   const int n = (int)c.n;
   double* A = c.A;
   const int pcap = sytrd1_pcap(n, G);
-  double* cols = sy_smem + 3 * n + pcap;  // RES: own columns
   double* vc = sy_smem;             // v_j (rows j+1 ..)
   double* ps = sy_smem + n;         // p_j (rows j+1 ..)
   double* bs = sy_smem + 2 * n;     // column j+1 (rows j+1 ..): a - p, then updated by step j
@@ -735,13 +736,6 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
   double* pub = c.QA;               // the steps' slabs
   const int tid = threadIdx.x;
   int parity = 0;
-  if (RES) {
-    for (int i = rank; i < n; i += G) {
-      const double* src = A + (int64_t)i * n;
-      double* dst = cols + (int64_t)((i - rank) / G) * n;
-      for (int r = tid; r < n; r += kSyThreads) dst[r] = __ldcg(src + r);
-    }
-  }
   if (n < 3) {
     __syncthreads();
     if (rank == 0 && tid == 0) {
@@ -777,8 +771,7 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
   __syncthreads();
   {
     double* s0 = slab(pub, n, 0);
-    column_pass_any<false, RES>(A, cols, n, 1, vc, sh + 1, nullptr, nullptr, 0.0, s0, s0 + (n - 1), psum, pcap,
-                                rank, G);
+    column_pass_any<false>(A, n, 1, vc, sh + 1, nullptr, nullptr, 0.0, s0, s0 + (n - 1), psum, pcap, rank, G);
   }
   for (int j = 0; j + 2 < n; ++j) {
     const int m = n - j - 1;
@@ -816,8 +809,7 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
         sh[0] = b1; sh[1] = t1; sh[2] = sc;
       }
       double* Pn = slab(pub, n, j + 1);
-      column_pass_any<true, RES>(A, cols, n, j + 2, bs + 1, sh + 1, vc, ps, 2.0 * K, Pn, Pn + (m - 1), psum, pcap,
-                                 rank, G);
+      column_pass_any<true>(A, n, j + 2, bs + 1, sh + 1, vc, ps, 2.0 * K, Pn, Pn + (m - 1), psum, pcap, rank, G);
       const double beta1 = sh[0], tau1 = sh[1], scal1 = sh[2];
       if (rank == 0 && tid == 0) {
         c.d[j + 1] = bs[0];
@@ -831,16 +823,14 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
       __syncthreads();
     } else {
       __syncthreads();
-      // the last 2 x 2 block (rows n-2, n-1); A(n-1, n-1) is current in its
-      // owner's copy (shared memory with RES, else A)
+      // the last 2 x 2 block (rows n-2, n-1); A(n-1, n-1) is current in A
       if (rank == 0 && tid == 0) {
         c.d[n - 2] = bs[0];
         c.e[n - 2] = bs[1];
         c.e[n - 1] = 0.0;
       }
       if (rank == (n - 1) % G && tid == 0) {
-        const double a = RES ? cols[(int64_t)((n - 1 - rank) / G) * n + (n - 1)]
-                             : __ldcg(A + (int64_t)(n - 1) + (int64_t)(n - 1) * n);
+        const double a = __ldcg(A + (int64_t)(n - 1) + (int64_t)(n - 1) * n);
         const double w1 = fma(-K, vc[1], ps[1]);
         c.d[n - 1] = a - 2.0 * vc[1] * w1;
       }
@@ -878,7 +868,7 @@ __global__ void __launch_bounds__(kSyThreads) sytrd1_kernel(const ConeDev* __res
     sytrd1_body_df<false>(c, rank, G, wait_limit, sy_smem, reinterpret_cast<dfl*>(red), sh,
                           reinterpret_cast<dfl*>(sh + 2), &coef_tag, half_tag, half_part);
   else
-    sytrd1_body<false>(c, rank, G, wait_limit, sy_smem, red, sh);
+    sytrd1_body(c, rank, G, wait_limit, sy_smem, red, sh);
 }
 
 // T factor of each 32-reflector block (one CTA per block): G = V^T V, then
