@@ -195,6 +195,8 @@ struct ScsPlan {
   void* mem = nullptr;
   double *p = nullptr, *hp = nullptr, *z = nullptr, *tk = nullptr, *part = nullptr, *tau = nullptr;
   double *tin = nullptr, *uty = nullptr;
+  double* tpart = nullptr;  // dense A^T: row-chunk partial dot products
+  int tchunks = 1;
   // structured operator: two work tensors of N^2 doubles and a status word
   void* kmem = nullptr;
   int64_t kdoubles = 0;
@@ -2297,7 +2299,9 @@ int scs_run(scs_psd_handle h, ScsOp op, int64_t kron_n2, const double* b, const 
       np->m = m;
       np->k = k;
       const int nparts = scs_dot_parts(k + m);
-      const size_t nd = (size_t)(k + m) * 2 + (size_t)std::max<int64_t>(k, 1) + (size_t)nparts + 2 + 2 * (size_t)m;
+      const int tchunks = scs_gemv_t_chunks(m, k);
+      const size_t nd = (size_t)(k + m) * 2 + (size_t)std::max<int64_t>(k, 1) + (size_t)nparts + 2 + 2 * (size_t)m +
+                        (size_t)tchunks * (size_t)std::max<int64_t>(k, 1);
       if (cudaMalloc(&np->mem, sizeof(double) * (nd + 64)) != cudaSuccess) return SCS_PSD_ENOMEM;
       double* q = (double*)np->mem;
       np->p = q; q += k + m;
@@ -2307,7 +2311,9 @@ int scs_run(scs_psd_handle h, ScsOp op, int64_t kron_n2, const double* b, const 
       np->hp = q++;
       np->tau = q++;
       np->tin = q; q += m;
-      np->uty = q;
+      np->uty = q; q += m;
+      np->tpart = q;
+      np->tchunks = tchunks;
       sp = np.get();
       h->scs[{m, k}] = std::move(np);
     }
@@ -2323,17 +2329,19 @@ int scs_run(scs_psd_handle h, ScsOp op, int64_t kron_n2, const double* b, const 
     }
   }
   cudaStream_t s = (cudaStream_t)stream;
-  int64_t launches = 5;
+  int64_t launches = 6;  // dense: A^T in two launches
+  op.tpart = sp->tpart;
+  op.tchunks = sp->tchunks;
   if (!op.A) {
     op.t0 = sp->t0;
     op.t1 = sp->t1;
     op.status = h->status_word;
     kron_prepare();
-    launches += 2 * (int64_t)kron_launches(op.kron) - 3;
+    launches += 2 * (int64_t)kron_launches(op.kron) - 4;
   }
   launch_scs_setup(op, b, c, m, k, sp->p, sp->hp, sp->tk, sp->part, s);
   if (cudaGetLastError() != cudaSuccess) return SCS_PSD_ECUDA;
-  const int64_t per_affine = op.A ? 6 : 3 + 2 * (int64_t)kron_launches(op.kron);
+  const int64_t per_affine = op.A ? 7 : 3 + 2 * (int64_t)kron_launches(op.kron);
   for (int it = 0; it < iters; ++it) {
     launch_scs_affine(op, b, c, m, k, sp->p, sp->hp, u, v, sp->z, sp->tk, sp->part, sp->tau, sp->tin, sp->uty, s);
     if (cudaGetLastError() != cudaSuccess) return SCS_PSD_ECUDA;

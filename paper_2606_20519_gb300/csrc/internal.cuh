@@ -305,8 +305,11 @@ struct ScsOp {
   double* t0 = nullptr;
   double* t1 = nullptr;
   int* status = nullptr;
+  double* tpart = nullptr;  // dense A^T: tchunks x k partial dot products
+  int tchunks = 1;
 };
 int scs_dot_parts(int64_t len);
+int scs_gemv_t_chunks(int64_t m, int64_t k);
 void launch_scs_setup(const ScsOp& op, const double* b, const double* c, int64_t m, int64_t k, double* p,
                       double* hp, double* tk, double* part, cudaStream_t s);
 void launch_scs_affine(const ScsOp& op, const double* b, const double* c, int64_t m, int64_t k, const double* p,

@@ -5,47 +5,74 @@
 // inverse z_x = (a_x - A^T a_y) / 2, z_y = a_y + A z_x (one product with A^T,
 // one with A), and (I + Q)^{-1} follows from z = M^{-1} w and p = M^{-1}(c, b):
 //   tau~ = (w_tau + c.z_x + b.z_y) / (1 + c.p_x + b.p_y),  (x~, y~) = z - tau~ p.
-// A dense A (column-major, m x k) is streamed from HBM once per product; a
+// A dense A (column-major, m x k) is streamed from HBM once per product (both
+// products are FP64-pipe-bound on this part: m k FMAs against 8 m k bytes); a
 // structured A is applied by the contractions of kron.cu; the rest are short
 // vector kernels; the cone projection of the y block is the library's own
 // launch sequence.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace scs {
 
 namespace {
 
-// out[j] = A(:, j) . (a1 + a2): one block per column, fixed-order reduction.
-__global__ void __launch_bounds__(256) gemv_t_kernel(const double* __restrict__ A, int64_t m, int64_t k,
-                                                     const double* __restrict__ a1, const double* __restrict__ a2,
-                                                     double* __restrict__ out) {
-  __shared__ double sh[8];
-  const int64_t j = blockIdx.x;
-  if (j >= k) return;
-  const double* __restrict__ col = A + j * m;
-  double s = 0.0;
-  for (int64_t i = threadIdx.x; i < m; i += 256) {
+// A^T (a1 + a2) in two launches with a fixed summation order: block (g, r)
+// forms, for the kGtCols columns of group g and the rows of chunk r, the
+// partial dot products part[r * k + j] (each thread kGtCols independent FMA
+// chains, the vector element read once for all of them); then
+// out[j] = sum_r part[r * k + j] in increasing r.
+constexpr int kGtCols = 8;
+__global__ void __launch_bounds__(256) gemv_t_part_kernel(const double* __restrict__ A, int64_t m, int64_t k,
+                                                          const double* __restrict__ a1,
+                                                          const double* __restrict__ a2, int chunks,
+                                                          double* __restrict__ part) {
+  __shared__ double sh[8][kGtCols];
+  const int64_t j0 = (int64_t)blockIdx.x * kGtCols;
+  const int64_t rows = (m + chunks - 1) / chunks;
+  const int64_t r0 = (int64_t)blockIdx.y * rows, r1 = r0 + rows < m ? r0 + rows : m;
+  const int nc = k - j0 < kGtCols ? (int)(k - j0) : kGtCols;
+  double acc[kGtCols];
+#pragma unroll
+  for (int c = 0; c < kGtCols; ++c) acc[c] = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += 256) {
     const double a = a2 ? a1[i] + a2[i] : a1[i];
-    s = fma(col[i], a, s);
+#pragma unroll
+    for (int c = 0; c < kGtCols; ++c)
+      if (c < nc) acc[c] = fma(A[(j0 + c) * m + i], a, acc[c]);
   }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+#pragma unroll
+  for (int c = 0; c < kGtCols; ++c) {
+    double s = acc[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][c] = s;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < nc) {
     double t = 0.0;
-    for (int q = 0; q < 8; ++q) t += sh[q];
-    out[j] = t;
+    for (int q = 0; q < 8; ++q) t += sh[q][threadIdx.x];
+    part[(int64_t)blockIdx.y * k + j0 + threadIdx.x] = t;
   }
 }
 
+__global__ void gemv_t_sum_kernel(const double* __restrict__ part, int chunks, int64_t k, double* __restrict__ out) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  double t = 0.0;
+  for (int r = 0; r < chunks; ++r) t += part[(int64_t)r * k + j];
+  out[j] = t;
+}
+
 // out[i] = a1[i] + a2[i] + A(i, :) . x: threads over rows (coalesced down the
-// columns), x staged in shared memory in chunks.
+// columns), x staged in shared memory in chunks; four independent FMA chains
+// per thread (columns q mod 4), summed in a fixed order.
 __global__ void __launch_bounds__(256) gemv_n_kernel(const double* __restrict__ A, int64_t m, int64_t k,
                                                      const double* __restrict__ x, const double* __restrict__ a1,
                                                      const double* __restrict__ a2, double* __restrict__ out) {
   __shared__ double xs[1024];
   const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
-  double s = 0.0;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   for (int64_t j0 = 0; j0 < k; j0 += 1024) {
     const int64_t nj = k - j0 < 1024 ? k - j0 : 1024;
     __syncthreads();
@@ -53,11 +80,18 @@ __global__ void __launch_bounds__(256) gemv_n_kernel(const double* __restrict__ 
     __syncthreads();
     if (i < m) {
       const double* __restrict__ p = A + i + j0 * m;
-#pragma unroll 8
-      for (int64_t q = 0; q < nj; ++q) s = fma(p[q * m], xs[q], s);
+      int64_t q = 0;
+#pragma unroll 2
+      for (; q + 3 < nj; q += 4) {
+        s0 = fma(p[q * m], xs[q], s0);
+        s1 = fma(p[(q + 1) * m], xs[q + 1], s1);
+        s2 = fma(p[(q + 2) * m], xs[q + 2], s2);
+        s3 = fma(p[(q + 3) * m], xs[q + 3], s3);
+      }
+      for (; q < nj; ++q) s0 = fma(p[q * m], xs[q], s0);
     }
   }
-  if (i < m) out[i] = (a2 ? a1[i] + a2[i] : a1[i]) + s;
+  if (i < m) out[i] = (a2 ? a1[i] + a2[i] : a1[i]) + ((s0 + s1) + (s2 + s3));
 }
 
 // out[j] = (a1[j] + a2[j] - t[j]) / 2  (a2 may be null)
@@ -130,6 +164,18 @@ __global__ void vy_kernel(double* __restrict__ vy, const double* __restrict__ ut
 
 }  // namespace
 
+// Row chunks of the A^T product: about four blocks per SM over all column groups
+// (eight measured the same).
+int scs_gemv_t_chunks(int64_t m, int64_t k) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t groups = (k + kGtCols - 1) / kGtCols;
+  int64_t r = (4 * (int64_t)sms + groups - 1) / std::max<int64_t>(1, groups);
+  r = std::min<int64_t>(r, std::max<int64_t>(1, m / 1024));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(r, 64));
+}
+
 int scs_dot_parts(int64_t len) {
   int64_t g = (len + 255) / 256;
   return (int)(g < 512 ? (g < 1 ? 1 : g) : 512);
@@ -138,8 +184,14 @@ int scs_dot_parts(int64_t len) {
 // out = A^T (a1 + a2), k entries
 void op_t(const ScsOp& op, int64_t m, int64_t k, const double* a1, const double* a2, double* out, cudaStream_t s) {
   if (k <= 0) return;
-  if (op.A) gemv_t_kernel<<<(unsigned)k, 256, 0, s>>>(op.A, m, k, a1, a2, out);
-  else launch_kron_apply_t(op.kron, a1, a2, out, op.t0, op.t1, op.status, s);
+  if (op.A) {
+    const int chunks = op.tchunks;
+    gemv_t_part_kernel<<<dim3((unsigned)((k + kGtCols - 1) / kGtCols), (unsigned)chunks), 256, 0, s>>>(
+        op.A, m, k, a1, a2, chunks, op.tpart);
+    gemv_t_sum_kernel<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(op.tpart, chunks, k, out);
+  } else {
+    launch_kron_apply_t(op.kron, a1, a2, out, op.t0, op.t1, op.status, s);
+  }
 }
 
 // out = a1 + a2 + A x, m entries
