@@ -1378,10 +1378,12 @@ int run_body(scs_psd_handle h, Plan& P, int mode, long long wait_limit, cudaStre
         const int* pos = P.ints_d + lv.pos_off;
         launch_dc_prepare(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
         LAUNCH_CHECK();
-        launch_dc_build_qin(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
-        LAUNCH_CHECK();
-        launch_dc_apply_rot(P.cones_d, nodes, pos, P.total_pos, s);
-        LAUNCH_CHECK();
+        if (lv.maxK > kDcFuseK) {  // else done inside dc_prepare_kernel
+          launch_dc_build_qin(P.cones_d, nodes, lv.nnodes, lv.maxK, s);
+          LAUNCH_CHECK();
+          launch_dc_apply_rot(P.cones_d, nodes, pos, P.total_pos, s);
+          LAUNCH_CHECK();
+        }
         launch_dc_secular(P.cones_d, nodes, pos, P.total_pos, lv.maxK, s);
         LAUNCH_CHECK();
         launch_dc_loewner(P.cones_d, nodes, pos, P.total_pos, s);

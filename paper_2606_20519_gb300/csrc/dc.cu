@@ -360,6 +360,33 @@ __global__ void __launch_bounds__(kDcThreads) dc_prepare_kernel(const ConeDev* _
     cnt[1] = K - kk;
     cnt[2] = sh_nrot;
   }
+  if (K <= kDcFuseK) {
+    // a small merge also builds its permuted block and applies the deflation's
+    // rotations here (the separate kernels skip it; two launches fewer per level)
+    __syncthreads();
+    const double* Qsrc = qin_buf(c, nd.level);
+    double* Qb = c.Qin;
+    for (int e = tid; e < K * K; e += kDcThreads) {
+      const int j = e / K, r = e - j * K;
+      const int src = perm[j], dst = fp[j];
+      const bool same = (src < n1) == (r < n1);
+      Qb[(s + r) + (int64_t)(s + dst) * n] = same ? Qsrc[(s + r) + (int64_t)(s + src) * n] : 0.0;
+    }
+    __syncthreads();
+    const int nr = sh_nrot;
+    for (int r = tid; r < K && nr > 0; r += kDcThreads) {
+      double* row = Qb + (s + r) + (int64_t)s * n;
+      for (int q = 0; q < nr; ++q) {
+        const int a = irot[2 * q], bcol = irot[2 * q + 1];
+        const double cc = rot[2 * q], sn = rot[2 * q + 1];
+        double* pa = row + (int64_t)a * n;
+        double* pb = row + (int64_t)bcol * n;
+        const double x = *pa, y = *pb;
+        *pa = cc * x - sn * y;
+        *pb = sn * x + cc * y;
+      }
+    }
+  }
 }
 
 // Permuted eigenvector block Qin(:, fp[j]) = Q(:, perm[j]) of each merge node;
@@ -373,6 +400,7 @@ __global__ void dc_build_qin_kernel(const ConeDev* __restrict__ cones, const Mer
   if (*c.status != 0) return;
   const int64_t n = c.n;
   const int s = nd.s, n1 = nd.n1, K = nd.n1 + nd.n2;
+  if (K <= kDcFuseK) return;  // built by dc_prepare_kernel
   const int j0 = blockIdx.y * kQinCols;
   if (j0 >= K) return;
   const double* Qi = qin_buf(c, nd.level);
@@ -401,6 +429,7 @@ __global__ void dc_apply_rot_kernel(const ConeDev* __restrict__ cones, const Mer
   const ConeDev& c = cones[nd.cone];
   if (*c.status != 0) return;
   const int s = nd.s;
+  if (nd.n1 + nd.n2 <= kDcFuseK) return;  // applied by dc_prepare_kernel
   const int nrot = c.icnt[4 * s + 2];
   if (nrot == 0) return;
   const int r = pos_node[gp];

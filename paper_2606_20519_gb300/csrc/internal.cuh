@@ -157,6 +157,10 @@ struct ConeDev {
 };
 
 // One merge node of the divide and conquer tree.
+// Merges of at most this many rows build their permuted eigenvector block and
+// apply their deflation rotations inside dc_prepare_kernel.
+constexpr int kDcFuseK = 64;
+
 struct MergeNode {
   int cone;
   int s;       // first row of the merged block
