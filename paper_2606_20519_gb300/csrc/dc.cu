@@ -487,10 +487,31 @@ __device__ bool secular_root_warp(const double* __restrict__ dk, const double* _
   if (i < K - 1) {
     const double di = dk[i];
     const double mid = 0.5 * (dk[i + 1] - di);
-    double f = 0.0;
-    for (int j = lane; j < K; j += 32) f += zk[j] * zk[j] * rcp_nr((dk[j] - di) - mid);
-    f = 1.0 + rho * warp_sum_d(f);
-    if (f >= 0.0) { org = i; lo = 0.0; hi = mid; }
+    // f at the midpoint decides the origin pole.  First in FP32 from the FP64
+    // pole differences: |d_j - d_i - mid| >= mid for every j, so each term is
+    // within a few FP32 roundings, and the sign is taken when |f| clears that
+    // bound; otherwise in FP64.
+    const float mid32 = f64_to_f32_rn(mid), rho32 = f64_to_f32_rn(rho);
+    float f32 = 0.0f, a32 = 0.0f;
+    for (int j = lane; j < K; j += 32) {
+      const float zz = f64_to_f32_rn(zk[j]);
+      const float term = zz * __fdividef(zz, f64_to_f32_rn(dk[j] - di) - mid32);
+      f32 += term;
+      a32 += fabsf(term);
+    }
+    f32 = 1.0f + rho32 * warp_sum_f(f32);
+    a32 = warp_sum_f(a32);
+    const float bound32 = (2.0f * (float)K + 32.0f) * 5.9604645e-8f * (1.0f + rho32 * a32);
+    bool right;  // f(mid) >= 0: the root lies left of the midpoint
+    if (fabsf(f32) > bound32 && isfinite(f32)) {
+      right = f32 >= 0.0f;
+    } else {
+      double f = 0.0;
+      for (int j = lane; j < K; j += 32) f += zk[j] * zk[j] * rcp_nr((dk[j] - di) - mid);
+      f = 1.0 + rho * warp_sum_d(f);
+      right = f >= 0.0;
+    }
+    if (right) { org = i; lo = 0.0; hi = mid; }
     else { org = i + 1; lo = -mid; hi = 0.0; }
   } else {
     org = i;
