@@ -252,6 +252,12 @@ __device__ __forceinline__ c_dot c_dot_add(c_dot d, cdf a, cdf x) {
   return d;
 }
 __device__ __forceinline__ cdf c_dot_value(c_dot d) { return c_make(df_dot_value(d.re), df_dot_value(d.im)); }
+// compensated accumulation of a x (no conjugate)
+__device__ __forceinline__ c_dot c_dotn_add(c_dot d, cdf a, cdf x) {
+  d.re = df_dot_add(df_dot_add(d.re, a.re, x.re), df_neg(a.im), x.im);
+  d.im = df_dot_add(df_dot_add(d.im, a.re, x.im), a.im, x.re);
+  return d;
+}
 __device__ __forceinline__ cdf c_shfl_xor(cdf v, int o) { return c_make(df_shfl_xor(v.re, o), df_shfl_xor(v.im, o)); }
 __device__ __forceinline__ cdf c_from_d(double re, double im) { return c_make(df_from_d(re), df_from_d(im)); }
 

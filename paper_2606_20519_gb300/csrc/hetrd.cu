@@ -510,7 +510,7 @@ __device__ void hbt_slab(const HConeDev& c, int j0, int ncols, cdf* zs, cdf* Ws,
   for (int e = tid; e < KC * n; e += kHThreads) {
     const int col = e / n, r = e - col * n;
     const double z = col < ncols ? c.Z[(int64_t)r + (int64_t)(j0 + col) * n] : 0.0;
-    zs[e] = c_make(df_from_d(z), df_zero());
+    zs[e] = c_make(df_from_d_int(z), df_zero());  // eigenvector entries, |z| <= 1
   }
   __syncthreads();
   const int nblk = (n - 2) / kHNb + 1;
@@ -521,18 +521,18 @@ __device__ void hbt_slab(const HConeDev& c, int j0, int ncols, cdf* zs, cdf* Ws,
     const cdf* Tq = c.T + (int64_t)q * kHNb * kHNb;
     // W(a, col) = sum_r conj(V(r, a)) z(r0 + r, col): warp w takes reflectors w, w + 8, ..
     for (int a = warp; a < kHNb; a += kHThreads / 32) {
-      cdf acc[KC];
+      c_dot acc[KC];
 #pragma unroll
-      for (int col = 0; col < KC; ++col) acc[col] = c_zero();
+      for (int col = 0; col < KC; ++col) acc[col] = c_dot_zero();
       if (a < bb)
         for (int r = lane + a; r < mq; r += 32) {  // rows above a are zero
           const cdf v = Vq[(int64_t)r + (int64_t)a * mq];
 #pragma unroll
-          for (int col = 0; col < KC; ++col) acc[col] = c_cfma(v, zs[col * n + r0 + r], acc[col]);
+          for (int col = 0; col < KC; ++col) acc[col] = c_dot_add(acc[col], v, zs[col * n + r0 + r]);
         }
 #pragma unroll
       for (int col = 0; col < KC; ++col) {
-        cdf s = acc[col];
+        cdf s = c_dot_value(acc[col]);
         for (int o = 16; o > 0; o >>= 1) s = c_add(s, c_shfl_xor(s, o));
         if (lane == 0) Ws[a * KC + col] = s;
       }
@@ -549,17 +549,17 @@ __device__ void hbt_slab(const HConeDev& c, int j0, int ncols, cdf* zs, cdf* Ws,
     __syncthreads();
     // z(r0 + r, col) -= sum_a V(r, a) W'(a, col)
     for (int r = tid; r < mq; r += kHThreads) {
-      cdf s[KC];
+      c_dot s[KC];
 #pragma unroll
-      for (int col = 0; col < KC; ++col) s[col] = c_zero();
+      for (int col = 0; col < KC; ++col) s[col] = c_dot_zero();
       const int amax = min(bb, r + 1);  // V(r, a) = 0 for a > r
       for (int a = 0; a < amax; ++a) {
         const cdf v = Vq[(int64_t)r + (int64_t)a * mq];
 #pragma unroll
-        for (int col = 0; col < KC; ++col) s[col] = c_fma(v, Wt[a * KC + col], s[col]);
+        for (int col = 0; col < KC; ++col) s[col] = c_dotn_add(s[col], v, Wt[a * KC + col]);
       }
 #pragma unroll
-      for (int col = 0; col < KC; ++col) zs[col * n + r0 + r] = c_add(zs[col * n + r0 + r], c_neg(s[col]));
+      for (int col = 0; col < KC; ++col) zs[col * n + r0 + r] = c_add(zs[col * n + r0 + r], c_neg(c_dot_value(s[col])));
     }
     __syncthreads();
   }
