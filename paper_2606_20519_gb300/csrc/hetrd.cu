@@ -690,7 +690,6 @@ size_t hcone_pub_doubles(int64_t n) { return (size_t)(2 * n * (n - 1) + 1); }
 size_t hcone_v_elems(int64_t n) { return (size_t)(((n - 2) / kHNb + 1) * n * kHNb); }
 size_t hcone_t_elems(int64_t n) { return (size_t)(((n - 2) / kHNb + 1) * kHNb * kHNb); }
 int hcone_blocks(int64_t n) { return n >= 2 ? (int)((n - 2) / kHNb + 1) : 0; }
-size_t hcdf_bytes() { return sizeof(cdf); }
 
 int launch_hetrd1(const HConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,
                   size_t smem, const IoSlot* io, long long wait_limit, cudaStream_t s) {
