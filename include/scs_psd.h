@@ -354,7 +354,8 @@ int scs_psd_proj_static(const double* x, double* y, int64_t n, void* stream);
  * scs_psd_proj_batched; not modified): the route and band width (automatic,
  * one-stage, two-stage with 8, 16, 32), the GEMM split-K target (1, 2, 4
  * CTAs per SM), and for one-stage cones the back-transformation slab width
- * (2, 4, 8 columns) and the one-stage group size (all or half of the SMs),
+ * (1, 2, 4, 8 columns at most) and the one-stage group size (all, a half or
+ * a quarter of the SMs),
  * by coordinate search, three timed runs each (CUDA events on `stream`).
  * The winner is kept in the handle and used by every later call with these
  * shapes and precision whose opts->band is 0.  chosen (may be NULL)

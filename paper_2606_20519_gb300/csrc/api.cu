@@ -1775,7 +1775,7 @@ int autotune(scs_psd_handle h, const double* x, const int64_t* offsets, const in
   }
   if (has_one) {
     const Tuning base = best;
-    for (int cols : {2, 4}) {
+    for (int cols : {1, 2, 4}) {
       Tuning t = base;
       t.bt1_cols = cols;
       consider(t);
