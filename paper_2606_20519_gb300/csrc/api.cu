@@ -760,13 +760,30 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
           const size_t res = sytrd1_smem_bytes(mx, 1, true);
           if (res <= 200 * 1024) gcap = std::max(1, sytrd1_max_ctas_for(res));
         }
+        // large cones whose matrices together exceed L2 but each fit it: one
+        // launch per L2-sized group (the double-float route with the columns in
+        // global memory then applies to each group)
+        constexpr double kL2Group = 112.0 * 1024 * 1024;
+        bool by_bytes = false;
+        if (spread) {
+          double total = 0.0, mxb = 0.0;
+          for (int c : list) {
+            const double b = 8.0 * (double)cones[c].n * (double)cones[c].n;
+            total += b;
+            mxb = std::max(mxb, b);
+          }
+          by_bytes = total > kL2Group && mxb <= kL2Group;
+        }
         size_t i = 0;
         while (i < list.size()) {
           std::vector<int> grp;
-          double work = 0.0;
+          double work = 0.0, bytes = 0.0;
           while (i < list.size() && (int)grp.size() < gcap) {
+            const double b = 8.0 * (double)cones[list[i]].n * (double)cones[list[i]].n;
+            if (by_bytes && !grp.empty() && bytes + b > kL2Group) break;
             grp.push_back(list[i]);
             work += std::pow((double)cones[list[i]].n, 3.0);
+            bytes += b;
             ++i;
           }
           // CTAs per cone: a share of the co-resident CTAs by work, at least 4
