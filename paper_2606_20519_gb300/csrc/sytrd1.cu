@@ -49,30 +49,11 @@ namespace {
 
 constexpr int kSyThreads = 256;
 constexpr int kNb = kSy1Block;
-// A NaN whose payload arithmetic never produces (NaN results carry the
-// canonical payload, and the matrix entering the kernel is finite).
-constexpr long long kSentinel = (long long)0xFFF5A5A5A5A5A5A5ull;
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
-}
-
-// Published values: single-copy-atomic 8-byte stores and loads at GPU scope.
-__device__ __forceinline__ void st_pub(double* p, double v) {
-  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
-}
-__device__ __forceinline__ double ld_pub(const double* p) {
-  double v;
-  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ bool pending(double v) { return __double_as_longlong(v) == kSentinel; }
-
-// Slab of step j: P_j (p_{j+1} .. p_{n-1}), then C_j (column j+1, rows j+1 ..).
-__device__ __forceinline__ double* slab(double* base, int n, int j) {
-  return base + (int64_t)2 * j * (n - 1) - (int64_t)j * (j - 1);
 }
 
 // Sum over the CTA; every thread gets the same value (pairwise, in the same
@@ -165,21 +146,19 @@ __device__ void store_reflector(const ConeDev& c, int n, int j, const double* u,
   }
 }
 
-// One pass over this CTA's columns i >= r0 (i mod G = rank), rows r0 .. n-1:
-// with UPDATE, first A(r, i) -= v_r (p_i - 2K v_i) + p_r v_i (vu, pu indexed
-// from row r0 - 1); then p_i = coef[0] (A(r0, i) + coef[1] sum_{r > r0} A(r, i) x_r)
-// published to Pn[i - r0], x indexed from row r0.  The next reflector is
-// u = coef[1] x with u_0 = 1, so p_i = tau u^T A(r0:, i) without x having
-// been rescaled; coef is read only after the pass's first barrier, so the
-// reflector's scalars may still be in the making (by thread 0) while the
-// pass starts.  The owner of column r0 -- the next reflector's source --
-// publishes its rows to Cn.  Work items are (column, CH-row chunk) pairs
-// spread over the warps; the columns are read from and written to L2.
+// One pass over this CTA's columns i >= r0 (i mod G = rank), rows r0 .. n-1,
+// read from and written to L2: with UPDATE, first A(r, i) -= v_r w_i + w_r v_i
+// (vu, wu indexed from row r0 - 1); then p_i = coef[0] (A(r0, i) + coef[1]
+// sum_{r > r0} A(r, i) x_r) into pbuf[i], x indexed from row r0.  The next
+// reflector is u = coef[1] x with u_0 = 1, so p_i = tau u^T A(r0:, i) without
+// x having been rescaled; coef is read only after the pass's first barrier,
+// so the reflector's scalars may still be in the making (by thread 0) while
+// the pass starts.  Work items are (column, CH-row chunk) pairs spread over
+// the warps.
 template <bool UPDATE, int CH>
-__device__ void column_pass(double* __restrict__ A, int n, int r0,
-                            const double* __restrict__ x, const double* coef, const double* __restrict__ vu,
-                            const double* __restrict__ pu, double K2, double* Pn, double* Cn, double* psum, int pcap,
-                            int rank, int G) {
+__device__ void column_pass(double* __restrict__ A, int n, int r0, const double* __restrict__ x, const double* coef,
+                            const double* __restrict__ vu, const double* __restrict__ wu, double* pbuf,
+                            double* psum, int pcap, int rank, int G) {
   constexpr int NR = CH / 32;
   const int L = n - r0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -200,33 +179,23 @@ __device__ void column_pass(double* __restrict__ A, int n, int r0,
         const int t = t0 + 32 * r;
         a[r] = t < L ? __ldcg(col + t) : 0.0;
       }
-      const bool publish = i == r0;
       if (UPDATE) {
-        const double vi = vu[i - r0 + 1], ai = fma(-K2, vi, pu[i - r0 + 1]);
+        const double vi = vu[i - r0 + 1], wi = wu[i - r0 + 1];
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           const int t = t0 + 32 * r;
           if (t < L) {
-            a[r] = fma(-vu[t + 1], ai, fma(-pu[t + 1], vi, a[r]));
+            a[r] = fma(-vu[t + 1], wi, fma(-wu[t + 1], vi, a[r]));
             __stcg(col + t, a[r]);
           }
         }
       }
-      if (publish) {
+      double acc = 0.0;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const int t = t0 + 32 * r;
-          if (t < L) st_pub(Cn + t, a[r]);
-        }
-      }
-      double acc0 = 0.0, acc1 = 0.0;
-#pragma unroll
-      for (int r = 0; r < NR; r += 2) {
+      for (int r = 0; r < NR; ++r) {
         const int t = t0 + 32 * r;
-        if (t < L && t > 0) acc0 = fma(a[r], x[t], acc0);
-        if (r + 1 < NR && t + 32 < L) acc1 = fma(a[r + 1], x[t + 32], acc1);
+        if (t < L && t > 0) acc = fma(a[r], x[t], acc);
       }
-      double acc = acc0 + acc1;
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (lane == 0) psum[it] = acc;
     }
@@ -236,75 +205,13 @@ __device__ void column_pass(double* __restrict__ A, int n, int r0,
       double sdot = 0.0;
       for (int ch = 0; ch < nch; ++ch) sdot += psum[kk * nch + ch];
       const int i = first + G * (k0 + kk);
-      const double a0 = __ldcg(A + (int64_t)i * n + r0);
-      st_pub(Pn + (i - r0), tau * fma(scal, sdot, a0));
+      __stcg(pbuf + i, tau * fma(scal, sdot, __ldcg(A + (int64_t)i * n + r0)));
     }
     __syncthreads();
   }
   // the caller reads the coefficients (written by thread 0 before the pass)
   // after it: a CTA without columns still passes one barrier
   if (ncol == 0) __syncthreads();
-}
-
-template <bool UPDATE>
-__device__ void column_pass_any(double* A, int n, int r0, const double* x, const double* coef, const double* vu,
-                                const double* pu, double K2, double* Pn, double* Cn, double* psum, int pcap, int rank,
-                                int G) {
-  // rows per work item by the column length: fewer idle lanes in ragged
-  // chunks against fewer cross-lane sums
-  const int L = n - r0;
-  if (L > 512)
-    column_pass<UPDATE, 256>(A, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
-  else if (L > 160)
-    column_pass<UPDATE, 128>(A, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
-  else
-    column_pass<UPDATE, 64>(A, n, r0, x, coef, vu, pu, K2, Pn, Cn, psum, pcap, rank, G);
-}
-
-// Waits for the m values of P and C of a step: p into ps[], a - p into bs[];
-// returns this thread's part of p^T v, and false (in every thread) when a
-// wait ran out.
-__device__ bool poll_step(const double* P, const double* C, int m, const double* v, double* ps, double* bs,
-                          long long limit, double* pt_out) {
-  double pt = 0.0;
-  int ok = 1;
-  for (int base = 0; base < m && ok; base += 4 * kSyThreads) {
-    double pr[4], ar[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int t = base + q * kSyThreads + threadIdx.x;
-      pr[q] = t < m ? ld_pub(P + t) : 0.0;
-      ar[q] = t < m ? ld_pub(C + t) : 0.0;
-    }
-    bool miss = false;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) miss = miss || pending(pr[q]) || pending(ar[q]);
-    if (miss) {
-      const long long t0 = clock64();
-      while (true) {
-        miss = false;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int t = base + q * kSyThreads + threadIdx.x;
-          if (pending(pr[q])) { pr[q] = ld_pub(P + t); miss = miss || pending(pr[q]); }
-          if (pending(ar[q])) { ar[q] = ld_pub(C + t); miss = miss || pending(ar[q]); }
-        }
-        if (!miss) break;
-        if (clock64() - t0 > limit) { ok = 0; break; }
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int t = base + q * kSyThreads + threadIdx.x;
-      if (t < m) {
-        ps[t] = pr[q];
-        bs[t] = ar[q] - pr[q];
-        pt = fma(pr[q], v[t], pt);
-      }
-    }
-  }
-  *pt_out = pt;
-  return __syncthreads_and(ok) != 0;
 }
 
 // Partial sums of the FP64 route's pass: (column, 64-row chunk) items per round.
@@ -723,19 +630,32 @@ __device__ void sytrd1_body_df(const ConeDev& c, int rank, int G, long long wait
 }
 
 // The FP64 route with the columns in L2 (cones beyond the double-float
-// routes' reach: matrices larger than L2).
+// routes' reach: launches whose matrices exceed L2).  Step j (reflector
+// H_j = I - tau_j v v^T from column j, v indexed from row j+1, m = n - j - 1
+// entries), with p = tau_j A22 v already in pbuf:
+//   every CTA, after one group barrier per column: w = p - (tau_j / 2)(p^T v) v
+//     and the updated column j+1 (rows j+1 ..) from its value in A, v and w,
+//     so the next reflector is formed redundantly, with no hand-off;
+//   then one pass over its own columns i >= j+2 applies A <- A - v w^T - w v^T
+//     to rows j+2 .. and forms the next step's p_i (one read and one write of A).
+// For matrices that stream from L2 and HBM this measured faster than the
+// polled slabs of the double-float routes (4 x 4096: 661 ms against 700 ms).
 __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_limit, double* sy_smem, double* red,
                             double* sh) {
   const int n = (int)c.n;
   double* A = c.A;
   const int pcap = sytrd1_pcap(n, G);
   double* vc = sy_smem;             // v_j (rows j+1 ..)
-  double* ps = sy_smem + n;         // p_j (rows j+1 ..)
-  double* bs = sy_smem + 2 * n;     // column j+1 (rows j+1 ..): a - p, then updated by step j
+  double* w = sy_smem + n;          // p_j, then w_j
+  double* vx = sy_smem + 2 * n;     // updated column j+1 (rows j+1 ..), then v_{j+1} at vx + 1
   double* psum = sy_smem + 3 * n;   // pcap partial dot products
-  double* pub = c.QA;               // the steps' slabs
+  // p, double-buffered by step parity: a CTA writes step j+2's values only
+  // after every CTA has passed step j+1's barrier, i.e. finished reading
+  // step j's values
+  double* pbuf2 = c.X;              // 2 x n
+  int* bar = c.prog;
   const int tid = threadIdx.x;
-  int parity = 0;
+  int parity = 0, bstep = 0;
   if (n < 3) {
     __syncthreads();
     if (rank == 0 && tid == 0) {
@@ -745,21 +665,12 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
     }
     return;
   }
-  // ---- every slab holds the sentinel before anything is published
-  {
-    const int64_t total = (int64_t)n * n - n - 2;
-    for (int64_t e = (int64_t)rank * kSyThreads + tid; e < total; e += (int64_t)G * kSyThreads)
-      pub[e] = __longlong_as_double(kSentinel);
-  }
-  if (!group_barrier8(c.prog, rank, G, 1, wait_limit)) {
-    if (tid == 0) atomicOr(c.status, ST_TIMEOUT);
-    return;
-  }
-  // ---- prologue: reflector 0 from column 0; p_0 for my columns and column 1, published into slab 0
+  // ---- prologue: reflector 0 from column 0, p_0 for my columns
   double beta, tau;
   for (int t = tid; t < n - 1; t += kSyThreads) vc[t] = __ldcg(A + 1 + t);
   __syncthreads();
   tau = make_reflector(vc, n - 1, red, parity, sh, &beta);
+  __syncthreads();
   if (rank == 0 && tid == 0) {
     c.d[0] = __ldcg(A);
     c.e[0] = beta;
@@ -769,70 +680,85 @@ __device__ void sytrd1_body(const ConeDev& c, int rank, int G, long long wait_li
   // v_0 is already scaled (u = v): coefficients (tau, 1)
   if (tid == 0) { sh[1] = tau; sh[2] = 1.0; }
   __syncthreads();
-  {
-    double* s0 = slab(pub, n, 0);
-    column_pass_any<false>(A, n, 1, vc, sh + 1, nullptr, nullptr, 0.0, s0, s0 + (n - 1), psum, pcap, rank, G);
-  }
+  if (n <= 256) column_pass<false, 128>(A, n, 1, vc, sh + 1, nullptr, nullptr, pbuf2, psum, pcap, rank, G);
+  else column_pass<false, 256>(A, n, 1, vc, sh + 1, nullptr, nullptr, pbuf2, psum, pcap, rank, G);
   for (int j = 0; j + 2 < n; ++j) {
     const int m = n - j - 1;
-    double* P = slab(pub, n, j);
-    // ---- p and column j+1 of this step, as they arrive
-    double pt;
-    if (!poll_step(P, P + m, m, vc, ps, bs, wait_limit, &pt)) {
+    const double* pbuf = pbuf2 + (j & 1) * n;
+    if (!group_barrier8(bar, rank, G, ++bstep, wait_limit)) {
       if (tid == 0) atomicOr(c.status, ST_TIMEOUT);
       return;
     }
+    // ---- w = p - K v and the updated column j+1, in every CTA: K = (tau / 2)
+    // p^T v from the full p; all loads of a round first (one L2 round trip)
+    double pt = 0.0;
+    for (int base = 0; base < m; base += 4 * kSyThreads) {
+      double pr[4], ar[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int t = base + q * kSyThreads + tid;
+        pr[q] = t < m ? __ldcg(pbuf + j + 1 + t) : 0.0;
+        ar[q] = t < m ? __ldcg(A + (int64_t)(j + 1 + t) + (int64_t)(j + 1) * n) : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int t = base + q * kSyThreads + tid;
+        if (t < m) {
+          w[t] = pr[q];
+          vx[t] = ar[q];
+          pt = fma(pr[q], vc[t], pt);
+        }
+      }
+    }
     const double K = 0.5 * tau * block_sum256(pt, red, parity);
-    // ---- column j+1 updated by step j: (a_t - p_t) - v_t (p_0 - 2K), and the
-    // next reflector's sum of squares (rows j+3 ..)
-    const double c0 = fma(-2.0, K, ps[0]);
-    double ss = 0.0;
-    for (int t = tid; t < m; t += kSyThreads) {
-      const double nc = fma(-vc[t], c0, bs[t]);
-      bs[t] = nc;
-      if (t >= 2) ss = fma(nc, nc, ss);
+    // w_t = p_t - K v_t, the updated column a_t - w_t v_0 - v_t w_0, and the
+    // next reflector's sum of squares (rows j+3 ..); w[0] keeps p_0 (every
+    // thread forms w_0 from it, and nothing later reads w[0])
+    double ps = 0.0;
+    {
+      const double v0 = vc[0];
+      const double w0 = fma(-K, v0, w[0]);
+      for (int t = tid; t < m; t += kSyThreads) {
+        const double wt = fma(-K, vc[t], w[t]);
+        if (t > 0) w[t] = wt;
+        const double nc = fma(-vc[t], w0, fma(-wt, v0, vx[t]));
+        vx[t] = nc;
+        if (t >= 2) ps = fma(nc, nc, ps);
+      }
     }
     if (j + 3 < n) {
-      // ---- reflector j+1 from rows j+2 .. of the updated column x = bs + 1:
+      // ---- reflector j+1 from rows j+2 .. of the updated column x = vx + 1:
       // thread 0 forms tau, beta and scal = 1/(x_0 - beta) while the other
       // warps already run the pass, which needs them only at its end
-      const double sigma = block_sum256(ss, red, parity);
+      const double sigma = block_sum256(ps, red, parity);
       if (tid == 0) {
-        const double alpha = bs[1];
-        double b1 = alpha, t1 = 0.0, sc = 0.0;
-        if (sigma != 0.0) {
-          const double nrm = sqrt(fma(alpha, alpha, sigma));
-          b1 = alpha >= 0.0 ? -nrm : nrm;
-          t1 = (b1 - alpha) / b1;
-          sc = 1.0 / (alpha - b1);
-        }
+        double b1, t1, sc;
+        reflector_scalars(vx[1], sigma, &b1, &t1, &sc);
         sh[0] = b1; sh[1] = t1; sh[2] = sc;
       }
-      double* Pn = slab(pub, n, j + 1);
-      column_pass_any<true>(A, n, j + 2, bs + 1, sh + 1, vc, ps, 2.0 * K, Pn, Pn + (m - 1), psum, pcap, rank, G);
+      double* pnext = pbuf2 + ((j + 1) & 1) * n;
+      if (n <= 256) column_pass<true, 128>(A, n, j + 2, vx + 1, sh + 1, vc, w, pnext, psum, pcap, rank, G);
+      else column_pass<true, 256>(A, n, j + 2, vx + 1, sh + 1, vc, w, pnext, psum, pcap, rank, G);
       const double beta1 = sh[0], tau1 = sh[1], scal1 = sh[2];
       if (rank == 0 && tid == 0) {
-        c.d[j + 1] = bs[0];
+        c.d[j + 1] = vx[0];
         c.e[j + 1] = beta1;
         c.tau1[j + 1] = tau1;
       }
-      store_reflector(c, n, j + 1, bs + 1, rank, G, scal1);
+      store_reflector(c, n, j + 1, vx + 1, rank, G, scal1);
       // v_{j+1} = scal x becomes the current reflector (v_0 = 1)
-      for (int t = tid; t < m - 1; t += kSyThreads) vc[t] = t == 0 ? 1.0 : scal1 * bs[1 + t];
+      for (int t = tid; t < m - 1; t += kSyThreads) vc[t] = t == 0 ? 1.0 : scal1 * vx[1 + t];
       tau = tau1;
       __syncthreads();
     } else {
       __syncthreads();
       // the last 2 x 2 block (rows n-2, n-1); A(n-1, n-1) is current in A
       if (rank == 0 && tid == 0) {
-        c.d[n - 2] = bs[0];
-        c.e[n - 2] = bs[1];
+        c.d[n - 2] = vx[0];
+        c.e[n - 2] = vx[1];
         c.e[n - 1] = 0.0;
-      }
-      if (rank == (n - 1) % G && tid == 0) {
         const double a = __ldcg(A + (int64_t)(n - 1) + (int64_t)(n - 1) * n);
-        const double w1 = fma(-K, vc[1], ps[1]);
-        c.d[n - 1] = a - 2.0 * vc[1] * w1;
+        c.d[n - 1] = a - fma(vc[1], w[1], w[1] * vc[1]);
       }
     }
   }
