@@ -149,8 +149,11 @@ void launch_backtr2(const ConeDev* cones, int ncones, int maxn, int maxk, int ke
 // reduction's panels, applied last block first.  A CTA holds a slab of up to
 // KC kept columns in shared memory for the whole pass; per block it forms
 // W = V^T Z (lanes over rows, four reflectors per warp, then a warp
-// reduce-scatter), W' = T W and Z -= V W'.  The reflector blocks are read
-// from L2 (every CTA streams them), the slab never leaves the SM.  CTA ->
+// reduce-scatter), W' = T W and Z -= V W'.  When the slab and the widest
+// block fit in shared memory together (sides up to about 830), each block is
+// first copied there by the whole CTA with every copy in flight at once
+// (staged); beyond, the warps stream the blocks from L2 inside their loops.
+// The slab never leaves the SM.  CTA ->
 // (cone, rank in the cone's group, group size) comes from tables, so big
 // cones get many CTAs and small ones one.
 namespace {
@@ -158,6 +161,7 @@ namespace {
 constexpr int kB1Threads = 256;
 constexpr int kB1MaxCols = 8;
 constexpr size_t kB1SmemMax = 200 * 1024;
+constexpr size_t kB1StagedMax = 220 * 1024;  // dynamic shared memory of a staged launch, at most
 
 template <typename E>
 struct Stage1Block {
@@ -223,10 +227,42 @@ __device__ __forceinline__ E warp_reduce_scatter(E (&v)[NV]) {
   return v[0];
 }
 
+// cnt 8-byte elements from global to shared memory: 16-byte asynchronous
+// copies when both addresses allow them (every thread issues its share at
+// once), element copies otherwise.  The caller waits (cp_async_wait_all) and
+// synchronises the CTA.
+template <typename E>
+__device__ __forceinline__ void stage_copy(E* dst, const E* src, int cnt) {
+  static_assert(sizeof(E) == 8, "8-byte elements");
+  const uint32_t sd = (uint32_t)__cvta_generic_to_shared(dst);
+  if (((reinterpret_cast<uintptr_t>(src) | (uintptr_t)sd) & 15u) == 0) {
+    const int pairs = cnt / 2;
+    for (int e = threadIdx.x; e < pairs; e += kB1Threads)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sd + 16u * (uint32_t)e), "l"(src + 2 * e)
+                   : "memory");
+    if ((cnt & 1) && threadIdx.x == 0) dst[cnt - 1] = src[cnt - 1];
+  } else {
+    for (int e = threadIdx.x; e < cnt; e += kB1Threads) dst[e] = src[e];
+  }
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// A reflector-block element: from shared memory (ST, the block staged there)
+// or through the read-only cache.
+template <bool ST, typename E>
+__device__ __forceinline__ E ld_blk(const E* p) {
+  if constexpr (ST) return *p;
+  else return g_ldg(p);
+}
+
 // One slab of KC columns through every block, in element type E (FP64, or
 // double-float when the reflectors and T factors were stored as FP32 pairs).
-template <int KC, typename E>
-__device__ void bt1_slab(const ConeDev& c, int j0, int ncols, E* zs, E* Wsm, E* Wt) {
+// ST: each block's reflectors V (bb x mq) and T factor are first copied into
+// shared memory (Vs, Ts) by the whole CTA, with every copy in flight at once,
+// and the products read them there; otherwise every warp streams them from
+// L2 inside its loops, one dependent round of loads after another.
+template <int KC, typename E, bool ST>
+__device__ void bt1_slab(const ConeDev& c, int j0, int ncols, E* zs, E* Wsm, E* Wt, E* Vs, E* Ts) {
   const int n = (int)c.n;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   double* Z = c.Z;
@@ -238,7 +274,15 @@ __device__ void bt1_slab(const ConeDev& c, int j0, int ncols, E* zs, E* Wsm, E* 
   __syncthreads();
   const int nblk = stage1_nblocks(c);
   for (int q = nblk - 1; q >= 0; --q) {
-    const Stage1Block<E> B = stage1_block<E>(c, q);
+    Stage1Block<E> B = stage1_block<E>(c, q);
+    if constexpr (ST) {
+      stage_copy(Vs, B.V, B.bb * B.mq);
+      stage_copy(Ts, B.T, B.bb * B.wb);
+      cp_async_wait_all();
+      __syncthreads();
+      B.V = Vs;
+      B.T = Ts;
+    }
     // ---- W = V^T Z(r0:, slab): warp w takes reflectors 4w .. 4w+3
     {
       E acc[4 * KC];
@@ -255,7 +299,7 @@ __device__ void bt1_slab(const ConeDev& c, int j0, int ncols, E* zs, E* Wsm, E* 
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             E v;
-            if (a0 + i < B.bb) v = g_ldg(B.V + r + (int64_t)(a0 + i) * B.mq);
+            if (a0 + i < B.bb) v = ld_blk<ST>(B.V + r + (int64_t)(a0 + i) * B.mq);
             else g_zero(v);
 #pragma unroll
             for (int col = 0; col < KC; ++col) acc[i * KC + col] = g_mad(v, z[col], acc[i * KC + col]);
@@ -279,10 +323,10 @@ __device__ void bt1_slab(const ConeDev& c, int j0, int ncols, E* zs, E* Wsm, E* 
       if (a < B.bb) {
         int bq = a;
         for (; bq + 1 < B.bb; bq += 2) {
-          s0 = g_mad(g_ldg(B.T + a + (int64_t)bq * B.wb), Wsm[bq * KC + col], s0);
-          s1 = g_mad(g_ldg(B.T + a + (int64_t)(bq + 1) * B.wb), Wsm[(bq + 1) * KC + col], s1);
+          s0 = g_mad(ld_blk<ST>(B.T + a + (int64_t)bq * B.wb), Wsm[bq * KC + col], s0);
+          s1 = g_mad(ld_blk<ST>(B.T + a + (int64_t)(bq + 1) * B.wb), Wsm[(bq + 1) * KC + col], s1);
         }
-        if (bq < B.bb) s0 = g_mad(g_ldg(B.T + a + (int64_t)bq * B.wb), Wsm[bq * KC + col], s0);
+        if (bq < B.bb) s0 = g_mad(ld_blk<ST>(B.T + a + (int64_t)bq * B.wb), Wsm[bq * KC + col], s0);
       }
       Wt[a * KC + col] = g_add(s0, s1);
     }
@@ -295,9 +339,9 @@ __device__ void bt1_slab(const ConeDev& c, int j0, int ncols, E* zs, E* Wsm, E* 
 #pragma unroll 8
       for (int a = 0; a < kSy1Block; a += 2) {
         if (a < B.bb) {
-          const E v0 = g_ldg(B.V + r + (int64_t)a * B.mq);
+          const E v0 = ld_blk<ST>(B.V + r + (int64_t)a * B.mq);
           E v1;
-          if (a + 1 < B.bb) v1 = g_ldg(B.V + r + (int64_t)(a + 1) * B.mq);
+          if (a + 1 < B.bb) v1 = ld_blk<ST>(B.V + r + (int64_t)(a + 1) * B.mq);
           else g_zero(v1);
 #pragma unroll
           for (int col = 0; col < KC; ++col) {
@@ -319,22 +363,40 @@ __device__ void bt1_slab(const ConeDev& c, int j0, int ncols, E* zs, E* Wsm, E* 
   __syncthreads();
 }
 
-template <typename E>
-__device__ void bt1_cols(const ConeDev& c, int lo, int hi, int kcmax, E* smem, E* Wsm, E* Wt) {
+template <typename E, bool ST>
+__device__ void bt1_cols(const ConeDev& c, int lo, int hi, int kcmax, E* smem, E* Wsm, E* Wt, E* Vs, E* Ts) {
   for (int j0 = lo; j0 < hi;) {
     const int left = hi - j0;
-    if (left > 4 && kcmax >= 8) { bt1_slab<8, E>(c, j0, min(left, 8), smem, Wsm, Wt); j0 += min(left, 8); }
-    else if (left > 2 && kcmax >= 4) { bt1_slab<4, E>(c, j0, min(left, 4), smem, Wsm, Wt); j0 += min(left, 4); }
-    else if (left >= 2 && kcmax >= 2) { bt1_slab<2, E>(c, j0, 2, smem, Wsm, Wt); j0 += 2; }
-    else { bt1_slab<1, E>(c, j0, 1, smem, Wsm, Wt); j0 += 1; }
+    if (left > 4 && kcmax >= 8) {
+      bt1_slab<8, E, ST>(c, j0, min(left, 8), smem, Wsm, Wt, Vs, Ts);
+      j0 += min(left, 8);
+    } else if (left > 2 && kcmax >= 4) {
+      bt1_slab<4, E, ST>(c, j0, min(left, 4), smem, Wsm, Wt, Vs, Ts);
+      j0 += min(left, 4);
+    } else if (left >= 2 && kcmax >= 2) {
+      bt1_slab<2, E, ST>(c, j0, 2, smem, Wsm, Wt, Vs, Ts);
+      j0 += 2;
+    } else {
+      bt1_slab<1, E, ST>(c, j0, 1, smem, Wsm, Wt, Vs, Ts);
+      j0 += 1;
+    }
   }
+}
+
+// Shared memory of a staged launch: the slabs (kcmax x maxn, rounded to an
+// even count so that the block copies start on 16 bytes), then the widest
+// reflector block (32 x maxn) and its T factor (32 x 32).
+__host__ __device__ inline size_t bt1_slab_elems(int kcmax, int maxn) { return ((size_t)kcmax * maxn + 1) / 2 * 2; }
+__host__ __device__ inline size_t bt1_staged_bytes(int kcmax, int maxn) {
+  return (bt1_slab_elems(kcmax, maxn) + (size_t)kMaxBand * maxn + (size_t)kMaxBand * kMaxBand) * 8;
 }
 
 __global__ void __launch_bounds__(kB1Threads) bt1_kernel(const ConeDev* __restrict__ cones,
                                                          const int* __restrict__ cta_cone,
                                                          const int* __restrict__ cta_rank,
-                                                         const int* __restrict__ cta_count, int kcmax) {
-  extern __shared__ double b1_smem[];
+                                                         const int* __restrict__ cta_count, int kcmax,
+                                                         int maxn, int staged) {
+  extern __shared__ __align__(16) double b1_smem[];
   // 8-byte elements either way (FP64, or an FP32 pair)
   __shared__ double Wsm[kSy1Block * kB1MaxCols];
   __shared__ double Wt[kSy1Block * kB1MaxCols];
@@ -348,11 +410,20 @@ __global__ void __launch_bounds__(kB1Threads) bt1_kernel(const ConeDev* __restri
   const int hi = lo + base + (rank < extra ? 1 : 0);
   // one-stage reflectors and T factors are FP32 pairs (written so by the
   // shared-memory reduction, or converted by larft1_kernel)
-  if (c.path == 1)
-    bt1_cols<dfl>(c, lo, hi, kcmax, reinterpret_cast<dfl*>(b1_smem), reinterpret_cast<dfl*>(Wsm),
-                  reinterpret_cast<dfl*>(Wt));
-  else
-    bt1_cols<double>(c, lo, hi, kcmax, b1_smem, Wsm, Wt);
+  double* Vs = b1_smem + bt1_slab_elems(kcmax, maxn);
+  double* Ts = Vs + (size_t)kMaxBand * maxn;
+  if (c.path == 1) {
+    dfl* sm = reinterpret_cast<dfl*>(b1_smem);
+    dfl* w0 = reinterpret_cast<dfl*>(Wsm);
+    dfl* w1 = reinterpret_cast<dfl*>(Wt);
+    if (staged)
+      bt1_cols<dfl, true>(c, lo, hi, kcmax, sm, w0, w1, reinterpret_cast<dfl*>(Vs), reinterpret_cast<dfl*>(Ts));
+    else
+      bt1_cols<dfl, false>(c, lo, hi, kcmax, sm, w0, w1, nullptr, nullptr);
+  } else {
+    if (staged) bt1_cols<double, true>(c, lo, hi, kcmax, b1_smem, Wsm, Wt, Vs, Ts);
+    else bt1_cols<double, false>(c, lo, hi, kcmax, b1_smem, Wsm, Wt, nullptr, nullptr);
+  }
 }
 
 }  // namespace
@@ -364,13 +435,25 @@ void launch_bt1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, 
   if (nctas <= 0 || maxn <= 0) return;
   int kcmax = kB1MaxCols;
   while (kcmax > 1 && (size_t)kcmax * maxn * sizeof(double) > kB1SmemMax) kcmax /= 2;
-  const size_t smem = (size_t)kcmax * maxn * sizeof(double);
+  size_t smem = (size_t)kcmax * maxn * sizeof(double);
+  // staged reflector blocks when a slab and the widest block fit (sides up to
+  // about 830): the widest slab that leaves room for them
+  int staged = 0;
+  {
+    int kc = kB1MaxCols;
+    while (kc > 1 && bt1_staged_bytes(kc, maxn) > kB1StagedMax) kc /= 2;
+    if (bt1_staged_bytes(kc, maxn) <= kB1StagedMax) {
+      staged = 1;
+      kcmax = kc;
+      smem = bt1_staged_bytes(kc, maxn);
+    }
+  }
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(bt1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kB1SmemMax);
+    cudaFuncSetAttribute(bt1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kB1StagedMax);
     attr = true;
   }
-  bt1_kernel<<<nctas, kB1Threads, smem, s>>>(cones, cta_cone, cta_rank, cta_count, kcmax);
+  bt1_kernel<<<nctas, kB1Threads, smem, s>>>(cones, cta_cone, cta_rank, cta_count, kcmax, maxn, staged);
 }
 
 }  // namespace scs

@@ -182,3 +182,50 @@ def test_precision_4096_construction(lib):
     assert rel(y, W.to_svec(P)) <= TOL
     yn, st = gpu_proj_batched(lib, -x, [4096])
     assert np.linalg.norm(y - yn - x) <= TOL * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("n", [256, 300, 401, 640, 660])
+def test_medium_sides_vs_oracle(lib, n):
+    """Lone cones between the one-CTA sizes and the ADMM side, on the
+    ADMM-like spectrum (48 % clustered at zero): 401 leaves some CTAs of the
+    group a column more than the others."""
+    rng = W.rng_for(8100 + n)
+    X, Q, lam = W.from_spectrum(rng, W.spectrum_admm(rng, n))
+    x = W.to_svec(X)
+    y, st = gpu_proj_batched(lib, x, [n])
+    assert st == lib.OK
+    assert rel(y, oracle.proj(x)) <= TOL
+
+
+def test_few_large_cones_with_small_ones_in_place(lib):
+    """Three large cones sharing the one-stage launch beside small cones on
+    the one-CTA route, in place."""
+    rng = W.rng_for(8200)
+    sides = [300, 7, 520, 33, 640]
+    x = np.concatenate([W.to_svec(W.sym_gaussian(rng, n) + rng.uniform(-0.5, 0.5) * np.eye(n)) for n in sides])
+    ref = oracle.proj_batched(x, lib.shapes(sides)[0])
+    xt = to_dev(x)
+    lib.proj_batched(xt, sides, out=xt)
+    assert lib.status(0) == lib.OK
+    y = xt.cpu().numpy()
+    offs = lib.shapes(sides)[0]
+    for i, n in enumerate(sides):
+        assert rel(y[offs[i]:offs[i + 1]], ref[offs[i]:offs[i + 1]]) <= TOL, n
+
+
+def test_medium_side_nonfinite_then_repeatable(lib):
+    """A NaN in a side-320 cone gives SCS_PSD_ENONFINITE and a NaN output;
+    the next clean calls are correct and bit-for-bit equal."""
+    rng = W.rng_for(8300)
+    n = 320
+    x = W.to_svec(W.sym_gaussian(rng, n))
+    bad = x.copy()
+    bad[1000] = np.nan
+    y, st = gpu_proj_batched(lib, bad, [n])
+    assert st == lib.ENONFINITE
+    assert np.all(np.isnan(y))
+    y1, st = gpu_proj_batched(lib, x, [n])
+    assert st == lib.OK
+    y2, _ = gpu_proj_batched(lib, x, [n])
+    np.testing.assert_array_equal(y1, y2)
+    assert rel(y1, oracle.proj(x)) <= TOL
