@@ -116,10 +116,9 @@ static int backtr2_cols(int n, int band, int kexp, int sms) {
 
 template <int B>
 static void launch_bt2(const ConeDev* cones, int ncones, int maxn, int maxk, int cs, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr{0};
+  if (first_on_device(attr)) {
     cudaFuncSetAttribute(backtr2_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-    attr = true;
   }
   const int gx = (maxk + cs - 1) / cs;
   const size_t rows = (size_t)maxn + maxn / B + 1;
@@ -448,10 +447,9 @@ void launch_bt1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, 
       smem = bt1_staged_bytes(kc, maxn);
     }
   }
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr{0};
+  if (first_on_device(attr)) {
     cudaFuncSetAttribute(bt1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kB1StagedMax);
-    attr = true;
   }
   bt1_kernel<<<nctas, kB1Threads, smem, s>>>(cones, cta_cone, cta_rank, cta_count, kcmax, maxn, staged);
 }

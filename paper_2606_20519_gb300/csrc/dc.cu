@@ -957,11 +957,10 @@ void launch_dc_leaves(const ConeDev* cones, int ncones, int64_t maxn, cudaStream
 void launch_dc_prepare(const ConeDev* cones, const MergeNode* nodes, int nnodes, int maxK, cudaStream_t s) {
   if (nnodes <= 0) return;
   const size_t smem = (size_t)maxK * (2 * sizeof(double) + 2 * sizeof(int));
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr{0};
+  if (first_on_device(attr)) {
     cudaFuncSetAttribute(dc_prepare_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     cudaFuncSetAttribute(dc_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr = true;
   }
   dc_prepare_kernel<<<nnodes, kDcThreads, smem, s>>>(cones, nodes);
 }
@@ -972,10 +971,9 @@ void launch_dc_secular(const ConeDev* cones, const MergeNode* nodes, const int* 
   // four warps per CTA, each with maxK doubles and maxK floats of shared
   // memory (none when that would not fit)
   constexpr size_t kSecSmemMax = 160 * 1024;
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr{0};
+  if (first_on_device(attr)) {
     cudaFuncSetAttribute(dc_secular_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSecSmemMax);
-    attr = true;
   }
   const size_t smem = (size_t)4 * maxK * (2 * sizeof(double) + sizeof(float));
   const int difmax = smem <= kSecSmemMax ? maxK : 0;

@@ -716,10 +716,9 @@ void launch_hbt(const HConeDev* cones, const int* cta_cone, const int* cta_rank,
                 int maxn, cudaStream_t s) {
   if (nctas <= 0) return;
   const size_t smem = (size_t)kHbtCols * maxn * sizeof(cdf);
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr{0};
+  if (first_on_device(attr)) {
     cudaFuncSetAttribute(hbt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
   }
   hbt_kernel<<<nctas, kHThreads, smem, s>>>(cones, cta_cone, cta_rank, cta_count);
 }

@@ -13,12 +13,25 @@
 //                          straight into svec (positive part, or X minus the
 //                          negative part by the Moreau decomposition)
 #pragma once
+#include <atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "dfloat.cuh"
 
 namespace scs {
+
+// True on the first call for the current device with this flag word.  The
+// launchers set their kernels' function attributes (dynamic shared memory
+// beyond 48 KB, non-portable cluster sizes) once per device: each device's
+// context keeps its own.
+inline bool first_on_device(std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  return (done.fetch_or(bit) & bit) == 0;
+}
+
 
 // Per-cone device status bits (OR-ed together).
 enum : int { ST_NONFINITE = 1, ST_NOCONV = 2, ST_TIMEOUT = 4, ST_BADARG = 8 };

@@ -266,11 +266,10 @@ size_t panel_smem_bytes(int b, int R) {
 void launch_panel(const ConeDev* cones, const int* cone_ids, int njobs, int panel, int b, int cluster, int R,
                   cudaStream_t s) {
   if (njobs <= 0) return;
-  static bool attr_done = false;
-  if (!attr_done) {
+  static std::atomic<unsigned long long> attr_done{0};
+  if (first_on_device(attr_done)) {
     cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute(panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr_done = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(njobs * cluster, 1, 1);

@@ -432,11 +432,10 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const GemmDesc* __restrict
 
 template <int BN>
 void launch_tc(const GemmDesc* descs, const int* prefix, int count, int tiles, cudaStream_t s) {
-  static bool attr = false;
+  static std::atomic<unsigned long long> attr{0};
   const size_t smem = sizeof(TcSmem<BN>) + 1024;
-  if (!attr) {
+  if (first_on_device(attr)) {
     cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
   }
   tc_gemm_kernel<BN><<<tiles, 128, smem, s>>>(descs, prefix, count);
 }

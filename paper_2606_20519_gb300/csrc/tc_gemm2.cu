@@ -420,21 +420,19 @@ __global__ void __launch_bounds__(288, 1) tc2_gemm_kernel(const GemmDesc* __rest
 
 void launch_tc2_slice(const SliceJob* jobs, const int* prefix, int njobs, int total, cudaStream_t s) {
   if (njobs <= 0 || total <= 0) return;
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr{0};
+  if (first_on_device(attr)) {
     cudaFuncSetAttribute(tc2_slice_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSliceSmem);
-    attr = true;
   }
   tc2_slice_kernel<<<total, 256, kSliceSmem, s>>>(jobs, prefix, njobs);
 }
 
 void launch_tc2_gemm(const GemmDesc* descs, const int* tile_prefix, int count, int total_tiles, cudaStream_t s) {
   if (count <= 0 || total_tiles <= 0) return;
-  static bool attr = false;
+  static std::atomic<unsigned long long> attr{0};
   const size_t smem = sizeof(Tc2Smem) + 1024;
-  if (!attr) {
+  if (first_on_device(attr)) {
     cudaFuncSetAttribute(tc2_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
   }
   tc2_gemm_kernel<<<total_tiles, 288, smem, s>>>(descs, tile_prefix, count);
 }
