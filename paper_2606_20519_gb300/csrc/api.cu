@@ -1023,7 +1023,10 @@ int build_plan(scs_psd_handle h, Plan& P, const int32_t* sides, int32_t count, i
         int per = 1;
         const int per_max = std::max(1, std::min(8, tune.bt1_cols));
         while (per < per_max && (kest + per - 1) / per > bud) per *= 2;
-        const int g = std::max(1, (kest + per - 1) / per);
+        int g = std::max(1, (kest + per - 1) / per);
+        // a lone cone whose reflector blocks are staged in shared memory runs
+        // one CTA per SM: keep its launch to one wave
+        if (fc.size() == 1 && bt1_stages((int)n)) g = std::min(g, std::max(1, mb.sms));
         for (int r = 0; r < g; ++r) { cc.push_back(c); cr.push_back(r); cn.push_back(g); }
         P.bt1k_maxn = std::max<int>(P.bt1k_maxn, (int)n);
       }

@@ -429,6 +429,8 @@ __global__ void __launch_bounds__(kB1Threads) bt1_kernel(const ConeDev* __restri
 
 int bt1_max_side() { return (int)(kB1SmemMax / sizeof(double)); }
 
+bool bt1_stages(int maxn) { return bt1_staged_bytes(1, maxn) <= kB1StagedMax; }
+
 void launch_bt1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,
                 int maxn, cudaStream_t s) {
   if (nctas <= 0 || maxn <= 0) return;
@@ -437,8 +439,13 @@ void launch_bt1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, 
   size_t smem = (size_t)kcmax * maxn * sizeof(double);
   // staged reflector blocks when a slab and the widest block fit (sides up to
   // about 830): the widest slab that leaves room for them
+  // staged CTAs take most of an SM's shared memory (one per SM): only launches
+  // of at most one wave
   int staged = 0;
-  {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (nctas <= sms) {
     int kc = kB1MaxCols;
     while (kc > 1 && bt1_staged_bytes(kc, maxn) > kB1StagedMax) kc /= 2;
     if (bt1_staged_bytes(kc, maxn) <= kB1StagedMax) {

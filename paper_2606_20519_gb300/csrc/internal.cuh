@@ -285,6 +285,9 @@ void launch_larft1(const ConeDev* cones, const int* blk_cone, const int* blk_ind
 void launch_bt1(const ConeDev* cones, const int* cta_cone, const int* cta_rank, const int* cta_count, int nctas,
                 int maxn, cudaStream_t s);
 int bt1_max_side();
+// whether a launch whose largest side is maxn can stage the reflector blocks in
+// shared memory (it then does when it has at most one CTA per SM)
+bool bt1_stages(int maxn);
 // y = svec(S) or x - svec(S) from the lower triangle of S = Z diag(l) Z^T held in QA (split mode)
 void launch_pack_recon(const ConeDev* cones, int ncones, int64_t maxn, const IoSlot* io, cudaStream_t s);
 // complex Hermitian cones <-> real symmetric embeddings of side 2n (meta: n, Hermitian offset, real offset)
